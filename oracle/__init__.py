@@ -1,0 +1,253 @@
+"""CPU oracle for the octahedron-model DTrDT simulation -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+legs of ``bench.py`` may import this package.  The product path (the CUDA
+library in ``paper_1705_01022_gb300``) never imports it, and the two share no
+code.
+
+The arithmetic lives in ``oct_oracle.c`` (plain C, one site and one attempt at
+a time); this module only compiles it with gcc and marshals numpy arrays.
+
+Lattices are pairs of ``uint8`` arrays ``X, Y`` of shape ``(L, L)`` indexed
+``[y, x]``: ``X[y, x] = 1`` iff ``h(x,y) - h(x-1,y) = +1`` and ``Y[y, x] = 1``
+iff ``h(x,y) - h(x,y-1) = +1`` (the paper's on-site slope convention, Sec. 3).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oct_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboct_oracle.so")
+_lib = None
+
+TAG_MCS, TAG_SET, TAG_SITE, TAG_ACC, TAG_SEQ, TAG_REPLICA = 1, 2, 3, 4, 5, 6
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into a shared library (gcc, C11, -O2)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    fresh = os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oct_oracle.h")))
+    if force or not fresh:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-Wall", "-Wextra",
+                        "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("Bx", ctypes.c_int64), ("By", ctypes.c_int64),
+                ("cx", ctypes.c_int64), ("cy", ctypes.c_int64), ("p", ctypes.c_double),
+                ("q", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+@dataclass(frozen=True)
+class Params:
+    """DTrDT parameters: lattice L, sub-tile Bx x By, thread cell cx x cy (sites)."""
+    L: int
+    p: float
+    q: float
+    seed: int
+    Bx: int = 64
+    By: int = 64
+    cx: int = 4
+    cy: int = 4
+
+    def c(self) -> _Params:
+        return _Params(self.L, self.Bx, self.By, self.cx, self.cy, self.p, self.q, self.seed)
+
+
+_P_u8 = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+_P_u32 = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+_P_i64 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        i64, u32, u64, dbl = ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+        P_i64 = ctypes.POINTER(ctypes.c_int64)
+        P_u64 = ctypes.POINTER(ctypes.c_uint64)
+        L.oo_philox4x32_10.argtypes = [_P_u32, _P_u32, _P_u32]
+        L.oo_threshold32.argtypes = [dbl]
+        L.oo_threshold32.restype = u64
+        L.oo_init_flat.argtypes = [i64, _P_u8, _P_u8]
+        L.oo_site_kind.argtypes = [i64, _P_u8, _P_u8, i64, i64]
+        L.oo_attempt.argtypes = [i64, _P_u8, _P_u8, i64, i64, dbl, dbl, u32,
+                                 ctypes.POINTER(ctypes.c_int)]
+        L.oo_seq_rs.argtypes = [i64, dbl, dbl, u64, _P_u8, _P_u8, u32, u32, P_i64]
+        L.oo_seq_rs_many.argtypes = [i64, dbl, dbl, u64, i64, u32, _P_u8, _P_u8]
+        L.oo_check_params.argtypes = [ctypes.POINTER(_Params)]
+        L.oo_mcs_draw.argtypes = [ctypes.POINTER(_Params), u32, P_i64, P_i64,
+                                  ctypes.POINTER(ctypes.c_int)]
+        L.oo_dtrdt_run.argtypes = [ctypes.POINTER(_Params), _P_u8, _P_u8, u32, u32, P_i64,
+                                   ctypes.c_void_p, P_i64]
+        L.oo_dtrdt_mcs_window.argtypes = [ctypes.POINTER(_Params), u32, i64, i64, i64, i64,
+                                          _P_u8, _P_u8, P_i64]
+        L.oo_w2_sums.argtypes = [i64, _P_u8, _P_u8, P_i64, P_u64, P_u64, P_i64]
+        L.oo_w2_sums_colfirst.argtypes = [i64, _P_u8, _P_u8, P_i64, P_u64, P_u64]
+        L.oo_w2_from_sums.argtypes = [i64, i64, u64, u64]
+        L.oo_w2_from_sums.restype = dbl
+        L.oo_invariants.argtypes = [i64, _P_u8, _P_u8]
+        L.oo_pack_canonical.argtypes = [i64, _P_u8, _P_u8, _P_u32]
+        L.oo_unpack_canonical.argtypes = [i64, _P_u32, _P_u8, _P_u8]
+        L.oo_dtrdt_many.argtypes = [ctypes.POINTER(_Params), u64, i64, u32, _P_u8, _P_u8]
+        L.oo_dtrdt_acc_uniform.argtypes = [u64, u32, u32, u32, u32, u32, ctypes.c_int]
+        L.oo_dtrdt_acc_uniform.restype = u32
+        L.oo_replica_seed.argtypes = [u64, u32]
+        L.oo_replica_seed.restype = u64
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- helpers ---
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().oo_philox4x32_10(c, k, out)
+    return out
+
+
+def threshold32(p: float) -> int:
+    return int(lib().oo_threshold32(float(p)))
+
+
+def flat(L: int):
+    X = np.zeros((L, L), dtype=np.uint8)
+    Y = np.zeros((L, L), dtype=np.uint8)
+    lib().oo_init_flat(L, X, Y)
+    return X, Y
+
+
+def site_kind(X, Y, x: int, y: int) -> int:
+    return int(lib().oo_site_kind(X.shape[0], X, Y, x, y))
+
+
+def attempt(X, Y, x: int, y: int, p: float, q: float, u: int):
+    kind = ctypes.c_int(0)
+    r = lib().oo_attempt(X.shape[0], X, Y, x, y, p, q, u & 0xFFFFFFFF, ctypes.byref(kind))
+    return int(r), int(kind.value)
+
+
+def seq_rs(X, Y, p: float, q: float, seed: int, t0: int, n_mcs: int) -> int:
+    """O1: sequential RS for n_mcs sweeps, in place.  Returns net flips."""
+    net = ctypes.c_int64(0)
+    lib().oo_seq_rs(X.shape[0], p, q, seed, X, Y, t0, n_mcs, ctypes.byref(net))
+    return int(net.value)
+
+
+def seq_rs_many(L: int, p: float, q: float, seed0: int, n_runs: int, n_mcs: int):
+    X = np.zeros((n_runs, L, L), dtype=np.uint8)
+    Y = np.zeros((n_runs, L, L), dtype=np.uint8)
+    lib().oo_seq_rs_many(L, p, q, seed0, n_runs, n_mcs, X, Y)
+    return X, Y
+
+
+def check_params(prm: Params) -> bool:
+    cp = prm.c()
+    return lib().oo_check_params(ctypes.byref(cp)) == 0
+
+
+def mcs_draw(prm: Params, t: int):
+    cp = prm.c()
+    ox, oy = ctypes.c_int64(), ctypes.c_int64()
+    perm = (ctypes.c_int * 4)()
+    lib().oo_mcs_draw(ctypes.byref(cp), t, ctypes.byref(ox), ctypes.byref(oy), perm)
+    return int(ox.value), int(oy.value), list(perm)
+
+
+def dtrdt_run(X, Y, prm: Params, t0: int, n_mcs: int, count_attempts: bool = False,
+              check_conflicts: bool = False):
+    """O2: DTrDT replay in place.  Returns (net_flips, attempts or None, conflicts or None)."""
+    cp = prm.c()
+    net = ctypes.c_int64(0)
+    att = np.zeros((prm.L, prm.L), dtype=np.int64) if count_attempts else None
+    conf = ctypes.c_int64(0)
+    rc = lib().oo_dtrdt_run(ctypes.byref(cp), X, Y, t0, n_mcs, ctypes.byref(net),
+                            att.ctypes.data_as(ctypes.c_void_p) if att is not None else None,
+                            ctypes.byref(conf) if check_conflicts else None)
+    if rc != 0:
+        raise ValueError(f"invalid DTrDT parameters {prm}")
+    return int(net.value), att, (int(conf.value) if check_conflicts else None)
+
+
+def dtrdt_many(prm: Params, seed0: int, n_runs: int, n_mcs: int):
+    """O2 from the flat start for seeds seed0 .. seed0+n_runs-1; returns final (X, Y) stacks."""
+    cp = prm.c()
+    X = np.zeros((n_runs, prm.L, prm.L), dtype=np.uint8)
+    Y = np.zeros((n_runs, prm.L, prm.L), dtype=np.uint8)
+    if lib().oo_dtrdt_many(ctypes.byref(cp), seed0, n_runs, n_mcs, X, Y) != 0:
+        raise ValueError(f"invalid DTrDT parameters {prm}")
+    return X, Y
+
+
+def acc_uniform(seed: int, t: int, k: int, T: int, g: int, s: int, pos: int) -> int:
+    """The acceptance uniform of the thread cell at bit position pos of group g."""
+    return int(lib().oo_dtrdt_acc_uniform(seed, t, k, T, g, s, pos))
+
+
+def dtrdt_mcs_window(Xw, Yw, prm: Params, t: int, wx: int, wy: int) -> int:
+    """O2 for one MCS on a window (H, W) whose corner is global site (wx, wy)."""
+    cp = prm.c()
+    H, W = Xw.shape
+    net = ctypes.c_int64(0)
+    rc = lib().oo_dtrdt_mcs_window(ctypes.byref(cp), t, wx, wy, W, H, Xw, Yw, ctypes.byref(net))
+    if rc != 0:
+        raise ValueError("invalid window replay arguments")
+    return int(net.value)
+
+
+def w2_sums(X, Y):
+    """O3: (S1, S2, hmax) over heights relative to h(0,0) = 0 (exact Python ints)."""
+    s1, lo, hi, hm = ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int64()
+    lib().oo_w2_sums(X.shape[0], X, Y, ctypes.byref(s1), ctypes.byref(lo), ctypes.byref(hi),
+                     ctypes.byref(hm))
+    return int(s1.value), (int(hi.value) << 64) | int(lo.value), int(hm.value)
+
+
+def w2_sums_colfirst(X, Y):
+    s1, lo, hi = ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_uint64()
+    lib().oo_w2_sums_colfirst(X.shape[0], X, Y, ctypes.byref(s1), ctypes.byref(lo),
+                              ctypes.byref(hi))
+    return int(s1.value), (int(hi.value) << 64) | int(lo.value)
+
+
+def w2_from_sums(L: int, s1: int, s2: int) -> float:
+    return float(lib().oo_w2_from_sums(L, s1, s2 & ((1 << 64) - 1), s2 >> 64))
+
+
+def w2(X, Y) -> float:
+    s1, s2, _ = w2_sums(X, Y)
+    return w2_from_sums(X.shape[0], s1, s2)
+
+
+def invariants(X, Y) -> int:
+    return int(lib().oo_invariants(X.shape[0], X, Y))
+
+
+def pack_canonical(X, Y) -> np.ndarray:
+    L = X.shape[0]
+    w = np.zeros((L // 4) * (L // 4), dtype=np.uint32)
+    lib().oo_pack_canonical(L, X, Y, w)
+    return w
+
+
+def unpack_canonical(words, L: int):
+    X = np.zeros((L, L), dtype=np.uint8)
+    Y = np.zeros((L, L), dtype=np.uint8)
+    lib().oo_unpack_canonical(L, np.ascontiguousarray(words, dtype=np.uint32), X, Y)
+    return X, Y
+
+
+def replica_seed(master: int, r: int) -> int:
+    return int(lib().oo_replica_seed(master, r))

@@ -1,0 +1,593 @@
+/*
+ * CPU oracle for the octahedron-model DTrDT simulation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the
+ * benchmark's CPU-baseline / reference legs load this library.  The product
+ * path (the CUDA library and its binding) never calls it, and the two share
+ * no code: this file is compiled on its own with gcc.
+ *
+ * Every routine is written for clarity, one site and one attempt at a time,
+ * in the order the paper states the method:
+ *   - the model and its update rule: Sec. 2.1, Eq. (1);
+ *   - the roughness: Eq. (3) (mean over the L^2 sites, see below);
+ *   - one MCS = one sweep = L^2 attempts: Sec. 2.1, definition of the MCS;
+ *   - random-sequential dynamics (O1): Sec. 1 (RS site selection);
+ *   - DTrDT (O2): device layer = double tiling with a random origin
+ *     (Sec. 3, "DT" and "DTr"; Fig. 2); block layer = single-hit double
+ *     tiling, one randomly drawn domain set per collective step
+ *     (Sec. 3.1, block layer paragraph).
+ * Where the paper is silent the schedule specification fixes the reading
+ * (random-number streams, thread-cell units, acceptance rounding); those
+ * readings are restated at each use below.
+ *
+ * Parity pins (tests/test_oracle_*.py): Philox known-answer vectors and an
+ * independent Philox implementation; flat-start closed forms; lattice
+ * invariants after every run; exact 4x4 master equations for O1 and for O2
+ * (degenerate 2x2 thread cells); site-selection and acceptance statistics
+ * for O2 at full thread-cell size; planted-mistake tests of the checker.
+ */
+#include "oct_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+/* ------------------------------------------------------------------------ */
+/* Philox-4x32-10, Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as  */
+/* easy as 1, 2, 3", SC'11: ten rounds of two 32x32->64 multiplications     */
+/* with the round constants below and a Weyl-sequence key schedule.         */
+/* ------------------------------------------------------------------------ */
+void oo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+static void seed_key(uint64_t seed, uint32_t key[2]) {
+    key[0] = (uint32_t)(seed & 0xFFFFFFFFu);
+    key[1] = (uint32_t)(seed >> 32);
+}
+
+static void philox_at(const uint32_t key[2], uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                      uint32_t out[4]) {
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    oo_philox4x32_10(ctr, key, out);
+}
+
+/* Acceptance: the paper gives probabilities p, q (Eq. (1)) but no rounding.
+ * Reading: P32 = floor(p * 2^32) (exact: scaling a double by 2^32 is exact),
+ * accept iff the attempt's uniform 32-bit word u < P32; p = 1 always accepts
+ * and p = 0 never does. */
+uint64_t oo_threshold32(double p) {
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return (uint64_t)1 << 32;
+    return (uint64_t)floor(ldexp(p, 32));
+}
+
+static inline int64_t wrap(int64_t a, int64_t L) {
+    int64_t r = a % L;
+    return r < 0 ? r + L : r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Model, Sec. 2.1 / Eq. (1)                                                 */
+/* ------------------------------------------------------------------------ */
+void oo_init_flat(int64_t L, uint8_t *X, uint8_t *Y) {
+    /* h(x,y) = (x+y) mod 2: the slope to the left/lower neighbour is +1
+     * exactly where x+y is odd. */
+    for (int64_t y = 0; y < L; ++y)
+        for (int64_t x = 0; x < L; ++x) {
+            X[y * L + x] = (uint8_t)((x + y) & 1);
+            Y[y * L + x] = (uint8_t)((x + y) & 1);
+        }
+}
+
+int oo_site_kind(int64_t L, const uint8_t *X, const uint8_t *Y, int64_t x, int64_t y) {
+    /* Eq. (1): the 2x2 matrix lists (x-slope at s, x-slope at s+x) in the
+     * first row and (y-slope at s, y-slope at s+y) in the second; [0 1;0 1]
+     * is a local minimum (deposition, prob. p), [1 0;1 0] a local maximum
+     * (removal, prob. q). */
+    int64_t xr = wrap(x + 1, L), yu = wrap(y + 1, L);
+    int xs = X[y * L + x], xn = X[y * L + xr];
+    int ys = Y[y * L + x], yn = Y[yu * L + x];
+    if (xs == 0 && xn == 1 && ys == 0 && yn == 1) return +1;
+    if (xs == 1 && xn == 0 && ys == 1 && yn == 0) return -1;
+    return 0;
+}
+
+static void flip_site(int64_t L, uint8_t *X, uint8_t *Y, int64_t x, int64_t y) {
+    int64_t xr = wrap(x + 1, L), yu = wrap(y + 1, L);
+    X[y * L + x] ^= 1;
+    X[y * L + xr] ^= 1;
+    Y[y * L + x] ^= 1;
+    Y[yu * L + x] ^= 1;
+}
+
+int oo_attempt(int64_t L, uint8_t *X, uint8_t *Y, int64_t x, int64_t y, double p, double q,
+               uint32_t u, int *kind_out) {
+    int kind = oo_site_kind(L, X, Y, x, y);
+    if (kind_out) *kind_out = kind;
+    if (kind == 0) return 0;
+    uint64_t thr = oo_threshold32(kind > 0 ? p : q);
+    if ((uint64_t)u >= thr) return 0;
+    flip_site(L, X, Y, x, y);
+    return kind;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O1: random-sequential updating (Sec. 1): each of the L^2 attempts of an   */
+/* MCS picks a site uniformly at random.  Stream: block                      */
+/* Philox(seed, (a mod 2^32, a div 2^32, t, SEQ<<28)) for attempt a of MCS  */
+/* t; x = (w0*L) >> 32, y = (w1*L) >> 32, u = w2.                            */
+/* ------------------------------------------------------------------------ */
+void oo_seq_rs(int64_t L, double p, double q, uint64_t seed, uint8_t *X, uint8_t *Y, uint32_t t0,
+               uint32_t n_mcs, int64_t *net_flips) {
+    uint32_t key[2];
+    seed_key(seed, key);
+    const int64_t N = L * L;
+    int64_t net = 0;
+    for (uint32_t dt = 0; dt < n_mcs; ++dt) {
+        uint32_t t = t0 + dt;
+        for (int64_t a = 0; a < N; ++a) {
+            uint32_t w[4];
+            philox_at(key, (uint32_t)a, (uint32_t)((uint64_t)a >> 32), t, OO_TAG_SEQ << 28, w);
+            int64_t x = (int64_t)(((uint64_t)w[0] * (uint64_t)L) >> 32);
+            int64_t y = (int64_t)(((uint64_t)w[1] * (uint64_t)L) >> 32);
+            net += oo_attempt(L, X, Y, x, y, p, q, w[2], NULL);
+        }
+    }
+    if (net_flips) *net_flips += net;
+}
+
+void oo_seq_rs_many(int64_t L, double p, double q, uint64_t seed0, int64_t n_runs, uint32_t n_mcs,
+                    uint8_t *Xout, uint8_t *Yout) {
+    const int64_t N = L * L;
+    for (int64_t r = 0; r < n_runs; ++r) {
+        uint8_t *X = Xout + r * N, *Y = Yout + r * N;
+        oo_init_flat(L, X, Y);
+        oo_seq_rs(L, p, q, seed0 + (uint64_t)r, X, Y, 0, n_mcs, NULL);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* O2: DTrDT                                                                 */
+/* ------------------------------------------------------------------------ */
+static int ilog2_exact(int64_t v) {
+    int k = 0;
+    if (v <= 0) return -1;
+    while (((int64_t)1 << k) < v) ++k;
+    return ((int64_t)1 << k) == v ? k : -1;
+}
+
+int oo_check_params(const oo_params *P) {
+    if (!P) return -1;
+    if (P->L < 2 || (P->L & 1)) return -1;
+    if (P->L > ((int64_t)1 << 31)) return -1;
+    if (ilog2_exact(P->cx) < 1 || ilog2_exact(P->cy) < 1) return -1;
+    if (P->Bx < P->cx || P->By < P->cy || P->Bx % P->cx || P->By % P->cy) return -1;
+    int64_t BW = P->Bx < 32 ? P->Bx : 32;
+    if (P->Bx % BW || BW % P->cx || BW / P->cx > 8) return -1;
+    if (P->L % (2 * P->Bx) || P->L % (2 * P->By)) return -1;
+    if (!(P->p >= 0.0 && P->p <= 1.0 && P->q >= 0.0 && P->q <= 1.0)) return -1;
+    if (P->cx * P->cy * 8 >= ((int64_t)1 << 30)) return -1;
+    int64_t groups = (P->Bx / BW) * ((P->By / P->cy + 3) / 4);
+    if (groups >= ((int64_t)1 << 28)) return -1;
+    int64_t tiles = (P->L / (2 * P->Bx)) * (P->L / (2 * P->By));
+    if (tiles > ((int64_t)1 << 32)) return -1;
+    return 0;
+}
+
+/* The index-th permutation of (0,1,2,3) in lexicographic order. */
+static void perm_from_index(uint32_t index, int perm[4]) {
+    int avail[4] = {0, 1, 2, 3};
+    int n = 4;
+    uint32_t fact[4] = {6, 2, 1, 1};
+    for (int i = 0; i < 4; ++i) {
+        uint32_t pick = index / fact[i];
+        index %= fact[i];
+        perm[i] = avail[pick];
+        for (int j = (int)pick; j < n - 1; ++j) avail[j] = avail[j + 1];
+        --n;
+    }
+}
+
+void oo_mcs_draw(const oo_params *P, uint32_t t, int64_t *ox, int64_t *oy, int perm[4]) {
+    /* Device layer (DTr): the tiling origin is moved to a uniformly random
+     * site once per MCS, and the four sub-tile sets are visited in a fresh
+     * uniformly shuffled order each MCS (Sec. 3, DT and DTr). */
+    uint32_t key[2], M[4];
+    seed_key(P->seed, key);
+    philox_at(key, t, 0, 0, OO_TAG_MCS << 28, M);
+    *ox = (int64_t)(((uint64_t)M[0] * (uint64_t)P->L) >> 32);
+    *oy = (int64_t)(((uint64_t)M[1] * (uint64_t)P->L) >> 32);
+    perm_from_index((uint32_t)(((uint64_t)M[2] * 24u) >> 32), perm);
+}
+
+/* A rectangular window of the periodic lattice. */
+typedef struct {
+    int64_t L, wx, wy, W, H;
+    uint8_t *X, *Y;
+} view_t;
+
+static inline int64_t vidx(const view_t *v, int64_t gx, int64_t gy) {
+    int64_t i = wrap(gx - v->wx, v->L), j = wrap(gy - v->wy, v->L);
+    return j * v->W + i;
+}
+
+typedef struct {
+    int64_t *dev_stamp, *dev_owner, *step_stamp, *step_owner; /* 2 per site: X then Y */
+    int64_t dev_serial, step_serial, count;
+} conflict_t;
+
+static void touch(conflict_t *cf, int64_t bit, int64_t tile, int64_t tc) {
+    if (!cf) return;
+    if (cf->dev_stamp[bit] == cf->dev_serial && cf->dev_owner[bit] != tile) cf->count++;
+    cf->dev_stamp[bit] = cf->dev_serial;
+    cf->dev_owner[bit] = tile;
+    if (cf->step_stamp[bit] == cf->step_serial && cf->step_owner[bit] != tc) cf->count++;
+    cf->step_stamp[bit] = cf->step_serial;
+    cf->step_owner[bit] = tc;
+}
+
+/* The 32 level words of the acceptance stream of group g at collective
+ * step s: word l is word l%4 of Philox(seed, (t, k|(s*8+l/4)<<2, T, ACC<<28|g)). */
+static void acc_level_words(const uint32_t key[2], uint32_t t, uint32_t k, uint32_t T, uint32_t g,
+                            uint32_t s, uint32_t acc_w[32]) {
+    for (uint32_t lb = 0; lb < 8; ++lb)
+        philox_at(key, t, k | ((s * 8 + lb) << 2), T, (OO_TAG_ACC << 28) | g, &acc_w[4 * lb]);
+}
+
+/* The uniform of the thread cell at bit position pos of its group: bit
+ * (31-l) of u is bit pos of level word l (most significant bit first). */
+static uint32_t acc_uniform(const uint32_t acc_w[32], int pos) {
+    uint32_t u = 0;
+    for (int l = 0; l < 32; ++l) u |= ((acc_w[l] >> pos) & 1u) << (31 - l);
+    return u;
+}
+
+uint32_t oo_dtrdt_acc_uniform(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t g,
+                              uint32_t s, int pos) {
+    uint32_t key[2], w[32];
+    seed_key(seed, key);
+    acc_level_words(key, t, k, T, g, s, w);
+    return acc_uniform(w, pos);
+}
+
+/* Block layer on one sub-tile: single-hit double tiling.
+ *
+ * The sub-tile (Bx x By sites, local origin (x0,y0)) is cut into thread
+ * cells (TC) of cx x cy sites; each TC is cut into four sub-cells of
+ * (cx/2) x (cy/2) sites, sub-cell d = (dx,dy) = (d&1, d>>1).  One collective
+ * step: the block draws d uniformly (with replacement, not a permutation),
+ * every TC performs exactly one attempt at a uniformly chosen site of its
+ * sub-cell d, then all synchronise.  cx*cy collective steps make one sweep
+ * of the sub-tile (Bx*By attempts).
+ *
+ * Random streams (reading fixed by the schedule specification):
+ *   set draw for step s : word (s%64)/16 of Philox(seed, (t, k|(s/64)<<2, T, SET<<28)),
+ *                         bits 2*(s%16) .. +1.
+ *   TCs are grouped: a band is one TC row, BW = min(32,Bx) sites wide; a group
+ *   is four vertically consecutive bands of one band column; g = (c/4)*(Bx/BW)
+ *   + band column, m = c%4 (c = TC row), j = TC index inside its band.
+ *   site draw           : word m of Philox(seed, (t, k|(s/spw)<<2, T, SITE<<28|g)),
+ *                         bits fw*j + (s%spw)*(fw/spw) .. + bpt-1, low log2(cx/2)
+ *                         bits = x offset, the rest = y offset.
+ *   acceptance uniform  : bit (31-l) of u is bit (4j+m) of word l%4 of
+ *                         Philox(seed, (t, k|(s*8+l/4)<<2, T, ACC<<28|g)).
+ */
+static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, uint32_t k,
+                        uint32_t T, int64_t x0, int64_t y0, view_t *v, int64_t *net,
+                        int64_t *attempts, conflict_t *cf) {
+    const int64_t L = P->L, Bx = P->Bx, By = P->By, cx = P->cx, cy = P->cy;
+    const int64_t BW = Bx < 32 ? Bx : 32;
+    const int64_t tcs_per_band = BW / cx;
+    const int64_t band_cols = Bx / BW;
+    const int64_t tc_rows = By / cy;
+    const int64_t group_rows = (tc_rows + 3) / 4;
+    const int bx_bits = ilog2_exact(cx / 2), by_bits = ilog2_exact(cy / 2);
+    const int bpt = bx_bits + by_bits;
+    const int64_t fw = 32 / tcs_per_band;
+    const int spw = (bpt > 0 && 2 * bpt <= fw) ? 2 : 1;
+    const int64_t n_steps = cx * cy;
+    const uint64_t thr_p = oo_threshold32(P->p), thr_q = oo_threshold32(P->q);
+    const int p_random = P->p > 0.0 && P->p < 1.0;
+    const int q_random = P->q > 0.0 && P->q < 1.0;
+
+    for (int64_t s = 0; s < n_steps; ++s) {
+        uint32_t sw[4];
+        philox_at(key, t, k | (uint32_t)((s / 64) << 2), T, OO_TAG_SET << 28, sw);
+        const int d = (int)((sw[(s % 64) / 16] >> (2 * (s % 16))) & 3u);
+        const int64_t dx = d & 1, dy = d >> 1;
+        if (cf) cf->step_serial++;
+
+        for (int64_t gr = 0; gr < group_rows; ++gr) {
+            for (int64_t bc = 0; bc < band_cols; ++bc) {
+                const uint32_t g = (uint32_t)(gr * band_cols + bc);
+                uint32_t site_w[4] = {0, 0, 0, 0};
+                if (bpt > 0)
+                    philox_at(key, t, k | (uint32_t)((s / spw) << 2), T,
+                              (OO_TAG_SITE << 28) | g, site_w);
+                int acc_ready = 0;
+                uint32_t acc_w[32];
+                for (int64_t m = 0; m < 4; ++m) {
+                    const int64_t c = 4 * gr + m; /* TC row */
+                    if (c >= tc_rows) break;
+                    for (int64_t j = 0; j < tcs_per_band; ++j) {
+                        const int64_t a = bc * tcs_per_band + j; /* TC column */
+                        int64_t rx = 0, ry = 0;
+                        if (bpt > 0) {
+                            const int64_t off = fw * j + (s % spw) * (fw / spw);
+                            const uint32_t r = (site_w[m] >> off) & ((1u << bpt) - 1u);
+                            rx = r & ((1u << bx_bits) - 1u);
+                            ry = r >> bx_bits;
+                        }
+                        const int64_t lx = a * cx + dx * (cx / 2) + rx;
+                        const int64_t ly = c * cy + dy * (cy / 2) + ry;
+                        const int64_t gx = wrap(x0 + lx, L), gy = wrap(y0 + ly, L);
+                        const int64_t is = vidx(v, gx, gy);
+                        const int64_t ir = vidx(v, gx + 1, gy);
+                        const int64_t iu = vidx(v, gx, gy + 1);
+                        if (attempts) attempts[gy * L + gx]++;
+                        if (cf) {
+                            const int64_t tc = c * (Bx / cx) + a;
+                            const int64_t nv = v->W * v->H;
+                            touch(cf, is, T, tc);
+                            touch(cf, ir, T, tc);
+                            touch(cf, nv + is, T, tc);
+                            touch(cf, nv + iu, T, tc);
+                        }
+                        int kind = 0;
+                        if (v->X[is] == 0 && v->X[ir] == 1 && v->Y[is] == 0 && v->Y[iu] == 1)
+                            kind = +1;
+                        else if (v->X[is] == 1 && v->X[ir] == 0 && v->Y[is] == 1 && v->Y[iu] == 0)
+                            kind = -1;
+                        if (kind == 0) continue;
+                        uint32_t u = 0;
+                        if ((kind > 0 && p_random) || (kind < 0 && q_random)) {
+                            if (!acc_ready) {
+                                acc_level_words(key, t, k, T, g, (uint32_t)s, acc_w);
+                                acc_ready = 1;
+                            }
+                            u = acc_uniform(acc_w, (int)(4 * j + m));
+                        }
+                        if ((uint64_t)u >= (kind > 0 ? thr_p : thr_q)) continue;
+                        v->X[is] ^= 1;
+                        v->X[ir] ^= 1;
+                        v->Y[is] ^= 1;
+                        v->Y[iu] ^= 1;
+                        *net += kind;
+                    }
+                }
+            }
+        }
+    }
+}
+
+static int footprint_inside(const view_t *v, int64_t x0, int64_t y0, int64_t Bx, int64_t By) {
+    int okx = (v->W == v->L) || (wrap(x0 - v->wx, v->L) + Bx < v->W);
+    int oky = (v->H == v->L) || (wrap(y0 - v->wy, v->L) + By < v->H);
+    return okx && oky;
+}
+
+static void run_mcs(const oo_params *P, uint32_t t, view_t *v, int64_t *net, int64_t *attempts,
+                    conflict_t *cf) {
+    uint32_t key[2];
+    seed_key(P->seed, key);
+    int64_t ox, oy;
+    int perm[4];
+    oo_mcs_draw(P, t, &ox, &oy, perm);
+    const int64_t tiles_x = P->L / (2 * P->Bx), tiles_y = P->L / (2 * P->By);
+    for (uint32_t k = 0; k < 4; ++k) {
+        /* Device step k updates the set perm[k]: quadrant (sx,sy) of every
+         * 2Bx x 2By device tile.  Sub-tiles of one set never share a slope
+         * bit, so their order is irrelevant (checked by the conflict
+         * tracker). */
+        const int sigma = perm[k];
+        const int64_t sx = sigma & 1, sy = sigma >> 1;
+        if (cf) cf->dev_serial++;
+        for (int64_t ty = 0; ty < tiles_y; ++ty)
+            for (int64_t tx = 0; tx < tiles_x; ++tx) {
+                const uint32_t T = (uint32_t)(ty * tiles_x + tx);
+                const int64_t x0 = wrap(ox + 2 * P->Bx * tx + P->Bx * sx, P->L);
+                const int64_t y0 = wrap(oy + 2 * P->By * ty + P->By * sy, P->L);
+                if (!footprint_inside(v, x0, y0, P->Bx, P->By)) continue;
+                run_subtile(P, key, t, k, T, x0, y0, v, net, attempts, cf);
+            }
+    }
+}
+
+int oo_dtrdt_run(const oo_params *P, uint8_t *X, uint8_t *Y, uint32_t t0, uint32_t n_mcs,
+                 int64_t *net_flips, int64_t *attempts, int64_t *conflicts) {
+    if (oo_check_params(P)) return -1;
+    view_t v = {P->L, 0, 0, P->L, P->L, X, Y};
+    conflict_t cfs, *cf = NULL;
+    const int64_t nbits = 2 * P->L * P->L;
+    if (conflicts) {
+        cfs.dev_stamp = (int64_t *)malloc(sizeof(int64_t) * nbits);
+        cfs.dev_owner = (int64_t *)malloc(sizeof(int64_t) * nbits);
+        cfs.step_stamp = (int64_t *)malloc(sizeof(int64_t) * nbits);
+        cfs.step_owner = (int64_t *)malloc(sizeof(int64_t) * nbits);
+        if (!cfs.dev_stamp || !cfs.dev_owner || !cfs.step_stamp || !cfs.step_owner) {
+            free(cfs.dev_stamp);
+            free(cfs.dev_owner);
+            free(cfs.step_stamp);
+            free(cfs.step_owner);
+            return -1;
+        }
+        for (int64_t i = 0; i < nbits; ++i) cfs.dev_stamp[i] = cfs.step_stamp[i] = -1;
+        cfs.dev_serial = cfs.step_serial = cfs.count = 0;
+        cf = &cfs;
+    }
+    int64_t net = 0;
+    for (uint32_t dt = 0; dt < n_mcs; ++dt) run_mcs(P, t0 + dt, &v, &net, attempts, cf);
+    if (net_flips) *net_flips += net;
+    if (cf) {
+        *conflicts = cf->count;
+        free(cfs.dev_stamp);
+        free(cfs.dev_owner);
+        free(cfs.step_stamp);
+        free(cfs.step_owner);
+    }
+    return 0;
+}
+
+int oo_dtrdt_mcs_window(const oo_params *P, uint32_t t, int64_t wx, int64_t wy, int64_t W,
+                        int64_t H, uint8_t *Xw, uint8_t *Yw, int64_t *net_flips) {
+    if (oo_check_params(P)) return -1;
+    if (W < 1 || H < 1 || W > P->L || H > P->L) return -1;
+    view_t v = {P->L, wrap(wx, P->L), wrap(wy, P->L), W, H, Xw, Yw};
+    int64_t net = 0;
+    run_mcs(P, t, &v, &net, NULL, NULL);
+    if (net_flips) *net_flips += net;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O3: roughness, Eq. (3).  The printed equation divides the squared mean by */
+/* L rather than L^2; read as the mean over all L^2 sites (the only          */
+/* translation-invariant reading).  W^2 = (N*S2 - S1^2) / N^2, N = L^2.      */
+/* ------------------------------------------------------------------------ */
+void oo_w2_sums(int64_t L, const uint8_t *X, const uint8_t *Y, int64_t *s1, uint64_t *s2_lo,
+                uint64_t *s2_hi, int64_t *hmax) {
+    i128 S1 = 0;
+    u128 S2 = 0;
+    int64_t hm = 0;
+    int64_t h0 = 0; /* h(0,y) */
+    for (int64_t y = 0; y < L; ++y) {
+        if (y > 0) h0 += 2 * (int64_t)Y[y * L + 0] - 1;
+        int64_t h = h0;
+        for (int64_t x = 0; x < L; ++x) {
+            if (x > 0) h += 2 * (int64_t)X[y * L + x] - 1;
+            S1 += h;
+            S2 += (u128)((i128)h * h);
+            int64_t ah = h < 0 ? -h : h;
+            if (ah > hm) hm = ah;
+        }
+    }
+    *s1 = (int64_t)S1;
+    *s2_lo = (uint64_t)S2;
+    *s2_hi = (uint64_t)(S2 >> 64);
+    if (hmax) *hmax = hm;
+}
+
+void oo_w2_sums_colfirst(int64_t L, const uint8_t *X, const uint8_t *Y, int64_t *s1,
+                         uint64_t *s2_lo, uint64_t *s2_hi) {
+    i128 S1 = 0;
+    u128 S2 = 0;
+    int64_t hx0 = 0; /* h(x,0) */
+    for (int64_t x = 0; x < L; ++x) {
+        if (x > 0) hx0 += 2 * (int64_t)X[0 * L + x] - 1;
+        int64_t h = hx0;
+        for (int64_t y = 0; y < L; ++y) {
+            if (y > 0) h += 2 * (int64_t)Y[y * L + x] - 1;
+            S1 += h;
+            S2 += (u128)((i128)h * h);
+        }
+    }
+    *s1 = (int64_t)S1;
+    *s2_lo = (uint64_t)S2;
+    *s2_hi = (uint64_t)(S2 >> 64);
+}
+
+double oo_w2_from_sums(int64_t L, int64_t s1, uint64_t s2_lo, uint64_t s2_hi) {
+    const i128 N = (i128)L * L;
+    const i128 S2 = (i128)(((u128)s2_hi << 64) | s2_lo);
+    const i128 num = N * S2 - (i128)s1 * s1;
+    return (double)num / ((double)N * (double)N);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Invariants fixed by the model: heights exist on the torus (row / column   */
+/* slope balance, zero circulation around every plaquette).                  */
+/* ------------------------------------------------------------------------ */
+int oo_invariants(int64_t L, const uint8_t *X, const uint8_t *Y) {
+    int bad = 0;
+    for (int64_t y = 0; y < L; ++y) {
+        int64_t n = 0;
+        for (int64_t x = 0; x < L; ++x) n += X[y * L + x];
+        if (2 * n != L) bad |= 1;
+    }
+    for (int64_t x = 0; x < L; ++x) {
+        int64_t n = 0;
+        for (int64_t y = 0; y < L; ++y) n += Y[y * L + x];
+        if (2 * n != L) bad |= 2;
+    }
+    for (int64_t y = 0; y < L; ++y)
+        for (int64_t x = 0; x < L; ++x) {
+            const int64_t x1 = wrap(x + 1, L), y1 = wrap(y + 1, L);
+            /* h(x+1,y)-h(x,y) + h(x+1,y+1)-h(x+1,y) - [h(x+1,y+1)-h(x,y+1)] - [h(x,y+1)-h(x,y)] */
+            const int64_t circ = (2 * X[y * L + x1] - 1) + (2 * Y[y1 * L + x1] - 1) -
+                                 (2 * X[y1 * L + x1] - 1) - (2 * Y[y1 * L + x] - 1);
+            if (circ != 0) bad |= 4;
+        }
+    return bad;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Canonical exchange layout (paper: one 32-bit word holds 4x4 sites, two    */
+/* slope bits per site; the bit order inside the word is this project's).   */
+/* ------------------------------------------------------------------------ */
+void oo_pack_canonical(int64_t L, const uint8_t *X, const uint8_t *Y, uint32_t *words) {
+    const int64_t nw = (L / 4) * (L / 4);
+    for (int64_t i = 0; i < nw; ++i) words[i] = 0;
+    for (int64_t y = 0; y < L; ++y)
+        for (int64_t x = 0; x < L; ++x) {
+            const int64_t w = (y / 4) * (L / 4) + x / 4;
+            const int b = 2 * (int)(4 * (y % 4) + (x % 4));
+            words[w] |= (uint32_t)X[y * L + x] << b;
+            words[w] |= (uint32_t)Y[y * L + x] << (b + 1);
+        }
+}
+
+void oo_unpack_canonical(int64_t L, const uint32_t *words, uint8_t *X, uint8_t *Y) {
+    for (int64_t y = 0; y < L; ++y)
+        for (int64_t x = 0; x < L; ++x) {
+            const int64_t w = (y / 4) * (L / 4) + x / 4;
+            const int b = 2 * (int)(4 * (y % 4) + (x % 4));
+            X[y * L + x] = (uint8_t)((words[w] >> b) & 1u);
+            Y[y * L + x] = (uint8_t)((words[w] >> (b + 1)) & 1u);
+        }
+}
+
+uint64_t oo_replica_seed(uint64_t master_seed, uint32_t r) {
+    uint32_t key[2], w[4];
+    seed_key(master_seed, key);
+    philox_at(key, r, 0, 0, OO_TAG_REPLICA << 28, w);
+    return (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+}
+
+int oo_dtrdt_many(const oo_params *P, uint64_t seed0, int64_t n_runs, uint32_t n_mcs,
+                  uint8_t *Xout, uint8_t *Yout) {
+    if (oo_check_params(P)) return -1;
+    const int64_t N = P->L * P->L;
+    for (int64_t r = 0; r < n_runs; ++r) {
+        oo_params Q = *P;
+        Q.seed = seed0 + (uint64_t)r;
+        uint8_t *X = Xout + r * N, *Y = Yout + r * N;
+        oo_init_flat(P->L, X, Y);
+        oo_dtrdt_run(&Q, X, Y, 0, n_mcs, NULL, NULL, NULL);
+    }
+    return 0;
+}

@@ -1,0 +1,143 @@
+/*
+ * CPU oracle for the octahedron-model DTrDT simulation (test infrastructure).
+ *
+ * This header and oct_oracle.c are the plain, slow, obviously-correct
+ * statement of what the GPU path computes.  Only the test-suite, the smoke
+ * check and the benchmark's CPU-baseline leg may load this library.  It
+ * shares no code, header, table or constant generator with the CUDA path.
+ *
+ * Lattice representation used by every oracle routine: two byte arrays X and
+ * Y of L*L entries, index y*L + x, each entry 0 or 1:
+ *   X[y*L+x] = 1  iff  h(x,y) - h(x-1,y) = +1   (slope to the left neighbour)
+ *   Y[y*L+x] = 1  iff  h(x,y) - h(x,y-1) = +1   (slope to the lower neighbour)
+ * with periodic indices.  This is the paper's on-site slope convention
+ * (Sec. 3, dead-border scheme: each site carries the slope towards its left
+ * neighbour; updates only reach the +x and +y neighbours).
+ *
+ * Parity status of each routine is listed in oct_oracle.c next to the code.
+ */
+#ifndef OCT_ORACLE_H
+#define OCT_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Stream tags (top 4 bits of counter word 3). */
+#define OO_TAG_MCS 1u
+#define OO_TAG_SET 2u
+#define OO_TAG_SITE 3u
+#define OO_TAG_ACC 4u
+#define OO_TAG_SEQ 5u
+#define OO_TAG_REPLICA 6u
+
+typedef struct {
+    int64_t L;        /* lateral size; periodic */
+    int64_t Bx, By;   /* device-layer sub-tile size in sites (device tile = 2Bx x 2By) */
+    int64_t cx, cy;   /* block-layer thread-cell size in sites */
+    double p, q;      /* deposition / removal probabilities, Eq. (1) */
+    uint64_t seed;    /* Philox key = (seed low 32 bits, seed high 32 bits) */
+} oo_params;
+
+/* Philox-4x32-10 (Salmon et al., SC'11), counter ctr[4], key key[2]. */
+void oo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Acceptance threshold: accept iff u < P32, u a uniform 32-bit word. */
+uint64_t oo_threshold32(double p);
+
+/* Flat initial condition h(x,y) = (x+y) mod 2. */
+void oo_init_flat(int64_t L, uint8_t *X, uint8_t *Y);
+
+/* One Kawasaki attempt at site (x,y), Eq. (1).  Returns +1 for an accepted
+ * deposition, -1 for an accepted removal, 0 otherwise.  kind_out (optional)
+ * receives +1 if the site was a local minimum, -1 if a maximum, 0 otherwise.
+ * u is the attempt's 32-bit uniform; it is only read when the relevant
+ * probability lies strictly between 0 and 1. */
+int oo_attempt(int64_t L, uint8_t *X, uint8_t *Y, int64_t x, int64_t y,
+               double p, double q, uint32_t u, int *kind_out);
+
+/* Site classification only: +1 local minimum, -1 local maximum, 0 neither. */
+int oo_site_kind(int64_t L, const uint8_t *X, const uint8_t *Y, int64_t x, int64_t y);
+
+/* O1: true random-sequential updating, n_mcs sweeps of L*L attempts starting
+ * at MCS index t0.  Adds accepted depositions minus removals to *net_flips. */
+void oo_seq_rs(int64_t L, double p, double q, uint64_t seed, uint8_t *X, uint8_t *Y,
+               uint32_t t0, uint32_t n_mcs, int64_t *net_flips);
+
+/* O1 on many independent seeds of one small lattice (seed0 + r for run r),
+ * writing every final lattice to Xout/Yout (n_runs * L*L bytes each). */
+void oo_seq_rs_many(int64_t L, double p, double q, uint64_t seed0, int64_t n_runs,
+                    uint32_t n_mcs, uint8_t *Xout, uint8_t *Yout);
+
+/* Validates a DTrDT parameter set; returns 0 if usable by the oracle. */
+int oo_check_params(const oo_params *prm);
+
+/* The per-MCS device-layer draw: origin (ox,oy) and the permutation perm[4]
+ * of the four sub-tile sets. */
+void oo_mcs_draw(const oo_params *prm, uint32_t t, int64_t *ox, int64_t *oy, int perm[4]);
+
+/* O2: replay of the DTrDT schedule for n_mcs sweeps starting at MCS t0.
+ * Optional instrumentation (pass NULL to skip):
+ *   attempts[L*L]  : incremented for every attempted site
+ *   conflicts      : if non-NULL, every read/written slope bit is tracked and
+ *                    *conflicts counts bits touched by two different thread
+ *                    cells in one collective step, or by two sub-tiles in one
+ *                    device step (must stay 0).
+ * Returns 0, or -1 on invalid parameters. */
+int oo_dtrdt_run(const oo_params *prm, uint8_t *X, uint8_t *Y, uint32_t t0, uint32_t n_mcs,
+                 int64_t *net_flips, int64_t *attempts, int64_t *conflicts);
+
+/* O2 on many independent seeds (seed0 + r) of one lattice from the flat
+ * start, writing every final lattice to Xout/Yout (n_runs * L*L bytes each). */
+int oo_dtrdt_many(const oo_params *prm, uint64_t seed0, int64_t n_runs, uint32_t n_mcs,
+                  uint8_t *Xout, uint8_t *Yout);
+
+/* The acceptance uniform O2 uses for the thread cell at bit position pos
+ * (= 4*j + m) of group g, collective step s, device step k, tile T, MCS t. */
+uint32_t oo_dtrdt_acc_uniform(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t g,
+                              uint32_t s, int pos);
+
+/* O2 restricted to a window: the lattice is only known on a W x H window whose
+ * lower-left corner is the global site (wx, wy) (periodic in L).  Xw/Yw hold
+ * the window, index j*W + i for global site ((wx+i) mod L, (wy+j) mod L).
+ * Runs MCS t and updates every sub-tile whose footprint (sub-tile plus its +x
+ * column and +y row) lies inside the window; other sub-tiles are skipped, so
+ * only sites far enough from the window edge end up exact. */
+int oo_dtrdt_mcs_window(const oo_params *prm, uint32_t t, int64_t wx, int64_t wy,
+                        int64_t W, int64_t H, uint8_t *Xw, uint8_t *Yw, int64_t *net_flips);
+
+/* O3: exact roughness sums, Eq. (3).  Heights relative to h(0,0) = 0 are
+ * integrated first up column 0 and then along each row.  s1 = sum h,
+ * s2 = sum h^2 returned as two 64-bit halves of an unsigned 128-bit value
+ * (s2 is non-negative), hmax = max |h|. */
+void oo_w2_sums(int64_t L, const uint8_t *X, const uint8_t *Y, int64_t *s1,
+                uint64_t *s2_lo, uint64_t *s2_hi, int64_t *hmax);
+
+/* Same sums, integrating first along row 0 and then up each column. */
+void oo_w2_sums_colfirst(int64_t L, const uint8_t *X, const uint8_t *Y, int64_t *s1,
+                         uint64_t *s2_lo, uint64_t *s2_hi);
+
+/* W^2 = (N*S2 - S1^2)/N^2 from exact integer sums, N = L*L. */
+double oo_w2_from_sums(int64_t L, int64_t s1, uint64_t s2_lo, uint64_t s2_hi);
+
+/* Invariants of the slope lattice.  Returns a bit set of violated properties:
+ *   1: some row does not hold exactly L/2 up-slopes in X
+ *   2: some column does not hold exactly L/2 up-slopes in Y
+ *   4: some plaquette has non-zero height circulation
+ * (0 = all hold). */
+int oo_invariants(int64_t L, const uint8_t *X, const uint8_t *Y);
+
+/* Canonical exchange layout: one 32-bit word per 4x4 block of sites, word
+ * index (y/4)*(L/4) + x/4, bit 2*(4*(y%4) + x%4) = X, the next bit = Y. */
+void oo_pack_canonical(int64_t L, const uint8_t *X, const uint8_t *Y, uint32_t *words);
+void oo_unpack_canonical(int64_t L, const uint32_t *words, uint8_t *X, uint8_t *Y);
+
+/* Per-replica key derivation for batched runs: key_r = the first two words of
+ * Philox(master key, (r, 0, 0, TAG_REPLICA << 28)). */
+uint64_t oo_replica_seed(uint64_t master_seed, uint32_t r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,176 @@
+/*
+ * oct.h -- C ABI of the GB300 octahedron-model DTrDT simulator.
+ *
+ * The library simulates random-sequential (RS) updating of the 2+1-d
+ * octahedron model for KPZ surface growth (Kelling, Odor, Gemming,
+ * "Suppressing correlations in massively parallel simulations of lattice
+ * models", arXiv:1705.01022) under the DTrDT domain decomposition: double
+ * tiling with a random origin at device level (Sec. 3, "DTr"), single-hit
+ * double tiling at block level (Sec. 3.1).  The roughness W^2 of Eq. (3) is
+ * measured exactly.
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return an oct error code (OCT_OK = 0).  No C++ exception
+ *     crosses this boundary.  oct_last_error() gives a message for the most
+ *     recent failure on the calling thread.
+ *   - A handle may be used by one host thread at a time.
+ *   - Work is enqueued on the handle's CUDA stream (the caller's, if one was
+ *     given to oct_create_ex, else one the library creates).  Functions that
+ *     return data to the host synchronise that stream; oct_run_mcs does not.
+ *   - Device pointers and streams are plain void* (cudaStream_t / device
+ *     addresses) so that no CUDA or PyTorch type appears in the ABI.
+ *
+ * Lattice layouts.
+ *   Slope bits (Sec. 2.1, Eq. (1); on-site convention of Sec. 3): for site
+ *   (x, y), X = 1 iff h(x,y) - h(x-1,y) = +1 and Y = 1 iff
+ *   h(x,y) - h(x,y-1) = +1, indices periodic in L.
+ *   - Canonical layout (the paper's data structure: one 32-bit word holds
+ *     4x4 sites, Sec. 3.1): L*L/16 words; word (y/4)*(L/4) + x/4 holds
+ *     X at bit 2*(4*(y%4) + x%4) and Y at the next bit.
+ *   - Planar layout (device-resident form): an X plane then a Y plane, each L
+ *     rows of L/32 words; bit i of word w of row y is the slope bit of site
+ *     (32w + i, y).  Both layouts occupy L*L/4 bytes.
+ */
+#ifndef OCT_H
+#define OCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define OCT_OK 0
+#define OCT_EINVAL 1       /* invalid argument (sizes, probabilities, layout)      */
+#define OCT_ENOMEM 2       /* device or host allocation failed                     */
+#define OCT_ECUDA 3        /* a CUDA runtime call failed                           */
+#define OCT_ETIMEDOUT 4    /* a bounded device wait gave up                        */
+#define OCT_EINTERNAL 5    /* an internal consistency check failed                 */
+#define OCT_EUNSUPPORTED 6 /* valid request this build does not implement          */
+
+typedef struct oct_sim oct_sim; /* opaque; owns its device memory unless told otherwise */
+
+/* Creation parameters (oct_create_ex).  Zero fields take the defaults.
+ *   L      lateral size; needs L % (2*Bx) == 0 and L % (2*By) == 0.
+ *   p, q   deposition / removal probabilities of Eq. (1), each in [0, 1].
+ *   seed   Philox-4x32-10 key (low word, high word).
+ *   Bx, By device-layer sub-tile in sites (device tile 2Bx x 2By).  Bx must be
+ *          a multiple of 32 and By a multiple of 4*cy; a sub-tile may hold at
+ *          most 32 groups of 32 x 4cy sites.  Defaults: 64 x 64 if L % 128 == 0,
+ *          else 32 x 16.
+ *   cx, cy block-layer thread cell in sites (default 4 x 4; this build
+ *          supports 4 x 4).
+ *   stream cudaStream_t to enqueue on, or NULL for a library-owned stream.
+ *   lattice  external device buffer of L*L/4 bytes (planar layout), or NULL
+ *          for a library-owned one.  An external buffer stays owned by the
+ *          caller and must outlive the handle.
+ *   no_init  0: write the flat start h = (x+y) mod 2; 1: keep the buffer. */
+typedef struct {
+    int64_t L;
+    double p, q;
+    uint64_t seed;
+    int32_t Bx, By;
+    int32_t cx, cy;
+    void *stream;
+    void *lattice;
+    int32_t no_init;
+    int32_t reserved[7];
+} oct_params;
+
+/* Exact roughness, Eq. (3), read as the mean over all L^2 sites:
+ *   heights relative to h(0,0) = 0, s1 = sum h, s2 = sum h^2 as an unsigned
+ *   128-bit value (s2_hi:s2_lo), w2 = (N*s2 - s1^2) / N^2 with N = n_sites,
+ *   formed in 128-bit integers and converted to double once.
+ *   net_flips = accepted depositions minus removals since the flat start
+ *   (the absolute mean height grows by 2*net_flips/N); hmax = max |h|. */
+typedef struct {
+    int64_t t;
+    int64_t n_sites;
+    int64_t s1;
+    uint64_t s2_lo, s2_hi;
+    int64_t net_flips;
+    int64_t hmax;
+    double w2;
+} oct_w2;
+
+typedef struct {
+    int64_t L;
+    int64_t t;
+    int32_t Bx, By, cx, cy;
+    double p, q;
+    uint64_t seed;
+    void *stream;
+    void *lattice; /* device address of the planar lattice */
+    int64_t lattice_bytes;
+} oct_info;
+
+/* Creates a simulation in the flat start with the default tiling (see
+ * oct_params).  *out receives the handle.  Errors: OCT_EINVAL (L, p, q),
+ * OCT_ENOMEM, OCT_ECUDA. */
+int oct_create(int64_t L, double p, double q, uint64_t seed, oct_sim **out);
+
+/* Creates a simulation from a parameter block (see oct_params). */
+int oct_create_ex(const oct_params *prm, oct_sim **out);
+
+/* Enqueues n >= 0 Monte Carlo steps (one MCS = one sweep of L^2 update
+ * attempts, Sec. 2.1) and advances the handle's time t by n.  Each MCS draws
+ * a new random origin and set order (DTr, Sec. 3) and runs four device steps
+ * of single-hit DT on every sub-tile of one set (Sec. 3.1).  Asynchronous on
+ * the handle's stream.  Errors: OCT_EINVAL (n < 0 or t would pass 2^32-1). */
+int oct_run_mcs(oct_sim *s, int64_t n);
+
+/* Computes the exact roughness of the current lattice (Eq. (3)); synchronises
+ * the handle's stream. */
+int oct_measure_w2(oct_sim *s, oct_w2 *out);
+
+/* Copies the lattice to host memory in the canonical 4x4-per-word layout;
+ * words must equal L*L/16.  Synchronises. */
+int oct_get_lattice(oct_sim *s, uint32_t *host, size_t words);
+
+/* Replaces the lattice from host memory (canonical layout, words = L*L/16)
+ * and sets the time to t (resume from a snapshot: the counter-based random
+ * streams make the continuation identical to an uninterrupted run).  The
+ * caller is responsible for the lattice being a valid slope field; the
+ * accumulated net-flip count is reset to 0. */
+int oct_set_lattice(oct_sim *s, const uint32_t *host, size_t words, int64_t t);
+
+/* Raw copies of the planar layout (words = L*L/16 in total: X plane then Y
+ * plane). */
+int oct_get_planes(oct_sim *s, uint32_t *host, size_t words);
+int oct_set_planes(oct_sim *s, const uint32_t *host, size_t words, int64_t t);
+
+/* Copies a W x H window whose corner is global site (wx, wy) (periodic) into
+ * host byte arrays X, Y of W*H entries each (index j*W + i for site
+ * (wx+i, wy+j)), one slope bit per byte.  Synchronises. */
+int oct_get_window(oct_sim *s, int64_t wx, int64_t wy, int64_t W, int64_t H, uint8_t *X,
+                   uint8_t *Y);
+
+/* Parameters and current time of a handle. */
+int oct_get_info(oct_sim *s, oct_info *out);
+
+/* Waits for all work enqueued on the handle's stream. */
+int oct_sync(oct_sim *s);
+
+/* Per-kernel device time (milliseconds) accumulated while timing is on:
+ * step_ms covers the device-step kernels (rows a2-a5), other_ms the rest of
+ * oct_run_mcs.  Timing brackets every device-step launch with CUDA events on
+ * the handle's stream.  oct_set_timing(s, 1) enables and resets the
+ * counters. */
+int oct_set_timing(oct_sim *s, int enable);
+int oct_get_timing(oct_sim *s, double *step_ms, int64_t *step_launches, double *other_ms);
+
+/* Releases the handle and the memory it owns.  NULL-safe. */
+int oct_destroy(oct_sim *s);
+
+/* Static text for an error code. */
+const char *oct_strerror(int code);
+
+/* Message describing the most recent failure on this thread ("" if none). */
+const char *oct_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCT_H */

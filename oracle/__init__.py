@@ -102,6 +102,8 @@ def lib():
         L.oo_dtrdt_many.argtypes = [ctypes.POINTER(_Params), u64, i64, u32, _P_u8, _P_u8]
         L.oo_dtrdt_acc_uniform.argtypes = [u64, u32, u32, u32, u32, u32, ctypes.c_int]
         L.oo_dtrdt_acc_uniform.restype = u32
+        L.oo_w2_sums_planar.argtypes = [i64, _P_u32, P_i64, P_u64, P_u64, P_i64]
+        L.oo_invariants_planar.argtypes = [i64, _P_u32, i64, i64]
         L.oo_replica_seed.argtypes = [u64, u32]
         L.oo_replica_seed.restype = u64
         _lib = L
@@ -229,6 +231,27 @@ def w2_from_sums(L: int, s1: int, s2: int) -> float:
 def w2(X, Y) -> float:
     s1, s2, _ = w2_sums(X, Y)
     return w2_from_sums(X.shape[0], s1, s2)
+
+
+def w2_sums_planar(words, L: int):
+    """O3 on the bit-packed planar layout: (S1, S2, hmax)."""
+    s1, lo, hi, hm = ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int64()
+    lib().oo_w2_sums_planar(L, np.ascontiguousarray(words, dtype=np.uint32), ctypes.byref(s1),
+                            ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(hm))
+    return int(s1.value), (int(hi.value) << 64) | int(lo.value), int(hm.value)
+
+
+def invariants_planar(words, L: int, circ_rows=None) -> int:
+    y0, y1 = (0, L) if circ_rows is None else circ_rows
+    return int(lib().oo_invariants_planar(L, np.ascontiguousarray(words, dtype=np.uint32), y0, y1))
+
+
+def pack_planar(X, Y) -> np.ndarray:
+    """Byte arrays -> planar words (X plane then Y plane); numpy bit packing."""
+    L = X.shape[0]
+    bits = np.stack([X, Y]).astype(np.uint8)
+    packed = np.packbits(bits.reshape(2, L, L // 8, 8), axis=-1, bitorder="little")
+    return packed.reshape(-1).view(np.uint32).copy()
 
 
 def invariants(X, Y) -> int:

@@ -591,3 +591,60 @@ int oo_dtrdt_many(const oo_params *P, uint64_t seed0, int64_t n_runs, uint32_t n
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The same roughness sums and invariants read straight from a bit-packed    */
+/* planar lattice (X plane then Y plane, L rows of L/32 words, bit x%32 of   */
+/* word x/32), for sizes where one byte per site would not fit in memory.    */
+/* ------------------------------------------------------------------------ */
+static inline int planar_bit(const uint32_t *plane, int64_t L, int64_t x, int64_t y) {
+    return (int)((plane[y * (L / 32) + x / 32] >> (x % 32)) & 1u);
+}
+
+void oo_w2_sums_planar(int64_t L, const uint32_t *words, int64_t *s1, uint64_t *s2_lo,
+                       uint64_t *s2_hi, int64_t *hmax) {
+    const uint32_t *Xp = words, *Yp = words + L * (L / 32);
+    i128 S1 = 0;
+    u128 S2 = 0;
+    int64_t hm = 0, h0 = 0;
+    for (int64_t y = 0; y < L; ++y) {
+        if (y > 0) h0 += 2 * (int64_t)planar_bit(Yp, L, 0, y) - 1;
+        int64_t h = h0;
+        for (int64_t x = 0; x < L; ++x) {
+            if (x > 0) h += 2 * (int64_t)planar_bit(Xp, L, x, y) - 1;
+            S1 += h;
+            S2 += (u128)((i128)h * h);
+            int64_t ah = h < 0 ? -h : h;
+            if (ah > hm) hm = ah;
+        }
+    }
+    *s1 = (int64_t)S1;
+    *s2_lo = (uint64_t)S2;
+    *s2_hi = (uint64_t)(S2 >> 64);
+    if (hmax) *hmax = hm;
+}
+
+int oo_invariants_planar(int64_t L, const uint32_t *words, int64_t circ_y0, int64_t circ_y1) {
+    const uint32_t *Xp = words, *Yp = words + L * (L / 32);
+    int bad = 0;
+    for (int64_t y = 0; y < L; ++y) {
+        int64_t n = 0;
+        for (int64_t x = 0; x < L; ++x) n += planar_bit(Xp, L, x, y);
+        if (2 * n != L) bad |= 1;
+    }
+    int64_t *col = (int64_t *)calloc((size_t)L, sizeof(int64_t));
+    if (!col) return -1;
+    for (int64_t y = 0; y < L; ++y)
+        for (int64_t x = 0; x < L; ++x) col[x] += planar_bit(Yp, L, x, y);
+    for (int64_t x = 0; x < L; ++x)
+        if (2 * col[x] != L) bad |= 2;
+    free(col);
+    for (int64_t y = circ_y0; y < circ_y1; ++y)
+        for (int64_t x = 0; x < L; ++x) {
+            const int64_t x1 = wrap(x + 1, L), y1 = wrap(y + 1, L);
+            const int64_t circ = (2 * planar_bit(Xp, L, x1, y) - 1) + (2 * planar_bit(Yp, L, x1, y1) - 1) -
+                                 (2 * planar_bit(Xp, L, x1, y1) - 1) - (2 * planar_bit(Yp, L, x, y1) - 1);
+            if (circ != 0) bad |= 4;
+        }
+    return bad;
+}

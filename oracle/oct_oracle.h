@@ -133,6 +133,13 @@ int oo_invariants(int64_t L, const uint8_t *X, const uint8_t *Y);
 void oo_pack_canonical(int64_t L, const uint8_t *X, const uint8_t *Y, uint32_t *words);
 void oo_unpack_canonical(int64_t L, const uint32_t *words, uint8_t *X, uint8_t *Y);
 
+/* O3 and the invariant checks on a bit-packed planar lattice (X plane then
+ * Y plane, L rows of L/32 words, bit x%32 of word x/32 is site x).  The
+ * circulation check covers rows [circ_y0, circ_y1). */
+void oo_w2_sums_planar(int64_t L, const uint32_t *words, int64_t *s1, uint64_t *s2_lo,
+                       uint64_t *s2_hi, int64_t *hmax);
+int oo_invariants_planar(int64_t L, const uint32_t *words, int64_t circ_y0, int64_t circ_y1);
+
 /* Per-replica key derivation for batched runs: key_r = the first two words of
  * Philox(master key, (r, 0, 0, TAG_REPLICA << 28)). */
 uint64_t oo_replica_seed(uint64_t master_seed, uint32_t r);

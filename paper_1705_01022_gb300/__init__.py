@@ -1,0 +1,107 @@
+"""GB300-native octahedron-model (2+1-d KPZ) simulator under DTrDT decomposition.
+
+The compute path is the CUDA library built from ``csrc/`` (sm_103a) behind the
+C ABI of ``include/oct.h``; ``_lib`` binds it with ctypes.  ``Simulation`` is a
+small convenience wrapper around one handle.  PyTorch is optional and only
+supplies streams and device memory.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib
+from ._lib import OctError, oct_params, oct_w2  # noqa: F401
+
+
+def build(force: bool = False) -> str:
+    from .nvcc_build import build as _build
+    return _build(force=force)
+
+
+class Simulation:
+    """One simulation handle.
+
+    ``stream``: a ``torch.cuda.Stream`` (or raw cudaStream_t address) to run on;
+    ``lattice``: an external device buffer (a torch tensor or raw address) of
+    L*L/4 bytes that the handle uses in place of its own allocation."""
+
+    def __init__(self, L: int, p: float, q: float, seed: int, Bx: int = 0, By: int = 0,
+                 cx: int = 0, cy: int = 0, stream=None, lattice=None, no_init: bool = False):
+        prm = oct_params()
+        prm.L, prm.p, prm.q, prm.seed = L, p, q, seed
+        prm.Bx, prm.By, prm.cx, prm.cy = Bx, By, cx, cy
+        prm.stream = _address(stream, "cuda_stream")
+        prm.lattice = _address(lattice, "data_ptr")
+        prm.no_init = 1 if no_init else 0
+        self._keep = (stream, lattice)
+        self.h = _lib.oct_create_ex(prm)
+        info = _lib.oct_get_info(self.h)
+        self.L, self.Bx, self.By, self.cx, self.cy = L, info.Bx, info.By, info.cx, info.cy
+        self.p, self.q, self.seed = p, q, seed
+
+    @property
+    def t(self) -> int:
+        return _lib.oct_get_info(self.h).t
+
+    def run(self, n: int) -> None:
+        _lib.oct_run_mcs(self.h, n)
+
+    def measure(self) -> oct_w2:
+        return _lib.oct_measure_w2(self.h)
+
+    def lattice(self) -> np.ndarray:
+        w = np.empty(self.L * self.L // 16, dtype=np.uint32)
+        _lib.oct_get_lattice(self.h, w, w.size)
+        return w
+
+    def set_lattice(self, words: np.ndarray, t: int) -> None:
+        w = np.ascontiguousarray(words, dtype=np.uint32)
+        _lib.oct_set_lattice(self.h, w, w.size, t)
+
+    def planes(self) -> np.ndarray:
+        w = np.empty(self.L * self.L // 16, dtype=np.uint32)
+        _lib.oct_get_planes(self.h, w, w.size)
+        return w
+
+    def window(self, wx: int, wy: int, W: int, H: int):
+        X = np.empty((H, W), dtype=np.uint8)
+        Y = np.empty((H, W), dtype=np.uint8)
+        _lib.oct_get_window(self.h, wx, wy, W, H, X, Y)
+        return X, Y
+
+    def sync(self) -> None:
+        _lib.oct_sync(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            _lib.oct_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _address(obj, attr: str):
+    if obj is None:
+        return None
+    if isinstance(obj, int):
+        return obj
+    v = getattr(obj, attr)
+    return v() if callable(v) else v
+
+
+def planes_to_bits(words: np.ndarray, L: int):
+    """Unpack the planar layout to per-site byte arrays X[y, x], Y[y, x]."""
+    w = words.reshape(2, L, L // 32)
+    bits = np.unpackbits(w.view(np.uint8).reshape(2, L, L // 32, 4), axis=-1, bitorder="little")
+    bits = bits.reshape(2, L, L)
+    return bits[0].copy(), bits[1].copy()

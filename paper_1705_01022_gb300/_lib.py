@@ -1,0 +1,182 @@
+"""ctypes binding of the C ABI in ``include/oct.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and raises
+``OctError`` when that entry point returns a non-zero code.  There is no
+fallback: if ``_build/liboct.so`` is missing the import of the library fails
+loudly (build it with ``paper_1705_01022_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liboct.so")
+
+OCT_OK, OCT_EINVAL, OCT_ENOMEM, OCT_ECUDA, OCT_ETIMEDOUT, OCT_EINTERNAL, OCT_EUNSUPPORTED = range(7)
+
+
+class OctError(RuntimeError):
+    def __init__(self, code: int, func: str, msg: str):
+        super().__init__(f"{func} failed with code {code}: {msg}")
+        self.code = code
+
+
+class oct_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("p", ctypes.c_double), ("q", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("Bx", ctypes.c_int32), ("By", ctypes.c_int32),
+                ("cx", ctypes.c_int32), ("cy", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("lattice", ctypes.c_void_p), ("no_init", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class oct_w2(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int64), ("n_sites", ctypes.c_int64), ("s1", ctypes.c_int64),
+                ("s2_lo", ctypes.c_uint64), ("s2_hi", ctypes.c_uint64),
+                ("net_flips", ctypes.c_int64), ("hmax", ctypes.c_int64), ("w2", ctypes.c_double)]
+
+    @property
+    def s2(self) -> int:
+        return (int(self.s2_hi) << 64) | int(self.s2_lo)
+
+
+class oct_info(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("t", ctypes.c_int64), ("Bx", ctypes.c_int32),
+                ("By", ctypes.c_int32), ("cx", ctypes.c_int32), ("cy", ctypes.c_int32),
+                ("p", ctypes.c_double), ("q", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("stream", ctypes.c_void_p), ("lattice", ctypes.c_void_p),
+                ("lattice_bytes", ctypes.c_int64)]
+
+
+# (name, argtypes, restype) of every entry point declared in include/oct.h
+_H = ctypes.c_void_p
+_SIGNATURES = [
+    ("oct_create", [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                    ctypes.POINTER(_H)], ctypes.c_int),
+    ("oct_create_ex", [ctypes.POINTER(oct_params), ctypes.POINTER(_H)], ctypes.c_int),
+    ("oct_run_mcs", [_H, ctypes.c_int64], ctypes.c_int),
+    ("oct_measure_w2", [_H, ctypes.POINTER(oct_w2)], ctypes.c_int),
+    ("oct_get_lattice", [_H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    ("oct_set_lattice", [_H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64], ctypes.c_int),
+    ("oct_get_planes", [_H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    ("oct_set_planes", [_H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64], ctypes.c_int),
+    ("oct_get_window", [_H, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                        ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    ("oct_get_info", [_H, ctypes.POINTER(oct_info)], ctypes.c_int),
+    ("oct_sync", [_H], ctypes.c_int),
+    ("oct_set_timing", [_H, ctypes.c_int], ctypes.c_int),
+    ("oct_get_timing", [_H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                        ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("oct_destroy", [_H], ctypes.c_int),
+    ("oct_strerror", [ctypes.c_int], ctypes.c_char_p),
+    ("oct_last_error", [], ctypes.c_char_p),
+]
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"the CUDA library {p} is missing; build it first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(p)
+        for name, args, res in _SIGNATURES:
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return [name for name, _, _ in _SIGNATURES]
+
+
+def _check(rc: int, func: str):
+    if rc != OCT_OK:
+        msg = load().oct_last_error().decode(errors="replace")
+        raise OctError(rc, func, msg)
+
+
+def _ptr(buf) -> int:
+    """Address of a numpy array or an integer address."""
+    if isinstance(buf, int):
+        return buf
+    return buf.ctypes.data
+
+
+# ---------------------------------------------------------------- wrappers --
+
+def oct_create(L: int, p: float, q: float, seed: int) -> int:
+    h = _H()
+    _check(load().oct_create(L, p, q, seed, ctypes.byref(h)), "oct_create")
+    return h.value
+
+
+def oct_create_ex(prm: oct_params) -> int:
+    h = _H()
+    _check(load().oct_create_ex(ctypes.byref(prm), ctypes.byref(h)), "oct_create_ex")
+    return h.value
+
+
+def oct_run_mcs(h: int, n: int) -> None:
+    _check(load().oct_run_mcs(h, n), "oct_run_mcs")
+
+
+def oct_measure_w2(h: int) -> oct_w2:
+    out = oct_w2()
+    _check(load().oct_measure_w2(h, ctypes.byref(out)), "oct_measure_w2")
+    return out
+
+
+def oct_get_lattice(h: int, buf, words: int) -> None:
+    _check(load().oct_get_lattice(h, _ptr(buf), words), "oct_get_lattice")
+
+
+def oct_set_lattice(h: int, buf, words: int, t: int) -> None:
+    _check(load().oct_set_lattice(h, _ptr(buf), words, t), "oct_set_lattice")
+
+
+def oct_get_planes(h: int, buf, words: int) -> None:
+    _check(load().oct_get_planes(h, _ptr(buf), words), "oct_get_planes")
+
+
+def oct_set_planes(h: int, buf, words: int, t: int) -> None:
+    _check(load().oct_set_planes(h, _ptr(buf), words, t), "oct_set_planes")
+
+
+def oct_get_window(h: int, wx: int, wy: int, W: int, H: int, X, Y) -> None:
+    _check(load().oct_get_window(h, wx, wy, W, H, _ptr(X), _ptr(Y)), "oct_get_window")
+
+
+def oct_get_info(h: int) -> oct_info:
+    out = oct_info()
+    _check(load().oct_get_info(h, ctypes.byref(out)), "oct_get_info")
+    return out
+
+
+def oct_sync(h: int) -> None:
+    _check(load().oct_sync(h), "oct_sync")
+
+
+def oct_set_timing(h: int, enable: bool) -> None:
+    _check(load().oct_set_timing(h, 1 if enable else 0), "oct_set_timing")
+
+
+def oct_get_timing(h: int):
+    ms, n, other = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+    _check(load().oct_get_timing(h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(other)),
+           "oct_get_timing")
+    return ms.value, n.value, other.value
+
+
+def oct_destroy(h: int) -> None:
+    _check(load().oct_destroy(h), "oct_destroy")
+
+
+def oct_strerror(code: int) -> str:
+    return load().oct_strerror(code).decode()

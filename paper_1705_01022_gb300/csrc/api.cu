@@ -1,0 +1,464 @@
+// C ABI of the simulator (include/oct.h): argument checks, memory ownership,
+// stream handling and the per-MCS launch sequence.  All arithmetic of the
+// method runs in the kernels of dtrdt.cu and lattice.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/oct.h"
+#include "oct_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(OCT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define OCT_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// Acceptance threshold P32 = floor(p * 2^32) for 0 < p < 1 (the attempt is
+// accepted iff its uniform 32-bit word is below it).
+uint32_t threshold32(double p) { return static_cast<uint32_t>(std::floor(std::ldexp(p, 32))); }
+
+constexpr int kEventPairs = 256;
+
+}  // namespace
+
+struct oct_sim {
+    int64_t L = 0;
+    double p = 0, q = 0;
+    uint64_t seed = 0;
+    int Bx = 0, By = 0, cx = 4, cy = 4;
+    uint32_t *lat = nullptr;
+    bool own_lat = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    uint32_t *d_t = nullptr;
+    unsigned long long *d_net = nullptr;
+    long long *d_net_sum = nullptr;
+    oct::W2RowSums *d_rows = nullptr;
+    oct::W2Result *d_w2 = nullptr;
+    void *h_small = nullptr;  // pinned: W2Result + net sum
+    uint64_t t = 0;
+    oct::StepArgs args{};
+    bool any_random = false;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // kEventPairs start/stop pairs
+    int ev_used = 0;
+    double step_ms = 0.0;
+    int64_t step_launches = 0;
+};
+
+namespace {
+
+int flush_timing(oct_sim *s) {
+    if (s->ev_used == 0) return OCT_OK;
+    OCT_CUDA(cudaEventSynchronize(s->ev[2 * (s->ev_used - 1) + 1]));
+    for (int i = 0; i < s->ev_used; ++i) {
+        float ms = 0.f;
+        OCT_CUDA(cudaEventElapsedTime(&ms, s->ev[2 * i], s->ev[2 * i + 1]));
+        s->step_ms += ms;
+    }
+    s->ev_used = 0;
+    return OCT_OK;
+}
+
+int validate(const oct_params *prm, int *Bx, int *By, int *cx, int *cy) {
+    const int64_t L = prm->L;
+    if (L < 64 || L > (int64_t{1} << 20) || (L % 64) != 0)
+        return fail(OCT_EINVAL, "L must be a multiple of 64 in [64, 2^20]");
+    if (!(prm->p >= 0.0 && prm->p <= 1.0) || !(prm->q >= 0.0 && prm->q <= 1.0))
+        return fail(OCT_EINVAL, "p and q must lie in [0, 1]");
+    *cx = prm->cx ? prm->cx : 4;
+    *cy = prm->cy ? prm->cy : 4;
+    if (*cx != 4 || *cy != 4) return fail(OCT_EUNSUPPORTED, "this build supports 4x4-site thread cells");
+    if (prm->Bx || prm->By) {
+        *Bx = prm->Bx;
+        *By = prm->By;
+    } else if (L % 128 == 0) {
+        *Bx = 64;
+        *By = 64;
+    } else {
+        *Bx = 32;
+        *By = 16;
+    }
+    if (*Bx < 32 || *By < 16 || *Bx % 32 || *By % (4 * *cy))
+        return fail(OCT_EINVAL, "Bx must be a multiple of 32 and By a multiple of 4*cy");
+    if ((*Bx / 32) * (*By / 16) > 32)
+        return fail(OCT_EINVAL, "a sub-tile may hold at most 32 groups of 32x16 sites");
+    if (L % (2 * *Bx) || L % (2 * *By)) return fail(OCT_EINVAL, "L must be a multiple of 2Bx and 2By");
+    return OCT_OK;
+}
+
+void destroy_members(oct_sim *s) {
+    if (s->own_lat && s->lat) cudaFree(s->lat);
+    if (s->d_t) cudaFree(s->d_t);
+    if (s->d_net) cudaFree(s->d_net);
+    if (s->d_net_sum) cudaFree(s->d_net_sum);
+    if (s->d_rows) cudaFree(s->d_rows);
+    if (s->d_w2) cudaFree(s->d_w2);
+    if (s->h_small) cudaFreeHost(s->h_small);
+    for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+}
+
+int sim_create(const oct_params *prm, oct_sim **out) {
+    int Bx, By, cx, cy;
+    int rc = validate(prm, &Bx, &By, &cx, &cy);
+    if (rc) return rc;
+    oct_sim *s = new (std::nothrow) oct_sim();
+    if (!s) return fail(OCT_ENOMEM, "host allocation of the handle failed");
+    s->L = prm->L;
+    s->p = prm->p;
+    s->q = prm->q;
+    s->seed = prm->seed;
+    s->Bx = Bx;
+    s->By = By;
+    s->cx = cx;
+    s->cy = cy;
+    cudaError_t e = cudaGetDevice(&s->device);
+    const size_t lat_bytes = static_cast<size_t>(s->L) * static_cast<size_t>(s->L) / 4;
+    if (e == cudaSuccess) {
+        if (prm->stream) {
+            s->stream = static_cast<cudaStream_t>(prm->stream);
+        } else {
+            e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+            s->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess) {
+        if (prm->lattice) {
+            if (reinterpret_cast<uintptr_t>(prm->lattice) % 16u != 0u) {
+                if (s->own_stream) cudaStreamDestroy(s->stream);
+                delete s;
+                return fail(OCT_EINVAL, "an external lattice buffer must be 16-byte aligned");
+            }
+            s->lat = static_cast<uint32_t *>(prm->lattice);
+        } else {
+            e = cudaMalloc(&s->lat, lat_bytes);
+            s->own_lat = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_t, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_net, sizeof(unsigned long long) * oct::kNetSlots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_net_sum, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_rows, sizeof(oct::W2RowSums) * s->L);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_w2, sizeof(oct::W2Result));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_small, 256);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_t, 0, sizeof(uint32_t), s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(s->d_net, 0, sizeof(unsigned long long) * oct::kNetSlots, s->stream);
+    if (e == cudaSuccess && !prm->no_init) e = oct::launch_init_flat(s->lat, static_cast<uint32_t>(s->L), s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        const bool oom = (e == cudaErrorMemoryAllocation);
+        destroy_members(s);
+        delete s;
+        return oom ? fail(OCT_ENOMEM, "device allocation failed") : cuda_fail(e, "oct_create");
+    }
+    oct::StepArgs &a = s->args;
+    a.lat = s->lat;
+    a.L = static_cast<uint32_t>(s->L);
+    a.wpr = static_cast<uint32_t>(s->L / 32);
+    a.Bx = static_cast<uint32_t>(Bx);
+    a.By = static_cast<uint32_t>(By);
+    a.GX = static_cast<uint32_t>(Bx / 32);
+    a.GY = static_cast<uint32_t>(By / 16);
+    a.tiles_x = static_cast<uint32_t>(s->L / (2 * Bx));
+    a.tiles_y = static_cast<uint32_t>(s->L / (2 * By));
+    a.k0 = static_cast<uint32_t>(s->seed & 0xFFFFFFFFu);
+    a.k1 = static_cast<uint32_t>(s->seed >> 32);
+    const bool p_rand = s->p > 0.0 && s->p < 1.0, q_rand = s->q > 0.0 && s->q < 1.0;
+    a.thr_p = p_rand ? threshold32(s->p) : 0u;
+    a.thr_q = q_rand ? threshold32(s->q) : 0u;
+    a.p_always = (s->p == 1.0) ? 0xFFFFFFFFu : 0u;
+    a.q_always = (s->q == 1.0) ? 0xFFFFFFFFu : 0u;
+    a.p_random = p_rand ? 0xFFFFFFFFu : 0u;
+    a.q_random = q_rand ? 0xFFFFFFFFu : 0u;
+    a.t_ptr = s->d_t;
+    a.k = 0;
+    a.net = s->d_net;
+    s->any_random = p_rand || q_rand;
+    *out = s;
+    return OCT_OK;
+}
+
+int set_time(oct_sim *s, int64_t t) {
+    if (t < 0 || t > 0xFFFFFFFFll) return fail(OCT_EINVAL, "t must lie in [0, 2^32-1]");
+    const uint32_t tt = static_cast<uint32_t>(t);
+    OCT_CUDA(cudaMemcpyAsync(s->d_t, &tt, sizeof(tt), cudaMemcpyHostToDevice, s->stream));
+    OCT_CUDA(cudaMemsetAsync(s->d_net, 0, sizeof(unsigned long long) * oct::kNetSlots, s->stream));
+    OCT_CUDA(cudaStreamSynchronize(s->stream));
+    s->t = static_cast<uint64_t>(t);
+    return OCT_OK;
+}
+
+size_t lattice_words(const oct_sim *s) { return static_cast<size_t>(s->L) * static_cast<size_t>(s->L) / 16; }
+
+// Canonical rows per conversion chunk: at most 64 MiB of staging.
+uint32_t canon_chunk_rows(const oct_sim *s) {
+    const size_t row_bytes = static_cast<size_t>(s->L / 4) * 4;
+    size_t rows = (size_t{64} << 20) / row_bytes;
+    if (rows < 1) rows = 1;
+    if (rows > static_cast<size_t>(s->L / 4)) rows = static_cast<size_t>(s->L / 4);
+    return static_cast<uint32_t>(rows);
+}
+
+}  // namespace
+
+extern "C" {
+
+int oct_create(int64_t L, double p, double q, uint64_t seed, oct_sim **out) {
+    if (!out) return fail(OCT_EINVAL, "out must not be NULL");
+    oct_params prm;
+    std::memset(&prm, 0, sizeof(prm));
+    prm.L = L;
+    prm.p = p;
+    prm.q = q;
+    prm.seed = seed;
+    return sim_create(&prm, out);
+}
+
+int oct_create_ex(const oct_params *prm, oct_sim **out) {
+    if (!prm || !out) return fail(OCT_EINVAL, "prm and out must not be NULL");
+    return sim_create(prm, out);
+}
+
+int oct_run_mcs(oct_sim *s, int64_t n) {
+    if (!s) return fail(OCT_EINVAL, "NULL handle");
+    if (n < 0) return fail(OCT_EINVAL, "n must be >= 0");
+    if (s->t + static_cast<uint64_t>(n) > 0xFFFFFFFFull) return fail(OCT_EINVAL, "MCS counter would pass 2^32-1");
+    OCT_CUDA(cudaSetDevice(s->device));
+    for (int64_t i = 0; i < n; ++i) {
+        for (uint32_t k = 0; k < 4; ++k) {
+            s->args.k = k;
+            if (s->timing) {
+                if (s->ev_used == kEventPairs) {
+                    int rc = flush_timing(s);
+                    if (rc) return rc;
+                }
+                OCT_CUDA(cudaEventRecord(s->ev[2 * s->ev_used], s->stream));
+            }
+            OCT_CUDA(oct::launch_dtrdt_step(s->args, s->any_random, s->stream));
+            if (s->timing) {
+                OCT_CUDA(cudaEventRecord(s->ev[2 * s->ev_used + 1], s->stream));
+                ++s->ev_used;
+                ++s->step_launches;
+            }
+        }
+        OCT_CUDA(oct::launch_advance_t(s->d_t, s->stream));
+    }
+    s->t += static_cast<uint64_t>(n);
+    return OCT_OK;
+}
+
+int oct_measure_w2(oct_sim *s, oct_w2 *out) {
+    if (!s || !out) return fail(OCT_EINVAL, "NULL argument");
+    OCT_CUDA(cudaSetDevice(s->device));
+    OCT_CUDA(oct::launch_net_sum(s->d_net, s->d_net_sum, s->stream));
+    OCT_CUDA(oct::launch_w2(s->lat, static_cast<uint32_t>(s->L), s->d_rows, s->d_w2, s->stream));
+    auto *res = static_cast<oct::W2Result *>(s->h_small);
+    auto *net = reinterpret_cast<long long *>(static_cast<char *>(s->h_small) + 128);
+    OCT_CUDA(cudaMemcpyAsync(res, s->d_w2, sizeof(oct::W2Result), cudaMemcpyDeviceToHost, s->stream));
+    OCT_CUDA(cudaMemcpyAsync(net, s->d_net_sum, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    OCT_CUDA(cudaStreamSynchronize(s->stream));
+    const __int128 N = static_cast<__int128>(s->L) * s->L;
+    const __int128 S2 = static_cast<__int128>((static_cast<unsigned __int128>(res->s2_hi) << 64) | res->s2_lo);
+    const __int128 num = N * S2 - static_cast<__int128>(res->s1) * res->s1;
+    out->t = static_cast<int64_t>(s->t);
+    out->n_sites = static_cast<int64_t>(N);
+    out->s1 = res->s1;
+    out->s2_lo = res->s2_lo;
+    out->s2_hi = res->s2_hi;
+    out->net_flips = *net;
+    out->hmax = res->hmax;
+    out->w2 = static_cast<double>(num) / (static_cast<double>(N) * static_cast<double>(N));
+    return OCT_OK;
+}
+
+int oct_get_lattice(oct_sim *s, uint32_t *host, size_t words) {
+    if (!s || !host) return fail(OCT_EINVAL, "NULL argument");
+    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal L*L/16");
+    OCT_CUDA(cudaSetDevice(s->device));
+    const uint32_t chunk = canon_chunk_rows(s), ncr = static_cast<uint32_t>(s->L / 4);
+    const size_t row_words = static_cast<size_t>(s->L / 4);
+    uint32_t *tmp = nullptr;
+    OCT_CUDA(cudaMalloc(&tmp, chunk * row_words * 4));
+    int rc = OCT_OK;
+    for (uint32_t r = 0; r < ncr && rc == OCT_OK; r += chunk) {
+        const uint32_t n = (ncr - r < chunk) ? ncr - r : chunk;
+        cudaError_t e = oct::launch_pack_canonical(s->lat, static_cast<uint32_t>(s->L), r, n, tmp, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host + r * row_words, tmp, n * row_words * 4, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "oct_get_lattice");
+    }
+    cudaFree(tmp);
+    return rc;
+}
+
+int oct_set_lattice(oct_sim *s, const uint32_t *host, size_t words, int64_t t) {
+    if (!s || !host) return fail(OCT_EINVAL, "NULL argument");
+    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal L*L/16");
+    if (t < 0 || t > 0xFFFFFFFFll) return fail(OCT_EINVAL, "t must lie in [0, 2^32-1]");
+    OCT_CUDA(cudaSetDevice(s->device));
+    const uint32_t chunk = canon_chunk_rows(s), ncr = static_cast<uint32_t>(s->L / 4);
+    const size_t row_words = static_cast<size_t>(s->L / 4);
+    uint32_t *tmp = nullptr;
+    OCT_CUDA(cudaMalloc(&tmp, chunk * row_words * 4));
+    int rc = OCT_OK;
+    for (uint32_t r = 0; r < ncr && rc == OCT_OK; r += chunk) {
+        const uint32_t n = (ncr - r < chunk) ? ncr - r : chunk;
+        cudaError_t e = cudaMemcpyAsync(tmp, host + r * row_words, n * row_words * 4, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = oct::launch_unpack_canonical(tmp, static_cast<uint32_t>(s->L), r, n, s->lat, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "oct_set_lattice");
+    }
+    cudaFree(tmp);
+    if (rc) return rc;
+    return set_time(s, t);
+}
+
+int oct_get_planes(oct_sim *s, uint32_t *host, size_t words) {
+    if (!s || !host) return fail(OCT_EINVAL, "NULL argument");
+    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal L*L/16");
+    OCT_CUDA(cudaSetDevice(s->device));
+    OCT_CUDA(cudaMemcpyAsync(host, s->lat, words * 4, cudaMemcpyDeviceToHost, s->stream));
+    OCT_CUDA(cudaStreamSynchronize(s->stream));
+    return OCT_OK;
+}
+
+int oct_set_planes(oct_sim *s, const uint32_t *host, size_t words, int64_t t) {
+    if (!s || !host) return fail(OCT_EINVAL, "NULL argument");
+    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal L*L/16");
+    if (t < 0 || t > 0xFFFFFFFFll) return fail(OCT_EINVAL, "t must lie in [0, 2^32-1]");
+    OCT_CUDA(cudaSetDevice(s->device));
+    OCT_CUDA(cudaMemcpyAsync(s->lat, host, words * 4, cudaMemcpyHostToDevice, s->stream));
+    return set_time(s, t);
+}
+
+int oct_get_window(oct_sim *s, int64_t wx, int64_t wy, int64_t W, int64_t H, uint8_t *X, uint8_t *Y) {
+    if (!s || !X || !Y) return fail(OCT_EINVAL, "NULL argument");
+    const int64_t L = s->L;
+    if (W < 1 || H < 1 || W > L || H > L) return fail(OCT_EINVAL, "window must satisfy 1 <= W, H <= L");
+    OCT_CUDA(cudaSetDevice(s->device));
+    const int64_t wpr = L / 32;
+    wx = ((wx % L) + L) % L;
+    wy = ((wy % L) + L) % L;
+    std::vector<uint32_t> rows(static_cast<size_t>(H) * wpr * 2);
+    // copy whole rows of both planes, at most two contiguous row ranges per plane
+    for (int plane = 0; plane < 2; ++plane) {
+        int64_t done = 0;
+        while (done < H) {
+            const int64_t y = (wy + done) % L;
+            const int64_t n = (L - y < H - done) ? L - y : H - done;
+            const uint32_t *src = s->lat + static_cast<size_t>(plane) * L * wpr + static_cast<size_t>(y) * wpr;
+            OCT_CUDA(cudaMemcpyAsync(rows.data() + (static_cast<size_t>(plane) * H + done) * wpr, src,
+                                     static_cast<size_t>(n) * wpr * 4, cudaMemcpyDeviceToHost, s->stream));
+            done += n;
+        }
+    }
+    OCT_CUDA(cudaStreamSynchronize(s->stream));
+    for (int64_t j = 0; j < H; ++j)
+        for (int64_t i = 0; i < W; ++i) {
+            const int64_t x = (wx + i) % L;
+            const uint32_t xw = rows[static_cast<size_t>(j) * wpr + x / 32];
+            const uint32_t yw = rows[(static_cast<size_t>(H) + j) * wpr + x / 32];
+            X[j * W + i] = static_cast<uint8_t>((xw >> (x % 32)) & 1u);
+            Y[j * W + i] = static_cast<uint8_t>((yw >> (x % 32)) & 1u);
+        }
+    return OCT_OK;
+}
+
+int oct_get_info(oct_sim *s, oct_info *out) {
+    if (!s || !out) return fail(OCT_EINVAL, "NULL argument");
+    out->L = s->L;
+    out->t = static_cast<int64_t>(s->t);
+    out->Bx = s->Bx;
+    out->By = s->By;
+    out->cx = s->cx;
+    out->cy = s->cy;
+    out->p = s->p;
+    out->q = s->q;
+    out->seed = s->seed;
+    out->stream = s->stream;
+    out->lattice = s->lat;
+    out->lattice_bytes = s->L * s->L / 4;
+    return OCT_OK;
+}
+
+int oct_sync(oct_sim *s) {
+    if (!s) return fail(OCT_EINVAL, "NULL handle");
+    OCT_CUDA(cudaSetDevice(s->device));
+    OCT_CUDA(cudaStreamSynchronize(s->stream));
+    return OCT_OK;
+}
+
+int oct_set_timing(oct_sim *s, int enable) {
+    if (!s) return fail(OCT_EINVAL, "NULL handle");
+    OCT_CUDA(cudaSetDevice(s->device));
+    if (s->ev.empty()) {
+        s->ev.resize(2 * kEventPairs);
+        for (auto &e : s->ev) OCT_CUDA(cudaEventCreate(&e));
+    }
+    int rc = flush_timing(s);
+    if (rc) return rc;
+    s->timing = enable != 0;
+    s->step_ms = 0.0;
+    s->step_launches = 0;
+    return OCT_OK;
+}
+
+int oct_get_timing(oct_sim *s, double *step_ms, int64_t *step_launches, double *other_ms) {
+    if (!s) return fail(OCT_EINVAL, "NULL handle");
+    int rc = flush_timing(s);
+    if (rc) return rc;
+    if (step_ms) *step_ms = s->step_ms;
+    if (step_launches) *step_launches = s->step_launches;
+    if (other_ms) *other_ms = 0.0;
+    return OCT_OK;
+}
+
+int oct_destroy(oct_sim *s) {
+    if (!s) return OCT_OK;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    destroy_members(s);
+    delete s;
+    return OCT_OK;
+}
+
+const char *oct_strerror(int code) {
+    switch (code) {
+        case OCT_OK: return "success";
+        case OCT_EINVAL: return "invalid argument";
+        case OCT_ENOMEM: return "out of memory";
+        case OCT_ECUDA: return "CUDA runtime error";
+        case OCT_ETIMEDOUT: return "bounded device wait timed out";
+        case OCT_EINTERNAL: return "internal consistency check failed";
+        case OCT_EUNSUPPORTED: return "unsupported configuration";
+        default: return "unknown error code";
+    }
+}
+
+const char *oct_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

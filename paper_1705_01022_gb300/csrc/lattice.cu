@@ -1,0 +1,306 @@
+// Lattice-wide kernels: flat start, exact roughness, layout conversion.
+//
+// Roughness (Eq. (3), mean over the L^2 sites): heights relative to h(0,0)=0,
+//   h(0,y) = sum_{y'=1..y} (2 Y(0,y') - 1),
+//   h(x,y) = h(0,y) + r(x,y),  r(x,y) = sum_{x'=1..x} (2 X(x',y) - 1).
+// Pass 1 (one warp per row): with q(x) = sum_{x'=0..x} (2X(x',y)-1) and
+// s0 = 2X(0,y)-1, r = q - s0, so the row sums of r and r^2 follow from those
+// of q, which a warp computes with 128-bit coalesced loads, a warp scan of
+// per-lane step counts and a 256-entry byte table (sum of the running step
+// inside a byte, its square, its extremes).  Pass 2 (one block): a scan of the
+// column bits gives h(0,y), and S1 = sum_y (L h0 + R1), S2 = sum_y (L h0^2 +
+// 2 h0 R1 + R2) accumulate in 128-bit integers.  Per-row terms are bounded by
+// 4 L^3 < 2^63 for L <= 2^20, so only the cross-row sums need 128 bits.
+#include "oct_internal.h"
+
+namespace oct {
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+__global__ void init_flat_kernel(uint32_t *lat, uint32_t L, uint64_t n_words, uint32_t wpr) {
+    // X = Y = (x+y) & 1: odd x set on even rows, even x set on odd rows.
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n_words;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t row = (i / wpr) % L;
+        lat[i] = (row & 1u) ? 0x55555555u : 0xAAAAAAAAu;
+    }
+}
+
+// Byte table: for byte value v, with running step e_i = sum_{j<=i} (2 b_j - 1):
+//   .x = (sum e_i) + 64 | (net = e_7) + 64 << 8     (net in [-8, 8])
+//   .y = sum e_i^2 | (min e_i + 16) << 16 | (max e_i + 16) << 24
+__device__ __forceinline__ uint2 byte_entry(uint32_t v) {
+    int e = 0, s1 = 0, s2 = 0, mn = 1 << 20, mx = -(1 << 20);
+    for (int i = 0; i < 8; ++i) {
+        e += ((v >> i) & 1u) ? 1 : -1;
+        s1 += e;
+        s2 += e * e;
+        mn = min(mn, e);
+        mx = max(mx, e);
+    }
+    uint2 r;
+    r.x = static_cast<uint32_t>(s1 + 64) | (static_cast<uint32_t>(e + 64) << 8);
+    r.y = static_cast<uint32_t>(s2) | (static_cast<uint32_t>(mn + 16) << 16) |
+          (static_cast<uint32_t>(mx + 16) << 24);
+    return r;
+}
+
+constexpr int kW2Warps = 8;
+
+__global__ void __launch_bounds__(kW2Warps * 32)
+    w2_rows_kernel(const uint32_t *lat, uint32_t L, W2RowSums *rows) {
+    __shared__ uint2 table[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) table[i] = byte_entry(static_cast<uint32_t>(i));
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t wpr = L >> 5;
+    const uint32_t *Yp = lat + static_cast<size_t>(L) * wpr;
+    // 16-byte loads need every row to start on a 16-byte boundary
+    const bool vec_ok = (wpr % 4u) == 0u && (reinterpret_cast<uintptr_t>(lat) % 16u) == 0u;
+    for (uint32_t y = blockIdx.x * kW2Warps + (threadIdx.x >> 5); y < L; y += gridDim.x * kW2Warps) {
+        const uint32_t *row = lat + static_cast<size_t>(y) * wpr;
+        long long base = 0;  // q just before the current chunk
+        long long q1 = 0, q2 = 0;
+        int qmin = 1 << 30, qmax = -(1 << 30);
+        // Chunks of 128 words: lane i takes words 4i..4i+3 (one 16-byte load).
+        for (uint32_t w0 = 0; w0 < wpr; w0 += 128u) {
+            const uint32_t w = w0 + 4u * lane;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            int nbits = 0;
+            if (vec_ok && w + 3u < wpr) {
+                v = *reinterpret_cast<const uint4 *>(row + w);
+                nbits = 128;
+            } else if (w < wpr) {
+                v.x = row[w];
+                nbits = 32;
+                if (w + 1u < wpr) { v.y = row[w + 1]; nbits = 64; }
+                if (w + 2u < wpr) { v.z = row[w + 2]; nbits = 96; }
+                if (w + 3u < wpr) { v.w = row[w + 3]; nbits = 128; }
+            }
+            const int step = 2 * (__popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w)) - nbits;
+            int incl = step;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int n = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += n;
+            }
+            long long b = base + (incl - step);  // q before this lane's first bit
+            const uint32_t words[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (32 * j >= nbits) break;
+#pragma unroll
+                for (int byte = 0; byte < 4; ++byte) {
+                    const uint2 te = table[(words[j] >> (8 * byte)) & 0xFFu];
+                    const long long t1 = static_cast<long long>(te.x & 0xFFu) - 64;
+                    const int net = static_cast<int>((te.x >> 8) & 0xFFu) - 64;
+                    const long long t2 = te.y & 0xFFFFu;
+                    const int mn = static_cast<int>((te.y >> 16) & 0xFFu) - 16;
+                    const int mx = static_cast<int>(te.y >> 24) - 16;
+                    q1 += 8 * b + t1;
+                    q2 += 8 * b * b + 2 * b * t1 + t2;
+                    qmin = min(qmin, static_cast<int>(b) + mn);
+                    qmax = max(qmax, static_cast<int>(b) + mx);
+                    b += net;
+                }
+            }
+            base += __shfl_sync(kFull, incl, 31);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            q1 += __shfl_xor_sync(kFull, q1, o);
+            q2 += __shfl_xor_sync(kFull, q2, o);
+        }
+        qmin = __reduce_min_sync(kFull, qmin);
+        qmax = __reduce_max_sync(kFull, qmax);
+        if (lane == 0) {
+            const long long s0 = (row[0] & 1u) ? 1 : -1;
+            const long long Ll = L;
+            W2RowSums o;
+            o.r1 = q1 - Ll * s0;
+            o.r2 = q2 - 2 * s0 * q1 + Ll * s0 * s0;
+            o.rmin = qmin - static_cast<int>(s0);
+            o.rmax = qmax - static_cast<int>(s0);
+            o.c = static_cast<int>(Yp[static_cast<size_t>(y) * wpr] & 1u);
+            o.pad = 0;
+            rows[y] = o;
+        }
+    }
+}
+
+constexpr int kFinalThreads = 1024;
+
+__global__ void __launch_bounds__(kFinalThreads)
+    w2_final_kernel(const W2RowSums *rows, uint32_t L, W2Result *out) {
+    __shared__ long long part[kFinalThreads];
+    __shared__ unsigned long long s2lo[kFinalThreads / 32], s2hi[kFinalThreads / 32];
+    __shared__ long long s1w[kFinalThreads / 32], hmw[kFinalThreads / 32];
+    const int tid = threadIdx.x;
+    const uint32_t per = (L + kFinalThreads - 1) / kFinalThreads;
+    const uint32_t y_begin = min(L, tid * per), y_end = min(L, (tid + 1) * per);
+    // column steps 2c-1 for rows 1..y (row 0 contributes nothing)
+    long long local = 0;
+    for (uint32_t y = y_begin; y < y_end; ++y)
+        if (y > 0) local += rows[y].c ? 1 : -1;
+    part[tid] = local;
+    __syncthreads();
+    // exclusive scan of the per-thread column sums (Hillis-Steele on shared memory)
+    for (int o = 1; o < kFinalThreads; o <<= 1) {
+        const long long v = (tid >= o) ? part[tid - o] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    long long h0 = part[tid] - local;
+    __int128 S1 = 0, S2 = 0;
+    long long hm = 0;
+    const long long Ll = L;
+    for (uint32_t y = y_begin; y < y_end; ++y) {
+        const W2RowSums r = rows[y];
+        if (y > 0) h0 += r.c ? 1 : -1;
+        S1 += static_cast<__int128>(Ll * h0 + r.r1);
+        S2 += static_cast<__int128>(Ll * h0 * h0) + static_cast<__int128>(2 * h0 * r.r1) +
+              static_cast<__int128>(r.r2);
+        const long long a = h0 + r.rmin, b = h0 + r.rmax;
+        hm = max(hm, max(a < 0 ? -a : a, b < 0 ? -b : b));
+    }
+    // block reduction of S1 (fits 64 bits for L <= 2^20), S2 (128 bits), hmax
+    long long s1 = static_cast<long long>(S1);
+    unsigned long long lo = static_cast<unsigned long long>(S2);
+    unsigned long long hi = static_cast<unsigned long long>(S2 >> 64);
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(kFull, s1, o);
+        const unsigned long long lo2 = __shfl_down_sync(kFull, lo, o);
+        const unsigned long long hi2 = __shfl_down_sync(kFull, hi, o);
+        const unsigned long long nlo = lo + lo2;
+        hi = hi + hi2 + (nlo < lo ? 1ull : 0ull);
+        lo = nlo;
+        hm = max(hm, __shfl_down_sync(kFull, hm, o));
+    }
+    if ((tid & 31) == 0) {
+        s1w[tid >> 5] = s1;
+        s2lo[tid >> 5] = lo;
+        s2hi[tid >> 5] = hi;
+        hmw[tid >> 5] = hm;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long a1 = 0, am = 0;
+        unsigned __int128 a2 = 0;
+        for (int w = 0; w < kFinalThreads / 32; ++w) {
+            a1 += s1w[w];
+            a2 += (static_cast<unsigned __int128>(s2hi[w]) << 64) | s2lo[w];
+            am = max(am, hmw[w]);
+        }
+        out->s1 = a1;
+        out->s2_lo = static_cast<unsigned long long>(a2);
+        out->s2_hi = static_cast<unsigned long long>(a2 >> 64);
+        out->hmax = am;
+    }
+}
+
+// Interleave two 4-bit values: a0 b0 a1 b1 a2 b2 a3 b3 (LSB first).
+__device__ __forceinline__ uint32_t interleave4(uint32_t a, uint32_t b) {
+    uint32_t r = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r |= (((a >> i) & 1u) << (2 * i)) | (((b >> i) & 1u) << (2 * i + 1));
+    return r;
+}
+
+__global__ void pack_canonical_kernel(const uint32_t *lat, uint32_t L, uint32_t cy0, uint32_t ncy,
+                                      uint32_t *out) {
+    const uint32_t wpr = L >> 5, cpr = L >> 2;  // canonical words per canonical row
+    const uint32_t *Yp = lat + static_cast<size_t>(L) * wpr;
+    const uint64_t n = static_cast<uint64_t>(ncy) * cpr;
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t cy = cy0 + static_cast<uint32_t>(i / cpr), cx = static_cast<uint32_t>(i % cpr);
+        const uint32_t w = (4u * cx) >> 5, b = (4u * cx) & 31u;
+        uint32_t v = 0;
+#pragma unroll
+        for (int yy = 0; yy < 4; ++yy) {
+            const size_t ro = static_cast<size_t>(4u * cy + yy) * wpr + w;
+            v |= interleave4((lat[ro] >> b) & 0xFu, (Yp[ro] >> b) & 0xFu) << (8 * yy);
+        }
+        out[i] = v;
+    }
+}
+
+__global__ void unpack_canonical_kernel(const uint32_t *in, uint32_t L, uint32_t cy0, uint32_t ncy,
+                                        uint32_t *lat) {
+    // one thread per planar word pair (X and Y) of lattice rows 4*cy0 .. 4*(cy0+ncy)-1
+    const uint32_t wpr = L >> 5, cpr = L >> 2;
+    uint32_t *Yp = lat + static_cast<size_t>(L) * wpr;
+    const uint64_t n = static_cast<uint64_t>(ncy) * 4u * wpr;
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t lr = static_cast<uint32_t>(i / wpr), w = static_cast<uint32_t>(i % wpr);
+        const uint32_t y = 4u * cy0 + lr, yy = y & 3u;
+        uint32_t xv = 0, yv = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t word = in[static_cast<size_t>(lr >> 2) * cpr + 8u * w + c] >> (8u * yy);
+#pragma unroll
+            for (int xx = 0; xx < 4; ++xx) {
+                xv |= ((word >> (2 * xx)) & 1u) << (4 * c + xx);
+                yv |= ((word >> (2 * xx + 1)) & 1u) << (4 * c + xx);
+            }
+        }
+        lat[static_cast<size_t>(y) * wpr + w] = xv;
+        Yp[static_cast<size_t>(y) * wpr + w] = yv;
+    }
+}
+
+__global__ void net_sum_kernel(const unsigned long long *net, long long *out) {
+    long long s = 0;
+    for (int i = threadIdx.x; i < kNetSlots; i += 32) s += static_cast<long long>(net[i]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
+    if (threadIdx.x == 0) *out = s;
+}
+
+int grid_for(uint64_t n, int threads) {
+    const uint64_t b = (n + threads - 1) / threads;
+    return static_cast<int>(b < 152ull * 32 ? (b ? b : 1) : 152ull * 32);
+}
+
+}  // namespace
+
+cudaError_t launch_init_flat(uint32_t *lat, uint32_t L, cudaStream_t st) {
+    const uint32_t wpr = L >> 5;
+    const uint64_t n = 2ull * L * wpr;
+    init_flat_kernel<<<grid_for(n, 256), 256, 0, st>>>(lat, L, n, wpr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_w2(const uint32_t *lat, uint32_t L, W2RowSums *rows, W2Result *out,
+                      cudaStream_t st) {
+    const uint64_t want = (static_cast<uint64_t>(L) + kW2Warps - 1) / kW2Warps;
+    const int blocks = static_cast<int>(want < 152ull * 16 ? want : 152ull * 16);
+    w2_rows_kernel<<<blocks, kW2Warps * 32, 0, st>>>(lat, L, rows);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    w2_final_kernel<<<1, kFinalThreads, 0, st>>>(rows, L, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_canonical(const uint32_t *lat, uint32_t L, uint32_t cy0, uint32_t ncy,
+                                  uint32_t *out, cudaStream_t st) {
+    pack_canonical_kernel<<<grid_for(static_cast<uint64_t>(ncy) * (L >> 2), 256), 256, 0, st>>>(
+        lat, L, cy0, ncy, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_canonical(const uint32_t *in, uint32_t L, uint32_t cy0, uint32_t ncy,
+                                    uint32_t *lat, cudaStream_t st) {
+    unpack_canonical_kernel<<<grid_for(static_cast<uint64_t>(ncy) * 4u * (L >> 5), 256), 256, 0,
+                              st>>>(in, L, cy0, ncy, lat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net_sum(const unsigned long long *net, long long *out, cudaStream_t st) {
+    net_sum_kernel<<<1, 32, 0, st>>>(net, out);
+    return cudaGetLastError();
+}
+
+}  // namespace oct

@@ -1,0 +1,64 @@
+// Internal declarations shared by the library's translation units (host side).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace oct {
+
+// Arguments of one device-step launch (one set of sub-tiles of one MCS).
+struct StepArgs {
+    uint32_t *lat;             // planar lattice: X plane, then Y plane
+    uint32_t L;                // lateral size
+    uint32_t wpr;              // words per row, L / 32
+    uint32_t Bx, By;           // sub-tile size in sites
+    uint32_t GX, GY;           // groups per sub-tile: Bx / 32 columns, By / 16 rows
+    uint32_t tiles_x, tiles_y; // device tiles per direction: L / (2Bx), L / (2By)
+    uint32_t k0, k1;           // Philox key
+    uint32_t thr_p, thr_q;     // P32(p), P32(q) when the probability is strictly inside (0,1)
+    uint32_t p_always, q_always;   // all-ones if p == 1 (resp. q == 1), else 0
+    uint32_t p_random, q_random;   // all-ones if 0 < p < 1 (resp. q), else 0
+    const uint32_t *t_ptr;     // device-resident MCS counter
+    uint32_t k;                // device step 0..3
+    unsigned long long *net;   // kNetSlots signed flip counters (two's complement)
+};
+
+constexpr int kNetSlots = 1024;
+constexpr int kStepWarpsPerBlock = 4;
+
+// Launches one device step; returns the CUDA launch status.
+cudaError_t launch_dtrdt_step(const StepArgs &a, bool any_random, cudaStream_t st);
+
+// Adds one to the device MCS counter.
+cudaError_t launch_advance_t(uint32_t *t_ptr, cudaStream_t st);
+
+// Flat start h = (x+y) mod 2 on the planar lattice.
+cudaError_t launch_init_flat(uint32_t *lat, uint32_t L, cudaStream_t st);
+
+// Exact roughness sums.
+struct W2RowSums {
+    long long r1;  // sum over x of r(x), r(x) = h(x,y) - h(0,y)
+    long long r2;  // sum over x of r(x)^2
+    int rmin, rmax;
+    int c;         // Y(0, y)
+    int pad;
+};
+struct W2Result {
+    long long s1;
+    unsigned long long s2_lo, s2_hi;
+    long long hmax;
+};
+cudaError_t launch_w2(const uint32_t *lat, uint32_t L, W2RowSums *rows, W2Result *out,
+                      cudaStream_t st);
+
+// Canonical 4x4-per-word layout conversion for canonical word rows
+// [cy0, cy0 + ncy) (each canonical row covers 4 lattice rows).
+cudaError_t launch_pack_canonical(const uint32_t *lat, uint32_t L, uint32_t cy0, uint32_t ncy,
+                                  uint32_t *out, cudaStream_t st);
+cudaError_t launch_unpack_canonical(const uint32_t *in, uint32_t L, uint32_t cy0, uint32_t ncy,
+                                    uint32_t *lat, cudaStream_t st);
+
+// Sum of the kNetSlots flip counters into out[0].
+cudaError_t launch_net_sum(const unsigned long long *net, long long *out, cudaStream_t st);
+
+}  // namespace oct

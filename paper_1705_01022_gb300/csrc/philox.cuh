@@ -1,0 +1,37 @@
+// Philox-4x32-10 counter-based generator for device code.
+//
+// Written from Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3" (SC'11): ten rounds, each multiplying counter words 0 and 2 by
+// the round constants (32x32 -> 64 bit), swapping and xoring the high halves
+// with the other counter words and the key; the key advances by a Weyl
+// increment between rounds.
+#pragma once
+#include <cstdint>
+
+namespace oct {
+
+constexpr uint32_t kTagMcs = 1u;
+constexpr uint32_t kTagSet = 2u;
+constexpr uint32_t kTagSite = 3u;
+constexpr uint32_t kTagAcc = 4u;
+constexpr uint32_t kTagReplica = 6u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                        uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c0;
+        const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c2;
+        const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ k1;
+        c1 = static_cast<uint32_t>(p1);
+        c3 = static_cast<uint32_t>(p0);
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+}  // namespace oct

@@ -1,0 +1,56 @@
+"""The C-ABI library loads and exports every entry point include/oct.h declares,
+and rejects invalid arguments before touching a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1705_01022_gb300 import nvcc_build as b
+    path = b.build()
+    return ctypes.CDLL(path)
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "oct.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(oct_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1705_01022_gb300 import _lib
+    assert sorted(_lib.exported_symbols()) == _declared()
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    from paper_1705_01022_gb300 import _lib
+    _lib.load()
+    with pytest.raises(_lib.OctError) as e:
+        _lib.oct_create(100, 1.0, 0.0, 1)  # not a multiple of 64
+    assert e.value.code == _lib.OCT_EINVAL
+    with pytest.raises(_lib.OctError) as e:
+        _lib.oct_create(256, 1.5, 0.0, 1)
+    assert e.value.code == _lib.OCT_EINVAL
+    prm = _lib.oct_params()
+    prm.L, prm.p, prm.q, prm.seed, prm.cx, prm.cy = 256, 1.0, 0.0, 1, 8, 8
+    with pytest.raises(_lib.OctError) as e:
+        _lib.oct_create_ex(prm)
+    assert e.value.code == _lib.OCT_EUNSUPPORTED
+    prm.cx, prm.cy, prm.Bx, prm.By = 4, 4, 48, 16
+    with pytest.raises(_lib.OctError) as e:
+        _lib.oct_create_ex(prm)
+    assert e.value.code == _lib.OCT_EINVAL
+    assert _lib.oct_destroy(None) is None
+    assert _lib.oct_strerror(0) == "success"

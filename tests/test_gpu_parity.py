@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bar (integer and bit work throughout): the GPU lattice equals the DTrDT
+replay (O2) bit for bit, the net flip count and the roughness sums S1, S2 are
+equal integers, and W^2 is the same double.  Small lattices are compared
+whole; L = 4096 is compared whole for 16 seeds; L = 2^17 is compared on
+sampled device tiles (window replay) and through properties that hold at any
+size (exact S1/S2 of a closed-form lattice, row balance)."""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1705_01022_gb300 as g
+    g.build()
+    return g
+
+
+def _oracle_bits(oracle, sim):
+    return oracle.unpack_canonical(sim.lattice(), sim.L)
+
+
+def _assert_same(oracle, sim, X, Y, net=None, what=""):
+    Xg, Yg = _oracle_bits(oracle, sim)
+    if not (np.array_equal(Xg, X) and np.array_equal(Yg, Y)):
+        bad = np.argwhere((Xg != X) | (Yg != Y))
+        raise AssertionError(f"{what}: {len(bad)} sites differ, first {bad[:5].tolist()}")
+    m = sim.measure()
+    s1, s2, hmax = oracle.w2_sums(X, Y)
+    assert (m.s1, m.s2, m.hmax) == (s1, s2, hmax), what
+    assert m.w2 == oracle.w2_from_sums(sim.L, s1, s2), what
+    if net is not None:
+        assert m.net_flips == net, what
+
+
+@pytest.mark.parametrize("L", [64, 192, 256, 1024])
+def test_flat_start(g, oracle, L):
+    with g.Simulation(L, 1.0, 0.0, 1) as sim:
+        X, Y = oracle.flat(L)
+        assert np.array_equal(sim.lattice(), oracle.pack_canonical(X, Y))
+        assert np.array_equal(sim.planes(), oracle.pack_planar(X, Y))
+        m = sim.measure()
+        N = L * L
+        assert (m.s1, m.s2, m.hmax, m.net_flips, m.w2) == (N // 2, N // 2, 1, 0, 0.25)
+
+
+def test_kpz_256_bit_exact_through_100_mcs(g, oracle):
+    """L = 256, p = 1, q = 0, 64 x 64 sub-tiles, 4 x 4 thread cells, seed 1."""
+    prm = oracle.Params(L=256, p=1.0, q=0.0, seed=1, Bx=64, By=64)
+    X, Y = oracle.flat(256)
+    net = 0
+    t = 0
+    with g.Simulation(256, 1.0, 0.0, 1, Bx=64, By=64) as sim:
+        for tt in (1, 2, 3, 5, 10, 20, 50, 100):
+            net += oracle.dtrdt_run(X, Y, prm, t, tt - t)[0]
+            sim.run(tt - t)
+            t = tt
+            _assert_same(oracle, sim, X, Y, net, f"t={t}")
+        assert sim.t == 100
+
+
+CONFIGS = [
+    dict(L=256, p=0.95, q=0.05, seed=1, Bx=64, By=64, n=6),
+    dict(L=256, p=0.5, q=0.5, seed=2, Bx=32, By=16, n=6),
+    dict(L=512, p=0.3, q=0.9, seed=3, Bx=256, By=64, n=4),
+    dict(L=192, p=0.8, q=0.2, seed=4, Bx=32, By=32, n=5),
+    dict(L=64, p=1.0, q=0.0, seed=5, Bx=32, By=16, n=12),
+    dict(L=1024, p=0.95, q=0.05, seed=6, Bx=512, By=32, n=3),
+    dict(L=2048, p=0.95, q=0.05, seed=7, Bx=1024, By=16, n=2),
+    dict(L=512, p=0.0, q=1.0, seed=8, Bx=128, By=128, n=4),
+    dict(L=256, p=0.0, q=0.0, seed=9, Bx=64, By=64, n=3),
+    dict(L=384, p=1.0, q=1.0, seed=10, Bx=64, By=32, n=4),
+    dict(L=256, p=0.999, q=1e-6, seed=2**40 + 11, Bx=128, By=32, n=5),
+]
+
+
+@pytest.mark.parametrize("c", CONFIGS, ids=lambda c: "L{L}_p{p}_q{q}_B{Bx}x{By}".format(**c))
+def test_bit_exact_configs(g, oracle, c):
+    prm = oracle.Params(L=c["L"], p=c["p"], q=c["q"], seed=c["seed"], Bx=c["Bx"], By=c["By"])
+    X, Y = oracle.flat(c["L"])
+    with g.Simulation(c["L"], c["p"], c["q"], c["seed"], Bx=c["Bx"], By=c["By"]) as sim:
+        net = 0
+        for t in range(c["n"]):
+            net += oracle.dtrdt_run(X, Y, prm, t, 1)[0]
+            sim.run(1)
+            _assert_same(oracle, sim, X, Y, net, f"t={t + 1}")
+
+
+def test_resume_is_bit_identical(g, oracle):
+    L, p, q, seed = 256, 0.95, 0.05, 21
+    with g.Simulation(L, p, q, seed) as a:
+        a.run(7)
+        ref = a.lattice()
+    with g.Simulation(L, p, q, seed) as b:
+        b.run(3)
+        snap = b.lattice()
+    with g.Simulation(L, p, q, seed) as c:
+        c.set_lattice(snap, 3)
+        assert c.t == 3
+        c.run(4)
+        assert np.array_equal(c.lattice(), ref)
+
+
+def test_window_and_planes_agree_with_lattice(g, oracle):
+    L = 512
+    with g.Simulation(L, 0.7, 0.3, 5, Bx=128, By=64) as sim:
+        sim.run(3)
+        X, Y = _oracle_bits(oracle, sim)
+        Xp, Yp = g.planes_to_bits(sim.planes(), L)
+        assert np.array_equal(X, Xp) and np.array_equal(Y, Yp)
+        for wx, wy, W, H in ((0, 0, 64, 32), (500, 490, 40, 50), (13, 7, 512, 3)):
+            Xw, Yw = sim.window(wx, wy, W, H)
+            ys = (wy + np.arange(H)) % L
+            xs = (wx + np.arange(W)) % L
+            assert np.array_equal(Xw, X[np.ix_(ys, xs)])
+            assert np.array_equal(Yw, Y[np.ix_(ys, xs)])
+
+
+def test_invalid_calls(g):
+    from paper_1705_01022_gb300 import _lib
+    with g.Simulation(256, 1.0, 0.0, 1) as sim:
+        with pytest.raises(_lib.OctError):
+            _lib.oct_set_lattice(sim.h, np.zeros(10, np.uint32), 10, 0)
+        with pytest.raises(_lib.OctError):
+            _lib.oct_run_mcs(sim.h, -1)
+        with pytest.raises(_lib.OctError):
+            sim.set_lattice(np.zeros(256 * 256 // 16, np.uint32), -5)
+
+
+def _tent(L):
+    return np.abs(np.arange(L) - L // 2).astype(np.int64)
+
+
+def _tent_lattice_planes(L):
+    """h(x,y) = tent(x) + tent(y), tent(x) = |x - L/2|: a valid periodic slope
+    field with heights of order L; returns planar words."""
+    tent = _tent(L)
+    up = (tent - np.roll(tent, 1)) == 1  # slope to the left/lower neighbour is +1
+    xrow = np.packbits(up.astype(np.uint8), bitorder="little").view(np.uint32)
+    Xplane = np.broadcast_to(xrow, (L, L // 32))
+    Yplane = np.where(up[:, None], np.uint32(0xFFFFFFFF), np.uint32(0)) * np.ones((1, L // 32), np.uint32)
+    return np.concatenate([Xplane.reshape(-1), Yplane.reshape(-1)]).astype(np.uint32)
+
+
+def _tent_sums(L):
+    a = _tent(L) - L // 2  # heights relative to h(0,0)
+    sa, sa2 = int(a.sum()), int((a * a).sum())
+    s1 = 2 * L * sa
+    s2 = 2 * L * sa2 + 2 * sa * sa
+    # extremes of a(x) + a(y) are sums of the extremes of a
+    hmax = max(abs(2 * int(a.min())), abs(2 * int(a.max())))
+    return s1, s2, hmax
+
+
+@pytest.mark.parametrize("L", [256, 4096])
+def test_roughness_of_closed_form_lattice(g, oracle, L):
+    words = _tent_lattice_planes(L)
+    s1, s2, hmax = _tent_sums(L)
+    assert oracle.w2_sums_planar(words, L) == (s1, s2, hmax)
+    with g.Simulation(L, 1.0, 0.0, 1) as sim:
+        g._lib.oct_set_planes(sim.h, words, words.size, 0)
+        m = sim.measure()
+        assert (m.s1, m.s2, m.hmax) == (s1, s2, hmax)
+
+
+def test_c2_sixteen_seeds(g, oracle):
+    """L = 4096 (16.8M sites, 4 MiB), 16 seeds: KPZ for 4 MCS and EW
+    (p = q = 0.5) for 2 MCS, whole lattices, default 64 x 64 sub-tiles."""
+    from oracle import jobs
+    jobs_list = [(4096, 1.0, 0.0, s, 64, 64, 4) for s in range(1, 17)]
+    jobs_list += [(4096, 0.5, 0.5, s, 64, 64, 2) for s in range(1, 17)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, mp.cpu_count())) as pool:
+        results = pool.map(jobs.dtrdt_final_canonical, jobs_list)
+    for (L, p, q, seed, Bx, By, n), (words, net, (s1, s2)) in zip(jobs_list, results):
+        with g.Simulation(L, p, q, seed, Bx=Bx, By=By) as sim:
+            sim.run(n)
+            got = sim.lattice()
+            assert np.array_equal(got, words), (p, q, seed)
+            m = sim.measure()
+            assert (m.net_flips, m.s1, m.s2) == (net, s1, s2), (p, q, seed)
+
+
+def test_c3_full_size_sampled(g, oracle):
+    """L = 2^17 (1.7e10 sites, 4 GiB), p = 0.95, q = 0.05, 256 x 64 sub-tiles.
+    After two MCS, MCS 2 is replayed by the oracle on windows of 5 x 5 device
+    tiles read from the GPU before the MCS; the centre tile must match the GPU
+    after the MCS.  Exact roughness at full size on the closed-form lattice."""
+    L, p, q, seed, Bx, By = 2**17, 0.95, 0.05, 1, 256, 64
+    prm = oracle.Params(L=L, p=p, q=q, seed=seed, Bx=Bx, By=By)
+    tw, th = 2 * Bx, 2 * By
+    with g.Simulation(L, p, q, seed, Bx=Bx, By=By) as sim:
+        sim.run(2)
+        t = 2
+        ox, oy, _ = oracle.mcs_draw(prm, t)
+        rng = np.random.default_rng(0)
+        tiles = [(0, 0), (L // tw - 1, L // th - 1)] + [
+            (int(rng.integers(0, L // tw)), int(rng.integers(0, L // th))) for _ in range(3)]
+        pre = []
+        for tx, ty in tiles:
+            wx, wy = ox + tw * (tx - 2), oy + th * (ty - 2)
+            pre.append((wx, wy, *sim.window(wx, wy, 5 * tw, 5 * th)))
+        sim.run(1)
+        for wx, wy, Xw, Yw in pre:
+            Xw, Yw = Xw.copy(), Yw.copy()
+            oracle.dtrdt_mcs_window(Xw, Yw, prm, t, wx, wy)
+            Xg, Yg = sim.window(wx + 2 * tw, wy + 2 * th, tw, th)
+            c = (slice(2 * th, 3 * th), slice(2 * tw, 3 * tw))
+            assert np.array_equal(Xg, Xw[c]) and np.array_equal(Yg, Yw[c]), (wx, wy)
+        # row balance at full size (X plane): L/2 up-slopes per row
+        planes = sim.planes()
+        table = np.array([bin(i).count("1") for i in range(256)], dtype=np.uint8)
+        xbytes = planes[: L * (L // 32)].view(np.uint8).reshape(L, L // 8)
+        for r0 in range(0, L, 4096):
+            counts = table[xbytes[r0:r0 + 4096]].sum(axis=1, dtype=np.int64)
+            assert np.all(counts == L // 2), r0
+        # exact roughness of the evolved lattice against the oracle
+        m = sim.measure()
+        s1, s2, hmax = oracle.w2_sums_planar(planes, L)
+        assert (m.s1, m.s2, m.hmax) == (s1, s2, hmax)
+        # 128-bit S2: the closed-form tent lattice at full size
+        words = _tent_lattice_planes(L)
+        g._lib.oct_set_planes(sim.h, words, words.size, 0)
+        del words
+        m = sim.measure()
+        assert (m.s1, m.s2, m.hmax) == _tent_sums(L)
+        assert m.s2_hi > 0

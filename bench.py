@@ -1,0 +1,337 @@
+"""Benchmark: octahedron-model DTrDT, site-update attempts per ns on GB300.
+
+One step = one MCS (L^2 update attempts: four device steps of DTr plus
+single-hit DT) over the whole lattice, resident in HBM.  Default workload:
+L = 2^17 (1.7e10 sites, 4 GiB packed), KPZ with p = 0.95, q = 0.05, flat
+start, seed 1 (+ rank), 256 x 64-site sub-tiles, 4 x 4-site thread cells.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica on its own GPU (the
+method has no exchange between replicas); the value is the total attempts of
+all ranks over the slowest rank's time.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "site-update attempts/ns at L=2^17 (plain vs batched) at bit-exact oracle match"
+UNIT = "attempts/ns"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--L", type=int, default=2**17)
+    ap.add_argument("--p", type=float, default=0.95)
+    ap.add_argument("--q", type=float, default=0.05)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--Bx", type=int, default=256)
+    ap.add_argument("--By", type=int, default=64)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(a):
+    return {
+        "workload": (f"octahedron model RS under DTrDT, L={a.L} ({a.L * a.L:.3g} sites, "
+                     f"{a.L * a.L // 4 / 2**30:.3g} GiB packed), p={a.p} q={a.q}, flat start, "
+                     f"{a.Bx}x{a.By}-site sub-tiles, 4x4-site thread cells, seed {a.seed}+rank"),
+        "L": a.L, "p": a.p, "q": a.q, "Bx": a.Bx, "By": a.By, "cx": 4, "cy": 4,
+        "form": "plain",
+        "l2": "lattice larger than L2 (no flush needed)",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.device}",
+                                       f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                v = [x.strip() for x in line.split(",")]
+                if len(v) >= 9 and v[1].replace(".", "").isdigit():
+                    rows.append(v)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(float(r[2]) for r in rows),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def step_traffic(dtrdt_src_hash: str):
+    """DRAM bytes per device-step launch from a committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dtrdt_step_traffic.json")) as f:
+            d = json.load(f)
+    except OSError:
+        return None
+    if d.get("dtrdt_cu_sha256") != dtrdt_src_hash:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def src_hash():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1705_01022_gb300", "csrc", "dtrdt.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def cpu_baseline_window(oracle, a, state_getter, t, target_s):
+    """Times the oracle replaying MCS t on windows of the lattice (read from the
+    running simulation), growing the window until about target_s of CPU work."""
+    prm = oracle.Params(L=a.L, p=a.p, q=a.q, seed=a.seed, Bx=a.Bx, By=a.By)
+    tw, th = 2 * a.Bx, 2 * a.By
+    ox, oy, _ = oracle.mcs_draw(prm, t)
+    nx, ny, spent, attempts = 2, 2, 0.0, 0
+    while True:
+        nx = min(nx, a.L // tw)
+        ny = min(ny, a.L // th)
+        W, H = min(nx * tw + 1, a.L), min(ny * th + 1, a.L)
+        Xw, Yw = state_getter(ox, oy, W, H)
+        t0 = time.perf_counter()
+        oracle.dtrdt_mcs_window(Xw, Yw, prm, t, ox, oy)
+        dt = time.perf_counter() - t0
+        spent, attempts = dt, nx * ny * tw * th
+        if dt >= target_s * 0.5 or (nx * tw >= a.L and ny * th >= a.L):
+            break
+        grow = max(1.5, min(8.0, target_s / max(dt, 1e-3)))
+        if nx <= ny:
+            nx = int(nx * grow) + 1
+        else:
+            ny = int(ny * grow) + 1
+    return {"value": attempts / (spent * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle DTrDT replay of MCS {t} on a {nx}x{ny} device-tile window "
+                       f"({attempts} attempts, {spent:.1f} s) of the GPU lattice state")}
+
+
+def run_reference(a, rank, world):
+    """The oracle as it stands, on the host cores, same metric and workload;
+    each step replays one MCS on a bounded window of the lattice."""
+    if rank != 0:
+        return None
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    prm = oracle.Params(L=a.L, p=a.p, q=a.q, seed=a.seed, Bx=a.Bx, By=a.By)
+    tw, th = 2 * a.Bx, 2 * a.By
+    nx, ny = max(1, min(a.L // tw, 4)), max(1, min(a.L // th, 4))
+    W, H = min(nx * tw + 1, a.L), min(ny * th + 1, a.L)
+    # flat start restricted to the window, which follows the origin of each MCS
+    times, total = [], 0
+    for step in range(a.warmup + a.steps):
+        ox, oy, _ = oracle.mcs_draw(prm, step)
+        xs = (ox + np.arange(W)) % a.L
+        ys = (oy + np.arange(H)) % a.L
+        flat = ((xs[None, :] + ys[:, None]) & 1).astype(np.uint8)
+        Xw, Yw = flat.copy(), flat.copy()
+        t0 = time.perf_counter()
+        oracle.dtrdt_mcs_window(Xw, Yw, prm, step, ox, oy)
+        dt = time.perf_counter() - t0
+        if step >= a.warmup:
+            times.append(dt)
+            total += nx * ny * tw * th
+    secs = sum(times)
+    value = total / (secs * 1e9)
+    sample = (f"oracle DTrDT replay of one MCS per step on a {nx}x{ny} device-tile window "
+              f"({nx * ny * tw * th} attempts per step) of the L={a.L} lattice")
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * secs / max(1, len(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": workload(a),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        out = run_reference(a, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+
+    import torch
+
+    import paper_1705_01022_gb300 as g
+    from paper_1705_01022_gb300 import _lib
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g.build()
+    stream = torch.cuda.current_stream()
+    L = a.L
+    lattice = torch.empty(L * L // 4, dtype=torch.uint8, device="cuda")
+    seed = a.seed + rank
+    sim = g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    sim.run(a.warmup)
+    barrier()
+    stats0 = _lib.oct_get_stats(sim.h)
+    _lib.oct_set_timing(sim.h, True)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        start.record(stream)
+        sim.run(a.steps)
+        end.record(stream)
+        barrier()
+    ms = start.elapsed_time(end)
+    step_ms, launches, _ = _lib.oct_get_timing(sim.h)
+    _lib.oct_set_timing(sim.h, False)
+    stats1 = _lib.oct_get_stats(sim.h)
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    attempts = L * L * a.steps
+    value = world * attempts / (ms_max * 1e6)
+
+    # ---- roofline of the device-step kernel (integer-ALU bound) ----
+    launch_ms = step_ms / max(1, launches)
+    att_per_launch = L * L / 4
+    tcs_per_subtile = (a.Bx // 4) * (a.By // 4)
+    f_draw = (stats1.draws - stats0.draws) / attempts
+    bits = 2.0 + 2.0 / tcs_per_subtile + 32.0 * f_draw
+    ops_per_attempt = 0.5 * bits + 4.0
+    lop3, probe_mhz, sms = _lib.oct_probe_int_rate(0)
+    imad, _, _ = _lib.oct_probe_int_rate(1)
+    pk = peaks()
+    max_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tops = sms * lop3 * max_mhz * 1e6 / 1e12
+    achieved_tops = ops_per_attempt * att_per_launch / (launch_ms * 1e-3) / 1e12
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    hbm_gbs = 2 * (L * L / 16) / (launch_ms * 1e-3) / 1e9  # quarter lattice read + written
+    roofline = {
+        "bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
+        "frac": achieved_tops / peak_tops, "traffic": step_traffic(src_hash()),
+        "kernel": "dtrdt_step_kernel", "launch_ms": launch_ms, "launches": launches,
+        "ops_per_attempt": ops_per_attempt, "draw_fraction": f_draw,
+        "peak_basis": (f"{sms} SMs x {lop3:.1f} LOP3/clk/SM (probe; IMAD {imad:.1f}) x "
+                       f"{max_mhz:.0f} MHz max SM clock"),
+        "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak},
+    }
+
+    # ---- CPU baseline: the oracle on a sample of the same state ----
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        import oracle
+        oracle.build()
+        cpu = cpu_baseline_window(oracle, a, lambda x, y, W, H: sim.window(x, y, W, H), sim.t,
+                                  a.cpu_seconds)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not a.no_e2e and a.e2e_steps > 0:
+        words = L * L // 16
+        host = torch.empty(words * 4, dtype=torch.uint8, pin_memory=True)
+        hp = host.data_ptr()
+        _lib.oct_get_planes(sim.h, hp, words)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            _lib.oct_set_planes(sim.h, hp, words, sim.t)
+            sim.run(1)
+            sim.measure()
+            _lib.oct_get_planes(sim.h, hp, words)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * L * L * a.e2e_steps / (e2e_s * 1e9), "unit": UNIT,
+               "h2d_bytes_per_step": L * L // 4, "d2h_bytes_per_step": L * L // 4 + 56,
+               "steps": a.e2e_steps,
+               "path": "oct_set_planes(pinned host) + oct_run_mcs(1) + oct_measure_w2 + oct_get_planes(pinned host)"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": workload(a), "clocks": clk.summary(), "roofline": roofline,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps,
+            "probe": {"lop3_per_clk_per_sm": lop3, "imad_per_clk_per_sm": imad, "probe_mhz": probe_mhz},
+        }
+        print(json.dumps(out), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

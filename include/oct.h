@@ -154,12 +154,32 @@ int oct_get_info(oct_sim *s, oct_info *out);
 int oct_sync(oct_sim *s);
 
 /* Per-kernel device time (milliseconds) accumulated while timing is on:
- * step_ms covers the device-step kernels (rows a2-a5), other_ms the rest of
- * oct_run_mcs.  Timing brackets every device-step launch with CUDA events on
+ * step_ms covers the device-step kernels (MCS draw, staging, single-hit
+ * steps, flip counting), other_ms the rest of oct_run_mcs.  Timing brackets every device-step launch with CUDA events on
  * the handle's stream.  oct_set_timing(s, 1) enables and resets the
  * counters. */
 int oct_set_timing(oct_sim *s, int enable);
 int oct_get_timing(oct_sim *s, double *step_ms, int64_t *step_launches, double *other_ms);
+
+/* Counters since the flat start or the last oct_set_lattice/oct_set_planes:
+ * net_flips = accepted depositions minus removals, draws = attempts that
+ * landed on an eligible site whose probability lies strictly in (0,1) and so
+ * needed an acceptance draw (counted only when p or q lies strictly inside
+ * (0,1)).  Synchronises. */
+typedef struct {
+    int64_t t;
+    int64_t net_flips;
+    int64_t draws;
+} oct_stats;
+int oct_get_stats(oct_sim *s, oct_stats *out);
+
+/* Measures the integer-pipe throughput of the current device: op 0 runs
+ * chains of three-input logic (LOP3), op 1 of 32-bit multiply-add (IMAD), on
+ * every SM.  Returns operations per SM per clock, the SM clock seen during the
+ * probe (from the SM cycle counter over the kernel's event time) and the SM
+ * count.  Used as the denominator of the hot path's integer roofline; the
+ * paper has no counterpart. */
+int oct_probe_int_rate(int op, double *ops_per_clk_per_sm, double *sm_mhz, int *sm_count);
 
 /* Releases the handle and the memory it owns.  NULL-safe. */
 int oct_destroy(oct_sim *s);

@@ -48,6 +48,10 @@ class oct_info(ctypes.Structure):
                 ("lattice_bytes", ctypes.c_int64)]
 
 
+class oct_stats(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int64), ("net_flips", ctypes.c_int64), ("draws", ctypes.c_int64)]
+
+
 # (name, argtypes, restype) of every entry point declared in include/oct.h
 _H = ctypes.c_void_p
 _SIGNATURES = [
@@ -67,6 +71,10 @@ _SIGNATURES = [
     ("oct_set_timing", [_H, ctypes.c_int], ctypes.c_int),
     ("oct_get_timing", [_H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                         ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("oct_get_stats", [_H, ctypes.POINTER(oct_stats)], ctypes.c_int),
+    ("oct_probe_int_rate", [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)],
+     ctypes.c_int),
     ("oct_destroy", [_H], ctypes.c_int),
     ("oct_strerror", [ctypes.c_int], ctypes.c_char_p),
     ("oct_last_error", [], ctypes.c_char_p),
@@ -172,6 +180,19 @@ def oct_get_timing(h: int):
     _check(load().oct_get_timing(h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(other)),
            "oct_get_timing")
     return ms.value, n.value, other.value
+
+
+def oct_get_stats(h: int) -> oct_stats:
+    out = oct_stats()
+    _check(load().oct_get_stats(h, ctypes.byref(out)), "oct_get_stats")
+    return out
+
+
+def oct_probe_int_rate(op: int):
+    r, mhz, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(load().oct_probe_int_rate(op, ctypes.byref(r), ctypes.byref(mhz), ctypes.byref(n)),
+           "oct_probe_int_rate")
+    return r.value, mhz.value, n.value
 
 
 def oct_destroy(h: int) -> None:

@@ -51,8 +51,8 @@ struct oct_sim {
     bool own_stream = false;
     int device = 0;
     uint32_t *d_t = nullptr;
-    unsigned long long *d_net = nullptr;
-    long long *d_net_sum = nullptr;
+    unsigned long long *d_net = nullptr;    // kNetSlots flip counters, then kNetSlots draw counters
+    long long *d_net_sum = nullptr;         // [net flips, acceptance draws]
     oct::W2RowSums *d_rows = nullptr;
     oct::W2Result *d_w2 = nullptr;
     void *h_small = nullptr;  // pinned: W2Result + net sum
@@ -65,6 +65,7 @@ struct oct_sim {
     int ev_used = 0;
     double step_ms = 0.0;
     int64_t step_launches = 0;
+    int64_t draws = 0;  // acceptance draws counted up to the last measurement
 };
 
 namespace {
@@ -158,14 +159,14 @@ int sim_create(const oct_params *prm, oct_sim **out) {
         }
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->d_t, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_net, sizeof(unsigned long long) * oct::kNetSlots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_net_sum, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_net, sizeof(unsigned long long) * 2 * oct::kNetSlots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_net_sum, 2 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_rows, sizeof(oct::W2RowSums) * s->L);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_w2, sizeof(oct::W2Result));
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_small, 256);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_t, 0, sizeof(uint32_t), s->stream);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(s->d_net, 0, sizeof(unsigned long long) * oct::kNetSlots, s->stream);
+        e = cudaMemsetAsync(s->d_net, 0, sizeof(unsigned long long) * 2 * oct::kNetSlots, s->stream);
     if (e == cudaSuccess && !prm->no_init) e = oct::launch_init_flat(s->lat, static_cast<uint32_t>(s->L), s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
@@ -196,6 +197,7 @@ int sim_create(const oct_params *prm, oct_sim **out) {
     a.t_ptr = s->d_t;
     a.k = 0;
     a.net = s->d_net;
+    a.draws = s->d_net + oct::kNetSlots;
     s->any_random = p_rand || q_rand;
     *out = s;
     return OCT_OK;
@@ -205,7 +207,7 @@ int set_time(oct_sim *s, int64_t t) {
     if (t < 0 || t > 0xFFFFFFFFll) return fail(OCT_EINVAL, "t must lie in [0, 2^32-1]");
     const uint32_t tt = static_cast<uint32_t>(t);
     OCT_CUDA(cudaMemcpyAsync(s->d_t, &tt, sizeof(tt), cudaMemcpyHostToDevice, s->stream));
-    OCT_CUDA(cudaMemsetAsync(s->d_net, 0, sizeof(unsigned long long) * oct::kNetSlots, s->stream));
+    OCT_CUDA(cudaMemsetAsync(s->d_net, 0, sizeof(unsigned long long) * 2 * oct::kNetSlots, s->stream));
     OCT_CUDA(cudaStreamSynchronize(s->stream));
     s->t = static_cast<uint64_t>(t);
     return OCT_OK;
@@ -273,12 +275,12 @@ int oct_run_mcs(oct_sim *s, int64_t n) {
 int oct_measure_w2(oct_sim *s, oct_w2 *out) {
     if (!s || !out) return fail(OCT_EINVAL, "NULL argument");
     OCT_CUDA(cudaSetDevice(s->device));
-    OCT_CUDA(oct::launch_net_sum(s->d_net, s->d_net_sum, s->stream));
+    OCT_CUDA(oct::launch_net_sum(s->d_net, s->d_net + oct::kNetSlots, s->d_net_sum, s->stream));
     OCT_CUDA(oct::launch_w2(s->lat, static_cast<uint32_t>(s->L), s->d_rows, s->d_w2, s->stream));
     auto *res = static_cast<oct::W2Result *>(s->h_small);
     auto *net = reinterpret_cast<long long *>(static_cast<char *>(s->h_small) + 128);
     OCT_CUDA(cudaMemcpyAsync(res, s->d_w2, sizeof(oct::W2Result), cudaMemcpyDeviceToHost, s->stream));
-    OCT_CUDA(cudaMemcpyAsync(net, s->d_net_sum, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    OCT_CUDA(cudaMemcpyAsync(net, s->d_net_sum, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
     OCT_CUDA(cudaStreamSynchronize(s->stream));
     const __int128 N = static_cast<__int128>(s->L) * s->L;
     const __int128 S2 = static_cast<__int128>((static_cast<unsigned __int128>(res->s2_hi) << 64) | res->s2_lo);
@@ -288,7 +290,8 @@ int oct_measure_w2(oct_sim *s, oct_w2 *out) {
     out->s1 = res->s1;
     out->s2_lo = res->s2_lo;
     out->s2_hi = res->s2_hi;
-    out->net_flips = *net;
+    out->net_flips = net[0];
+    s->draws = net[1];
     out->hmax = res->hmax;
     out->w2 = static_cast<double>(num) / (static_cast<double>(N) * static_cast<double>(N));
     return OCT_OK;
@@ -443,6 +446,29 @@ int oct_destroy(oct_sim *s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     destroy_members(s);
     delete s;
+    return OCT_OK;
+}
+
+int oct_get_stats(oct_sim *s, oct_stats *out) {
+    if (!s || !out) return fail(OCT_EINVAL, "NULL argument");
+    OCT_CUDA(cudaSetDevice(s->device));
+    OCT_CUDA(oct::launch_net_sum(s->d_net, s->d_net + oct::kNetSlots, s->d_net_sum, s->stream));
+    auto *net = reinterpret_cast<long long *>(static_cast<char *>(s->h_small) + 128);
+    OCT_CUDA(cudaMemcpyAsync(net, s->d_net_sum, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    OCT_CUDA(cudaStreamSynchronize(s->stream));
+    out->t = static_cast<int64_t>(s->t);
+    out->net_flips = net[0];
+    out->draws = net[1];
+    return OCT_OK;
+}
+
+int oct_probe_int_rate(int op, double *ops_per_clk_per_sm, double *sm_mhz, int *sm_count) {
+    if (!ops_per_clk_per_sm || !sm_mhz || (op != 0 && op != 1)) return fail(OCT_EINVAL, "bad probe arguments");
+    int dev = 0, sms = 0;
+    OCT_CUDA(cudaGetDevice(&dev));
+    OCT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    OCT_CUDA(oct::measure_int_rate(op, sms, ops_per_clk_per_sm, sm_mhz));
+    if (sm_count) *sm_count = sms;
     return OCT_OK;
 }
 

@@ -71,7 +71,7 @@ struct LaneCtx {
 template <int DX, int DY, bool RANDOM>
 __device__ __forceinline__ void collective_step(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E,
                                                 uint32_t &D, const uint4 &site, uint32_t s,
-                                                const LaneCtx &c, int &net) {
+                                                const LaneCtx &c, int &net, int &draws) {
     const uint32_t sw[4] = {site.x, site.y, site.z, site.w};
     const uint32_t par = 2u * (s & 1u);
     uint32_t mn0[4], mx0[4], mn1[4], mx1[4];
@@ -108,6 +108,7 @@ __device__ __forceinline__ void collective_step(uint32_t (&X)[16], uint32_t (&Y)
         }
         // u < P32 decided at the first random bit that differs from P32's bit.
         uint32_t und = pmin | pmax;
+        draws += __popc(und);
         for (uint32_t lb = 0; lb < 8u && und != 0u; ++lb) {
             const uint4 W = philox4x32_10(c.t, c.k | ((s * 8u + lb) << 2), c.T,
                                           (kTagAcc << 28) | c.g, c.k0, c.k1);
@@ -277,17 +278,17 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32)
 
     // Block layer: 16 single-hit collective steps.
     const uint4 setw = philox4x32_10(t, a.k, T, kTagSet << 28, a.k0, a.k1);
-    int net = 0;
+    int net = 0, draws = 0;
     uint4 site = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t s = 0; s < 16u; ++s) {
         if ((s & 1u) == 0u)
             site = philox4x32_10(t, a.k | ((s >> 1) << 2), T, (kTagSite << 28) | c.g, a.k0, a.k1);
         const uint32_t d = (setw.x >> (2u * s)) & 3u;
         switch (d) {
-            case 0: collective_step<0, 0, RANDOM>(X, Y, E, D, site, s, c, net); break;
-            case 1: collective_step<1, 0, RANDOM>(X, Y, E, D, site, s, c, net); break;
-            case 2: collective_step<0, 1, RANDOM>(X, Y, E, D, site, s, c, net); break;
-            default: collective_step<1, 1, RANDOM>(X, Y, E, D, site, s, c, net); break;
+            case 0: collective_step<0, 0, RANDOM>(X, Y, E, D, site, s, c, net, draws); break;
+            case 1: collective_step<1, 0, RANDOM>(X, Y, E, D, site, s, c, net, draws); break;
+            case 2: collective_step<0, 1, RANDOM>(X, Y, E, D, site, s, c, net, draws); break;
+            default: collective_step<1, 1, RANDOM>(X, Y, E, D, site, s, c, net, draws); break;
         }
     }
 
@@ -331,10 +332,14 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32)
         }
     }
 
-    // Net flips: one atomic per warp into a spread of counters.
+    // Net flips (and acceptance draws): one atomic per warp into a spread of counters.
     const int total = __reduce_add_sync(kFull, net);
     if (lane == 0 && total != 0)
         atomicAdd(&a.net[T % kNetSlots], static_cast<unsigned long long>(static_cast<long long>(total)));
+    if (RANDOM) {
+        const unsigned nd = __reduce_add_sync(kFull, static_cast<unsigned>(draws));
+        if (lane == 0 && nd != 0u) atomicAdd(&a.draws[T % kNetSlots], static_cast<unsigned long long>(nd));
+    }
 }
 
 __global__ void advance_t_kernel(uint32_t *t_ptr) { *t_ptr += 1u; }

@@ -252,11 +252,21 @@ __global__ void unpack_canonical_kernel(const uint32_t *in, uint32_t L, uint32_t
     }
 }
 
-__global__ void net_sum_kernel(const unsigned long long *net, long long *out) {
-    long long s = 0;
-    for (int i = threadIdx.x; i < kNetSlots; i += 32) s += static_cast<long long>(net[i]);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
-    if (threadIdx.x == 0) *out = s;
+__global__ void net_sum_kernel(const unsigned long long *net, const unsigned long long *draws,
+                               long long *out) {
+    long long s = 0, d = 0;
+    for (int i = threadIdx.x; i < kNetSlots; i += 32) {
+        s += static_cast<long long>(net[i]);
+        d += static_cast<long long>(draws[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(kFull, s, o);
+        d += __shfl_down_sync(kFull, d, o);
+    }
+    if (threadIdx.x == 0) {
+        out[0] = s;
+        out[1] = d;
+    }
 }
 
 int grid_for(uint64_t n, int threads) {
@@ -298,8 +308,9 @@ cudaError_t launch_unpack_canonical(const uint32_t *in, uint32_t L, uint32_t cy0
     return cudaGetLastError();
 }
 
-cudaError_t launch_net_sum(const unsigned long long *net, long long *out, cudaStream_t st) {
-    net_sum_kernel<<<1, 32, 0, st>>>(net, out);
+cudaError_t launch_net_sum(const unsigned long long *net, const unsigned long long *draws,
+                           long long *out, cudaStream_t st) {
+    net_sum_kernel<<<1, 32, 0, st>>>(net, draws, out);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ struct StepArgs {
     const uint32_t *t_ptr;     // device-resident MCS counter
     uint32_t k;                // device step 0..3
     unsigned long long *net;   // kNetSlots signed flip counters (two's complement)
+    unsigned long long *draws; // kNetSlots counters of attempts that needed an acceptance draw
 };
 
 constexpr int kNetSlots = 1024;
@@ -58,7 +59,12 @@ cudaError_t launch_pack_canonical(const uint32_t *lat, uint32_t L, uint32_t cy0,
 cudaError_t launch_unpack_canonical(const uint32_t *in, uint32_t L, uint32_t cy0, uint32_t ncy,
                                     uint32_t *lat, cudaStream_t st);
 
-// Sum of the kNetSlots flip counters into out[0].
-cudaError_t launch_net_sum(const unsigned long long *net, long long *out, cudaStream_t st);
+// Sum of the kNetSlots flip counters into out[0] and of the draw counters into out[1].
+cudaError_t launch_net_sum(const unsigned long long *net, const unsigned long long *draws,
+                           long long *out, cudaStream_t st);
+
+// Integer-pipe probe (op 0: LOP3, op 1: IMAD): operations per SM per clock
+// and the SM clock during the probe.
+cudaError_t measure_int_rate(int op, int sms, double *ops_per_clk_per_sm, double *mhz);
 
 }  // namespace oct

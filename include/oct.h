@@ -181,6 +181,28 @@ int oct_get_stats(oct_sim *s, oct_stats *out);
  * paper has no counterpart. */
 int oct_probe_int_rate(int op, double *ops_per_clk_per_sm, double *sm_mhz, int *sm_count);
 
+/* Exact roughness of a lattice the caller owns, without allocating memory.
+ * (The paper has no counterpart; this serves callers that cannot allocate.)
+ * For callers such as a plugin or framework that owns all device memory and
+ * hands over only a buffer and a stream, or a latency-critical loop where
+ * cudaMalloc/cudaFree are not allowed because they may synchronise the
+ * device.  It computes what oct_measure_w2 computes (Eq. (3), mean over the
+ * L^2 sites) for the planar lattice at device address `lattice` (L*L/4 bytes,
+ * 16-byte aligned), enqueued on `stream` (a cudaStream_t, NULL for the
+ * default stream), then synchronises that stream and writes out->s1, s2,
+ * hmax, n_sites and w2 (out->t = -1 and out->net_flips = 0: a bare lattice
+ * carries neither).  Scratch lives in one fixed device array of 4 MiB + 256
+ * bytes compiled into the library, which every GPU that loads the library
+ * holds until the process exits; it serves L up to 131072 (2^17) and larger L
+ * is rejected with OCT_EINVAL and a message in oct_last_error().  The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array: calls that may
+ * overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine. */
+int oct_w2_noalloc(const void *lattice, int64_t L, void *stream, oct_w2 *out);
+
 /* Releases the handle and the memory it owns.  NULL-safe. */
 int oct_destroy(oct_sim *s);
 

@@ -75,6 +75,8 @@ _SIGNATURES = [
     ("oct_probe_int_rate", [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)],
      ctypes.c_int),
+    ("oct_w2_noalloc", [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(oct_w2)],
+     ctypes.c_int),
     ("oct_destroy", [_H], ctypes.c_int),
     ("oct_strerror", [ctypes.c_int], ctypes.c_char_p),
     ("oct_last_error", [], ctypes.c_char_p),
@@ -193,6 +195,12 @@ def oct_probe_int_rate(op: int):
     _check(load().oct_probe_int_rate(op, ctypes.byref(r), ctypes.byref(mhz), ctypes.byref(n)),
            "oct_probe_int_rate")
     return r.value, mhz.value, n.value
+
+
+def oct_w2_noalloc(lattice: int, L: int, stream: int | None) -> oct_w2:
+    out = oct_w2()
+    _check(load().oct_w2_noalloc(lattice, L, stream, ctypes.byref(out)), "oct_w2_noalloc")
+    return out
 
 
 def oct_destroy(h: int) -> None:

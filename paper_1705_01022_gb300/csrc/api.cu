@@ -40,6 +40,8 @@ constexpr int kEventPairs = 256;
 
 }  // namespace
 
+void oct::set_last_error(const std::string &msg) { g_last_error = msg; }
+
 struct oct_sim {
     int64_t L = 0;
     double p = 0, q = 0;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 namespace oct {
 
@@ -66,5 +67,8 @@ cudaError_t launch_net_sum(const unsigned long long *net, const unsigned long lo
 // Integer-pipe probe (op 0: LOP3, op 1: IMAD): operations per SM per clock
 // and the SM clock during the probe.
 cudaError_t measure_int_rate(int op, int sms, double *ops_per_clk_per_sm, double *mhz);
+
+// Records the message oct_last_error() returns on this thread.
+void set_last_error(const std::string &msg);
 
 }  // namespace oct

@@ -225,7 +225,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     g.build()
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: torch events and the library's kernels share it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     L = a.L
     lattice = torch.empty(L * L // 4, dtype=torch.uint8, device="cuda")
     seed = a.seed + rank

@@ -62,7 +62,8 @@ typedef struct oct_sim oct_sim; /* opaque; owns its device memory unless told ot
  *          else 32 x 16.
  *   cx, cy block-layer thread cell in sites (default 4 x 4; this build
  *          supports 4 x 4).
- *   stream cudaStream_t to enqueue on, or NULL for a library-owned stream.
+ *   stream cudaStream_t to enqueue on, or NULL for a library-owned stream
+ *          (pass cudaStreamLegacy, 0x1, for the legacy default stream).
  *   lattice  external device buffer of L*L/4 bytes (planar layout), or NULL
  *          for a library-owned one.  An external buffer stays owned by the
  *          caller and must outlive the handle.

@@ -90,13 +90,21 @@ class Simulation:
             pass
 
 
+_CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy: the legacy default stream
+
+
 def _address(obj, attr: str):
     if obj is None:
         return None
     if isinstance(obj, int):
         return obj
     v = getattr(obj, attr)
-    return v() if callable(v) else v
+    v = v() if callable(v) else v
+    if attr == "cuda_stream" and v == 0:
+        # a torch stream object for the legacy default stream has handle 0,
+        # which the C ABI reads as "no stream given"
+        return _CUDA_STREAM_LEGACY
+    return v
 
 
 def planes_to_bits(words: np.ndarray, L: int):

@@ -58,6 +58,17 @@ __device__ __forceinline__ int perm_element(uint32_t idx, uint32_t k) {
     return e;
 }
 
+// Sets the bits of *w selected by mask to those of v, leaving the others, as
+// two reductions (no value returned, so the warp does not wait for them).
+__device__ __forceinline__ void merge_bits(uint32_t *w, uint32_t v, uint32_t mask) {
+    if (mask == 0xFFFFFFFFu) {
+        *w = v;
+        return;
+    }
+    atomicAnd(w, v | ~mask);
+    atomicOr(w, v & mask);
+}
+
 struct LaneCtx {
     uint32_t t, k, T, g;
     uint32_t k0, k1;
@@ -66,65 +77,73 @@ struct LaneCtx {
     int gx, gy, GX, GY;
 };
 
-// One collective step with sub-cell set (DX, DY).  X/Y hold the lane's 16
+// Acceptance of the packed candidates (bit 4j+m = thread cell column j, TC
+// row m): u < P32 is decided at the first random level bit that differs from
+// P32's bit, most significant first; all 32 thread cells of the lane advance
+// together, four levels per Philox block.
+__device__ __forceinline__ uint32_t accept_levels(uint32_t pmin, uint32_t pmax, uint32_t s,
+                                                  const LaneCtx &c) {
+    uint32_t acc = 0, und = pmin | pmax;
+    for (uint32_t lb = 0; lb < 8u && und != 0u; ++lb) {
+        const uint4 W = philox4x32_10(c.t, c.k | ((s * 8u + lb) << 2), c.T, (kTagAcc << 28) | c.g,
+                                      c.k0, c.k1);
+        const uint32_t lw[4] = {W.x, W.y, W.z, W.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t bit = 31u - (4u * lb + i);
+            const uint32_t tb = (((c.thr_p >> bit) & 1u) ? pmin : 0u) | (((c.thr_q >> bit) & 1u) ? pmax : 0u);
+            acc |= und & tb & ~lw[i];
+            und &= ~(tb ^ lw[i]);
+        }
+    }
+    return acc;
+}
+
+// One collective step with sub-cell set (dx, DY).  X/Y hold the lane's 16
 // rows, E bit r the X bit just right of row r, D the Y row just below row 15.
-template <int DX, int DY, bool RANDOM>
+// An attempt at s is eligible iff X(s) != X(s+x), Y(s) != Y(s+y) and
+// X(s) == Y(s): then X(s) = 0 is the minimum of Eq. (1), X(s) = 1 the maximum.
+template <int DY, bool RANDOM>
 __device__ __forceinline__ void collective_step(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E,
                                                 uint32_t &D, const uint4 &site, uint32_t s,
-                                                const LaneCtx &c, int &net, int &draws) {
+                                                uint32_t dx, const LaneCtx &c, int &net, int &draws) {
     const uint32_t sw[4] = {site.x, site.y, site.z, site.w};
     const uint32_t par = 2u * (s & 1u);
-    uint32_t mn0[4], mx0[4], mn1[4], mx1[4];
+    const uint32_t sh2 = 2u * dx;
+    uint32_t cnd0[4], cnd1[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         // Site draw: bit 4j = x offset, bit 4j+1 = y offset of TC column j.
         const uint32_t u = sw[m] >> par;
-        const uint32_t col = (((u & kNib) << 1) | (~u & kNib)) << (2 * DX);
+        const uint32_t col = (((u & kNib) << 1) | (~u & kNib)) << sh2;
         const uint32_t yoff = ((u >> 1) & kNib) * 0xFu;
-        const uint32_t sel0 = col & ~yoff;  // attempts in row r0
-        const uint32_t sel1 = col & yoff;   // attempts in row r1
         const int r0 = 4 * m + 2 * DY, r1 = r0 + 1;
         const uint32_t xa = X[r0], xb = X[r1];
-        const uint32_t xra = DX ? __funnelshift_r(xa, E >> r0, 1) : (xa >> 1);
-        const uint32_t xrb = DX ? __funnelshift_r(xb, E >> r1, 1) : (xb >> 1);
+        const uint32_t xra = __funnelshift_r(xa, E >> r0, 1);
+        const uint32_t xrb = __funnelshift_r(xb, E >> r1, 1);
         const uint32_t ya = Y[r0], yb = Y[r1];
         const uint32_t yc = (r1 + 1 < 16) ? Y[(r1 + 1) & 15] : D;
-        mn0[m] = sel0 & ~xa & xra & ~ya & yb;
-        mx0[m] = sel0 & xa & ~xra & ya & ~yb;
-        mn1[m] = sel1 & ~xb & xrb & ~yb & yc;
-        mx1[m] = sel1 & xb & ~xrb & yb & ~yc;
+        cnd0[m] = col & ~yoff & (xa ^ xra) & (ya ^ yb) & ~(xa ^ ya);
+        cnd1[m] = col & yoff & (xb ^ xrb) & (yb ^ yc) & ~(xb ^ yb);
     }
 
     uint32_t acc = 0;
     if (RANDOM) {
-        // Pack the candidates that need a draw to bit 4j+m (TC column j, row m).
         uint32_t pmin = 0, pmax = 0;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            const uint32_t cmn = (mn0[m] | mn1[m]) & c.p_random;
-            const uint32_t cmx = (mx0[m] | mx1[m]) & c.q_random;
-            pmin |= (((cmn >> (2 * DX)) | (cmn >> (2 * DX + 1))) & kNib) << m;
-            pmax |= (((cmx >> (2 * DX)) | (cmx >> (2 * DX + 1))) & kNib) << m;
+            const int r0 = 4 * m + 2 * DY, r1 = r0 + 1;
+            const uint32_t mn = (cnd0[m] & ~X[r0]) | (cnd1[m] & ~X[r1]);
+            const uint32_t mx = (cnd0[m] & X[r0]) | (cnd1[m] & X[r1]);
+            const uint32_t cmn = mn & c.p_random, cmx = mx & c.q_random;
+            pmin |= (((cmn >> sh2) | (cmn >> (sh2 + 1u))) & kNib) << m;
+            pmax |= (((cmx >> sh2) | (cmx >> (sh2 + 1u))) & kNib) << m;
         }
-        // u < P32 decided at the first random bit that differs from P32's bit.
-        uint32_t und = pmin | pmax;
-        draws += __popc(und);
-        for (uint32_t lb = 0; lb < 8u && und != 0u; ++lb) {
-            const uint4 W = philox4x32_10(c.t, c.k | ((s * 8u + lb) << 2), c.T,
-                                          (kTagAcc << 28) | c.g, c.k0, c.k1);
-            const uint32_t lw[4] = {W.x, W.y, W.z, W.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint32_t bit = 31u - (4u * lb + i);
-                const uint32_t tb = (((c.thr_p >> bit) & 1u) ? pmin : 0u) |
-                                    (((c.thr_q >> bit) & 1u) ? pmax : 0u);
-                acc |= und & tb & ~lw[i];
-                und &= ~(tb ^ lw[i]);
-            }
-        }
+        draws += __popc(pmin | pmax);
+        acc = accept_levels(pmin, pmax, s, c);
     }
 
-    uint32_t dE = 0, dB0 = 0, dY0 = 0, dD = 0;
+    uint32_t f0s[4], f1s[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const int r0 = 4 * m + 2 * DY, r1 = r0 + 1;
@@ -134,31 +153,32 @@ __device__ __forceinline__ void collective_step(uint32_t (&X)[16], uint32_t (&Y)
             amin |= spread & c.p_random;
             amax |= spread & c.q_random;
         }
-        const uint32_t fmin0 = mn0[m] & amin, fmax0 = mx0[m] & amax;
-        const uint32_t fmin1 = mn1[m] & amin, fmax1 = mx1[m] & amax;
-        const uint32_t f0 = fmin0 | fmax0, f1 = fmin1 | fmax1;
-        net += __popc(fmin0 | fmin1) - __popc(fmax0 | fmax1);
-        X[r0] ^= f0 ^ (f0 << 1);
-        X[r1] ^= f1 ^ (f1 << 1);
-        if (DX) {
-            dE |= ((f0 >> 31) << r0) | ((f1 >> 31) << r1);
-        } else {
-            dB0 |= ((f0 & 1u) << r0) | ((f1 & 1u) << r1);
-        }
+        const uint32_t xa = X[r0], xb = X[r1];
+        // accepted minima are where the candidate has X(s) = 0
+        const uint32_t f0 = cnd0[m] & ((~xa & amin) | (xa & amax));
+        const uint32_t f1 = cnd1[m] & ((~xb & amin) | (xb & amax));
+        net += __popc((f0 & ~xa) | (f1 & ~xb)) - __popc((f0 & xa) | (f1 & xb));
+        X[r0] = xa ^ f0 ^ (f0 << 1);
+        X[r1] = xb ^ f1 ^ (f1 << 1);
         Y[r0] ^= f0;
         Y[r1] ^= f0 ^ f1;
-        if (r1 + 1 < 16) {
+        if (r1 + 1 < 16)
             Y[(r1 + 1) & 15] ^= f1;
-        } else {
+        else
             D ^= f1;
-            dD = f1;
-        }
-        if (!DY && m == 0) dY0 = f0;
+        f0s[m] = f0;
+        f1s[m] = f1;
     }
 
     // Keep the neighbour copies consistent.
-    if (DX) {
-        // This lane flipped bits of its right neighbour's column 0.
+    if (dx) {
+        // Flips at bit 31 changed column 0 of the right neighbour (this lane's E).
+        uint32_t dE = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int r0 = 4 * m + 2 * DY;
+            dE |= ((f0s[m] >> 31) << r0) | ((f1s[m] >> 31) << (r0 + 1));
+        }
         E ^= dE;
         const uint32_t v = __shfl_up_sync(kFull, dE, 1);
         if (c.gx > 0) {
@@ -170,23 +190,29 @@ __device__ __forceinline__ void collective_step(uint32_t (&X)[16], uint32_t (&Y)
             }
         }
     } else {
-        // This lane may have flipped its own column 0, which its left neighbour mirrors.
+        // Flips at bit 0 changed this lane's column 0, mirrored by the left neighbour's E.
+        uint32_t dB0 = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int r0 = 4 * m + 2 * DY;
+            dB0 |= ((f0s[m] & 1u) << r0) | ((f1s[m] & 1u) << (r0 + 1));
+        }
         const uint32_t v = __shfl_down_sync(kFull, dB0, 1);
         if (c.gx < c.GX - 1) E ^= v;
     }
     if (DY) {
-        // This lane flipped bits of the row below it (owned by the lane below).
-        const uint32_t v = __shfl_up_sync(kFull, dD, c.GX);
+        // Row 16 (D) belongs to the lane below.
+        const uint32_t v = __shfl_up_sync(kFull, f1s[3], c.GX);
         if (c.gy > 0) Y[0] ^= v;
     } else {
-        // This lane may have flipped its own row 0, which the lane above mirrors.
-        const uint32_t v = __shfl_down_sync(kFull, dY0, c.GX);
+        // Row 0 is mirrored by the lane above in its D.
+        const uint32_t v = __shfl_down_sync(kFull, f0s[0], c.GX);
         if (c.gy < c.GY - 1) D ^= v;
     }
 }
 
 template <bool RANDOM>
-__global__ void __launch_bounds__(kStepWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSM)
     dtrdt_step_kernel(const StepArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t T = blockIdx.x * kStepWarpsPerBlock + (threadIdx.x >> 5);
@@ -284,20 +310,20 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32)
         if ((s & 1u) == 0u)
             site = philox4x32_10(t, a.k | ((s >> 1) << 2), T, (kTagSite << 28) | c.g, a.k0, a.k1);
         const uint32_t d = (setw.x >> (2u * s)) & 3u;
-        switch (d) {
-            case 0: collective_step<0, 0, RANDOM>(X, Y, E, D, site, s, c, net, draws); break;
-            case 1: collective_step<1, 0, RANDOM>(X, Y, E, D, site, s, c, net, draws); break;
-            case 2: collective_step<0, 1, RANDOM>(X, Y, E, D, site, s, c, net, draws); break;
-            default: collective_step<1, 1, RANDOM>(X, Y, E, D, site, s, c, net, draws); break;
-        }
+        if (d & 2u)
+            collective_step<1, RANDOM>(X, Y, E, D, site, s, d & 1u, c, net, draws);
+        else
+            collective_step<0, RANDOM>(X, Y, E, D, site, s, d & 1u, c, net, draws);
     }
 
     // Write back.  Global word wA of a row receives the high bits of the left
-    // lane and the low bits of this lane; the leftmost lane keeps the bits
-    // left of x0 and the rightmost lane writes word wB: its own high bits, the
-    // halo column bit (X) and the untouched bits beyond.  No two warps of one
-    // device step write the same word, because active sub-tiles are at least
-    // 32 sites apart.
+    // lane and the low bits of this lane; the leftmost lane shares word wA
+    // with the bits left of x0, the rightmost lane also owns the low bits of
+    // word wB (its own high bits, and for X the halo-column bit).  Words shared
+    // with sites outside the sub-tile are merged with an AND/OR reduction pair
+    // (no read, so no load latency), full words are stored.  No other warp of
+    // this device step touches these words: active sub-tiles are at least 32
+    // sites apart.
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const uint32_t leftX = __shfl_up_sync(kFull, X[r], 1);
@@ -306,18 +332,17 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32)
             uint32_t yr = ybase + r;
             if (yr >= L) yr -= L;
             const size_t ro = static_cast<size_t>(yr) * wpr;
-            uint32_t loX = leftX, loY = leftY;
-            if (c.gx == 0) {
-                loX = sh ? (Xp[ro + wA] << (32u - sh)) : 0u;
-                loY = sh ? (Yp[ro + wA] << (32u - sh)) : 0u;
+            if (c.gx == 0 && sh) {
+                merge_bits(&Xp[ro + wA], X[r] << sh, ~0u << sh);
+                merge_bits(&Yp[ro + wA], Y[r] << sh, ~0u << sh);
+            } else {
+                Xp[ro + wA] = __funnelshift_l(leftX, X[r], sh);
+                Yp[ro + wA] = __funnelshift_l(leftY, Y[r], sh);
             }
-            Xp[ro + wA] = __funnelshift_l(loX, X[r], sh);
-            Yp[ro + wA] = __funnelshift_l(loY, Y[r], sh);
             if (c.gx == c.GX - 1) {
-                const uint32_t keepX = ~((2u << sh) - 1u);
                 const uint32_t hiX = sh ? (X[r] >> (32u - sh)) : 0u;
-                Xp[ro + wB] = (Xp[ro + wB] & keepX) | (((E >> r) & 1u) << sh) | hiX;
-                if (sh) Yp[ro + wB] = (Yp[ro + wB] & ~((1u << sh) - 1u)) | (Y[r] >> (32u - sh));
+                merge_bits(&Xp[ro + wB], hiX | (((E >> r) & 1u) << sh), (2u << sh) - 1u);
+                if (sh) merge_bits(&Yp[ro + wB], Y[r] >> (32u - sh), (1u << sh) - 1u);
             }
         }
     }
@@ -325,10 +350,11 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32)
         const uint32_t leftD = __shfl_up_sync(kFull, D, 1);
         if (active && c.gy == c.GY - 1) {
             const size_t ro = static_cast<size_t>(yh) * wpr;
-            const uint32_t lo = (c.gx == 0) ? (sh ? (Yp[ro + wA] << (32u - sh)) : 0u) : leftD;
-            Yp[ro + wA] = __funnelshift_l(lo, D, sh);
-            if (c.gx == c.GX - 1 && sh)
-                Yp[ro + wB] = (Yp[ro + wB] & ~((1u << sh) - 1u)) | (D >> (32u - sh));
+            if (c.gx == 0 && sh)
+                merge_bits(&Yp[ro + wA], D << sh, ~0u << sh);
+            else
+                Yp[ro + wA] = __funnelshift_l(leftD, D, sh);
+            if (c.gx == c.GX - 1 && sh) merge_bits(&Yp[ro + wB], D >> (32u - sh), (1u << sh) - 1u);
         }
     }
 

@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-replicas", type=int, default=2048)
+    ap.add_argument("--batch-steps", type=int, default=100)
+    ap.add_argument("--loop-steps", type=int, default=3)
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -160,6 +164,75 @@ def cpu_baseline_window(oracle, a, state_getter, t, target_s):
     return {"value": attempts / (spent * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": (f"oracle DTrDT replay of MCS {t} on a {nx}x{ny} device-tile window "
                        f"({attempts} attempts, {spent:.1f} s) of the GPU lattice state")}
+
+
+BATCH_PQ = [(1.0, 0.0), (0.95, 0.05), (0.5, 0.5)]
+
+
+def batch_replicas(n, _lib, master=1):
+    """Replica r: L drawn uniformly from {64, 128, ..., 4096} (numpy PCG64 seeded
+    by the master seed), (p, q) cycled over the three pairs by index, key
+    derived from the master seed with oct_replica_seed."""
+    import numpy as np
+    Ls = (np.random.default_rng(master).integers(1, 65, size=n) * 64).tolist()
+    return [(int(Ls[r]), *BATCH_PQ[r % 3], _lib.oct_replica_seed(master, r)) for r in range(n)]
+
+
+def batched_leg(a, g, _lib, torch, stream, peak_tops):
+    """Many independent replicas of uneven L in one launch per device step and
+    mode (graph replay), against a loop of plain per-replica launches."""
+    reps = batch_replicas(a.batch_replicas, _lib)
+    sites = sum(r[0] * r[0] for r in reps)
+    out = {"workload": (f"{len(reps)} replicas, L uniform in {{64,...,4096}} (multiples of 64), "
+                        f"(p,q) cycled over {BATCH_PQ}, flat start, keys from master seed 1; "
+                        "64x64 sub-tiles if L%128==0 else 32x32; 4x4 thread cells"),
+           "replicas": len(reps), "sites": sites}
+    with g.Batch(reps, stream=stream) as b:
+        b.run(5)
+        b.sync()
+        t0 = b.stats()[3]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        b.run(a.batch_steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+        ms = start.elapsed_time(end)
+        draws = b.stats()[3] - t0
+        out.update({"value": sites * a.batch_steps / (ms * 1e6), "unit": UNIT,
+                    "mcs": a.batch_steps, "ms_per_mcs": ms / a.batch_steps})
+        # per-launch kernel time, launch by launch
+        _lib.oct_batch_set_timing(b.h, True)
+        b.run(5)
+        kms, klaunch = _lib.oct_batch_get_timing(b.h)
+        _lib.oct_batch_set_timing(b.h, False)
+        f_draw = draws / (sites * a.batch_steps)
+        ops = 0.5 * (2.0 + 32.0 * f_draw) + 4.0
+        achieved = ops * sites / 4 / (kms / klaunch * 1e-3) / 1e12
+        out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                           "frac": achieved / peak_tops, "kernel": "batch_step_kernel",
+                           "device_step_ms": kms / klaunch, "draw_fraction": f_draw}
+    # the same replicas, one plain handle each, launched one after another
+    sims = [g.Simulation(L, p, q, seed, Bx=(64 if L % 128 == 0 else 32), By=(64 if L % 128 == 0 else 32),
+                         stream=stream) for (L, p, q, seed) in reps]
+    for s_ in sims:
+        s_.run(1)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(a.loop_steps):
+        for s_ in sims:
+            s_.run(1)
+    end.record(stream)
+    torch.cuda.synchronize()
+    ms_loop = start.elapsed_time(end)
+    for s_ in sims:
+        s_.close()
+    out["plain_loop"] = {"value": sites * a.loop_steps / (ms_loop * 1e6), "unit": UNIT,
+                         "mcs": a.loop_steps,
+                         "how": "one plain handle per replica, oct_run_mcs(1) per replica in turn, one stream"}
+    out["batched_over_plain_loop"] = out["value"] / out["plain_loop"]["value"]
+    out["gpu_launches_per_mcs"] = 9
+    return out
 
 
 def run_reference(a, rank, world):
@@ -287,6 +360,11 @@ def main():
         "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak},
     }
 
+    # ---- batched replicas (uneven L) against a loop of plain launches ----
+    batched = None
+    if rank == 0 and not a.no_batch and a.batch_replicas > 0:
+        batched = batched_leg(a, g, _lib, torch, stream, peak_tops)
+
     # ---- CPU baseline: the oracle on a sample of the same state ----
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
@@ -326,7 +404,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload(a), "clocks": clk.summary(), "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "batched": batched,
             "probe": {"lop3_per_clk_per_sm": lop3, "imad_per_clk_per_sm": imad, "probe_mhz": probe_mhz},
         }
         print(json.dumps(out), flush=True)

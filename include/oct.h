@@ -204,6 +204,59 @@ int oct_probe_int_rate(int op, double *ops_per_clk_per_sm, double *sm_mhz, int *
  * allocating routine. */
 int oct_w2_noalloc(const void *lattice, int64_t L, void *stream, oct_w2 *out);
 
+/* ---------------------------------------------------------------------------
+ * Batched replicas.  Many independent realizations (each its own L, p, q and
+ * key; every one the same DTrDT dynamics as a single handle, bit for bit) are
+ * advanced together: every device step of every replica runs in one launch
+ * per acceptance mode, and one MCS is captured once in a CUDA graph and
+ * replayed.  Replica lattices are device-resident, planar layout.
+ * ------------------------------------------------------------------------- */
+typedef struct oct_batch oct_batch;
+
+/* One replica: L a multiple of 64 in [64, 16384]; p, q in [0, 1]; seed its
+ * Philox key; Bx, By its sub-tile (0, 0: 64 x 64 if L % 128 == 0, else
+ * 32 x 32).  The sub-tile must hold a power-of-two number of 32 x 16-site
+ * groups in each direction, at most 32 in all. */
+typedef struct {
+    int64_t L;
+    double p, q;
+    uint64_t seed;
+    int32_t Bx, By;
+    int32_t reserved[6];
+} oct_replica;
+
+/* Key of replica r under a master seed: the first two words of
+ * Philox-4x32-10 at counter (r, 0, 0, 6 << 28) under the master key. */
+int oct_replica_seed(uint64_t master_seed, uint32_t r, uint64_t *seed);
+
+/* Creates n replicas in the flat start on `stream` (NULL: library-owned). */
+int oct_batch_create(int64_t n, const oct_replica *reps, void *stream, oct_batch **out);
+
+/* Enqueues n MCS for every replica (asynchronous). */
+int oct_batch_run(oct_batch *b, int64_t n);
+
+/* Exact roughness of every replica (out holds n = replica count entries;
+ * net_flips per replica since the flat start).  Synchronises. */
+int oct_batch_measure_w2(oct_batch *b, oct_w2 *out, int64_t n);
+
+/* Planar lattice of replica r (words = L*L/16).  Synchronises. */
+int oct_batch_get_planes(oct_batch *b, int64_t r, uint32_t *host, size_t words);
+
+/* Time, replica count, total sites over replicas, acceptance draws so far. */
+int oct_batch_get_stats(oct_batch *b, int64_t *t, int64_t *n_replicas, int64_t *total_sites,
+                        int64_t *draws);
+
+/* Waits for the batch's stream. */
+int oct_batch_sync(oct_batch *b);
+
+/* With timing on, oct_batch_run launches device step by device step (no
+ * graph) and brackets each with CUDA events; step_ms sums them. */
+int oct_batch_set_timing(oct_batch *b, int enable);
+int oct_batch_get_timing(oct_batch *b, double *step_ms, int64_t *step_launches);
+
+/* Releases the batch.  NULL-safe. */
+int oct_batch_destroy(oct_batch *b);
+
 /* Releases the handle and the memory it owns.  NULL-safe. */
 int oct_destroy(oct_sim *s);
 

@@ -93,6 +93,62 @@ class Simulation:
 _CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy: the legacy default stream
 
 
+class Batch:
+    """Many independent replicas advanced together (see oct_batch_* in include/oct.h).
+
+    ``replicas``: iterable of (L, p, q, seed) or (L, p, q, seed, Bx, By)."""
+
+    def __init__(self, replicas, stream=None):
+        reps = []
+        for r in replicas:
+            o = _lib.oct_replica()
+            o.L, o.p, o.q, o.seed = int(r[0]), float(r[1]), float(r[2]), int(r[3])
+            if len(r) > 4:
+                o.Bx, o.By = int(r[4]), int(r[5])
+            reps.append(o)
+        self.replicas = reps
+        self._keep = stream
+        self.h = _lib.oct_batch_create(reps, _address(stream, "cuda_stream"))
+
+    def __len__(self):
+        return len(self.replicas)
+
+    def run(self, n: int) -> None:
+        _lib.oct_batch_run(self.h, n)
+
+    def measure(self):
+        return _lib.oct_batch_measure_w2(self.h, len(self.replicas))
+
+    def planes(self, r: int) -> np.ndarray:
+        L = self.replicas[r].L
+        w = np.empty(L * L // 16, dtype=np.uint32)
+        _lib.oct_batch_get_planes(self.h, r, w, w.size)
+        return w
+
+    def stats(self):
+        return _lib.oct_batch_get_stats(self.h)
+
+    def sync(self) -> None:
+        _lib.oct_batch_sync(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            _lib.oct_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def _address(obj, attr: str):
     if obj is None:
         return None

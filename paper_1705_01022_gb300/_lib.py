@@ -3,7 +3,7 @@
 Every function here has the name of the C entry point it calls and raises
 ``OctError`` when that entry point returns a non-zero code.  There is no
 fallback: if ``_build/liboct.so`` is missing the import of the library fails
-loudly (build it with ``paper_1705_01022_gb300.build.build()``).
+loudly (build it with ``paper_1705_01022_gb300.build()``).
 """
 from __future__ import annotations
 
@@ -52,6 +52,12 @@ class oct_stats(ctypes.Structure):
     _fields_ = [("t", ctypes.c_int64), ("net_flips", ctypes.c_int64), ("draws", ctypes.c_int64)]
 
 
+class oct_replica(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("p", ctypes.c_double), ("q", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("Bx", ctypes.c_int32), ("By", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
 # (name, argtypes, restype) of every entry point declared in include/oct.h
 _H = ctypes.c_void_p
 _SIGNATURES = [
@@ -77,6 +83,21 @@ _SIGNATURES = [
      ctypes.c_int),
     ("oct_w2_noalloc", [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(oct_w2)],
      ctypes.c_int),
+    ("oct_replica_seed", [ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)],
+     ctypes.c_int),
+    ("oct_batch_create", [ctypes.c_int64, ctypes.POINTER(oct_replica), ctypes.c_void_p,
+                          ctypes.POINTER(_H)], ctypes.c_int),
+    ("oct_batch_run", [_H, ctypes.c_int64], ctypes.c_int),
+    ("oct_batch_measure_w2", [_H, ctypes.POINTER(oct_w2), ctypes.c_int64], ctypes.c_int),
+    ("oct_batch_get_planes", [_H, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    ("oct_batch_get_stats", [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+     ctypes.c_int),
+    ("oct_batch_sync", [_H], ctypes.c_int),
+    ("oct_batch_set_timing", [_H, ctypes.c_int], ctypes.c_int),
+    ("oct_batch_get_timing", [_H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+     ctypes.c_int),
+    ("oct_batch_destroy", [_H], ctypes.c_int),
     ("oct_destroy", [_H], ctypes.c_int),
     ("oct_strerror", [ctypes.c_int], ctypes.c_char_p),
     ("oct_last_error", [], ctypes.c_char_p),
@@ -201,6 +222,58 @@ def oct_w2_noalloc(lattice: int, L: int, stream: int | None) -> oct_w2:
     out = oct_w2()
     _check(load().oct_w2_noalloc(lattice, L, stream, ctypes.byref(out)), "oct_w2_noalloc")
     return out
+
+
+def oct_replica_seed(master: int, r: int) -> int:
+    out = ctypes.c_uint64()
+    _check(load().oct_replica_seed(master, r, ctypes.byref(out)), "oct_replica_seed")
+    return out.value
+
+
+def oct_batch_create(reps, stream=None) -> int:
+    arr = (oct_replica * len(reps))(*reps)
+    h = _H()
+    _check(load().oct_batch_create(len(reps), arr, stream, ctypes.byref(h)), "oct_batch_create")
+    return h.value
+
+
+def oct_batch_run(h: int, n: int) -> None:
+    _check(load().oct_batch_run(h, n), "oct_batch_run")
+
+
+def oct_batch_measure_w2(h: int, n: int):
+    out = (oct_w2 * n)()
+    _check(load().oct_batch_measure_w2(h, out, n), "oct_batch_measure_w2")
+    return list(out)
+
+
+def oct_batch_get_planes(h: int, r: int, buf, words: int) -> None:
+    _check(load().oct_batch_get_planes(h, r, _ptr(buf), words), "oct_batch_get_planes")
+
+
+def oct_batch_get_stats(h: int):
+    t, n, sites, draws = (ctypes.c_int64() for _ in range(4))
+    _check(load().oct_batch_get_stats(h, ctypes.byref(t), ctypes.byref(n), ctypes.byref(sites),
+                                      ctypes.byref(draws)), "oct_batch_get_stats")
+    return t.value, n.value, sites.value, draws.value
+
+
+def oct_batch_sync(h: int) -> None:
+    _check(load().oct_batch_sync(h), "oct_batch_sync")
+
+
+def oct_batch_set_timing(h: int, enable: bool) -> None:
+    _check(load().oct_batch_set_timing(h, 1 if enable else 0), "oct_batch_set_timing")
+
+
+def oct_batch_get_timing(h: int):
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(load().oct_batch_get_timing(h, ctypes.byref(ms), ctypes.byref(n)), "oct_batch_get_timing")
+    return ms.value, n.value
+
+
+def oct_batch_destroy(h: int) -> None:
+    _check(load().oct_batch_destroy(h), "oct_batch_destroy")
 
 
 def oct_destroy(h: int) -> None:

@@ -1,0 +1,518 @@
+// Batched DTrDT: many independent realizations (replicas) of different L, p, q
+// advanced together, one device step of every replica per launch.
+//
+// Each replica is its own DTrDT simulation (its own key, origin, set order
+// and lattice; Sec. 3 / 3.1); batching changes only how the work reaches the
+// GPU.  The device-step work of all replicas is a list of (replica, device
+// tile) items.  A replica whose sub-tile holds G lane groups of 32 x 16
+// sites (G = 8 for 64 x 64 sub-tiles, 2 for 32 x 32) takes G consecutive
+// lanes, so one warp carries 32/G sub-tiles, possibly of different replicas.
+// Items are bucketed by G and by acceptance mode and packed into warp
+// descriptors; persistent warps claim descriptors from an atomic queue.
+// Because the sub-tiles of one warp draw their own block-level sets, the
+// collective step takes the set per lane (collective_step_rt).  All replicas
+// advance in lock step: one MCS is four device steps, each one launch per
+// acceptance mode, captured once in a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/oct.h"
+#include "oct_internal.h"
+#include "subtile.cuh"
+
+namespace oct {
+namespace {
+
+struct ReplicaDev {
+    uint32_t *lat;
+    unsigned long long *counters;  // [net flips, acceptance draws]
+    uint32_t L, wpr, Bx, By, GX, GY, tiles_x, tiles_y;
+    uint32_t k0, k1, thr_p, thr_q;
+    uint32_t p_always, q_always, p_random, q_random;
+};
+
+struct BatchItem {
+    uint32_t rep;
+    uint32_t T;
+};
+
+struct WarpDesc {
+    uint32_t first;  // first item
+    uint32_t n;      // items in this warp (32 / G at most)
+    uint32_t G;      // lanes per item
+    uint32_t GX;     // lane columns per item
+};
+
+constexpr int kBatchWarps = 4;
+constexpr int kBatchBlocksPerSM = 4;
+
+template <bool RANDOM>
+__global__ void __launch_bounds__(kBatchWarps * 32, kBatchBlocksPerSM)
+    batch_step_kernel(const ReplicaDev *reps, const BatchItem *items, const WarpDesc *descs,
+                      uint32_t n_descs, const uint32_t *t_ptr, uint32_t k, uint32_t *queue) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t t = *t_ptr;
+    for (;;) {
+        uint32_t di = 0;
+        if (lane == 0) di = atomicAdd(queue, 1u);
+        di = __shfl_sync(kFull, di, 0);
+        if (di >= n_descs) break;  // the whole warp leaves together
+        const WarpDesc wd = descs[di];
+        const int G = static_cast<int>(wd.G);
+        const int slot = lane / G, sub = lane % G;
+        const bool active = slot < static_cast<int>(wd.n);
+        const BatchItem it = items[wd.first + (active ? slot : 0)];
+        const ReplicaDev R = reps[it.rep];
+        const uint32_t L = R.L;
+        const uint4 M = philox4x32_10(t, 0u, 0u, kTagMcs << 28, R.k0, R.k1);
+        const uint32_t ox = static_cast<uint32_t>((static_cast<uint64_t>(M.x) * L) >> 32);
+        const uint32_t oy = static_cast<uint32_t>((static_cast<uint64_t>(M.y) * L) >> 32);
+        const uint32_t pidx = static_cast<uint32_t>((static_cast<uint64_t>(M.z) * 24u) >> 32);
+        const int sigma = perm_element(pidx, k);
+        const uint32_t tx = it.T % R.tiles_x, ty = it.T / R.tiles_x;
+        const uint32_t x0 = static_cast<uint32_t>(
+            (static_cast<uint64_t>(ox) + 2ull * R.Bx * tx + static_cast<uint64_t>(R.Bx) * (sigma & 1)) % L);
+        const uint32_t y0 = static_cast<uint32_t>(
+            (static_cast<uint64_t>(oy) + 2ull * R.By * ty + static_cast<uint64_t>(R.By) * (sigma >> 1)) % L);
+        LaneCtx c;
+        c.GX = static_cast<int>(wd.GX);
+        c.GY = G / c.GX;
+        c.gx = sub % c.GX;
+        c.gy = sub / c.GX;
+        c.t = t;
+        c.k = k;
+        c.T = it.T;
+        c.g = static_cast<uint32_t>(sub);
+        c.k0 = R.k0;
+        c.k1 = R.k1;
+        c.thr_p = R.thr_p;
+        c.thr_q = R.thr_q;
+        c.p_always = R.p_always;
+        c.q_always = R.q_always;
+        c.p_random = R.p_random;
+        c.q_random = R.q_random;
+        int net = 0, draws = 0;
+        run_subtile<RANDOM, true>(R.lat, L, R.wpr, R.Bx, R.By, x0, y0, active, c, net, draws);
+        // sum over the G lanes of the item (items start at multiples of G)
+        for (int o = G >> 1; o > 0; o >>= 1) {
+            net += __shfl_xor_sync(kFull, net, o);
+            draws += __shfl_xor_sync(kFull, draws, o);
+        }
+        if (active && sub == 0) {
+            if (net != 0)
+                atomicAdd(&R.counters[0], static_cast<unsigned long long>(static_cast<long long>(net)));
+            if (RANDOM && draws != 0) atomicAdd(&R.counters[1], static_cast<unsigned long long>(draws));
+        }
+    }
+}
+
+__global__ void batch_advance_kernel(uint32_t *t_ptr) { *t_ptr += 1u; }
+
+}  // namespace
+}  // namespace oct
+
+namespace {
+
+int bfail(int code, const std::string &msg) {
+    oct::set_last_error(msg);
+    return code;
+}
+
+#define BATCH_CUDA(call)                                                                  \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return bfail(OCT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+uint32_t thr32(double p) { return static_cast<uint32_t>(std::floor(std::ldexp(p, 32))); }
+
+}  // namespace
+
+struct oct_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<oct_replica> reps;
+    std::vector<size_t> lat_offset;  // in words
+    uint32_t *lat = nullptr;         // all lattices, 256-byte aligned each
+    unsigned long long *counters = nullptr;
+    oct::ReplicaDev *d_reps = nullptr;
+    oct::BatchItem *d_items = nullptr;
+    oct::WarpDesc *d_descs = nullptr;
+    uint32_t n_desc[2] = {0, 0};  // [mode without draws, mode with draws]
+    uint32_t desc_first[2] = {0, 0};
+    uint32_t *d_queue = nullptr;  // 8 counters: (device step, mode)
+    uint32_t *d_t = nullptr;
+    oct::W2RowSums *d_rows = nullptr;
+    oct::W2Result *d_w2 = nullptr;
+    void *h_small = nullptr;
+    int64_t max_L = 0;
+    uint64_t t = 0;
+    int grid = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    double step_ms = 0.0;
+    int64_t step_launches = 0;
+};
+
+namespace {
+
+void batch_free(oct_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->lat);
+    cudaFree(b->counters);
+    cudaFree(b->d_reps);
+    cudaFree(b->d_items);
+    cudaFree(b->d_descs);
+    cudaFree(b->d_queue);
+    cudaFree(b->d_t);
+    cudaFree(b->d_rows);
+    cudaFree(b->d_w2);
+    if (b->h_small) cudaFreeHost(b->h_small);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+// Enqueues device step k of the current MCS for every replica.
+cudaError_t enqueue_step(oct_batch *b, uint32_t k, cudaStream_t st) {
+    for (int mode = 0; mode < 2; ++mode) {
+        if (b->n_desc[mode] == 0) continue;
+        uint32_t *q = b->d_queue + 2 * k + mode;
+        cudaError_t e = cudaMemsetAsync(q, 0, sizeof(uint32_t), st);
+        if (e != cudaSuccess) return e;
+        const oct::WarpDesc *descs = b->d_descs + b->desc_first[mode];
+        const int blocks = std::min<int>(b->grid, static_cast<int>((b->n_desc[mode] + oct::kBatchWarps - 1) / oct::kBatchWarps));
+        if (mode)
+            oct::batch_step_kernel<true><<<blocks, oct::kBatchWarps * 32, 0, st>>>(
+                b->d_reps, b->d_items, descs, b->n_desc[mode], b->d_t, k, q);
+        else
+            oct::batch_step_kernel<false><<<blocks, oct::kBatchWarps * 32, 0, st>>>(
+                b->d_reps, b->d_items, descs, b->n_desc[mode], b->d_t, k, q);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_mcs(oct_batch *b, cudaStream_t st) {
+    for (uint32_t k = 0; k < 4; ++k) {
+        cudaError_t e = enqueue_step(b, k, st);
+        if (e != cudaSuccess) return e;
+    }
+    oct::batch_advance_kernel<<<1, 1, 0, st>>>(b->d_t);
+    return cudaGetLastError();
+}
+
+int flush_batch_timing(oct_batch *b) {
+    if (b->ev_used == 0) return OCT_OK;
+    BATCH_CUDA(cudaEventSynchronize(b->ev[2 * (b->ev_used - 1) + 1]));
+    for (int i = 0; i < b->ev_used; ++i) {
+        float ms = 0.f;
+        BATCH_CUDA(cudaEventElapsedTime(&ms, b->ev[2 * i], b->ev[2 * i + 1]));
+        b->step_ms += ms;
+    }
+    b->ev_used = 0;
+    return OCT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int oct_replica_seed(uint64_t master_seed, uint32_t r, uint64_t *seed) {
+    if (!seed) return bfail(OCT_EINVAL, "seed must not be NULL");
+    const uint4 w = oct::philox4x32_10(r, 0u, 0u, oct::kTagReplica << 28,
+                                       static_cast<uint32_t>(master_seed & 0xFFFFFFFFu),
+                                       static_cast<uint32_t>(master_seed >> 32));
+    *seed = static_cast<uint64_t>(w.x) | (static_cast<uint64_t>(w.y) << 32);
+    return OCT_OK;
+}
+
+int oct_batch_create(int64_t n, const oct_replica *reps, void *stream, oct_batch **out) {
+    if (n < 1 || !reps || !out) return bfail(OCT_EINVAL, "need n >= 1 replicas and non-NULL arrays");
+    oct_batch *b = new (std::nothrow) oct_batch();
+    if (!b) return bfail(OCT_ENOMEM, "host allocation failed");
+    b->reps.assign(reps, reps + n);
+    // validate and fill defaults
+    size_t total_words = 0;
+    for (int64_t r = 0; r < n; ++r) {
+        oct_replica &R = b->reps[r];
+        if (R.L < 64 || R.L > 16384 || R.L % 64) {
+            delete b;
+            return bfail(OCT_EINVAL, "replica L must be a multiple of 64 in [64, 16384]");
+        }
+        if (!(R.p >= 0.0 && R.p <= 1.0 && R.q >= 0.0 && R.q <= 1.0)) {
+            delete b;
+            return bfail(OCT_EINVAL, "replica p and q must lie in [0, 1]");
+        }
+        if (R.Bx == 0 && R.By == 0) {
+            R.Bx = (R.L % 128 == 0) ? 64 : 32;
+            R.By = R.Bx;
+        }
+        const int GX = R.Bx / 32, GY = R.By / 16, G = GX * GY;
+        if (R.Bx < 32 || R.By < 16 || R.Bx % 32 || R.By % 16 || R.L % (2 * R.Bx) || R.L % (2 * R.By) ||
+            (GX & (GX - 1)) || (GY & (GY - 1)) || G > 32) {
+            delete b;
+            return bfail(OCT_EINVAL, "replica sub-tile must be a power-of-two number (at most 32) of "
+                                     "32x16-site groups in each direction and divide L/2");
+        }
+        b->lat_offset.push_back(total_words);
+        const size_t words = static_cast<size_t>(R.L) * R.L / 16;
+        total_words += (words + 63) & ~size_t{63};
+        b->max_L = std::max<int64_t>(b->max_L, R.L);
+    }
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) {
+        if (stream) {
+            b->stream = static_cast<cudaStream_t>(stream);
+        } else {
+            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+            b->own_stream = (e == cudaSuccess);
+        }
+    }
+    // replica table and work list
+    std::vector<oct::ReplicaDev> rd(n);
+    std::vector<oct::BatchItem> items;
+    std::vector<oct::WarpDesc> descs;
+    if (e == cudaSuccess) e = cudaMalloc(&b->lat, total_words * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&b->counters, sizeof(unsigned long long) * 2 * n);
+    if (e == cudaSuccess) {
+        // buckets: (mode, lane columns GX, lane rows GY) -> items
+        std::vector<oct::BatchItem> bucket[2][6][6];
+        for (int64_t r = 0; r < n; ++r) {
+            const oct_replica &R = b->reps[r];
+            oct::ReplicaDev &D = rd[r];
+            D.lat = b->lat + b->lat_offset[r];
+            D.counters = b->counters + 2 * r;
+            D.L = static_cast<uint32_t>(R.L);
+            D.wpr = static_cast<uint32_t>(R.L / 32);
+            D.Bx = static_cast<uint32_t>(R.Bx);
+            D.By = static_cast<uint32_t>(R.By);
+            D.GX = static_cast<uint32_t>(R.Bx / 32);
+            D.GY = static_cast<uint32_t>(R.By / 16);
+            D.tiles_x = static_cast<uint32_t>(R.L / (2 * R.Bx));
+            D.tiles_y = static_cast<uint32_t>(R.L / (2 * R.By));
+            D.k0 = static_cast<uint32_t>(R.seed & 0xFFFFFFFFu);
+            D.k1 = static_cast<uint32_t>(R.seed >> 32);
+            const bool pr = R.p > 0.0 && R.p < 1.0, qr = R.q > 0.0 && R.q < 1.0;
+            D.thr_p = pr ? thr32(R.p) : 0u;
+            D.thr_q = qr ? thr32(R.q) : 0u;
+            D.p_always = (R.p == 1.0) ? 0xFFFFFFFFu : 0u;
+            D.q_always = (R.q == 1.0) ? 0xFFFFFFFFu : 0u;
+            D.p_random = pr ? 0xFFFFFFFFu : 0u;
+            D.q_random = qr ? 0xFFFFFFFFu : 0u;
+            const int mode = (pr || qr) ? 1 : 0;
+            int gxi = 0, gyi = 0;
+            while ((1u << gxi) < D.GX) ++gxi;
+            while ((1u << gyi) < D.GY) ++gyi;
+            for (uint32_t T = 0; T < D.tiles_x * D.tiles_y; ++T)
+                bucket[mode][gxi][gyi].push_back({static_cast<uint32_t>(r), T});
+        }
+        for (int mode = 0; mode < 2; ++mode) {
+            b->desc_first[mode] = static_cast<uint32_t>(descs.size());
+            for (int gxi = 5; gxi >= 0; --gxi)
+                for (int gyi = 5; gyi >= 0; --gyi) {
+                    const uint32_t GX = 1u << gxi, G = GX << gyi;
+                    if (G > 32u) continue;
+                    const uint32_t per = 32u / G;
+                    auto &bk = bucket[mode][gxi][gyi];
+                    for (size_t i = 0; i < bk.size(); i += per) {
+                        oct::WarpDesc d;
+                        d.first = static_cast<uint32_t>(items.size());
+                        d.n = static_cast<uint32_t>(std::min<size_t>(per, bk.size() - i));
+                        d.G = G;
+                        d.GX = GX;
+                        for (uint32_t j = 0; j < d.n; ++j) items.push_back(bk[i + j]);
+                        descs.push_back(d);
+                    }
+                }
+            b->n_desc[mode] = static_cast<uint32_t>(descs.size()) - b->desc_first[mode];
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_reps, sizeof(oct::ReplicaDev) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(oct::BatchItem) * std::max<size_t>(1, items.size()));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_descs, sizeof(oct::WarpDesc) * std::max<size_t>(1, descs.size()));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(uint32_t) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_t, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_rows, sizeof(oct::W2RowSums) * b->max_L);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_w2, sizeof(oct::W2Result));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_small, 256);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_reps, rd.data(), sizeof(oct::ReplicaDev) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(oct::BatchItem) * items.size(),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !descs.empty())
+        e = cudaMemcpyAsync(b->d_descs, descs.data(), sizeof(oct::WarpDesc) * descs.size(),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_t, 0, sizeof(uint32_t), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long) * 2 * n, b->stream);
+    for (int64_t r = 0; r < n && e == cudaSuccess; ++r)
+        e = oct::launch_init_flat(b->lat + b->lat_offset[r], static_cast<uint32_t>(b->reps[r].L), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) {
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        b->grid = sms * oct::kBatchBlocksPerSM;
+    }
+    if (e != cudaSuccess) {
+        const bool oom = (e == cudaErrorMemoryAllocation);
+        batch_free(b);
+        delete b;
+        return oom ? bfail(OCT_ENOMEM, "device allocation failed")
+                   : bfail(OCT_ECUDA, std::string("oct_batch_create: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return OCT_OK;
+}
+
+int oct_batch_run(oct_batch *b, int64_t n) {
+    if (!b) return bfail(OCT_EINVAL, "NULL batch");
+    if (n < 0 || b->t + static_cast<uint64_t>(n) > 0xFFFFFFFFull) return bfail(OCT_EINVAL, "bad MCS count");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    if (b->timing) {
+        // launch by launch, each device step bracketed by events
+        for (int64_t i = 0; i < n; ++i) {
+            for (uint32_t k = 0; k < 4; ++k) {
+                if (b->ev_used == 256) {
+                    int rc = flush_batch_timing(b);
+                    if (rc) return rc;
+                }
+                BATCH_CUDA(cudaEventRecord(b->ev[2 * b->ev_used], b->stream));
+                BATCH_CUDA(enqueue_step(b, k, b->stream));
+                BATCH_CUDA(cudaEventRecord(b->ev[2 * b->ev_used + 1], b->stream));
+                ++b->ev_used;
+                ++b->step_launches;
+            }
+            oct::batch_advance_kernel<<<1, 1, 0, b->stream>>>(b->d_t);
+            BATCH_CUDA(cudaGetLastError());
+        }
+    } else {
+        if (!b->exec) {
+            // one MCS captured once on a private stream, replayed on the batch's stream
+            cudaStream_t cap = nullptr;
+            BATCH_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e2 = enqueue_mcs(b, cap);
+                e = cudaStreamEndCapture(cap, &b->graph);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+            cudaStreamDestroy(cap);
+            if (e != cudaSuccess) return bfail(OCT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        }
+        for (int64_t i = 0; i < n; ++i) BATCH_CUDA(cudaGraphLaunch(b->exec, b->stream));
+    }
+    b->t += static_cast<uint64_t>(n);
+    return OCT_OK;
+}
+
+int oct_batch_measure_w2(oct_batch *b, oct_w2 *out, int64_t n) {
+    if (!b || !out || n != static_cast<int64_t>(b->reps.size())) return bfail(OCT_EINVAL, "out must hold one entry per replica");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    auto *res = static_cast<oct::W2Result *>(b->h_small);
+    std::vector<unsigned long long> cnt(2 * b->reps.size());
+    BATCH_CUDA(cudaMemcpyAsync(cnt.data(), b->counters, sizeof(unsigned long long) * cnt.size(),
+                               cudaMemcpyDeviceToHost, b->stream));
+    for (size_t r = 0; r < b->reps.size(); ++r) {
+        const int64_t L = b->reps[r].L;
+        BATCH_CUDA(oct::launch_w2(b->lat + b->lat_offset[r], static_cast<uint32_t>(L), b->d_rows, b->d_w2, b->stream));
+        BATCH_CUDA(cudaMemcpyAsync(res, b->d_w2, sizeof(oct::W2Result), cudaMemcpyDeviceToHost, b->stream));
+        BATCH_CUDA(cudaStreamSynchronize(b->stream));
+        const __int128 N = static_cast<__int128>(L) * L;
+        const __int128 S2 = static_cast<__int128>((static_cast<unsigned __int128>(res->s2_hi) << 64) | res->s2_lo);
+        const __int128 num = N * S2 - static_cast<__int128>(res->s1) * res->s1;
+        out[r].t = static_cast<int64_t>(b->t);
+        out[r].n_sites = static_cast<int64_t>(N);
+        out[r].s1 = res->s1;
+        out[r].s2_lo = res->s2_lo;
+        out[r].s2_hi = res->s2_hi;
+        out[r].net_flips = static_cast<int64_t>(cnt[2 * r]);
+        out[r].hmax = res->hmax;
+        out[r].w2 = static_cast<double>(num) / (static_cast<double>(N) * static_cast<double>(N));
+    }
+    return OCT_OK;
+}
+
+int oct_batch_get_planes(oct_batch *b, int64_t r, uint32_t *host, size_t words) {
+    if (!b || !host || r < 0 || r >= static_cast<int64_t>(b->reps.size())) return bfail(OCT_EINVAL, "bad replica");
+    const int64_t L = b->reps[r].L;
+    if (words != static_cast<size_t>(L) * L / 16) return bfail(OCT_EINVAL, "words must equal L*L/16");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    BATCH_CUDA(cudaMemcpyAsync(host, b->lat + b->lat_offset[r], words * 4, cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(cudaStreamSynchronize(b->stream));
+    return OCT_OK;
+}
+
+int oct_batch_get_stats(oct_batch *b, int64_t *t, int64_t *n_replicas, int64_t *total_sites, int64_t *draws) {
+    if (!b) return bfail(OCT_EINVAL, "NULL batch");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    int64_t sites = 0;
+    for (const auto &R : b->reps) sites += R.L * R.L;
+    if (t) *t = static_cast<int64_t>(b->t);
+    if (n_replicas) *n_replicas = static_cast<int64_t>(b->reps.size());
+    if (total_sites) *total_sites = sites;
+    if (draws) {
+        std::vector<unsigned long long> cnt(2 * b->reps.size());
+        BATCH_CUDA(cudaMemcpyAsync(cnt.data(), b->counters, sizeof(unsigned long long) * cnt.size(),
+                                   cudaMemcpyDeviceToHost, b->stream));
+        BATCH_CUDA(cudaStreamSynchronize(b->stream));
+        int64_t d = 0;
+        for (size_t r = 0; r < b->reps.size(); ++r) d += static_cast<int64_t>(cnt[2 * r + 1]);
+        *draws = d;
+    }
+    return OCT_OK;
+}
+
+int oct_batch_sync(oct_batch *b) {
+    if (!b) return bfail(OCT_EINVAL, "NULL batch");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    BATCH_CUDA(cudaStreamSynchronize(b->stream));
+    return OCT_OK;
+}
+
+int oct_batch_set_timing(oct_batch *b, int enable) {
+    if (!b) return bfail(OCT_EINVAL, "NULL batch");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    if (b->ev.empty()) {
+        b->ev.resize(512);
+        for (auto &e : b->ev) BATCH_CUDA(cudaEventCreate(&e));
+    }
+    int rc = flush_batch_timing(b);
+    if (rc) return rc;
+    b->timing = enable != 0;
+    b->step_ms = 0.0;
+    b->step_launches = 0;
+    return OCT_OK;
+}
+
+int oct_batch_get_timing(oct_batch *b, double *step_ms, int64_t *step_launches) {
+    if (!b) return bfail(OCT_EINVAL, "NULL batch");
+    int rc = flush_batch_timing(b);
+    if (rc) return rc;
+    if (step_ms) *step_ms = b->step_ms;
+    if (step_launches) *step_launches = b->step_launches;
+    return OCT_OK;
+}
+
+int oct_batch_destroy(oct_batch *b) {
+    if (!b) return OCT_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    delete b;
+    return OCT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,400 @@
+// Device code shared by the plain and the batched device-step kernels: one
+// DTrDT device step on a sub-tile held by warp lanes (see dtrdt.cu for the
+// method and the lane layout).
+#pragma once
+#include <cstdint>
+
+#include "philox.cuh"
+
+namespace oct {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kNib = 0x11111111u;  // bit 0 of every 4-bit TC column
+
+// Element k of the idx-th permutation of (0,1,2,3) in lexicographic order.
+__device__ __forceinline__ int perm_element(uint32_t idx, uint32_t k) {
+    uint32_t remaining = 0x3210u;  // nibbles: the symbols not used yet, in order
+    uint32_t radix = 6u;            // (3 - i)!
+    int e = 0;
+    for (uint32_t i = 0; i <= k; ++i) {
+        const uint32_t pick = idx / radix;
+        idx -= pick * radix;
+        e = static_cast<int>((remaining >> (4u * pick)) & 0xFu);
+        const uint32_t low = remaining & ((1u << (4u * pick)) - 1u);
+        const uint32_t high = remaining >> (4u * (pick + 1u));
+        remaining = low | (high << (4u * pick));
+        radix = (i == 0) ? 2u : 1u;
+    }
+    return e;
+}
+
+// Sets the bits of *w selected by mask to those of v, leaving the others, as
+// two reductions (no value returned, so the warp does not wait for them).
+__device__ __forceinline__ void merge_bits(uint32_t *w, uint32_t v, uint32_t mask) {
+    if (mask == 0xFFFFFFFFu) {
+        *w = v;
+        return;
+    }
+    atomicAnd(w, v | ~mask);
+    atomicOr(w, v & mask);
+}
+
+struct LaneCtx {
+    uint32_t t, k, T, g;
+    uint32_t k0, k1;
+    uint32_t thr_p, thr_q;
+    uint32_t p_always, q_always, p_random, q_random;
+    int gx, gy, GX, GY;
+};
+
+// Acceptance of the packed candidates (bit 4j+m = thread cell column j, TC
+// row m): u < P32 is decided at the first random level bit that differs from
+// P32's bit, most significant first; all 32 thread cells of the lane advance
+// together, four levels per Philox block.
+__device__ __forceinline__ uint32_t accept_levels(uint32_t pmin, uint32_t pmax, uint32_t s,
+                                                  const LaneCtx &c) {
+    uint32_t acc = 0, und = pmin | pmax;
+    for (uint32_t lb = 0; lb < 8u && und != 0u; ++lb) {
+        const uint4 W = philox4x32_10(c.t, c.k | ((s * 8u + lb) << 2), c.T, (kTagAcc << 28) | c.g,
+                                      c.k0, c.k1);
+        const uint32_t lw[4] = {W.x, W.y, W.z, W.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t bit = 31u - (4u * lb + i);
+            const uint32_t tb = (((c.thr_p >> bit) & 1u) ? pmin : 0u) | (((c.thr_q >> bit) & 1u) ? pmax : 0u);
+            acc |= und & tb & ~lw[i];
+            und &= ~(tb ^ lw[i]);
+        }
+    }
+    return acc;
+}
+
+// One collective step with sub-cell set (dx, DY).  X/Y hold the lane's 16
+// rows, E bit r the X bit just right of row r, D the Y row just below row 15.
+// An attempt at s is eligible iff X(s) != X(s+x), Y(s) != Y(s+y) and
+// X(s) == Y(s): then X(s) = 0 is the minimum of Eq. (1), X(s) = 1 the maximum.
+template <int DY, bool RANDOM>
+__device__ __forceinline__ void collective_step(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E,
+                                                uint32_t &D, const uint4 &site, uint32_t s,
+                                                uint32_t dx, const LaneCtx &c, int &net, int &draws) {
+    const uint32_t sw[4] = {site.x, site.y, site.z, site.w};
+    const uint32_t par = 2u * (s & 1u);
+    const uint32_t sh2 = 2u * dx;
+    uint32_t cnd0[4], cnd1[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        // Site draw: bit 4j = x offset, bit 4j+1 = y offset of TC column j.
+        const uint32_t u = sw[m] >> par;
+        const uint32_t col = (((u & kNib) << 1) | (~u & kNib)) << sh2;
+        const uint32_t yoff = ((u >> 1) & kNib) * 0xFu;
+        const int r0 = 4 * m + 2 * DY, r1 = r0 + 1;
+        const uint32_t xa = X[r0], xb = X[r1];
+        const uint32_t xra = __funnelshift_r(xa, E >> r0, 1);
+        const uint32_t xrb = __funnelshift_r(xb, E >> r1, 1);
+        const uint32_t ya = Y[r0], yb = Y[r1];
+        const uint32_t yc = (r1 + 1 < 16) ? Y[(r1 + 1) & 15] : D;
+        cnd0[m] = col & ~yoff & (xa ^ xra) & (ya ^ yb) & ~(xa ^ ya);
+        cnd1[m] = col & yoff & (xb ^ xrb) & (yb ^ yc) & ~(xb ^ yb);
+    }
+
+    uint32_t acc = 0;
+    if (RANDOM) {
+        uint32_t pmin = 0, pmax = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int r0 = 4 * m + 2 * DY, r1 = r0 + 1;
+            const uint32_t mn = (cnd0[m] & ~X[r0]) | (cnd1[m] & ~X[r1]);
+            const uint32_t mx = (cnd0[m] & X[r0]) | (cnd1[m] & X[r1]);
+            const uint32_t cmn = mn & c.p_random, cmx = mx & c.q_random;
+            pmin |= (((cmn >> sh2) | (cmn >> (sh2 + 1u))) & kNib) << m;
+            pmax |= (((cmx >> sh2) | (cmx >> (sh2 + 1u))) & kNib) << m;
+        }
+        draws += __popc(pmin | pmax);
+        acc = accept_levels(pmin, pmax, s, c);
+    }
+
+    uint32_t f0s[4], f1s[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int r0 = 4 * m + 2 * DY, r1 = r0 + 1;
+        uint32_t amin = c.p_always, amax = c.q_always;
+        if (RANDOM) {
+            const uint32_t spread = ((acc >> m) & kNib) * 0xFu;
+            amin |= spread & c.p_random;
+            amax |= spread & c.q_random;
+        }
+        const uint32_t xa = X[r0], xb = X[r1];
+        // accepted minima are where the candidate has X(s) = 0
+        const uint32_t f0 = cnd0[m] & ((~xa & amin) | (xa & amax));
+        const uint32_t f1 = cnd1[m] & ((~xb & amin) | (xb & amax));
+        net += __popc((f0 & ~xa) | (f1 & ~xb)) - __popc((f0 & xa) | (f1 & xb));
+        X[r0] = xa ^ f0 ^ (f0 << 1);
+        X[r1] = xb ^ f1 ^ (f1 << 1);
+        Y[r0] ^= f0;
+        Y[r1] ^= f0 ^ f1;
+        if (r1 + 1 < 16)
+            Y[(r1 + 1) & 15] ^= f1;
+        else
+            D ^= f1;
+        f0s[m] = f0;
+        f1s[m] = f1;
+    }
+
+    // Keep the neighbour copies consistent.
+    if (dx) {
+        // Flips at bit 31 changed column 0 of the right neighbour (this lane's E).
+        uint32_t dE = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int r0 = 4 * m + 2 * DY;
+            dE |= ((f0s[m] >> 31) << r0) | ((f1s[m] >> 31) << (r0 + 1));
+        }
+        E ^= dE;
+        const uint32_t v = __shfl_up_sync(kFull, dE, 1);
+        if (c.gx > 0) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int r0 = 4 * m + 2 * DY, r1 = r0 + 1;
+                X[r0] ^= (v >> r0) & 1u;
+                X[r1] ^= (v >> r1) & 1u;
+            }
+        }
+    } else {
+        // Flips at bit 0 changed this lane's column 0, mirrored by the left neighbour's E.
+        uint32_t dB0 = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int r0 = 4 * m + 2 * DY;
+            dB0 |= ((f0s[m] & 1u) << r0) | ((f1s[m] & 1u) << (r0 + 1));
+        }
+        const uint32_t v = __shfl_down_sync(kFull, dB0, 1);
+        if (c.gx < c.GX - 1) E ^= v;
+    }
+    if (DY) {
+        // Row 16 (D) belongs to the lane below.
+        const uint32_t v = __shfl_up_sync(kFull, f1s[3], c.GX);
+        if (c.gy > 0) Y[0] ^= v;
+    } else {
+        // Row 0 is mirrored by the lane above in its D.
+        const uint32_t v = __shfl_down_sync(kFull, f0s[0], c.GX);
+        if (c.gy < c.GY - 1) D ^= v;
+    }
+}
+
+
+// The same collective step when the lanes of one warp belong to different
+// sub-tiles, each with its own set draw: the row offset dy is a run-time value
+// per lane (rows picked with selects instead of branches), and every shuffle
+// runs unconditionally so that all 32 lanes take part.
+template <bool RANDOM>
+__device__ __forceinline__ void collective_step_rt(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E,
+                                                   uint32_t &D, const uint4 &site, uint32_t s,
+                                                   uint32_t dx, uint32_t dy, const LaneCtx &c, int &net,
+                                                   int &draws) {
+    const uint32_t sw[4] = {site.x, site.y, site.z, site.w};
+    const uint32_t par = 2u * (s & 1u);
+    const uint32_t sh2 = 2u * dx;
+    const uint32_t ro = 2u * dy;
+    const uint32_t dym = dy ? 0xFFFFFFFFu : 0u;
+    uint32_t cnd0[4], cnd1[4], xas[4], xbs[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const uint32_t u = sw[m] >> par;
+        const uint32_t col = (((u & kNib) << 1) | (~u & kNib)) << sh2;
+        const uint32_t yoff = ((u >> 1) & kNib) * 0xFu;
+        const uint32_t xa = dy ? X[4 * m + 2] : X[4 * m];
+        const uint32_t xb = dy ? X[4 * m + 3] : X[4 * m + 1];
+        const uint32_t ya = dy ? Y[4 * m + 2] : Y[4 * m];
+        const uint32_t yb = dy ? Y[4 * m + 3] : Y[4 * m + 1];
+        const uint32_t yc = dy ? (m < 3 ? Y[(4 * m + 4) & 15] : D) : Y[4 * m + 2];
+        const uint32_t r0 = 4u * m + ro;
+        const uint32_t xra = __funnelshift_r(xa, E >> r0, 1);
+        const uint32_t xrb = __funnelshift_r(xb, E >> (r0 + 1u), 1);
+        cnd0[m] = col & ~yoff & (xa ^ xra) & (ya ^ yb) & ~(xa ^ ya);
+        cnd1[m] = col & yoff & (xb ^ xrb) & (yb ^ yc) & ~(xb ^ yb);
+        xas[m] = xa;
+        xbs[m] = xb;
+    }
+
+    uint32_t acc = 0;
+    if (RANDOM) {
+        uint32_t pmin = 0, pmax = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const uint32_t mn = (cnd0[m] & ~xas[m]) | (cnd1[m] & ~xbs[m]);
+            const uint32_t mx = (cnd0[m] & xas[m]) | (cnd1[m] & xbs[m]);
+            const uint32_t cmn = mn & c.p_random, cmx = mx & c.q_random;
+            pmin |= (((cmn >> sh2) | (cmn >> (sh2 + 1u))) & kNib) << m;
+            pmax |= (((cmx >> sh2) | (cmx >> (sh2 + 1u))) & kNib) << m;
+        }
+        draws += __popc(pmin | pmax);
+        acc = accept_levels(pmin, pmax, s, c);
+    }
+
+    uint32_t dE = 0, dB0 = 0, dD = 0, dY0 = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        uint32_t amin = c.p_always, amax = c.q_always;
+        if (RANDOM) {
+            const uint32_t spread = ((acc >> m) & kNib) * 0xFu;
+            amin |= spread & c.p_random;
+            amax |= spread & c.q_random;
+        }
+        const uint32_t xa = xas[m], xb = xbs[m];
+        const uint32_t f0 = cnd0[m] & ((~xa & amin) | (xa & amax));
+        const uint32_t f1 = cnd1[m] & ((~xb & amin) | (xb & amax));
+        net += __popc((f0 & ~xa) | (f1 & ~xb)) - __popc((f0 & xa) | (f1 & xb));
+        const uint32_t nxa = xa ^ f0 ^ (f0 << 1), nxb = xb ^ f1 ^ (f1 << 1);
+        X[4 * m] = dy ? X[4 * m] : nxa;
+        X[4 * m + 1] = dy ? X[4 * m + 1] : nxb;
+        X[4 * m + 2] = dy ? nxa : X[4 * m + 2];
+        X[4 * m + 3] = dy ? nxb : X[4 * m + 3];
+        const uint32_t f01 = f0 ^ f1;
+        Y[4 * m] ^= f0 & ~dym;
+        Y[4 * m + 1] ^= f01 & ~dym;
+        Y[4 * m + 2] ^= (f0 & dym) | (f1 & ~dym);
+        Y[4 * m + 3] ^= f01 & dym;
+        if (m < 3)
+            Y[(4 * m + 4) & 15] ^= f1 & dym;
+        else
+            D ^= f1 & dym;
+        const uint32_t r0 = 4u * m + ro;
+        dE |= ((f0 >> 31) << r0) | ((f1 >> 31) << (r0 + 1u));
+        dB0 |= ((f0 & 1u) << r0) | ((f1 & 1u) << (r0 + 1u));
+        if (m == 3) dD = f1 & dym;
+        if (m == 0) dY0 = f0 & ~dym;
+    }
+    // dE is zero unless dx = 1, dB0 zero unless dx = 0; dD zero unless dy = 1,
+    // dY0 zero unless dy = 0, so both directions can always be exchanged.
+    E ^= dE;
+    const uint32_t vr = __shfl_up_sync(kFull, dE, 1);
+    const uint32_t vl = __shfl_down_sync(kFull, dB0, 1);
+    if (c.gx > 0) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) X[r] ^= (vr >> r) & 1u;
+    }
+    if (c.gx < c.GX - 1) E ^= vl;
+    const uint32_t vd = __shfl_up_sync(kFull, dD, c.GX);
+    const uint32_t vu = __shfl_down_sync(kFull, dY0, c.GX);
+    if (c.gy > 0) Y[0] ^= vd;
+    if (c.gy < c.GY - 1) D ^= vu;
+}
+
+// Device step on one sub-tile (Bx x By sites at (x0, y0)) held by the lanes of
+// one warp that share it: stage the lane's group from the planar lattice,
+// run the 16 single-hit collective steps, write back.  LANE_SETS: lanes of the
+// warp may belong to different sub-tiles (each with its own set draws).
+template <bool RANDOM, bool LANE_SETS>
+__device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t Bx,
+                                            uint32_t By, uint32_t x0, uint32_t y0, bool active,
+                                            const LaneCtx &c, int &net, int &draws) {
+    uint32_t *const Xp = lat;
+    uint32_t *const Yp = lat + static_cast<size_t>(L) * wpr;
+    const uint32_t sh = x0 & 31u;
+    const uint32_t wA = ((x0 >> 5) + static_cast<uint32_t>(c.gx)) % wpr;
+    const uint32_t wB = (wA + 1u == wpr) ? 0u : wA + 1u;
+    uint32_t ybase = y0 + 16u * static_cast<uint32_t>(c.gy);
+    if (ybase >= L) ybase -= L;
+
+    // Stage the group: 16 rows of X and Y, funnel-shifted to local bit 0.
+    uint32_t X[16], Y[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        X[r] = 0u;
+        Y[r] = 0u;
+    }
+    if (active) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            uint32_t yr = ybase + r;
+            if (yr >= L) yr -= L;
+            const size_t ro = static_cast<size_t>(yr) * wpr;
+            X[r] = __funnelshift_r(Xp[ro + wA], Xp[ro + wB], sh);
+            Y[r] = __funnelshift_r(Yp[ro + wA], Yp[ro + wB], sh);
+        }
+    }
+    // E: column 0 of the right neighbour; D: row 0 of the lane below.
+    uint32_t b0 = 0;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) b0 |= (X[r] & 1u) << r;
+    uint32_t E = __shfl_down_sync(kFull, b0, 1);
+    uint32_t D = __shfl_down_sync(kFull, Y[0], c.GX);
+    if (active && c.gx == c.GX - 1) {  // halo column x0 + Bx
+        uint32_t xc = x0 + Bx;
+        if (xc >= L) xc -= L;
+        const uint32_t wc = xc >> 5, bc = xc & 31u;
+        E = 0u;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            uint32_t yr = ybase + r;
+            if (yr >= L) yr -= L;
+            E |= ((Xp[static_cast<size_t>(yr) * wpr + wc] >> bc) & 1u) << r;
+        }
+    }
+    uint32_t yh = y0 + By;
+    if (yh >= L) yh -= L;
+    if (active && c.gy == c.GY - 1) {  // halo row y0 + By
+        const size_t ro = static_cast<size_t>(yh) * wpr;
+        D = __funnelshift_r(Yp[ro + wA], Yp[ro + wB], sh);
+    }
+
+    // Block layer: 16 single-hit collective steps.
+    const uint4 setw = philox4x32_10(c.t, c.k, c.T, kTagSet << 28, c.k0, c.k1);
+    uint4 site = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t s = 0; s < 16u; ++s) {
+        if ((s & 1u) == 0u)
+            site = philox4x32_10(c.t, c.k | ((s >> 1) << 2), c.T, (kTagSite << 28) | c.g, c.k0, c.k1);
+        const uint32_t d = (setw.x >> (2u * s)) & 3u;
+        if (LANE_SETS)
+            collective_step_rt<RANDOM>(X, Y, E, D, site, s, d & 1u, d >> 1, c, net, draws);
+        else if (d & 2u)
+            collective_step<1, RANDOM>(X, Y, E, D, site, s, d & 1u, c, net, draws);
+        else
+            collective_step<0, RANDOM>(X, Y, E, D, site, s, d & 1u, c, net, draws);
+    }
+
+    // Write back.  Global word wA of a row receives the high bits of the left
+    // lane and the low bits of this lane; the leftmost lane shares word wA
+    // with the bits left of x0, the rightmost lane also owns the low bits of
+    // word wB (its own high bits, and for X the halo-column bit).  Words shared
+    // with sites outside the sub-tile are merged with an AND/OR reduction pair
+    // (no read, so no load latency), full words are stored.  No other warp of
+    // this device step touches these words: active sub-tiles are at least 32
+    // sites apart.
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const uint32_t leftX = __shfl_up_sync(kFull, X[r], 1);
+        const uint32_t leftY = __shfl_up_sync(kFull, Y[r], 1);
+        if (active) {
+            uint32_t yr = ybase + r;
+            if (yr >= L) yr -= L;
+            const size_t ro = static_cast<size_t>(yr) * wpr;
+            if (c.gx == 0 && sh) {
+                merge_bits(&Xp[ro + wA], X[r] << sh, ~0u << sh);
+                merge_bits(&Yp[ro + wA], Y[r] << sh, ~0u << sh);
+            } else {
+                Xp[ro + wA] = __funnelshift_l(leftX, X[r], sh);
+                Yp[ro + wA] = __funnelshift_l(leftY, Y[r], sh);
+            }
+            if (c.gx == c.GX - 1) {
+                const uint32_t hiX = sh ? (X[r] >> (32u - sh)) : 0u;
+                merge_bits(&Xp[ro + wB], hiX | (((E >> r) & 1u) << sh), (2u << sh) - 1u);
+                if (sh) merge_bits(&Yp[ro + wB], Y[r] >> (32u - sh), (1u << sh) - 1u);
+            }
+        }
+    }
+    {
+        const uint32_t leftD = __shfl_up_sync(kFull, D, 1);
+        if (active && c.gy == c.GY - 1) {
+            const size_t ro = static_cast<size_t>(yh) * wpr;
+            if (c.gx == 0 && sh)
+                merge_bits(&Yp[ro + wA], D << sh, ~0u << sh);
+            else
+                Yp[ro + wA] = __funnelshift_l(leftD, D, sh);
+            if (c.gx == c.GX - 1 && sh) merge_bits(&Yp[ro + wB], D >> (32u - sh), (1u << sh) - 1u);
+        }
+    }
+
+}
+
+}  // namespace oct

@@ -1,0 +1,92 @@
+"""Batched replicas: every replica of a batch equals, bit for bit, the same
+realization run alone through the plain entry points (and so the oracle), for
+mixed L, p, q and sub-tile shapes; graph replay and launch-by-launch runs agree;
+replica keys match the oracle's derivation."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1705_01022_gb300 as g
+    g.build()
+    return g
+
+
+def test_replica_seed_matches_oracle(g, oracle):
+    from paper_1705_01022_gb300 import _lib
+    for master in (1, 7, 2**40 + 3, 2**64 - 1):
+        for r in (0, 1, 2, 1000, 2047, 2**31):
+            assert _lib.oct_replica_seed(master, r) == oracle.replica_seed(master, r)
+
+
+PQ = [(1.0, 0.0), (0.95, 0.05), (0.5, 0.5)]
+
+
+def _replicas(g, master=7):
+    from paper_1705_01022_gb300 import _lib
+    reps = []
+    Ls = [64, 128, 192, 256, 320, 384, 448, 512]
+    for i, L in enumerate(Ls):
+        for j, (p, q) in enumerate(PQ):
+            r = len(reps)
+            reps.append((L, p, q, _lib.oct_replica_seed(master, r)))
+    # explicit shapes too: a full-warp sub-tile and a two-group one
+    reps.append((1024, 0.95, 0.05, 99, 256, 64))
+    reps.append((512, 0.5, 0.5, 98, 64, 32))
+    return reps
+
+
+def test_batch_equals_plain_runs(g):
+    reps = _replicas(g)
+    n = 5
+    with g.Batch(reps) as b:
+        b.run(n)
+        res = b.measure()
+        for i, r in enumerate(reps):
+            L, p, q, seed = r[:4]
+            Bx, By = (r[4], r[5]) if len(r) > 4 else ((64, 64) if L % 128 == 0 else (32, 32))
+            with g.Simulation(L, p, q, seed, Bx=Bx, By=By) as sim:
+                sim.run(n)
+                assert np.array_equal(b.planes(i), sim.planes()), (i, r)
+                m = sim.measure()
+                assert (res[i].s1, res[i].s2, res[i].hmax, res[i].net_flips) == \
+                    (m.s1, m.s2, m.hmax, m.net_flips), (i, r)
+                assert res[i].w2 == m.w2
+
+
+def test_batch_matches_oracle(g, oracle):
+    reps = [(192, 0.95, 0.05, 5), (256, 0.5, 0.5, 6), (64, 1.0, 0.0, 7)]
+    with g.Batch(reps) as b:
+        b.run(4)
+        for i, (L, p, q, seed) in enumerate(reps):
+            B = 64 if L % 128 == 0 else 32
+            X, Y = oracle.flat(L)
+            oracle.dtrdt_run(X, Y, oracle.Params(L=L, p=p, q=q, seed=seed, Bx=B, By=B), 0, 4)
+            assert np.array_equal(b.planes(i), oracle.pack_planar(X, Y)), i
+
+
+def test_graph_and_timed_launches_agree(g):
+    from paper_1705_01022_gb300 import _lib
+    reps = _replicas(g, master=11)[:12]
+    with g.Batch(reps) as a, g.Batch(reps) as b:
+        a.run(3)
+        _lib.oct_batch_set_timing(b.h, True)
+        b.run(3)
+        ms, launches = _lib.oct_batch_get_timing(b.h)
+        assert launches == 12 and ms > 0
+        for i in range(len(reps)):
+            assert np.array_equal(a.planes(i), b.planes(i))
+        t, n, sites, draws = a.stats()
+        assert (t, n) == (3, len(reps))
+        assert sites == sum(r[0] * r[0] for r in reps)
+
+
+def test_invalid_replicas_rejected(g):
+    from paper_1705_01022_gb300 import _lib
+    with pytest.raises(_lib.OctError):
+        g.Batch([(100, 1.0, 0.0, 1)])
+    with pytest.raises(_lib.OctError):
+        g.Batch([(256, 1.0, 0.0, 1, 96, 32)])

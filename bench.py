@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--loop-steps", type=int, default=3)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=32)
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -235,6 +237,30 @@ def batched_leg(a, g, _lib, torch, stream, peak_tops):
     return out
 
 
+def serving_leg(a, g, _lib, torch, stream, capacity):
+    """Poisson streams of simulation jobs at offered loads of 0.5, 0.8 and 1.0
+    times the batched capacity, served by continuous batching."""
+    from paper_1705_01022_gb300 import serve
+    work = serve.expected_work()
+    out = {"workload": ("Poisson job stream: L log-uniform in [128, 16384] (multiples of 128), t_max "
+                        "log-uniform in [10, 10^4] MCS, (p,q) uniform over (1,0), (0.8,0.2), (0.5,0.5), "
+                        "W^2 streamed at 8 log-spaced times per job, HBM budget 64 GiB"),
+           "capacity_attempts_per_ns": capacity, "expected_attempts_per_job": work, "loads": []}
+    for rho in (0.5, 0.8, 1.0):
+        rate = rho * capacity * 1e9 / work
+        jobs = serve.poisson_jobs(a.serve_jobs, rate, master_seed=1, seed_fn=_lib.oct_replica_seed)
+        eng = serve.ServingEngine(64 << 30, stream=stream, max_chunk=64)
+        t0 = time.perf_counter()
+        done = eng.run(jobs)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        res = serve.summary(done, wall)
+        res.update({"offered_load": rho, "rate_jobs_per_s": rate, "ticks": eng.ticks})
+        out["loads"].append(res)
+        eng.batch.close()
+    return out
+
+
 def run_reference(a, rank, world):
     """The oracle as it stands, on the host cores, same metric and workload;
     each step replays one MCS on a bounded window of the lattice."""
@@ -365,6 +391,12 @@ def main():
     if rank == 0 and not a.no_batch and a.batch_replicas > 0:
         batched = batched_leg(a, g, _lib, torch, stream, peak_tops)
 
+    # ---- serving: continuous batching of a Poisson job stream ----
+    serving = None
+    if rank == 0 and not a.no_serve and a.serve_jobs > 0:
+        cap = batched["value"] if batched else value
+        serving = serving_leg(a, g, _lib, torch, stream, cap)
+
     # ---- CPU baseline: the oracle on a sample of the same state ----
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
@@ -404,7 +436,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload(a), "clocks": clk.summary(), "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "batched": batched,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "batched": batched, "serving": serving,
             "probe": {"lop3_per_clk_per_sm": lop3, "imad_per_clk_per_sm": imad, "probe_mhz": probe_mhz},
         }
         print(json.dumps(out), flush=True)

@@ -229,21 +229,38 @@ typedef struct {
  * Philox-4x32-10 at counter (r, 0, 0, 6 << 28) under the master key. */
 int oct_replica_seed(uint64_t master_seed, uint32_t r, uint64_t *seed);
 
-/* Creates n replicas in the flat start on `stream` (NULL: library-owned). */
+/* Creates a batch holding n >= 0 replicas in the flat start, in slots
+ * 0..n-1, on `stream` (NULL: library-owned).  Replica lattices come from a
+ * stream-ordered memory pool private to the batch. */
 int oct_batch_create(int64_t n, const oct_replica *reps, void *stream, oct_batch **out);
 
-/* Enqueues n MCS for every replica (asynchronous). */
+/* Adds one replica in the flat start at its own time t = 0 (continuous
+ * batching: replicas may join while others are running); *slot receives its
+ * slot index (a freed slot is reused).  Errors: OCT_EINVAL, OCT_ENOMEM. */
+int oct_batch_add(oct_batch *b, const oct_replica *r, int64_t *slot);
+
+/* Removes the replica in `slot` and returns its lattice to the pool. */
+int oct_batch_remove(oct_batch *b, int64_t slot);
+
+/* Enqueues n MCS for every replica in the batch (asynchronous); each replica
+ * advances its own time t.  The work list and graph are rebuilt first if
+ * replicas were added or removed. */
 int oct_batch_run(oct_batch *b, int64_t n);
 
-/* Exact roughness of every replica (out holds n = replica count entries;
- * net_flips per replica since the flat start).  Synchronises. */
+/* Exact roughness of every slot (out holds one entry per slot index handed
+ * out so far; free slots read as zeros; t is each replica's own time,
+ * net_flips since its flat start).  Synchronises. */
 int oct_batch_measure_w2(oct_batch *b, oct_w2 *out, int64_t n);
 
-/* Planar lattice of replica r (words = L*L/16).  Synchronises. */
-int oct_batch_get_planes(oct_batch *b, int64_t r, uint32_t *host, size_t words);
+/* Exact roughness of the replica in one slot.  Synchronises. */
+int oct_batch_measure_slot(oct_batch *b, int64_t slot, oct_w2 *out);
 
-/* Time, replica count, total sites over replicas, acceptance draws so far. */
-int oct_batch_get_stats(oct_batch *b, int64_t *t, int64_t *n_replicas, int64_t *total_sites,
+/* Planar lattice of the replica in `slot` (words = L*L/16).  Synchronises. */
+int oct_batch_get_planes(oct_batch *b, int64_t slot, uint32_t *host, size_t words);
+
+/* MCS run by oct_batch_run so far, replicas present, their total sites, and
+ * their acceptance draws. */
+int oct_batch_get_stats(oct_batch *b, int64_t *ticks, int64_t *n_active, int64_t *active_sites,
                         int64_t *draws);
 
 /* Waits for the batch's stream. */

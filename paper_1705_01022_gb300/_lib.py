@@ -87,7 +87,10 @@ _SIGNATURES = [
      ctypes.c_int),
     ("oct_batch_create", [ctypes.c_int64, ctypes.POINTER(oct_replica), ctypes.c_void_p,
                           ctypes.POINTER(_H)], ctypes.c_int),
+    ("oct_batch_add", [_H, ctypes.POINTER(oct_replica), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    ("oct_batch_remove", [_H, ctypes.c_int64], ctypes.c_int),
     ("oct_batch_run", [_H, ctypes.c_int64], ctypes.c_int),
+    ("oct_batch_measure_slot", [_H, ctypes.c_int64, ctypes.POINTER(oct_w2)], ctypes.c_int),
     ("oct_batch_measure_w2", [_H, ctypes.POINTER(oct_w2), ctypes.c_int64], ctypes.c_int),
     ("oct_batch_get_planes", [_H, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
     ("oct_batch_get_stats", [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
@@ -231,10 +234,26 @@ def oct_replica_seed(master: int, r: int) -> int:
 
 
 def oct_batch_create(reps, stream=None) -> int:
-    arr = (oct_replica * len(reps))(*reps)
+    arr = (oct_replica * max(1, len(reps)))(*reps)
     h = _H()
     _check(load().oct_batch_create(len(reps), arr, stream, ctypes.byref(h)), "oct_batch_create")
     return h.value
+
+
+def oct_batch_add(h: int, rep: oct_replica) -> int:
+    slot = ctypes.c_int64()
+    _check(load().oct_batch_add(h, ctypes.byref(rep), ctypes.byref(slot)), "oct_batch_add")
+    return slot.value
+
+
+def oct_batch_remove(h: int, slot: int) -> None:
+    _check(load().oct_batch_remove(h, slot), "oct_batch_remove")
+
+
+def oct_batch_measure_slot(h: int, slot: int) -> oct_w2:
+    out = oct_w2()
+    _check(load().oct_batch_measure_slot(h, slot, ctypes.byref(out)), "oct_batch_measure_slot")
+    return out
 
 
 def oct_batch_run(h: int, n: int) -> None:

@@ -55,9 +55,8 @@ constexpr int kBatchBlocksPerSM = 4;
 template <bool RANDOM>
 __global__ void __launch_bounds__(kBatchWarps * 32, kBatchBlocksPerSM)
     batch_step_kernel(const ReplicaDev *reps, const BatchItem *items, const WarpDesc *descs,
-                      uint32_t n_descs, const uint32_t *t_ptr, uint32_t k, uint32_t *queue) {
+                      uint32_t n_descs, const uint32_t *t_of, uint32_t k, uint32_t *queue) {
     const int lane = threadIdx.x & 31;
-    const uint32_t t = *t_ptr;
     for (;;) {
         uint32_t di = 0;
         if (lane == 0) di = atomicAdd(queue, 1u);
@@ -69,6 +68,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, kBatchBlocksPerSM)
         const bool active = slot < static_cast<int>(wd.n);
         const BatchItem it = items[wd.first + (active ? slot : 0)];
         const ReplicaDev R = reps[it.rep];
+        const uint32_t t = t_of[it.rep];  // this replica's MCS index
         const uint32_t L = R.L;
         const uint4 M = philox4x32_10(t, 0u, 0u, kTagMcs << 28, R.k0, R.k1);
         const uint32_t ox = static_cast<uint32_t>((static_cast<uint64_t>(M.x) * L) >> 32);
@@ -112,7 +112,11 @@ __global__ void __launch_bounds__(kBatchWarps * 32, kBatchBlocksPerSM)
     }
 }
 
-__global__ void batch_advance_kernel(uint32_t *t_ptr) { *t_ptr += 1u; }
+// Advances the MCS counter of every active replica.
+__global__ void batch_advance_kernel(uint32_t *t_of, const uint32_t *active, uint32_t n_active) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_active; i += gridDim.x * blockDim.x)
+        t_of[active[i]] += 1u;
+}
 
 }  // namespace
 }  // namespace oct
@@ -138,22 +142,33 @@ struct oct_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaMemPool_t pool = nullptr;     // replica lattices, stream-ordered
+    // slots (a replica keeps its slot until removed)
     std::vector<oct_replica> reps;
-    std::vector<size_t> lat_offset;  // in words
-    uint32_t *lat = nullptr;         // all lattices, 256-byte aligned each
-    unsigned long long *counters = nullptr;
-    oct::ReplicaDev *d_reps = nullptr;
+    std::vector<uint32_t *> lat;      // per slot, nullptr if free
+    std::vector<char> used;
+    std::vector<int64_t> free_slots;
+    size_t capacity = 0;
+    oct::ReplicaDev *d_reps = nullptr;  // capacity entries
+    uint32_t *d_t = nullptr;            // capacity MCS counters
+    unsigned long long *counters = nullptr;  // 2 * capacity: net flips, draws
+    // work list of the current membership
+    bool dirty = true;
     oct::BatchItem *d_items = nullptr;
+    size_t items_cap = 0;
     oct::WarpDesc *d_descs = nullptr;
-    uint32_t n_desc[2] = {0, 0};  // [mode without draws, mode with draws]
+    size_t descs_cap = 0;
+    uint32_t *d_active = nullptr;
+    size_t active_cap = 0;
+    uint32_t n_active = 0;
+    uint32_t n_desc[2] = {0, 0};
     uint32_t desc_first[2] = {0, 0};
     uint32_t *d_queue = nullptr;  // 8 counters: (device step, mode)
-    uint32_t *d_t = nullptr;
     oct::W2RowSums *d_rows = nullptr;
+    int64_t rows_cap = 0;
     oct::W2Result *d_w2 = nullptr;
     void *h_small = nullptr;
-    int64_t max_L = 0;
-    uint64_t t = 0;
+    uint64_t ticks = 0;  // MCS run by oct_batch_run
     int grid = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -166,24 +181,178 @@ struct oct_batch {
 
 namespace {
 
-void batch_free(oct_batch *b) {
+void drop_graph(oct_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    cudaFree(b->lat);
-    cudaFree(b->counters);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+void batch_free(oct_batch *b) {
+    drop_graph(b);
+    for (uint32_t *p : b->lat)
+        if (p) cudaFreeAsync(p, b->stream);
+    if (b->stream) cudaStreamSynchronize(b->stream);
     cudaFree(b->d_reps);
+    cudaFree(b->d_t);
+    cudaFree(b->counters);
     cudaFree(b->d_items);
     cudaFree(b->d_descs);
+    cudaFree(b->d_active);
     cudaFree(b->d_queue);
-    cudaFree(b->d_t);
     cudaFree(b->d_rows);
     cudaFree(b->d_w2);
     if (b->h_small) cudaFreeHost(b->h_small);
     for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    if (b->pool) cudaMemPoolDestroy(b->pool);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
-// Enqueues device step k of the current MCS for every replica.
+int check_replica(oct_replica &R) {
+    if (R.L < 64 || R.L > 16384 || R.L % 64) return bfail(OCT_EINVAL, "replica L must be a multiple of 64 in [64, 16384]");
+    if (!(R.p >= 0.0 && R.p <= 1.0 && R.q >= 0.0 && R.q <= 1.0))
+        return bfail(OCT_EINVAL, "replica p and q must lie in [0, 1]");
+    if (R.Bx == 0 && R.By == 0) {
+        R.Bx = (R.L % 128 == 0) ? 64 : 32;
+        R.By = R.Bx;
+    }
+    const int GX = R.Bx / 32, GY = R.By / 16, G = GX * GY;
+    if (R.Bx < 32 || R.By < 16 || R.Bx % 32 || R.By % 16 || R.L % (2 * R.Bx) || R.L % (2 * R.By) ||
+        (GX & (GX - 1)) || (GY & (GY - 1)) || G > 32)
+        return bfail(OCT_EINVAL, "replica sub-tile must be a power-of-two number (at most 32) of "
+                                 "32x16-site groups in each direction and divide L/2");
+    return OCT_OK;
+}
+
+oct::ReplicaDev replica_dev(const oct_batch *b, int64_t slot) {
+    const oct_replica &R = b->reps[slot];
+    oct::ReplicaDev D;
+    D.lat = b->lat[slot];
+    D.counters = b->counters + 2 * slot;
+    D.L = static_cast<uint32_t>(R.L);
+    D.wpr = static_cast<uint32_t>(R.L / 32);
+    D.Bx = static_cast<uint32_t>(R.Bx);
+    D.By = static_cast<uint32_t>(R.By);
+    D.GX = static_cast<uint32_t>(R.Bx / 32);
+    D.GY = static_cast<uint32_t>(R.By / 16);
+    D.tiles_x = static_cast<uint32_t>(R.L / (2 * R.Bx));
+    D.tiles_y = static_cast<uint32_t>(R.L / (2 * R.By));
+    D.k0 = static_cast<uint32_t>(R.seed & 0xFFFFFFFFu);
+    D.k1 = static_cast<uint32_t>(R.seed >> 32);
+    const bool pr = R.p > 0.0 && R.p < 1.0, qr = R.q > 0.0 && R.q < 1.0;
+    D.thr_p = pr ? thr32(R.p) : 0u;
+    D.thr_q = qr ? thr32(R.q) : 0u;
+    D.p_always = (R.p == 1.0) ? 0xFFFFFFFFu : 0u;
+    D.q_always = (R.q == 1.0) ? 0xFFFFFFFFu : 0u;
+    D.p_random = pr ? 0xFFFFFFFFu : 0u;
+    D.q_random = qr ? 0xFFFFFFFFu : 0u;
+    return D;
+}
+
+template <typename T>
+cudaError_t ensure(T **p, size_t *cap, size_t need) {
+    if (need <= *cap) return cudaSuccess;
+    size_t n = std::max<size_t>(need, 2 * *cap);
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(p, sizeof(T) * n);
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
+// Grows the per-slot tables, keeping the device-resident counters.
+cudaError_t grow_slots(oct_batch *b, size_t need) {
+    if (need <= b->capacity) return cudaSuccess;
+    const size_t n = std::max<size_t>(need, std::max<size_t>(64, 2 * b->capacity));
+    oct::ReplicaDev *r = nullptr;
+    uint32_t *t = nullptr;
+    unsigned long long *c = nullptr;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&r, sizeof(oct::ReplicaDev) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&t, sizeof(uint32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&c, sizeof(unsigned long long) * 2 * n);
+    if (e == cudaSuccess && b->capacity) {
+        e = cudaMemcpy(t, b->d_t, sizeof(uint32_t) * b->capacity, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c, b->counters, sizeof(unsigned long long) * 2 * b->capacity, cudaMemcpyDeviceToDevice);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(r);
+        cudaFree(t);
+        cudaFree(c);
+        return e;
+    }
+    cudaFree(b->d_reps);
+    cudaFree(b->d_t);
+    cudaFree(b->counters);
+    b->d_reps = r;
+    b->d_t = t;
+    b->counters = c;
+    b->capacity = n;
+    b->dirty = true;
+    return cudaSuccess;
+}
+
+// Rebuilds the replica table and the warp work list of the active replicas.
+cudaError_t rebuild(oct_batch *b) {
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return e;
+    drop_graph(b);
+    std::vector<oct::ReplicaDev> rd(b->capacity);
+    std::vector<uint32_t> active;
+    std::vector<oct::BatchItem> bucket[2][6][6];
+    for (size_t slot = 0; slot < b->reps.size(); ++slot) {
+        if (!b->used[slot]) continue;
+        rd[slot] = replica_dev(b, static_cast<int64_t>(slot));
+        const oct::ReplicaDev &D = rd[slot];
+        active.push_back(static_cast<uint32_t>(slot));
+        const int mode = (D.p_random || D.q_random) ? 1 : 0;
+        int gxi = 0, gyi = 0;
+        while ((1u << gxi) < D.GX) ++gxi;
+        while ((1u << gyi) < D.GY) ++gyi;
+        for (uint32_t T = 0; T < D.tiles_x * D.tiles_y; ++T)
+            bucket[mode][gxi][gyi].push_back({static_cast<uint32_t>(slot), T});
+    }
+    std::vector<oct::BatchItem> items;
+    std::vector<oct::WarpDesc> descs;
+    for (int mode = 0; mode < 2; ++mode) {
+        b->desc_first[mode] = static_cast<uint32_t>(descs.size());
+        for (int gxi = 5; gxi >= 0; --gxi)
+            for (int gyi = 5; gyi >= 0; --gyi) {
+                const uint32_t GX = 1u << gxi, G = GX << gyi;
+                if (G > 32u) continue;
+                const uint32_t per = 32u / G;
+                auto &bk = bucket[mode][gxi][gyi];
+                for (size_t i = 0; i < bk.size(); i += per) {
+                    oct::WarpDesc d;
+                    d.first = static_cast<uint32_t>(items.size());
+                    d.n = static_cast<uint32_t>(std::min<size_t>(per, bk.size() - i));
+                    d.G = G;
+                    d.GX = GX;
+                    for (uint32_t j = 0; j < d.n; ++j) items.push_back(bk[i + j]);
+                    descs.push_back(d);
+                }
+            }
+        b->n_desc[mode] = static_cast<uint32_t>(descs.size()) - b->desc_first[mode];
+    }
+    b->n_active = static_cast<uint32_t>(active.size());
+    e = ensure(&b->d_items, &b->items_cap, std::max<size_t>(1, items.size()));
+    if (e == cudaSuccess) e = ensure(&b->d_descs, &b->descs_cap, std::max<size_t>(1, descs.size()));
+    if (e == cudaSuccess) e = ensure(&b->d_active, &b->active_cap, std::max<size_t>(1, active.size()));
+    if (e == cudaSuccess && b->capacity)
+        e = cudaMemcpy(b->d_reps, rd.data(), sizeof(oct::ReplicaDev) * b->capacity, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpy(b->d_items, items.data(), sizeof(oct::BatchItem) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !descs.empty())
+        e = cudaMemcpy(b->d_descs, descs.data(), sizeof(oct::WarpDesc) * descs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !active.empty())
+        e = cudaMemcpy(b->d_active, active.data(), sizeof(uint32_t) * active.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) b->dirty = false;
+    return e;
+}
+
+// Enqueues device step k of the current MCS of every active replica.
 cudaError_t enqueue_step(oct_batch *b, uint32_t k, cudaStream_t st) {
     for (int mode = 0; mode < 2; ++mode) {
         if (b->n_desc[mode] == 0) continue;
@@ -204,13 +373,19 @@ cudaError_t enqueue_step(oct_batch *b, uint32_t k, cudaStream_t st) {
     return cudaSuccess;
 }
 
+cudaError_t enqueue_advance(oct_batch *b, cudaStream_t st) {
+    if (b->n_active == 0) return cudaSuccess;
+    const int blocks = static_cast<int>(std::min<uint32_t>(1024u, (b->n_active + 255u) / 256u));
+    oct::batch_advance_kernel<<<blocks, 256, 0, st>>>(b->d_t, b->d_active, b->n_active);
+    return cudaGetLastError();
+}
+
 cudaError_t enqueue_mcs(oct_batch *b, cudaStream_t st) {
     for (uint32_t k = 0; k < 4; ++k) {
         cudaError_t e = enqueue_step(b, k, st);
         if (e != cudaSuccess) return e;
     }
-    oct::batch_advance_kernel<<<1, 1, 0, st>>>(b->d_t);
-    return cudaGetLastError();
+    return enqueue_advance(b, st);
 }
 
 int flush_batch_timing(oct_batch *b) {
@@ -222,6 +397,75 @@ int flush_batch_timing(oct_batch *b) {
         b->step_ms += ms;
     }
     b->ev_used = 0;
+    return OCT_OK;
+}
+
+bool valid_slot(const oct_batch *b, int64_t slot) {
+    return slot >= 0 && slot < static_cast<int64_t>(b->reps.size()) && b->used[slot];
+}
+
+int add_replica(oct_batch *b, const oct_replica *in, int64_t *slot_out) {
+    oct_replica R = *in;
+    int rc = check_replica(R);
+    if (rc) return rc;
+    int64_t slot;
+    if (!b->free_slots.empty()) {
+        slot = b->free_slots.back();
+        b->free_slots.pop_back();
+    } else {
+        slot = static_cast<int64_t>(b->reps.size());
+        BATCH_CUDA(grow_slots(b, static_cast<size_t>(slot) + 1));
+        b->reps.emplace_back();
+        b->lat.push_back(nullptr);
+        b->used.push_back(0);
+    }
+    const size_t bytes = static_cast<size_t>(R.L) * R.L / 4;
+    uint32_t *p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&p), bytes, b->pool, b->stream);
+    if (e != cudaSuccess) {
+        b->free_slots.push_back(slot);
+        return e == cudaErrorMemoryAllocation ? bfail(OCT_ENOMEM, "no device memory for the replica lattice")
+                                              : bfail(OCT_ECUDA, std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e));
+    }
+    b->reps[slot] = R;
+    b->lat[slot] = p;
+    b->used[slot] = 1;
+    BATCH_CUDA(oct::launch_init_flat(p, static_cast<uint32_t>(R.L), b->stream));
+    BATCH_CUDA(cudaMemsetAsync(b->d_t + slot, 0, sizeof(uint32_t), b->stream));
+    BATCH_CUDA(cudaMemsetAsync(b->counters + 2 * slot, 0, 2 * sizeof(unsigned long long), b->stream));
+    b->dirty = true;
+    if (slot_out) *slot_out = slot;
+    return OCT_OK;
+}
+
+int measure_slot(oct_batch *b, int64_t slot, oct_w2 *out) {
+    const int64_t L = b->reps[slot].L;
+    if (L > b->rows_cap) {
+        cudaFree(b->d_rows);
+        b->d_rows = nullptr;
+        b->rows_cap = 0;
+        BATCH_CUDA(cudaMalloc(&b->d_rows, sizeof(oct::W2RowSums) * L));
+        b->rows_cap = L;
+    }
+    auto *res = static_cast<oct::W2Result *>(b->h_small);
+    auto *cnt = reinterpret_cast<unsigned long long *>(static_cast<char *>(b->h_small) + 64);
+    auto *tt = reinterpret_cast<uint32_t *>(static_cast<char *>(b->h_small) + 96);
+    BATCH_CUDA(oct::launch_w2(b->lat[slot], static_cast<uint32_t>(L), b->d_rows, b->d_w2, b->stream));
+    BATCH_CUDA(cudaMemcpyAsync(res, b->d_w2, sizeof(oct::W2Result), cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(cudaMemcpyAsync(cnt, b->counters + 2 * slot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(cudaMemcpyAsync(tt, b->d_t + slot, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(cudaStreamSynchronize(b->stream));
+    const __int128 N = static_cast<__int128>(L) * L;
+    const __int128 S2 = static_cast<__int128>((static_cast<unsigned __int128>(res->s2_hi) << 64) | res->s2_lo);
+    const __int128 num = N * S2 - static_cast<__int128>(res->s1) * res->s1;
+    out->t = static_cast<int64_t>(*tt);
+    out->n_sites = static_cast<int64_t>(N);
+    out->s1 = res->s1;
+    out->s2_lo = res->s2_lo;
+    out->s2_hi = res->s2_hi;
+    out->net_flips = static_cast<int64_t>(cnt[0]);
+    out->hmax = res->hmax;
+    out->w2 = static_cast<double>(num) / (static_cast<double>(N) * static_cast<double>(N));
     return OCT_OK;
 }
 
@@ -239,38 +483,14 @@ int oct_replica_seed(uint64_t master_seed, uint32_t r, uint64_t *seed) {
 }
 
 int oct_batch_create(int64_t n, const oct_replica *reps, void *stream, oct_batch **out) {
-    if (n < 1 || !reps || !out) return bfail(OCT_EINVAL, "need n >= 1 replicas and non-NULL arrays");
+    if (n < 0 || (n > 0 && !reps) || !out) return bfail(OCT_EINVAL, "need n >= 0 replicas and non-NULL arrays");
+    for (int64_t r = 0; r < n; ++r) {
+        oct_replica R = reps[r];
+        int rc = check_replica(R);
+        if (rc) return rc;
+    }
     oct_batch *b = new (std::nothrow) oct_batch();
     if (!b) return bfail(OCT_ENOMEM, "host allocation failed");
-    b->reps.assign(reps, reps + n);
-    // validate and fill defaults
-    size_t total_words = 0;
-    for (int64_t r = 0; r < n; ++r) {
-        oct_replica &R = b->reps[r];
-        if (R.L < 64 || R.L > 16384 || R.L % 64) {
-            delete b;
-            return bfail(OCT_EINVAL, "replica L must be a multiple of 64 in [64, 16384]");
-        }
-        if (!(R.p >= 0.0 && R.p <= 1.0 && R.q >= 0.0 && R.q <= 1.0)) {
-            delete b;
-            return bfail(OCT_EINVAL, "replica p and q must lie in [0, 1]");
-        }
-        if (R.Bx == 0 && R.By == 0) {
-            R.Bx = (R.L % 128 == 0) ? 64 : 32;
-            R.By = R.Bx;
-        }
-        const int GX = R.Bx / 32, GY = R.By / 16, G = GX * GY;
-        if (R.Bx < 32 || R.By < 16 || R.Bx % 32 || R.By % 16 || R.L % (2 * R.Bx) || R.L % (2 * R.By) ||
-            (GX & (GX - 1)) || (GY & (GY - 1)) || G > 32) {
-            delete b;
-            return bfail(OCT_EINVAL, "replica sub-tile must be a power-of-two number (at most 32) of "
-                                     "32x16-site groups in each direction and divide L/2");
-        }
-        b->lat_offset.push_back(total_words);
-        const size_t words = static_cast<size_t>(R.L) * R.L / 16;
-        total_words += (words + 63) & ~size_t{63};
-        b->max_L = std::max<int64_t>(b->max_L, R.L);
-    }
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) {
         if (stream) {
@@ -280,91 +500,28 @@ int oct_batch_create(int64_t n, const oct_replica *reps, void *stream, oct_batch
             b->own_stream = (e == cudaSuccess);
         }
     }
-    // replica table and work list
-    std::vector<oct::ReplicaDev> rd(n);
-    std::vector<oct::BatchItem> items;
-    std::vector<oct::WarpDesc> descs;
-    if (e == cudaSuccess) e = cudaMalloc(&b->lat, total_words * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&b->counters, sizeof(unsigned long long) * 2 * n);
     if (e == cudaSuccess) {
-        // buckets: (mode, lane columns GX, lane rows GY) -> items
-        std::vector<oct::BatchItem> bucket[2][6][6];
-        for (int64_t r = 0; r < n; ++r) {
-            const oct_replica &R = b->reps[r];
-            oct::ReplicaDev &D = rd[r];
-            D.lat = b->lat + b->lat_offset[r];
-            D.counters = b->counters + 2 * r;
-            D.L = static_cast<uint32_t>(R.L);
-            D.wpr = static_cast<uint32_t>(R.L / 32);
-            D.Bx = static_cast<uint32_t>(R.Bx);
-            D.By = static_cast<uint32_t>(R.By);
-            D.GX = static_cast<uint32_t>(R.Bx / 32);
-            D.GY = static_cast<uint32_t>(R.By / 16);
-            D.tiles_x = static_cast<uint32_t>(R.L / (2 * R.Bx));
-            D.tiles_y = static_cast<uint32_t>(R.L / (2 * R.By));
-            D.k0 = static_cast<uint32_t>(R.seed & 0xFFFFFFFFu);
-            D.k1 = static_cast<uint32_t>(R.seed >> 32);
-            const bool pr = R.p > 0.0 && R.p < 1.0, qr = R.q > 0.0 && R.q < 1.0;
-            D.thr_p = pr ? thr32(R.p) : 0u;
-            D.thr_q = qr ? thr32(R.q) : 0u;
-            D.p_always = (R.p == 1.0) ? 0xFFFFFFFFu : 0u;
-            D.q_always = (R.q == 1.0) ? 0xFFFFFFFFu : 0u;
-            D.p_random = pr ? 0xFFFFFFFFu : 0u;
-            D.q_random = qr ? 0xFFFFFFFFu : 0u;
-            const int mode = (pr || qr) ? 1 : 0;
-            int gxi = 0, gyi = 0;
-            while ((1u << gxi) < D.GX) ++gxi;
-            while ((1u << gyi) < D.GY) ++gyi;
-            for (uint32_t T = 0; T < D.tiles_x * D.tiles_y; ++T)
-                bucket[mode][gxi][gyi].push_back({static_cast<uint32_t>(r), T});
-        }
-        for (int mode = 0; mode < 2; ++mode) {
-            b->desc_first[mode] = static_cast<uint32_t>(descs.size());
-            for (int gxi = 5; gxi >= 0; --gxi)
-                for (int gyi = 5; gyi >= 0; --gyi) {
-                    const uint32_t GX = 1u << gxi, G = GX << gyi;
-                    if (G > 32u) continue;
-                    const uint32_t per = 32u / G;
-                    auto &bk = bucket[mode][gxi][gyi];
-                    for (size_t i = 0; i < bk.size(); i += per) {
-                        oct::WarpDesc d;
-                        d.first = static_cast<uint32_t>(items.size());
-                        d.n = static_cast<uint32_t>(std::min<size_t>(per, bk.size() - i));
-                        d.G = G;
-                        d.GX = GX;
-                        for (uint32_t j = 0; j < d.n; ++j) items.push_back(bk[i + j]);
-                        descs.push_back(d);
-                    }
-                }
-            b->n_desc[mode] = static_cast<uint32_t>(descs.size()) - b->desc_first[mode];
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = b->device;
+        e = cudaMemPoolCreate(&b->pool, &props);
+        if (e == cudaSuccess) {
+            uint64_t keep = ~uint64_t{0};  // keep freed lattices in the pool for reuse
+            e = cudaMemPoolSetAttribute(b->pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
     }
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_reps, sizeof(oct::ReplicaDev) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(oct::BatchItem) * std::max<size_t>(1, items.size()));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_descs, sizeof(oct::WarpDesc) * std::max<size_t>(1, descs.size()));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(uint32_t) * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_t, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_rows, sizeof(oct::W2RowSums) * b->max_L);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_w2, sizeof(oct::W2Result));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_small, 256);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_reps, rd.data(), sizeof(oct::ReplicaDev) * n, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess && !items.empty())
-        e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(oct::BatchItem) * items.size(),
-                            cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess && !descs.empty())
-        e = cudaMemcpyAsync(b->d_descs, descs.data(), sizeof(oct::WarpDesc) * descs.size(),
-                            cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_t, 0, sizeof(uint32_t), b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long) * 2 * n, b->stream);
-    for (int64_t r = 0; r < n && e == cudaSuccess; ++r)
-        e = oct::launch_init_flat(b->lat + b->lat_offset[r], static_cast<uint32_t>(b->reps[r].L), b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e == cudaSuccess) {
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
         b->grid = sms * oct::kBatchBlocksPerSM;
     }
+    if (e == cudaSuccess) e = grow_slots(b, static_cast<size_t>(std::max<int64_t>(n, 1)));
     if (e != cudaSuccess) {
         const bool oom = (e == cudaErrorMemoryAllocation);
         batch_free(b);
@@ -372,14 +529,49 @@ int oct_batch_create(int64_t n, const oct_replica *reps, void *stream, oct_batch
         return oom ? bfail(OCT_ENOMEM, "device allocation failed")
                    : bfail(OCT_ECUDA, std::string("oct_batch_create: ") + cudaGetErrorString(e));
     }
+    for (int64_t r = 0; r < n; ++r) {
+        int rc = add_replica(b, &reps[r], nullptr);
+        if (rc) {
+            batch_free(b);
+            delete b;
+            return rc;
+        }
+    }
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        batch_free(b);
+        delete b;
+        return bfail(OCT_ECUDA, "oct_batch_create: initialisation failed");
+    }
     *out = b;
+    return OCT_OK;
+}
+
+int oct_batch_add(oct_batch *b, const oct_replica *r, int64_t *slot) {
+    if (!b || !r) return bfail(OCT_EINVAL, "NULL argument");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    return add_replica(b, r, slot);
+}
+
+int oct_batch_remove(oct_batch *b, int64_t slot) {
+    if (!b || !valid_slot(b, slot)) return bfail(OCT_EINVAL, "no replica in that slot");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    BATCH_CUDA(cudaFreeAsync(b->lat[slot], b->stream));
+    b->lat[slot] = nullptr;
+    b->used[slot] = 0;
+    b->free_slots.push_back(slot);
+    b->dirty = true;
     return OCT_OK;
 }
 
 int oct_batch_run(oct_batch *b, int64_t n) {
     if (!b) return bfail(OCT_EINVAL, "NULL batch");
-    if (n < 0 || b->t + static_cast<uint64_t>(n) > 0xFFFFFFFFull) return bfail(OCT_EINVAL, "bad MCS count");
+    if (n < 0) return bfail(OCT_EINVAL, "bad MCS count");
     BATCH_CUDA(cudaSetDevice(b->device));
+    if (b->dirty) BATCH_CUDA(rebuild(b));
+    if (b->n_active == 0 || n == 0) {
+        b->ticks += static_cast<uint64_t>(n);
+        return OCT_OK;
+    }
     if (b->timing) {
         // launch by launch, each device step bracketed by events
         for (int64_t i = 0; i < n; ++i) {
@@ -394,12 +586,11 @@ int oct_batch_run(oct_batch *b, int64_t n) {
                 ++b->ev_used;
                 ++b->step_launches;
             }
-            oct::batch_advance_kernel<<<1, 1, 0, b->stream>>>(b->d_t);
-            BATCH_CUDA(cudaGetLastError());
+            BATCH_CUDA(enqueue_advance(b, b->stream));
         }
     } else {
         if (!b->exec) {
-            // one MCS captured once on a private stream, replayed on the batch's stream
+            // one MCS captured on a private stream, replayed on the batch's stream
             cudaStream_t cap = nullptr;
             BATCH_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
             cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
@@ -414,62 +605,63 @@ int oct_batch_run(oct_batch *b, int64_t n) {
         }
         for (int64_t i = 0; i < n; ++i) BATCH_CUDA(cudaGraphLaunch(b->exec, b->stream));
     }
-    b->t += static_cast<uint64_t>(n);
+    b->ticks += static_cast<uint64_t>(n);
     return OCT_OK;
 }
 
 int oct_batch_measure_w2(oct_batch *b, oct_w2 *out, int64_t n) {
-    if (!b || !out || n != static_cast<int64_t>(b->reps.size())) return bfail(OCT_EINVAL, "out must hold one entry per replica");
+    if (!b || !out || n != static_cast<int64_t>(b->reps.size()))
+        return bfail(OCT_EINVAL, "out must hold one entry per slot");
     BATCH_CUDA(cudaSetDevice(b->device));
-    auto *res = static_cast<oct::W2Result *>(b->h_small);
-    std::vector<unsigned long long> cnt(2 * b->reps.size());
-    BATCH_CUDA(cudaMemcpyAsync(cnt.data(), b->counters, sizeof(unsigned long long) * cnt.size(),
-                               cudaMemcpyDeviceToHost, b->stream));
-    for (size_t r = 0; r < b->reps.size(); ++r) {
-        const int64_t L = b->reps[r].L;
-        BATCH_CUDA(oct::launch_w2(b->lat + b->lat_offset[r], static_cast<uint32_t>(L), b->d_rows, b->d_w2, b->stream));
-        BATCH_CUDA(cudaMemcpyAsync(res, b->d_w2, sizeof(oct::W2Result), cudaMemcpyDeviceToHost, b->stream));
-        BATCH_CUDA(cudaStreamSynchronize(b->stream));
-        const __int128 N = static_cast<__int128>(L) * L;
-        const __int128 S2 = static_cast<__int128>((static_cast<unsigned __int128>(res->s2_hi) << 64) | res->s2_lo);
-        const __int128 num = N * S2 - static_cast<__int128>(res->s1) * res->s1;
-        out[r].t = static_cast<int64_t>(b->t);
-        out[r].n_sites = static_cast<int64_t>(N);
-        out[r].s1 = res->s1;
-        out[r].s2_lo = res->s2_lo;
-        out[r].s2_hi = res->s2_hi;
-        out[r].net_flips = static_cast<int64_t>(cnt[2 * r]);
-        out[r].hmax = res->hmax;
-        out[r].w2 = static_cast<double>(num) / (static_cast<double>(N) * static_cast<double>(N));
+    for (int64_t slot = 0; slot < n; ++slot) {
+        if (!b->used[slot]) {
+            std::memset(&out[slot], 0, sizeof(oct_w2));
+            continue;
+        }
+        int rc = measure_slot(b, slot, &out[slot]);
+        if (rc) return rc;
     }
     return OCT_OK;
 }
 
-int oct_batch_get_planes(oct_batch *b, int64_t r, uint32_t *host, size_t words) {
-    if (!b || !host || r < 0 || r >= static_cast<int64_t>(b->reps.size())) return bfail(OCT_EINVAL, "bad replica");
-    const int64_t L = b->reps[r].L;
+int oct_batch_measure_slot(oct_batch *b, int64_t slot, oct_w2 *out) {
+    if (!b || !out || !valid_slot(b, slot)) return bfail(OCT_EINVAL, "no replica in that slot");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    return measure_slot(b, slot, out);
+}
+
+int oct_batch_get_planes(oct_batch *b, int64_t slot, uint32_t *host, size_t words) {
+    if (!b || !host || !valid_slot(b, slot)) return bfail(OCT_EINVAL, "no replica in that slot");
+    const int64_t L = b->reps[slot].L;
     if (words != static_cast<size_t>(L) * L / 16) return bfail(OCT_EINVAL, "words must equal L*L/16");
     BATCH_CUDA(cudaSetDevice(b->device));
-    BATCH_CUDA(cudaMemcpyAsync(host, b->lat + b->lat_offset[r], words * 4, cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(cudaMemcpyAsync(host, b->lat[slot], words * 4, cudaMemcpyDeviceToHost, b->stream));
     BATCH_CUDA(cudaStreamSynchronize(b->stream));
     return OCT_OK;
 }
 
-int oct_batch_get_stats(oct_batch *b, int64_t *t, int64_t *n_replicas, int64_t *total_sites, int64_t *draws) {
+int oct_batch_get_stats(oct_batch *b, int64_t *ticks, int64_t *n_active, int64_t *active_sites, int64_t *draws) {
     if (!b) return bfail(OCT_EINVAL, "NULL batch");
     BATCH_CUDA(cudaSetDevice(b->device));
-    int64_t sites = 0;
-    for (const auto &R : b->reps) sites += R.L * R.L;
-    if (t) *t = static_cast<int64_t>(b->t);
-    if (n_replicas) *n_replicas = static_cast<int64_t>(b->reps.size());
-    if (total_sites) *total_sites = sites;
+    int64_t sites = 0, na = 0;
+    for (size_t s = 0; s < b->reps.size(); ++s)
+        if (b->used[s]) {
+            sites += b->reps[s].L * b->reps[s].L;
+            ++na;
+        }
+    if (ticks) *ticks = static_cast<int64_t>(b->ticks);
+    if (n_active) *n_active = na;
+    if (active_sites) *active_sites = sites;
     if (draws) {
         std::vector<unsigned long long> cnt(2 * b->reps.size());
-        BATCH_CUDA(cudaMemcpyAsync(cnt.data(), b->counters, sizeof(unsigned long long) * cnt.size(),
-                                   cudaMemcpyDeviceToHost, b->stream));
-        BATCH_CUDA(cudaStreamSynchronize(b->stream));
+        if (!cnt.empty()) {
+            BATCH_CUDA(cudaMemcpyAsync(cnt.data(), b->counters, sizeof(unsigned long long) * cnt.size(),
+                                       cudaMemcpyDeviceToHost, b->stream));
+            BATCH_CUDA(cudaStreamSynchronize(b->stream));
+        }
         int64_t d = 0;
-        for (size_t r = 0; r < b->reps.size(); ++r) d += static_cast<int64_t>(cnt[2 * r + 1]);
+        for (size_t s = 0; s < b->reps.size(); ++s)
+            if (b->used[s]) d += static_cast<int64_t>(cnt[2 * s + 1]);
         *draws = d;
     }
     return OCT_OK;

@@ -1,0 +1,246 @@
+"""Continuous-batching serving loop for octahedron-model simulation jobs.
+
+A job is one realization (L, p, q, seed) to run for t_max MCS, with W^2 sent
+back at log-spaced times.  Jobs arrive over time (e.g. as a Poisson stream).
+The engine keeps one batch (``oct_batch_*`` in include/oct.h) whose replicas
+are the running jobs:
+
+* admission: a waiting job that has arrived joins the batch as soon as its
+  lattice fits the HBM budget (first come, first served);
+* every tick advances all running jobs together by the same number of MCS
+  (up to the next measurement or finish among them, at most ``max_chunk``),
+  so work of jobs that arrived at different times overlaps on the device;
+* at a job's measurement times its exact W^2 is computed on the device and
+  handed to the ``on_result`` callback (streamed back);
+* a job that reaches t_max leaves the batch and returns its memory.
+
+Each job's trajectory is the same as running it alone: its random numbers
+depend only on its own key and its own time, not on the mix.
+"""
+from __future__ import annotations
+
+import bisect
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+PQ_SET = [(1.0, 0.0), (0.8, 0.2), (0.5, 0.5)]
+
+
+@dataclass
+class Job:
+    jid: int
+    L: int
+    p: float
+    q: float
+    seed: int
+    t_max: int
+    arrival: float = 0.0
+    measure_at: list = field(default_factory=list)
+    # set by the engine
+    slot: int = -1
+    t: int = 0
+    admitted: float | None = None
+    done: float | None = None
+    results: list = field(default_factory=list)  # (t, s1, s2, w2, net_flips)
+
+    @property
+    def attempts(self) -> int:
+        return self.L * self.L * self.t_max
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def footprint(L: int) -> int:
+    """Device bytes a job holds while running: its packed lattice."""
+    return L * L // 4
+
+
+def log_times(t_max: int, n: int = 8):
+    """t = round(t_max^(i/(n-1))), i = 0..n-1, made strictly increasing, ending at t_max."""
+    out = []
+    for i in range(n):
+        t = max(1, int(round(t_max ** (i / (n - 1))))) if n > 1 else t_max
+        if out and t <= out[-1]:
+            t = out[-1] + 1
+        if t > t_max:
+            break
+        out.append(t)
+    if not out or out[-1] != t_max:
+        out.append(t_max)
+    return out
+
+
+def poisson_jobs(n: int, rate: float, master_seed: int = 1, L_range=(128, 16384),
+                 t_range=(10, 10_000), seed_fn=None, n_measure: int = 8):
+    """n jobs with exponential inter-arrival times (rate jobs/s), L log-uniform
+    in L_range rounded to a multiple of 128, t_max log-uniform in t_range,
+    (p, q) uniform over PQ_SET, keys from seed_fn(master_seed, jid)."""
+    import numpy as np
+    rng = np.random.default_rng(master_seed)
+    t = 0.0
+    jobs = []
+    for jid in range(n):
+        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        L = math.exp(rng.uniform(math.log(L_range[0]), math.log(L_range[1])))
+        L = int(min(L_range[1], max(L_range[0], 128 * round(L / 128))))
+        t_max = int(round(math.exp(rng.uniform(math.log(t_range[0]), math.log(t_range[1])))))
+        p, q = PQ_SET[int(rng.integers(0, len(PQ_SET)))]
+        seed = seed_fn(master_seed, jid) if seed_fn else (master_seed << 32) + jid
+        jobs.append(Job(jid, L, p, q, seed, t_max, arrival=t, measure_at=log_times(t_max, n_measure)))
+    return jobs
+
+
+def expected_work(L_range=(128, 16384), t_range=(10, 10_000)) -> float:
+    """E[L^2 * t_max] of poisson_jobs (attempts per job), ignoring rounding."""
+    a, b = L_range
+    eL2 = (b * b - a * a) / (2.0 * math.log(b / a))
+    c, d = t_range
+    et = (d - c) / math.log(d / c)
+    return eL2 * et
+
+
+class ServingEngine:
+    """Runs jobs through one dynamic batch.  ``batch`` must offer add(job),
+    remove(slot), run(n) and measure(slot) -> (t, s1, s2, w2, net_flips);
+    by default it is the GPU batch of this package."""
+
+    def __init__(self, hbm_budget: int, batch=None, stream=None, max_chunk: int = 64,
+                 on_result=None, clock=time.perf_counter):
+        self.budget = int(hbm_budget)
+        self.used = 0
+        self.batch = batch if batch is not None else GpuBatch(stream)
+        self.max_chunk = max_chunk
+        self.on_result = on_result
+        self.clock = clock
+        self.waiting: deque[Job] = deque()
+        self.running: dict[int, Job] = {}
+        self.finished: list[Job] = []
+        self.ticks = 0
+        self.mcs_attempts = 0
+
+    def submit(self, job: Job) -> None:
+        if footprint(job.L) > self.budget:
+            raise ValueError(f"job {job.jid} needs {footprint(job.L)} B, more than the budget")
+        self.waiting.append(job)
+
+    def _admit(self, now: float) -> None:
+        while self.waiting and self.waiting[0].arrival <= now:
+            job = self.waiting[0]
+            if self.used + footprint(job.L) > self.budget:
+                break  # first come, first served: later jobs wait behind it
+            self.waiting.popleft()
+            job.slot = self.batch.add(job)
+            job.admitted = now
+            job.t = 0
+            self.used += footprint(job.L)
+            self.running[job.slot] = job
+
+    def _chunk(self) -> int:
+        n = self.max_chunk
+        for job in self.running.values():
+            i = bisect.bisect_right(job.measure_at, job.t)
+            nxt = job.measure_at[i] if i < len(job.measure_at) else job.t_max
+            n = min(n, nxt - job.t)
+        return max(1, n)
+
+    def tick(self, now: float | None = None) -> bool:
+        """Admits arrived jobs and advances the running ones to their next
+        event.  Returns False if nothing was running."""
+        self._admit(self.clock() if now is None else now)
+        if not self.running:
+            return False
+        n = self._chunk()
+        self.batch.run(n)
+        self.ticks += 1
+        for slot, job in list(self.running.items()):
+            job.t += n
+            self.mcs_attempts += n * job.L * job.L
+            if job.t in job.measure_at:
+                res = self.batch.measure(slot)
+                assert res[0] == job.t, (res[0], job.t)
+                job.results.append(res)
+                if self.on_result:
+                    self.on_result(job, res)
+            if job.t >= job.t_max:
+                self.batch.remove(slot)
+                del self.running[slot]
+                self.used -= footprint(job.L)
+                job.done = self.clock() if now is None else now
+                self.finished.append(job)
+        return True
+
+    def run(self, jobs, realtime: bool = True, sleep=time.sleep) -> list[Job]:
+        """Serves jobs (sorted by arrival, times relative to the start).  In
+        real time a job becomes visible when the clock passes its arrival."""
+        t0 = self.clock()
+        for job in sorted(jobs, key=lambda j: j.arrival):
+            job.arrival += t0
+            self.submit(job)
+        while self.waiting or self.running:
+            now = self.clock()
+            if not self.tick(now) and self.waiting:
+                wait = self.waiting[0].arrival - self.clock()
+                if wait > 0 and realtime:
+                    sleep(min(wait, 0.05))
+                elif not realtime:
+                    self.clock_skip(self.waiting[0].arrival)
+        return self.finished
+
+    def clock_skip(self, t: float) -> None:
+        """Advances a virtual clock (only meaningful with an injected clock)."""
+        if hasattr(self.clock, "advance_to"):
+            self.clock.advance_to(t)
+
+
+def summary(jobs, wall_s: float) -> dict:
+    lat = sorted(j.latency for j in jobs)
+
+    def pct(x):
+        if not lat:
+            return None
+        i = min(len(lat) - 1, max(0, int(math.ceil(x / 100.0 * len(lat))) - 1))
+        return lat[i]
+
+    attempts = sum(j.attempts for j in jobs)
+    return {"jobs": len(jobs), "p50_latency_s": pct(50), "p99_latency_s": pct(99),
+            "attempts": attempts, "wall_s": wall_s, "attempts_per_ns": attempts / (wall_s * 1e9)}
+
+
+class GpuBatch:
+    """Adapter from the engine's batch interface to the C ABI batch."""
+
+    def __init__(self, stream=None):
+        from . import _address, _lib
+        self._lib = _lib
+        self._keep = stream
+        self.h = _lib.oct_batch_create([], _address(stream, "cuda_stream"))
+
+    def add(self, job: Job) -> int:
+        r = self._lib.oct_replica()
+        r.L, r.p, r.q, r.seed = job.L, job.p, job.q, job.seed
+        return self._lib.oct_batch_add(self.h, r)
+
+    def remove(self, slot: int) -> None:
+        self._lib.oct_batch_remove(self.h, slot)
+
+    def run(self, n: int) -> None:
+        self._lib.oct_batch_run(self.h, n)
+
+    def measure(self, slot: int):
+        m = self._lib.oct_batch_measure_slot(self.h, slot)
+        return (m.t, m.s1, m.s2, m.w2, m.net_flips)
+
+    def close(self) -> None:
+        if self.h:
+            self._lib.oct_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

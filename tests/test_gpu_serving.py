@@ -1,0 +1,38 @@
+"""Serving on the GPU: jobs that arrive while others run join the batch, and
+every job's streamed W^2(t) equals, exactly, the same job run alone."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1705_01022_gb300 as g
+    g.build()
+    return g
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix(g):
+    from paper_1705_01022_gb300 import _lib, serve
+    jobs = serve.poisson_jobs(14, rate=400.0, master_seed=5, L_range=(128, 1024),
+                              t_range=(5, 60), seed_fn=_lib.oct_replica_seed)
+    # a budget that holds only part of the jobs at a time forces staggered admission
+    budget = 3 * serve.footprint(1024)
+    streamed = []
+    eng = serve.ServingEngine(budget, max_chunk=8, on_result=lambda j, r: streamed.append((j.jid, r)))
+    done = eng.run(jobs)
+    assert len(done) == len(jobs) and eng.used == 0
+    assert len(streamed) == sum(len(j.measure_at) for j in jobs)
+    for job in done:
+        with g.Simulation(job.L, job.p, job.q, job.seed, Bx=64, By=64) as sim:
+            t = 0
+            for (tt, s1, s2, w2, net) in job.results:
+                sim.run(tt - t)
+                t = tt
+                m = sim.measure()
+                assert (tt, s1, s2, w2, net) == (m.t, m.s1, m.s2, m.w2, m.net_flips), job.jid
+    # work of different jobs overlapped: some job was admitted before another finished
+    by_adm = sorted(done, key=lambda j: j.admitted)
+    assert any(b.admitted < a.done for a, b in zip(by_adm, by_adm[1:]))
+    s = serve.summary(done, max(j.done for j in done) - min(j.arrival for j in done))
+    assert s["p50_latency_s"] > 0

@@ -26,7 +26,7 @@ _SRC = os.path.join(_HERE, "oct_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboct_oracle.so")
 _lib = None
 
-TAG_MCS, TAG_SET, TAG_SITE, TAG_ACC, TAG_SEQ, TAG_REPLICA = 1, 2, 3, 4, 5, 6
+TAG_MCS, TAG_SET, TAG_SITE, TAG_ACC, TAG_SEQ, TAG_REPLICA, TAG_TAIL = 1, 2, 3, 4, 5, 6, 7
 
 
 def build(force: bool = False) -> str:
@@ -100,8 +100,10 @@ def lib():
         L.oo_pack_canonical.argtypes = [i64, _P_u8, _P_u8, _P_u32]
         L.oo_unpack_canonical.argtypes = [i64, _P_u32, _P_u8, _P_u8]
         L.oo_dtrdt_many.argtypes = [ctypes.POINTER(_Params), u64, i64, u32, _P_u8, _P_u8]
-        L.oo_dtrdt_acc_uniform.argtypes = [u64, u32, u32, u32, u32, u32, ctypes.c_int]
-        L.oo_dtrdt_acc_uniform.restype = u32
+        L.oo_dtrdt_acc_prefix.argtypes = [u64, u32, u32, u32, u32, u32, ctypes.c_int]
+        L.oo_dtrdt_acc_prefix.restype = u32
+        L.oo_dtrdt_tail_word.argtypes = [u64, u32, u32, u32, u32]
+        L.oo_dtrdt_tail_word.restype = u32
         L.oo_w2_sums_planar.argtypes = [i64, _P_u32, P_i64, P_u64, P_u64, P_i64]
         L.oo_invariants_planar.argtypes = [i64, _P_u32, i64, i64]
         L.oo_replica_seed.argtypes = [u64, u32]
@@ -193,9 +195,14 @@ def dtrdt_many(prm: Params, seed0: int, n_runs: int, n_mcs: int):
     return X, Y
 
 
-def acc_uniform(seed: int, t: int, k: int, T: int, g: int, s: int, pos: int) -> int:
-    """The acceptance uniform of the thread cell at bit position pos of group g."""
-    return int(lib().oo_dtrdt_acc_uniform(seed, t, k, T, g, s, pos))
+def acc_prefix(seed: int, t: int, k: int, T: int, g: int, s: int, pos: int) -> int:
+    """Bits 31..28 of the acceptance uniform of the thread cell at position pos of group g."""
+    return int(lib().oo_dtrdt_acc_prefix(seed, t, k, T, g, s, pos))
+
+
+def tail_word(seed: int, t: int, k: int, T: int, i: int) -> int:
+    """Word i of a sub-tile's tail stream in device step k of MCS t."""
+    return int(lib().oo_dtrdt_tail_word(seed, t, k, T, i))
 
 
 def dtrdt_mcs_window(Xw, Yw, prm: Params, t: int, wx: int, wy: int) -> int:

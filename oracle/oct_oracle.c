@@ -251,28 +251,61 @@ static void touch(conflict_t *cf, int64_t bit, int64_t tile, int64_t tc) {
     cf->step_owner[bit] = tc;
 }
 
-/* The 32 level words of the acceptance stream of group g at collective
- * step s: word l is word l%4 of Philox(seed, (t, k|(s*8+l/4)<<2, T, ACC<<28|g)). */
+/* Acceptance uniforms (reading fixed by the schedule specification).  The
+ * uniform u of a thread cell's attempt is 32 bits, most significant first:
+ *   - bits 31..28: "level" bits, positional per group: bit (31-l) of u is bit
+ *     pos = 4j+m of word l (l = 0..3) of Philox(seed, (t, k|(s*8)<<2, T, ACC<<28|g));
+ *   - bits 27..0: only needed when bits 31..28 equal those of P32 (otherwise
+ *     u < P32 is already decided); they are the top 28 bits of the next word
+ *     of the sub-tile's tail stream, word i = word i%4 of
+ *     Philox(seed, (t, k|(i/4)<<2, T, TAIL<<28)), i counted from 0 at the start
+ *     of each device step; within a collective step the candidates that need
+ *     one take words in order of group g, then position pos. */
 static void acc_level_words(const uint32_t key[2], uint32_t t, uint32_t k, uint32_t T, uint32_t g,
-                            uint32_t s, uint32_t acc_w[32]) {
-    for (uint32_t lb = 0; lb < 8; ++lb)
-        philox_at(key, t, k | ((s * 8 + lb) << 2), T, (OO_TAG_ACC << 28) | g, &acc_w[4 * lb]);
+                            uint32_t s, uint32_t lw[4]) {
+    philox_at(key, t, k | ((s * 8) << 2), T, (OO_TAG_ACC << 28) | g, lw);
 }
 
-/* The uniform of the thread cell at bit position pos of its group: bit
- * (31-l) of u is bit pos of level word l (most significant bit first). */
-static uint32_t acc_uniform(const uint32_t acc_w[32], int pos) {
-    uint32_t u = 0;
-    for (int l = 0; l < 32; ++l) u |= ((acc_w[l] >> pos) & 1u) << (31 - l);
-    return u;
+/* Bits 31..28 of the uniform of the thread cell at position pos. */
+static uint32_t acc_prefix(const uint32_t lw[4], int pos) {
+    uint32_t hi = 0;
+    for (int l = 0; l < 4; ++l) hi |= ((lw[l] >> pos) & 1u) << (3 - l);
+    return hi;
 }
 
-uint32_t oo_dtrdt_acc_uniform(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t g,
-                              uint32_t s, int pos) {
-    uint32_t key[2], w[32];
+static uint32_t tail_word(const uint32_t key[2], uint32_t t, uint32_t k, uint32_t T, uint32_t i) {
+    uint32_t w[4];
+    philox_at(key, t, k | ((i / 4) << 2), T, OO_TAG_TAIL << 28, w);
+    return w[i % 4];
+}
+
+uint32_t oo_dtrdt_acc_prefix(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t g,
+                             uint32_t s, int pos) {
+    uint32_t key[2], w[4];
     seed_key(seed, key);
     acc_level_words(key, t, k, T, g, s, w);
-    return acc_uniform(w, pos);
+    return acc_prefix(w, pos);
+}
+
+uint32_t oo_dtrdt_tail_word(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t i) {
+    uint32_t key[2];
+    seed_key(seed, key);
+    return tail_word(key, t, k, T, i);
+}
+
+typedef struct {
+    int64_t is, ir, iu; /* view indices of s, s+x, s+y */
+    int kind;           /* +1 minimum, -1 maximum */
+    uint32_t g;
+    int pos;
+    int decided;        /* 1 accepted, 0 rejected, -1 needs a tail word */
+    uint64_t thr;
+} attempt_t;
+
+static int by_group_then_position(const void *pa, const void *pb) {
+    const attempt_t *a = (const attempt_t *)pa, *b = (const attempt_t *)pb;
+    if (a->g != b->g) return a->g < b->g ? -1 : 1;
+    return (a->pos > b->pos) - (a->pos < b->pos);
 }
 
 /* Block layer on one sub-tile: single-hit double tiling.
@@ -283,7 +316,9 @@ uint32_t oo_dtrdt_acc_uniform(uint64_t seed, uint32_t t, uint32_t k, uint32_t T,
  * step: the block draws d uniformly (with replacement, not a permutation),
  * every TC performs exactly one attempt at a uniformly chosen site of its
  * sub-cell d, then all synchronise.  cx*cy collective steps make one sweep
- * of the sub-tile (Bx*By attempts).
+ * of the sub-tile (Bx*By attempts).  Attempts of one step never share a slope
+ * bit, so every decision can be taken on the state before the step and the
+ * flips applied afterwards.
  *
  * Random streams (reading fixed by the schedule specification):
  *   set draw for step s : word (s%64)/16 of Philox(seed, (t, k|(s/64)<<2, T, SET<<28)),
@@ -294,8 +329,7 @@ uint32_t oo_dtrdt_acc_uniform(uint64_t seed, uint32_t t, uint32_t k, uint32_t T,
  *   site draw           : word m of Philox(seed, (t, k|(s/spw)<<2, T, SITE<<28|g)),
  *                         bits fw*j + (s%spw)*(fw/spw) .. + bpt-1, low log2(cx/2)
  *                         bits = x offset, the rest = y offset.
- *   acceptance uniform  : bit (31-l) of u is bit (4j+m) of word l%4 of
- *                         Philox(seed, (t, k|(s*8+l/4)<<2, T, ACC<<28|g)).
+ *   acceptance uniform  : see acc_level_words / tail_word above.
  */
 static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, uint32_t k,
                         uint32_t T, int64_t x0, int64_t y0, view_t *v, int64_t *net,
@@ -314,6 +348,9 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
     const uint64_t thr_p = oo_threshold32(P->p), thr_q = oo_threshold32(P->q);
     const int p_random = P->p > 0.0 && P->p < 1.0;
     const int q_random = P->q > 0.0 && P->q < 1.0;
+    attempt_t *att = (attempt_t *)malloc(sizeof(attempt_t) * (size_t)((Bx / cx) * (By / cy)));
+    attempt_t *tied = (attempt_t *)malloc(sizeof(attempt_t) * (size_t)((Bx / cx) * (By / cy)));
+    uint32_t tail_next = 0; /* tail-stream words used so far in this device step */
 
     for (int64_t s = 0; s < n_steps; ++s) {
         uint32_t sw[4];
@@ -321,7 +358,9 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
         const int d = (int)((sw[(s % 64) / 16] >> (2 * (s % 16))) & 3u);
         const int64_t dx = d & 1, dy = d >> 1;
         if (cf) cf->step_serial++;
+        int64_t na = 0;
 
+        /* 1: every thread cell's attempt on the state before the step */
         for (int64_t gr = 0; gr < group_rows; ++gr) {
             for (int64_t bc = 0; bc < band_cols; ++bc) {
                 const uint32_t g = (uint32_t)(gr * band_cols + bc);
@@ -329,8 +368,8 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
                 if (bpt > 0)
                     philox_at(key, t, k | (uint32_t)((s / spw) << 2), T,
                               (OO_TAG_SITE << 28) | g, site_w);
-                int acc_ready = 0;
-                uint32_t acc_w[32];
+                uint32_t lw[4];
+                acc_level_words(key, t, k, T, g, (uint32_t)s, lw);
                 for (int64_t m = 0; m < 4; ++m) {
                     const int64_t c = 4 * gr + m; /* TC row */
                     if (c >= tc_rows) break;
@@ -364,25 +403,49 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
                         else if (v->X[is] == 1 && v->X[ir] == 0 && v->Y[is] == 1 && v->Y[iu] == 0)
                             kind = -1;
                         if (kind == 0) continue;
-                        uint32_t u = 0;
-                        if ((kind > 0 && p_random) || (kind < 0 && q_random)) {
-                            if (!acc_ready) {
-                                acc_level_words(key, t, k, T, g, (uint32_t)s, acc_w);
-                                acc_ready = 1;
-                            }
-                            u = acc_uniform(acc_w, (int)(4 * j + m));
+                        attempt_t *A = &att[na++];
+                        A->is = is;
+                        A->ir = ir;
+                        A->iu = iu;
+                        A->kind = kind;
+                        A->g = g;
+                        A->pos = (int)(4 * j + m);
+                        A->thr = kind > 0 ? thr_p : thr_q;
+                        const int random = kind > 0 ? p_random : q_random;
+                        if (!random) {
+                            A->decided = A->thr > 0 ? 1 : 0; /* probability 1 or 0 */
+                        } else {
+                            /* u < P32 from the four leading bits unless they tie */
+                            const uint32_t hi = acc_prefix(lw, A->pos);
+                            const uint32_t thr_hi = (uint32_t)(A->thr >> 28);
+                            A->decided = hi < thr_hi ? 1 : (hi > thr_hi ? 0 : -1);
                         }
-                        if ((uint64_t)u >= (kind > 0 ? thr_p : thr_q)) continue;
-                        v->X[is] ^= 1;
-                        v->X[ir] ^= 1;
-                        v->Y[is] ^= 1;
-                        v->Y[iu] ^= 1;
-                        *net += kind;
                     }
                 }
             }
         }
+        /* 2: ties take tail words in order of group, then position */
+        int64_t nt = 0;
+        for (int64_t i = 0; i < na; ++i)
+            if (att[i].decided < 0) tied[nt++] = att[i];
+        qsort(tied, (size_t)nt, sizeof(attempt_t), by_group_then_position);
+        for (int64_t i = 0; i < nt; ++i) {
+            const uint32_t low28 = tail_word(key, t, k, T, tail_next++) >> 4;
+            tied[i].decided = (uint64_t)low28 < (tied[i].thr & 0x0FFFFFFFu) ? 1 : 0;
+        }
+        /* 3: apply the accepted flips (no two share a bit) */
+        for (int64_t i = 0; i < na + nt; ++i) {
+            const attempt_t *A = i < na ? &att[i] : &tied[i - na];
+            if (A->decided != 1) continue;
+            v->X[A->is] ^= 1;
+            v->X[A->ir] ^= 1;
+            v->Y[A->is] ^= 1;
+            v->Y[A->iu] ^= 1;
+            *net += A->kind;
+        }
     }
+    free(att);
+    free(tied);
 }
 
 static int footprint_inside(const view_t *v, int64_t x0, int64_t y0, int64_t Bx, int64_t By) {

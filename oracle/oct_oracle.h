@@ -31,6 +31,7 @@ extern "C" {
 #define OO_TAG_ACC 4u
 #define OO_TAG_SEQ 5u
 #define OO_TAG_REPLICA 6u
+#define OO_TAG_TAIL 7u
 
 typedef struct {
     int64_t L;        /* lateral size; periodic */
@@ -93,10 +94,14 @@ int oo_dtrdt_run(const oo_params *prm, uint8_t *X, uint8_t *Y, uint32_t t0, uint
 int oo_dtrdt_many(const oo_params *prm, uint64_t seed0, int64_t n_runs, uint32_t n_mcs,
                   uint8_t *Xout, uint8_t *Yout);
 
-/* The acceptance uniform O2 uses for the thread cell at bit position pos
- * (= 4*j + m) of group g, collective step s, device step k, tile T, MCS t. */
-uint32_t oo_dtrdt_acc_uniform(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t g,
-                              uint32_t s, int pos);
+/* The acceptance randomness O2 uses: the four leading bits (31..28) of the
+ * uniform of the thread cell at position pos (= 4*j + m) of group g at
+ * collective step s, device step k, tile T, MCS t; and word i of the
+ * sub-tile's tail stream of a device step (its top 28 bits complete a uniform
+ * whose leading bits tie with P32's). */
+uint32_t oo_dtrdt_acc_prefix(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t g,
+                             uint32_t s, int pos);
+uint32_t oo_dtrdt_tail_word(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t i);
 
 /* O2 restricted to a window: the lattice is only known on a W x H window whose
  * lower-left corner is the global site (wx, wy) (periodic in L).  Xw/Yw hold

@@ -56,6 +56,7 @@ template <bool RANDOM>
 __global__ void __launch_bounds__(kBatchWarps * 32, kBatchBlocksPerSM)
     batch_step_kernel(const ReplicaDev *reps, const BatchItem *items, const WarpDesc *descs,
                       uint32_t n_descs, const uint32_t *t_of, uint32_t k, uint32_t *queue) {
+    __shared__ __align__(16) uint32_t ring[kBatchWarps * 32 * kRingWordsPerLane];
     const int lane = threadIdx.x & 31;
     for (;;) {
         uint32_t di = 0;
@@ -85,6 +86,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32, kBatchBlocksPerSM)
         c.GY = G / c.GX;
         c.gx = sub % c.GX;
         c.gy = sub / c.GX;
+        c.active = active;
+        c.last = lane | (G - 1);
         c.t = t;
         c.k = k;
         c.T = it.T;
@@ -98,7 +101,9 @@ __global__ void __launch_bounds__(kBatchWarps * 32, kBatchBlocksPerSM)
         c.p_random = R.p_random;
         c.q_random = R.q_random;
         int net = 0, draws = 0;
-        run_subtile<RANDOM, true>(R.lat, L, R.wpr, R.Bx, R.By, x0, y0, active, c, net, draws);
+        run_subtile<RANDOM, true>(R.lat, L, R.wpr, R.Bx, R.By, x0, y0, active, c,
+                                  ring + ((threadIdx.x >> 5) * 32 + (lane & ~(G - 1))) * kRingWordsPerLane,
+                                  net, draws);
         // sum over the G lanes of the item (items start at multiples of G)
         for (int o = G >> 1; o > 0; o >>= 1) {
             net += __shfl_xor_sync(kFull, net, o);

@@ -22,16 +22,19 @@
 // and XOR flips.  The neighbour bits the update rule needs at the group edge
 // (the X column just right of the group, the Y row just below it) are kept
 // as copies (E, D) and refreshed by warp shuffles after every step.  Acceptance
-// draws for 0 < p, q < 1 compare all 32 TCs of a lane against P32 at once,
-// one random bit level at a time, most significant bit first.
+// draws for 0 < p, q < 1 compare all 32 TCs of a lane against P32 at once on
+// four random bit levels; the rare ties finish from a tail stream shared by the
+// sub-tile through a ring in shared memory.
 //
 // Random streams (Philox-4x32-10, key = seed):
 //   MCS draw  (t, 0, 0, MCS<<28): ox, oy, set permutation
 //   set draw  (t, k, T, SET<<28): 2 bits per collective step
 //   site draw (t, k|(s/2)<<2, T, SITE<<28|g): word m = TC row, bits 4j+2(s&1)
 //             (x offset) and 4j+2(s&1)+1 (y offset) for the TC in column j
-//   acceptance level words (t, k|(s*8+lb)<<2, T, ACC<<28|g): level l = 4lb+i,
-//             bit 4j+m is bit 31-l of the uniform of TC (j, m)
+//   acceptance: bits 31..28 of the uniform of TC (j, m) are bit 4j+m of the
+//             four words of (t, k|(s*8)<<2, T, ACC<<28|g); bits 27..0, needed
+//             only when those tie with P32's, are the top of the next word of
+//             the sub-tile's tail stream (t, k|(i/4)<<2, T, TAIL<<28)
 #include "oct_internal.h"
 
 #include "subtile.cuh"
@@ -42,6 +45,7 @@ namespace {
 template <bool RANDOM>
 __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSM)
     dtrdt_step_kernel(const StepArgs a) {
+    __shared__ __align__(16) uint32_t ring[kStepWarpsPerBlock * 32 * kRingWordsPerLane];
     const int lane = threadIdx.x & 31;
     const uint32_t T = blockIdx.x * kStepWarpsPerBlock + (threadIdx.x >> 5);
     if (T >= a.tiles_x * a.tiles_y) return;  // the whole warp leaves together
@@ -66,6 +70,8 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSM)
     c.gx = lane % c.GX;
     c.gy = lane / c.GX;
     const bool active = c.gy < c.GY;
+    c.active = active;
+    c.last = c.GX * c.GY - 1;
     c.t = t;
     c.k = a.k;
     c.T = T;
@@ -81,7 +87,8 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSM)
 
     const uint32_t wpr = a.wpr;
     int net = 0, draws = 0;
-    run_subtile<RANDOM, false>(a.lat, L, wpr, a.Bx, a.By, x0, y0, active, c, net, draws);
+    run_subtile<RANDOM, false>(a.lat, L, wpr, a.Bx, a.By, x0, y0, active, c,
+                               ring + (threadIdx.x >> 5) * 32 * kRingWordsPerLane, net, draws);
 
     // Net flips (and acceptance draws): one atomic per warp into a spread of counters.
     const int total = __reduce_add_sync(kFull, net);

@@ -45,42 +45,108 @@ struct LaneCtx {
     uint32_t thr_p, thr_q;
     uint32_t p_always, q_always, p_random, q_random;
     int gx, gy, GX, GY;
+    int last;      // lane holding the sub-tile's last group
+    bool active;   // this lane holds a group of a sub-tile
+};
+
+// Shared-memory ring holding a sub-tile's tail stream (see accept_candidates).
+// 36 words per lane bound the live window: fewer than (ties of one step) +
+// 4 x (groups) words, and one step has at most 32 ties per group.
+constexpr int kRingWordsPerLane = 36;
+
+struct TailPool {
+    uint32_t *ring;    // this sub-tile's ring
+    uint32_t rs;       // ring size in words = 36 x groups
+    uint32_t head;     // tail words used so far in this device step
+    uint32_t end;      // tail words generated so far in this device step
+    uint32_t head_at;  // head modulo rs
+    uint32_t end_at;   // end modulo rs
 };
 
 // Acceptance of the packed candidates (bit 4j+m = thread cell column j, TC
-// row m): u < P32 is decided at the first random level bit that differs from
-// P32's bit, most significant first; all 32 thread cells of the lane advance
-// together, four levels per Philox block.
-__device__ __forceinline__ uint32_t accept_levels(uint32_t pmin, uint32_t pmax, uint32_t s,
-                                                  const LaneCtx &c) {
+// row m).  The uniform u of a candidate, most significant bit first:
+//  * bits 31..28 come from the four level words of the lane's group (bit
+//    4j+m of word l is bit 31-l), one Philox block per step; all 32 thread
+//    cells of the lane are compared with P32 together, one level at a time;
+//    the comparison is decided unless the four bits equal P32's;
+//  * a candidate still tied takes its bits 27..0 from the top of the next word
+//    of the sub-tile's tail stream (word i = word i%4 of Philox(t, k|(i/4)<<2,
+//    T, TAIL<<28), counted from 0 each device step), in order of group, then
+//    position.  The lanes of the sub-tile fill a shared ring with one Philox
+//    block each whenever the words a step needs run past what was generated.
+__device__ __forceinline__ uint32_t accept_candidates(uint32_t pmin, uint32_t pmax, uint32_t s,
+                                                      const LaneCtx &c, TailPool &tp) {
+    const uint4 W = philox4x32_10(c.t, c.k | ((s * 8u) << 2), c.T, (kTagAcc << 28) | c.g, c.k0, c.k1);
+    const uint32_t lw[4] = {W.x, W.y, W.z, W.w};
     uint32_t acc = 0, und = pmin | pmax;
-    for (uint32_t lb = 0; lb < 8u && und != 0u; ++lb) {
-        const uint4 W = philox4x32_10(c.t, c.k | ((s * 8u + lb) << 2), c.T, (kTagAcc << 28) | c.g,
-                                      c.k0, c.k1);
-        const uint32_t lw[4] = {W.x, W.y, W.z, W.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t bit = 31u - (4u * lb + i);
-            const uint32_t tb = (((c.thr_p >> bit) & 1u) ? pmin : 0u) | (((c.thr_q >> bit) & 1u) ? pmax : 0u);
-            acc |= und & tb & ~lw[i];
-            und &= ~(tb ^ lw[i]);
-        }
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t bit = 31u - static_cast<uint32_t>(i);
+        const uint32_t tb = (((c.thr_p >> bit) & 1u) ? pmin : 0u) | (((c.thr_q >> bit) & 1u) ? pmax : 0u);
+        acc |= und & tb & ~lw[i];
+        und &= ~(tb ^ lw[i]);
     }
+    // ties: exclusive prefix of their counts over the groups of the sub-tile
+    const uint32_t n = static_cast<uint32_t>(__popc(und));
+    uint32_t incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, o);
+        if (static_cast<int>(c.g) >= o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, c.last);
+    // Skip the tail stage only when no lane of the warp needs it: in a batched
+    // warp the sub-tiles differ, and every lane must reach the __syncwarp below.
+    if (__all_sync(kFull, total == 0u)) return acc;
+    const uint32_t G = static_cast<uint32_t>(c.GX * c.GY);
+    while (tp.end < tp.head + total) {
+        const uint4 B = philox4x32_10(c.t, c.k | (((tp.end >> 2) + c.g) << 2), c.T, kTagTail << 28,
+                                      c.k0, c.k1);
+        uint32_t at = tp.end_at + 4u * c.g;  // < 2 rs
+        if (at >= tp.rs) at -= tp.rs;
+        if (c.active) *reinterpret_cast<uint4 *>(tp.ring + at) = B;
+        tp.end += 4u * G;
+        tp.end_at += 4u * G;
+        if (tp.end_at >= tp.rs) tp.end_at -= tp.rs;
+    }
+    __syncwarp();
+    uint32_t at = tp.head_at + (incl - n);  // < 2 rs
+    if (at >= tp.rs) at -= tp.rs;
+    const uint32_t low_p = c.thr_p & 0x0FFFFFFFu, low_q = c.thr_q & 0x0FFFFFFFu;
+    while (und) {
+        const uint32_t bit = und & (0u - und);  // lowest tied position
+        und ^= bit;
+        const uint32_t w = tp.ring[at];
+        if (++at == tp.rs) at = 0u;
+        acc |= ((w >> 4) < ((pmin & bit) ? low_p : low_q)) ? bit : 0u;
+    }
+    __syncwarp();
+    tp.head += total;
+    tp.head_at += total;  // total <= 32 G < rs
+    if (tp.head_at >= tp.rs) tp.head_at -= tp.rs;
     return acc;
 }
 
-// One collective step with sub-cell set (dx, DY).  X/Y hold the lane's 16
-// rows, E bit r the X bit just right of row r, D the Y row just below row 15.
-// An attempt at s is eligible iff X(s) != X(s+x), Y(s) != Y(s+y) and
-// X(s) == Y(s): then X(s) = 0 is the minimum of Eq. (1), X(s) = 1 the maximum.
+// A collective step runs in three phases: the candidates of every thread
+// cell of the lane (specialised on the set's row offset dy), the acceptance
+// draws (one copy of the code, shared by both offsets), and the flips with
+// the neighbour exchange (specialised again).
+//
+// Phase 1 with sub-cell set (dx, DY).  X/Y hold the lane's 16 rows, E bit r
+// the X bit just right of row r, D the Y row just below row 15.  An attempt at
+// s is eligible iff X(s) != X(s+x), Y(s) != Y(s+y) and X(s) == Y(s): then
+// X(s) = 0 is the minimum of Eq. (1), X(s) = 1 the maximum.  Candidates that
+// need an acceptance draw are packed to bit 4j+m (TC column j, TC row m).
 template <int DY, bool RANDOM>
-__device__ __forceinline__ void collective_step(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E,
-                                                uint32_t &D, const uint4 &site, uint32_t s,
-                                                uint32_t dx, const LaneCtx &c, int &net, int &draws) {
+__device__ __forceinline__ void step_candidates(const uint32_t (&X)[16], const uint32_t (&Y)[16],
+                                                uint32_t E, uint32_t D, const uint4 &site, uint32_t s,
+                                                uint32_t dx, const LaneCtx &c, uint32_t (&cnd0)[4],
+                                                uint32_t (&cnd1)[4], uint32_t &pmin, uint32_t &pmax) {
     const uint32_t sw[4] = {site.x, site.y, site.z, site.w};
     const uint32_t par = 2u * (s & 1u);
     const uint32_t sh2 = 2u * dx;
-    uint32_t cnd0[4], cnd1[4];
+    pmin = 0u;
+    pmax = 0u;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         // Site draw: bit 4j = x offset, bit 4j+1 = y offset of TC column j.
@@ -95,24 +161,22 @@ __device__ __forceinline__ void collective_step(uint32_t (&X)[16], uint32_t (&Y)
         const uint32_t yc = (r1 + 1 < 16) ? Y[(r1 + 1) & 15] : D;
         cnd0[m] = col & ~yoff & (xa ^ xra) & (ya ^ yb) & ~(xa ^ ya);
         cnd1[m] = col & yoff & (xb ^ xrb) & (yb ^ yc) & ~(xb ^ yb);
-    }
-
-    uint32_t acc = 0;
-    if (RANDOM) {
-        uint32_t pmin = 0, pmax = 0;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int r0 = 4 * m + 2 * DY, r1 = r0 + 1;
-            const uint32_t mn = (cnd0[m] & ~X[r0]) | (cnd1[m] & ~X[r1]);
-            const uint32_t mx = (cnd0[m] & X[r0]) | (cnd1[m] & X[r1]);
+        if (RANDOM) {
+            const uint32_t mn = (cnd0[m] & ~xa) | (cnd1[m] & ~xb);
+            const uint32_t mx = (cnd0[m] & xa) | (cnd1[m] & xb);
             const uint32_t cmn = mn & c.p_random, cmx = mx & c.q_random;
             pmin |= (((cmn >> sh2) | (cmn >> (sh2 + 1u))) & kNib) << m;
             pmax |= (((cmx >> sh2) | (cmx >> (sh2 + 1u))) & kNib) << m;
         }
-        draws += __popc(pmin | pmax);
-        acc = accept_levels(pmin, pmax, s, c);
     }
+}
 
+// Phase 3 with sub-cell set (dx, DY): flips of the accepted candidates (acc:
+// packed acceptance bits) and the exchange with the neighbouring lanes.
+template <int DY, bool RANDOM>
+__device__ __forceinline__ void step_apply(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E, uint32_t &D,
+                                           uint32_t dx, uint32_t acc, const uint32_t (&cnd0)[4],
+                                           const uint32_t (&cnd1)[4], const LaneCtx &c, int &net) {
     uint32_t f0s[4], f1s[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -140,7 +204,7 @@ __device__ __forceinline__ void collective_step(uint32_t (&X)[16], uint32_t (&Y)
         f1s[m] = f1;
     }
 
-    // Keep the neighbour copies consistent.
+    // Keep the neighbour copies consistent (dx is uniform over the warp here).
     if (dx) {
         // Flips at bit 31 changed column 0 of the right neighbour (this lane's E).
         uint32_t dE = 0;
@@ -181,22 +245,22 @@ __device__ __forceinline__ void collective_step(uint32_t (&X)[16], uint32_t (&Y)
     }
 }
 
-
-// The same collective step when the lanes of one warp belong to different
+// The same two phases when the lanes of one warp belong to different
 // sub-tiles, each with its own set draw: the row offset dy is a run-time value
 // per lane (rows picked with selects instead of branches), and every shuffle
 // runs unconditionally so that all 32 lanes take part.
 template <bool RANDOM>
-__device__ __forceinline__ void collective_step_rt(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E,
-                                                   uint32_t &D, const uint4 &site, uint32_t s,
-                                                   uint32_t dx, uint32_t dy, const LaneCtx &c, int &net,
-                                                   int &draws) {
+__device__ __forceinline__ void step_candidates_rt(const uint32_t (&X)[16], const uint32_t (&Y)[16],
+                                                   uint32_t E, uint32_t D, const uint4 &site, uint32_t s,
+                                                   uint32_t dx, uint32_t dy, const LaneCtx &c,
+                                                   uint32_t (&cnd0)[4], uint32_t (&cnd1)[4],
+                                                   uint32_t &pmin, uint32_t &pmax) {
     const uint32_t sw[4] = {site.x, site.y, site.z, site.w};
     const uint32_t par = 2u * (s & 1u);
     const uint32_t sh2 = 2u * dx;
     const uint32_t ro = 2u * dy;
-    const uint32_t dym = dy ? 0xFFFFFFFFu : 0u;
-    uint32_t cnd0[4], cnd1[4], xas[4], xbs[4];
+    pmin = 0u;
+    pmax = 0u;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const uint32_t u = sw[m] >> par;
@@ -212,25 +276,22 @@ __device__ __forceinline__ void collective_step_rt(uint32_t (&X)[16], uint32_t (
         const uint32_t xrb = __funnelshift_r(xb, E >> (r0 + 1u), 1);
         cnd0[m] = col & ~yoff & (xa ^ xra) & (ya ^ yb) & ~(xa ^ ya);
         cnd1[m] = col & yoff & (xb ^ xrb) & (yb ^ yc) & ~(xb ^ yb);
-        xas[m] = xa;
-        xbs[m] = xb;
-    }
-
-    uint32_t acc = 0;
-    if (RANDOM) {
-        uint32_t pmin = 0, pmax = 0;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const uint32_t mn = (cnd0[m] & ~xas[m]) | (cnd1[m] & ~xbs[m]);
-            const uint32_t mx = (cnd0[m] & xas[m]) | (cnd1[m] & xbs[m]);
+        if (RANDOM) {
+            const uint32_t mn = (cnd0[m] & ~xa) | (cnd1[m] & ~xb);
+            const uint32_t mx = (cnd0[m] & xa) | (cnd1[m] & xb);
             const uint32_t cmn = mn & c.p_random, cmx = mx & c.q_random;
             pmin |= (((cmn >> sh2) | (cmn >> (sh2 + 1u))) & kNib) << m;
             pmax |= (((cmx >> sh2) | (cmx >> (sh2 + 1u))) & kNib) << m;
         }
-        draws += __popc(pmin | pmax);
-        acc = accept_levels(pmin, pmax, s, c);
     }
+}
 
+template <bool RANDOM>
+__device__ __forceinline__ void step_apply_rt(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E, uint32_t &D,
+                                              uint32_t dy, uint32_t acc, const uint32_t (&cnd0)[4],
+                                              const uint32_t (&cnd1)[4], const LaneCtx &c, int &net) {
+    const uint32_t ro = 2u * dy;
+    const uint32_t dym = dy ? 0xFFFFFFFFu : 0u;
     uint32_t dE = 0, dB0 = 0, dD = 0, dY0 = 0;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -240,7 +301,8 @@ __device__ __forceinline__ void collective_step_rt(uint32_t (&X)[16], uint32_t (
             amin |= spread & c.p_random;
             amax |= spread & c.q_random;
         }
-        const uint32_t xa = xas[m], xb = xbs[m];
+        const uint32_t xa = dy ? X[4 * m + 2] : X[4 * m];
+        const uint32_t xb = dy ? X[4 * m + 3] : X[4 * m + 1];
         const uint32_t f0 = cnd0[m] & ((~xa & amin) | (xa & amax));
         const uint32_t f1 = cnd1[m] & ((~xb & amin) | (xb & amax));
         net += __popc((f0 & ~xa) | (f1 & ~xb)) - __popc((f0 & xa) | (f1 & xb));
@@ -287,7 +349,14 @@ __device__ __forceinline__ void collective_step_rt(uint32_t (&X)[16], uint32_t (
 template <bool RANDOM, bool LANE_SETS>
 __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t Bx,
                                             uint32_t By, uint32_t x0, uint32_t y0, bool active,
-                                            const LaneCtx &c, int &net, int &draws) {
+                                            const LaneCtx &c, uint32_t *ring, int &net, int &draws) {
+    TailPool tp;
+    tp.ring = ring;
+    tp.rs = static_cast<uint32_t>(kRingWordsPerLane * c.GX * c.GY);
+    tp.head = 0u;
+    tp.end = 0u;
+    tp.head_at = 0u;
+    tp.end_at = 0u;
     uint32_t *const Xp = lat;
     uint32_t *const Yp = lat + static_cast<size_t>(L) * wpr;
     const uint32_t sh = x0 & 31u;
@@ -345,12 +414,24 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
         if ((s & 1u) == 0u)
             site = philox4x32_10(c.t, c.k | ((s >> 1) << 2), c.T, (kTagSite << 28) | c.g, c.k0, c.k1);
         const uint32_t d = (setw.x >> (2u * s)) & 3u;
+        uint32_t cnd0[4], cnd1[4], pmin, pmax;
         if (LANE_SETS)
-            collective_step_rt<RANDOM>(X, Y, E, D, site, s, d & 1u, d >> 1, c, net, draws);
+            step_candidates_rt<RANDOM>(X, Y, E, D, site, s, d & 1u, d >> 1, c, cnd0, cnd1, pmin, pmax);
         else if (d & 2u)
-            collective_step<1, RANDOM>(X, Y, E, D, site, s, d & 1u, c, net, draws);
+            step_candidates<1, RANDOM>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
         else
-            collective_step<0, RANDOM>(X, Y, E, D, site, s, d & 1u, c, net, draws);
+            step_candidates<0, RANDOM>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
+        uint32_t acc = 0u;
+        if (RANDOM) {
+            draws += __popc(pmin | pmax);
+            acc = accept_candidates(pmin, pmax, s, c, tp);
+        }
+        if (LANE_SETS)
+            step_apply_rt<RANDOM>(X, Y, E, D, d >> 1, acc, cnd0, cnd1, c, net);
+        else if (d & 2u)
+            step_apply<1, RANDOM>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
+        else
+            step_apply<0, RANDOM>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
     }
 
     // Write back.  Global word wA of a row receives the high bits of the left

@@ -76,24 +76,30 @@ def test_set_and_site_draws_are_uniform(oracle):
     assert chi.pvalue > 1e-4, chi
 
 
-def test_acceptance_uniforms(oracle):
-    """u(pos) must be uniform on 32 bits and independent across the 32
-    thread-cell positions of a group (a pos collision or a repeated level word
-    breaks one of these)."""
-    n = 2000
-    U = np.zeros((n, 32), dtype=np.float64)
+def test_acceptance_randomness(oracle):
+    """Leading bits: the 4-bit prefixes of the 32 thread-cell positions of a
+    group must be uniform and independent across positions and steps (a
+    position collision or a repeated level word breaks this).  Tail words must
+    be uniform 32-bit words."""
+    n = 3000
+    H = np.zeros((n, 32), dtype=np.int64)
     for i in range(n):
         for pos in range(32):
-            U[i, pos] = oracle.acc_uniform(1, i // 16, i % 4, 5, i % 7, i % 16, pos)
-    U /= 2.0**32
-    ks = stats.kstest(U.reshape(-1), "uniform")
-    assert ks.pvalue > 1e-4, ks
-    C = np.corrcoef(U.T)
+            H[i, pos] = oracle.acc_prefix(1, i // 16, i % 4, 5, i % 7, i % 16, pos)
+    assert H.min() == 0 and H.max() == 15
+    counts = np.bincount(H.reshape(-1), minlength=16)
+    assert stats.chisquare(counts).pvalue > 1e-4
+    C = np.corrcoef(H.T.astype(float))
     off = C[~np.eye(32, dtype=bool)]
     assert np.max(np.abs(off)) < 5.0 / np.sqrt(n)
-    # identical arguments reproduce, different steps differ
-    assert oracle.acc_uniform(1, 2, 3, 4, 5, 6, 7) == oracle.acc_uniform(1, 2, 3, 4, 5, 6, 7)
-    assert oracle.acc_uniform(1, 2, 3, 4, 5, 6, 7) != oracle.acc_uniform(1, 2, 3, 4, 5, 7, 7)
+    # each of the four level bits separately balanced
+    for l in range(4):
+        b = (H >> l) & 1
+        assert abs(b.mean() - 0.5) < 4 * 0.5 / np.sqrt(b.size)
+    tails = np.array([oracle.tail_word(3, 2, 1, 7, i) for i in range(20000)], dtype=np.float64)
+    assert stats.kstest(tails / 2.0**32, "uniform").pvalue > 1e-4
+    assert oracle.tail_word(3, 2, 1, 7, 5) != oracle.tail_word(3, 2, 1, 8, 5)
+    assert oracle.acc_prefix(1, 2, 3, 4, 5, 6, 7) == oracle.acc_prefix(1, 2, 3, 4, 5, 6, 7)
 
 
 def test_acceptance_rate_on_flat_start(oracle):

@@ -302,6 +302,23 @@ def run_reference(a, rank, world):
     }
 
 
+def replica_seed(seed: int, rank: int) -> int:
+    """Each rank runs an independent replica: its key is the base seed plus the rank."""
+    return seed + rank
+
+
+def combine_ranks(ms_local: float, attempts_local: int, dist=None, device="cpu"):
+    """Slowest rank's time and total attempts over all ranks (weak scaling)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms_local, attempts_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    n = torch.tensor([attempts_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -329,7 +346,7 @@ def main():
     torch.cuda.set_stream(stream)
     L = a.L
     lattice = torch.empty(L * L // 4, dtype=torch.uint8, device="cuda")
-    seed = a.seed + rank
+    seed = replica_seed(a.seed, rank)
     sim = g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice)
 
     def barrier():
@@ -353,13 +370,9 @@ def main():
     step_ms, launches, _ = _lib.oct_get_timing(sim.h)
     _lib.oct_set_timing(sim.h, False)
     stats1 = _lib.oct_get_stats(sim.h)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
     attempts = L * L * a.steps
-    value = world * attempts / (ms_max * 1e6)
+    ms_max, total_attempts = combine_ranks(ms, attempts, dist, device="cuda")
+    value = total_attempts / (ms_max * 1e6)
 
     # ---- roofline of the device-step kernel (integer-ALU bound) ----
     launch_ms = step_ms / max(1, launches)

@@ -26,7 +26,8 @@ _SRC = os.path.join(_HERE, "oct_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboct_oracle.so")
 _lib = None
 
-TAG_MCS, TAG_SET, TAG_SITE, TAG_ACC, TAG_SEQ, TAG_REPLICA, TAG_TAIL = 1, 2, 3, 4, 5, 6, 7
+TAG_MCS, TAG_SET, TAG_SITE, TAG_ACC, TAG_SEQ, TAG_REPLICA, TAG_TAIL, TAG_SITE_DB = 1, 2, 3, 4, 5, 6, 7, 8
+SCHEME_DT, SCHEME_DB, SCHEME_DB_IGNORE = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -45,7 +46,7 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int64), ("Bx", ctypes.c_int64), ("By", ctypes.c_int64),
                 ("cx", ctypes.c_int64), ("cy", ctypes.c_int64), ("p", ctypes.c_double),
-                ("q", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("q", ctypes.c_double), ("seed", ctypes.c_uint64), ("scheme", ctypes.c_int64)]
 
 
 @dataclass(frozen=True)
@@ -59,9 +60,11 @@ class Params:
     By: int = 64
     cx: int = 4
     cy: int = 4
+    scheme: int = 0  # SCHEME_DT, SCHEME_DB or SCHEME_DB_IGNORE
 
     def c(self) -> _Params:
-        return _Params(self.L, self.Bx, self.By, self.cx, self.cy, self.p, self.q, self.seed)
+        return _Params(self.L, self.Bx, self.By, self.cx, self.cy, self.p, self.q, self.seed,
+                       self.scheme)
 
 
 _P_u8 = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")

@@ -192,6 +192,7 @@ int oo_check_params(const oo_params *P) {
     if (P->L % (2 * P->Bx) || P->L % (2 * P->By)) return -1;
     if (!(P->p >= 0.0 && P->p <= 1.0 && P->q >= 0.0 && P->q <= 1.0)) return -1;
     if (P->cx * P->cy * 8 >= ((int64_t)1 << 30)) return -1;
+    if (P->scheme < OO_SCHEME_DT || P->scheme > OO_SCHEME_DB_IGNORE) return -1;
     int64_t groups = (P->Bx / BW) * ((P->By / P->cy + 3) / 4);
     if (groups >= ((int64_t)1 << 28)) return -1;
     int64_t tiles = (P->L / (2 * P->Bx)) * (P->L / (2 * P->By));
@@ -238,6 +239,7 @@ static inline int64_t vidx(const view_t *v, int64_t gx, int64_t gy) {
 
 typedef struct {
     int64_t *dev_stamp, *dev_owner, *step_stamp, *step_owner; /* 2 per site: X then Y */
+    int64_t *flip_stamp;                                      /* last batch that flipped the bit */
     int64_t dev_serial, step_serial, count;
 } conflict_t;
 
@@ -300,6 +302,11 @@ typedef struct {
     int pos;
     int decided;        /* 1 accepted, 0 rejected, -1 needs a tail word */
     uint64_t thr;
+    uint32_t hi;        /* leading four bits of the acceptance uniform */
+    int random;         /* the probability lies strictly inside (0,1) */
+    uint64_t thr_min, thr_max;
+    int random_min, random_max;
+    int64_t tc;         /* thread-cell index (conflict tracking) */
 } attempt_t;
 
 static int by_group_then_position(const void *pa, const void *pb) {
@@ -331,43 +338,145 @@ static int by_group_then_position(const void *pa, const void *pb) {
  *                         bits = x offset, the rest = y offset.
  *   acceptance uniform  : see acc_level_words / tail_word above.
  */
+/* Decides, flips and counts the attempts of one conflict-free batch (a
+ * collective step of DT, or one phase of a DB step): attempts whose site is
+ * eligible on the current state are decided by the four leading level bits of
+ * their uniform; ties take tail words in order of group, then position. */
+static void decide_and_flip(const uint32_t key[2], uint32_t t, uint32_t k, uint32_t T, view_t *v,
+                            attempt_t *att, int64_t na, attempt_t *tied, uint32_t *tail_next,
+                            int64_t *net, conflict_t *cf) {
+    int64_t nt = 0;
+    for (int64_t i = 0; i < na; ++i) {
+        attempt_t *A = &att[i];
+        A->kind = 0;
+        if (v->X[A->is] == 0 && v->X[A->ir] == 1 && v->Y[A->is] == 0 && v->Y[A->iu] == 1)
+            A->kind = +1;
+        else if (v->X[A->is] == 1 && v->X[A->ir] == 0 && v->Y[A->is] == 1 && v->Y[A->iu] == 0)
+            A->kind = -1;
+        A->decided = 0;
+        if (A->kind == 0) continue;
+        A->thr = A->kind > 0 ? A->thr_min : A->thr_max;
+        A->random = A->kind > 0 ? A->random_min : A->random_max;
+        if (!A->random) {
+            A->decided = A->thr > 0 ? 1 : 0; /* probability 1 or 0 */
+        } else {
+            const uint32_t thr_hi = (uint32_t)(A->thr >> 28);
+            A->decided = A->hi < thr_hi ? 1 : (A->hi > thr_hi ? 0 : -1);
+            if (A->decided < 0) tied[nt++] = *A;
+        }
+    }
+    qsort(tied, (size_t)nt, sizeof(attempt_t), by_group_then_position);
+    for (int64_t i = 0; i < nt; ++i) {
+        const uint32_t low28 = tail_word(key, t, k, T, (*tail_next)++) >> 4;
+        tied[i].decided = (uint64_t)low28 < (tied[i].thr & 0x0FFFFFFFu) ? 1 : 0;
+    }
+    /* apply the accepted flips (no two share a bit; tracked when cf is set) */
+    for (int64_t i = 0; i < na + nt; ++i) {
+        const attempt_t *A = i < na ? &att[i] : &tied[i - na];
+        if (A->decided != 1) continue;
+        if (cf) {
+            const int64_t nv = v->W * v->H;
+            const int64_t bits[4] = {A->is, A->ir, nv + A->is, nv + A->iu};
+            for (int b = 0; b < 4; ++b) {
+                if (cf->flip_stamp[bits[b]] == cf->step_serial) cf->count++;
+                cf->flip_stamp[bits[b]] = cf->step_serial;
+            }
+        }
+        v->X[A->is] ^= 1;
+        v->X[A->ir] ^= 1;
+        v->Y[A->is] ^= 1;
+        v->Y[A->iu] ^= 1;
+        *net += A->kind;
+    }
+}
+
+/* Block layer on one sub-tile.
+ *
+ * The sub-tile (Bx x By sites, local origin (x0,y0)) is cut into thread
+ * cells (TC) of cx x cy sites.  Per collective step every TC performs exactly
+ * one attempt (single hit), then all synchronise; cx*cy collective steps make
+ * one sweep of the sub-tile (Bx*By attempts).
+ *
+ * DT (double tiling): each TC is cut into four sub-cells of (cx/2) x (cy/2)
+ * sites, sub-cell d = (dx,dy) = (d&1, d>>1); per step the block draws d
+ * uniformly (with replacement, not a permutation) and every TC attempts a
+ * uniform site of its sub-cell d.  Attempts of one step never share a slope
+ * bit, so every decision is taken on the state before the step.
+ *
+ * DB (dead border): every TC attempts a uniform site of its whole cell.  The
+ * cell's last column (x = cx-1) and last row (y = cy-1) form its border,
+ * since an update there reaches the next cell.  With delayed borders, bulk
+ * attempts are carried out first, then border attempts, and attempts at the
+ * corner (cx-1, cy-1), which touch two borders, last; each phase is
+ * conflict-free and sees the flips of the earlier ones.  The paper delays
+ * borders only when both p and q are non-zero; with one of them zero two
+ * neighbouring sites are never both accepted, and its DB runs carry out all
+ * attempts of a step together (reading of the schedule specification: DB does
+ * the same).  DB_IGNORE carries out all attempts together for any p, q; with
+ * both non-zero two accepted flips can then hit the same slope bit, which the
+ * flip tracker counts.
+ *
+ * Random streams (reading fixed by the schedule specification):
+ *   set draw (DT) for step s : word (s%64)/16 of Philox(seed, (t, k|(s/64)<<2, T, SET<<28)),
+ *                         bits 2*(s%16) .. +1.
+ *   TCs are grouped: a band is one TC row, BW = min(32,Bx) sites wide; a group
+ *   is four vertically consecutive bands of one band column; g = (c/4)*(Bx/BW)
+ *   + band column, m = c%4 (c = TC row), j = TC index inside its band.
+ *   site draw           : word m of Philox(seed, (t, k|(s/spw)<<2, T, TAG<<28|g)),
+ *                         TAG = SITE (DT) or SITE_DB (DB), bits fw*j +
+ *                         (s%spw)*(fw/spw) .. + bpt-1 (bpt = log2 of the
+ *                         sub-cell (DT) or cell (DB) area), low bits = x offset.
+ *   acceptance uniform  : see acc_level_words / tail_word above; with DB the
+ *                         tail words are taken phase by phase.
+ */
 static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, uint32_t k,
                         uint32_t T, int64_t x0, int64_t y0, view_t *v, int64_t *net,
                         int64_t *attempts, conflict_t *cf) {
     const int64_t L = P->L, Bx = P->Bx, By = P->By, cx = P->cx, cy = P->cy;
+    const int db = P->scheme != OO_SCHEME_DT;
+    /* The paper delays border attempts only where two neighbouring sites can
+     * both be accepted, i.e. when both p and q are non-zero; with one of them
+     * zero its DB runs carry out all attempts of a step together. */
+    const int delayed = P->scheme == OO_SCHEME_DB && P->p > 0.0 && P->q > 0.0;
     const int64_t BW = Bx < 32 ? Bx : 32;
     const int64_t tcs_per_band = BW / cx;
     const int64_t band_cols = Bx / BW;
     const int64_t tc_rows = By / cy;
     const int64_t group_rows = (tc_rows + 3) / 4;
-    const int bx_bits = ilog2_exact(cx / 2), by_bits = ilog2_exact(cy / 2);
+    const int64_t ux = db ? cx : cx / 2, uy = db ? cy : cy / 2; /* the region a TC draws from */
+    const int bx_bits = ilog2_exact(ux), by_bits = ilog2_exact(uy);
     const int bpt = bx_bits + by_bits;
     const int64_t fw = 32 / tcs_per_band;
     const int spw = (bpt > 0 && 2 * bpt <= fw) ? 2 : 1;
+    const uint32_t site_tag = db ? OO_TAG_SITE_DB : OO_TAG_SITE;
     const int64_t n_steps = cx * cy;
     const uint64_t thr_p = oo_threshold32(P->p), thr_q = oo_threshold32(P->q);
     const int p_random = P->p > 0.0 && P->p < 1.0;
     const int q_random = P->q > 0.0 && P->q < 1.0;
-    attempt_t *att = (attempt_t *)malloc(sizeof(attempt_t) * (size_t)((Bx / cx) * (By / cy)));
-    attempt_t *tied = (attempt_t *)malloc(sizeof(attempt_t) * (size_t)((Bx / cx) * (By / cy)));
+    const int64_t n_tc = (Bx / cx) * (By / cy);
+    attempt_t *all = (attempt_t *)malloc(sizeof(attempt_t) * (size_t)n_tc);
+    attempt_t *phase = (attempt_t *)malloc(sizeof(attempt_t) * (size_t)n_tc);
+    attempt_t *tied = (attempt_t *)malloc(sizeof(attempt_t) * (size_t)n_tc);
+    int *cls = (int *)malloc(sizeof(int) * (size_t)n_tc);
     uint32_t tail_next = 0; /* tail-stream words used so far in this device step */
 
     for (int64_t s = 0; s < n_steps; ++s) {
-        uint32_t sw[4];
-        philox_at(key, t, k | (uint32_t)((s / 64) << 2), T, OO_TAG_SET << 28, sw);
-        const int d = (int)((sw[(s % 64) / 16] >> (2 * (s % 16))) & 3u);
-        const int64_t dx = d & 1, dy = d >> 1;
-        if (cf) cf->step_serial++;
+        int64_t dx = 0, dy = 0;
+        if (!db) {
+            uint32_t sw[4];
+            philox_at(key, t, k | (uint32_t)((s / 64) << 2), T, OO_TAG_SET << 28, sw);
+            const int d = (int)((sw[(s % 64) / 16] >> (2 * (s % 16))) & 3u);
+            dx = d & 1;
+            dy = d >> 1;
+        }
         int64_t na = 0;
-
-        /* 1: every thread cell's attempt on the state before the step */
+        /* every thread cell's attempt: site and leading acceptance bits */
         for (int64_t gr = 0; gr < group_rows; ++gr) {
             for (int64_t bc = 0; bc < band_cols; ++bc) {
                 const uint32_t g = (uint32_t)(gr * band_cols + bc);
                 uint32_t site_w[4] = {0, 0, 0, 0};
                 if (bpt > 0)
-                    philox_at(key, t, k | (uint32_t)((s / spw) << 2), T,
-                              (OO_TAG_SITE << 28) | g, site_w);
+                    philox_at(key, t, k | (uint32_t)((s / spw) << 2), T, (site_tag << 28) | g, site_w);
                 uint32_t lw[4];
                 acc_level_words(key, t, k, T, g, (uint32_t)s, lw);
                 for (int64_t m = 0; m < 4; ++m) {
@@ -385,67 +494,53 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
                         const int64_t lx = a * cx + dx * (cx / 2) + rx;
                         const int64_t ly = c * cy + dy * (cy / 2) + ry;
                         const int64_t gx = wrap(x0 + lx, L), gy = wrap(y0 + ly, L);
-                        const int64_t is = vidx(v, gx, gy);
-                        const int64_t ir = vidx(v, gx + 1, gy);
-                        const int64_t iu = vidx(v, gx, gy + 1);
                         if (attempts) attempts[gy * L + gx]++;
-                        if (cf) {
-                            const int64_t tc = c * (Bx / cx) + a;
-                            const int64_t nv = v->W * v->H;
-                            touch(cf, is, T, tc);
-                            touch(cf, ir, T, tc);
-                            touch(cf, nv + is, T, tc);
-                            touch(cf, nv + iu, T, tc);
-                        }
-                        int kind = 0;
-                        if (v->X[is] == 0 && v->X[ir] == 1 && v->Y[is] == 0 && v->Y[iu] == 1)
-                            kind = +1;
-                        else if (v->X[is] == 1 && v->X[ir] == 0 && v->Y[is] == 1 && v->Y[iu] == 0)
-                            kind = -1;
-                        if (kind == 0) continue;
-                        attempt_t *A = &att[na++];
-                        A->is = is;
-                        A->ir = ir;
-                        A->iu = iu;
-                        A->kind = kind;
+                        attempt_t *A = &all[na];
+                        A->is = vidx(v, gx, gy);
+                        A->ir = vidx(v, gx + 1, gy);
+                        A->iu = vidx(v, gx, gy + 1);
                         A->g = g;
                         A->pos = (int)(4 * j + m);
-                        A->thr = kind > 0 ? thr_p : thr_q;
-                        const int random = kind > 0 ? p_random : q_random;
-                        if (!random) {
-                            A->decided = A->thr > 0 ? 1 : 0; /* probability 1 or 0 */
-                        } else {
-                            /* u < P32 from the four leading bits unless they tie */
-                            const uint32_t hi = acc_prefix(lw, A->pos);
-                            const uint32_t thr_hi = (uint32_t)(A->thr >> 28);
-                            A->decided = hi < thr_hi ? 1 : (hi > thr_hi ? 0 : -1);
-                        }
+                        A->hi = acc_prefix(lw, A->pos);
+                        A->thr_min = thr_p;
+                        A->thr_max = thr_q;
+                        A->random_min = p_random;
+                        A->random_max = q_random;
+                        A->tc = c * (Bx / cx) + a;
+                        /* DB phase: 0 bulk, 1 border, 2 corner (DT, ignored borders: all 0) */
+                        const int on_x = (rx == cx - 1), on_y = (ry == cy - 1);
+                        cls[na] = delayed ? on_x + on_y : 0;
+                        ++na;
                     }
                 }
             }
         }
-        /* 2: ties take tail words in order of group, then position */
-        int64_t nt = 0;
-        for (int64_t i = 0; i < na; ++i)
-            if (att[i].decided < 0) tied[nt++] = att[i];
-        qsort(tied, (size_t)nt, sizeof(attempt_t), by_group_then_position);
-        for (int64_t i = 0; i < nt; ++i) {
-            const uint32_t low28 = tail_word(key, t, k, T, tail_next++) >> 4;
-            tied[i].decided = (uint64_t)low28 < (tied[i].thr & 0x0FFFFFFFu) ? 1 : 0;
-        }
-        /* 3: apply the accepted flips (no two share a bit) */
-        for (int64_t i = 0; i < na + nt; ++i) {
-            const attempt_t *A = i < na ? &att[i] : &tied[i - na];
-            if (A->decided != 1) continue;
-            v->X[A->is] ^= 1;
-            v->X[A->ir] ^= 1;
-            v->Y[A->is] ^= 1;
-            v->Y[A->iu] ^= 1;
-            *net += A->kind;
+        for (int ph = 0; ph < 3; ++ph) {
+            int64_t np = 0;
+            for (int64_t i = 0; i < na; ++i)
+                if (cls[i] == ph) phase[np++] = all[i];
+            if (np == 0) continue;
+            if (cf) {
+                cf->step_serial++;
+                /* DT and delayed DB phases: no bit is even read by two thread
+                 * cells; DB with borders carried out together: only flips are
+                 * disjoint (checked in decide_and_flip) */
+                const int64_t nv = v->W * v->H;
+                if (!db || delayed)
+                    for (int64_t i = 0; i < np; ++i) {
+                        touch(cf, phase[i].is, T, phase[i].tc);
+                        touch(cf, phase[i].ir, T, phase[i].tc);
+                        touch(cf, nv + phase[i].is, T, phase[i].tc);
+                        touch(cf, nv + phase[i].iu, T, phase[i].tc);
+                    }
+            }
+            decide_and_flip(key, t, k, T, v, phase, np, tied, &tail_next, net, cf);
         }
     }
-    free(att);
+    free(all);
+    free(phase);
     free(tied);
+    free(cls);
 }
 
 static int footprint_inside(const view_t *v, int64_t x0, int64_t y0, int64_t Bx, int64_t By) {
@@ -492,14 +587,16 @@ int oo_dtrdt_run(const oo_params *P, uint8_t *X, uint8_t *Y, uint32_t t0, uint32
         cfs.dev_owner = (int64_t *)malloc(sizeof(int64_t) * nbits);
         cfs.step_stamp = (int64_t *)malloc(sizeof(int64_t) * nbits);
         cfs.step_owner = (int64_t *)malloc(sizeof(int64_t) * nbits);
-        if (!cfs.dev_stamp || !cfs.dev_owner || !cfs.step_stamp || !cfs.step_owner) {
+        cfs.flip_stamp = (int64_t *)malloc(sizeof(int64_t) * nbits);
+        if (!cfs.dev_stamp || !cfs.dev_owner || !cfs.step_stamp || !cfs.step_owner || !cfs.flip_stamp) {
             free(cfs.dev_stamp);
             free(cfs.dev_owner);
             free(cfs.step_stamp);
             free(cfs.step_owner);
+            free(cfs.flip_stamp);
             return -1;
         }
-        for (int64_t i = 0; i < nbits; ++i) cfs.dev_stamp[i] = cfs.step_stamp[i] = -1;
+        for (int64_t i = 0; i < nbits; ++i) cfs.dev_stamp[i] = cfs.step_stamp[i] = cfs.flip_stamp[i] = -1;
         cfs.dev_serial = cfs.step_serial = cfs.count = 0;
         cf = &cfs;
     }
@@ -512,6 +609,7 @@ int oo_dtrdt_run(const oo_params *P, uint8_t *X, uint8_t *Y, uint32_t t0, uint32
         free(cfs.dev_owner);
         free(cfs.step_stamp);
         free(cfs.step_owner);
+        free(cfs.flip_stamp);
     }
     return 0;
 }

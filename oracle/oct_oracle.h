@@ -32,6 +32,12 @@ extern "C" {
 #define OO_TAG_SEQ 5u
 #define OO_TAG_REPLICA 6u
 #define OO_TAG_TAIL 7u
+#define OO_TAG_SITE_DB 8u
+
+/* Block-layer schemes (Sec. 3.1). */
+#define OO_SCHEME_DT 0          /* single-hit double tiling (DTrDT)                     */
+#define OO_SCHEME_DB 1          /* single-hit dead border, delayed borders (DTrDB)      */
+#define OO_SCHEME_DB_IGNORE 2   /* dead border with border attempts not delayed         */
 
 typedef struct {
     int64_t L;        /* lateral size; periodic */
@@ -39,6 +45,7 @@ typedef struct {
     int64_t cx, cy;   /* block-layer thread-cell size in sites */
     double p, q;      /* deposition / removal probabilities, Eq. (1) */
     uint64_t seed;    /* Philox key = (seed low 32 bits, seed high 32 bits) */
+    int64_t scheme;   /* OO_SCHEME_*; 0 = DTrDT */
 } oo_params;
 
 /* Philox-4x32-10 (Salmon et al., SC'11), counter ctr[4], key key[2]. */

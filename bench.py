@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=32)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--db-steps", type=int, default=30)
     return ap.parse_args()
 
 
@@ -399,6 +400,29 @@ def main():
         "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak},
     }
 
+    # ---- the DTrDB block layer on the same workload (the paper's Fig. 7 pair) ----
+    dtrdb = None
+    if rank == 0 and a.db_steps > 0:
+        sim.close()
+        with g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice,
+                          scheme=_lib.OCT_SCHEME_DB) as db:
+            db.run(3)
+            torch.cuda.synchronize()
+            _lib.oct_set_timing(db.h, True)
+            st_, en_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            st_.record(stream)
+            db.run(a.db_steps)
+            en_.record(stream)
+            torch.cuda.synchronize()
+            dms = st_.elapsed_time(en_)
+            kms, kl, _ = _lib.oct_get_timing(db.h)
+        dtrdb = {"value": L * L * a.db_steps / (dms * 1e6), "unit": UNIT, "mcs": a.db_steps,
+                 "device_step_ms": kms / max(1, kl),
+                 "scheme": "DTrDB: single-hit dead border at block level, borders delayed (p, q > 0)",
+                 "relative_to_dtrdt": (L * L * a.db_steps / (dms * 1e6)) / (value / world)}
+        sim = g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice)
+        sim.run(a.warmup + a.steps)
+
     # ---- batched replicas (uneven L) against a loop of plain launches ----
     batched = None
     if rank == 0 and not a.no_batch and a.batch_replicas > 0:
@@ -449,7 +473,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload(a), "clocks": clk.summary(), "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "batched": batched, "serving": serving,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "dtrdb": dtrdb, "batched": batched, "serving": serving,
             "probe": {"lop3_per_clk_per_sm": lop3, "imad_per_clk_per_sm": imad, "probe_mhz": probe_mhz},
         }
         print(json.dumps(out), flush=True)

@@ -67,7 +67,14 @@ typedef struct oct_sim oct_sim; /* opaque; owns its device memory unless told ot
  *   lattice  external device buffer of L*L/4 bytes (planar layout), or NULL
  *          for a library-owned one.  An external buffer stays owned by the
  *          caller and must outlive the handle.
- *   no_init  0: write the flat start h = (x+y) mod 2; 1: keep the buffer. */
+ *   no_init  0: write the flat start h = (x+y) mod 2; 1: keep the buffer.
+ *   scheme   block-layer decomposition (Sec. 3.1): OCT_SCHEME_DT (default,
+ *          DTrDT: single-hit double tiling) or OCT_SCHEME_DB (DTrDB:
+ *          single-hit dead border; border attempts are delayed after the bulk
+ *          ones when both p and q are non-zero, otherwise all attempts of a
+ *          step are carried out together, as in the paper's runs). */
+#define OCT_SCHEME_DT 0
+#define OCT_SCHEME_DB 1
 typedef struct {
     int64_t L;
     double p, q;
@@ -77,7 +84,8 @@ typedef struct {
     void *stream;
     void *lattice;
     int32_t no_init;
-    int32_t reserved[7];
+    int32_t scheme;
+    int32_t reserved[6];
 } oct_params;
 
 /* Exact roughness, Eq. (3), read as the mean over all L^2 sites:
@@ -105,6 +113,8 @@ typedef struct {
     void *stream;
     void *lattice; /* device address of the planar lattice */
     int64_t lattice_bytes;
+    int32_t scheme;
+    int32_t reserved;
 } oct_info;
 
 /* Creates a simulation in the flat start with the default tiling (see

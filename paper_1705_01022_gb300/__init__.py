@@ -26,13 +26,15 @@ class Simulation:
     L*L/4 bytes that the handle uses in place of its own allocation."""
 
     def __init__(self, L: int, p: float, q: float, seed: int, Bx: int = 0, By: int = 0,
-                 cx: int = 0, cy: int = 0, stream=None, lattice=None, no_init: bool = False):
+                 cx: int = 0, cy: int = 0, stream=None, lattice=None, no_init: bool = False,
+                 scheme: int = 0):
         prm = oct_params()
         prm.L, prm.p, prm.q, prm.seed = L, p, q, seed
         prm.Bx, prm.By, prm.cx, prm.cy = Bx, By, cx, cy
         prm.stream = _address(stream, "cuda_stream")
         prm.lattice = _address(lattice, "data_ptr")
         prm.no_init = 1 if no_init else 0
+        prm.scheme = scheme
         self._keep = (stream, lattice)
         self.h = _lib.oct_create_ex(prm)
         info = _lib.oct_get_info(self.h)

@@ -14,6 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liboct.so")
 
 OCT_OK, OCT_EINVAL, OCT_ENOMEM, OCT_ECUDA, OCT_ETIMEDOUT, OCT_EINTERNAL, OCT_EUNSUPPORTED = range(7)
+OCT_SCHEME_DT, OCT_SCHEME_DB = 0, 1
 
 
 class OctError(RuntimeError):
@@ -27,7 +28,7 @@ class oct_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("Bx", ctypes.c_int32), ("By", ctypes.c_int32),
                 ("cx", ctypes.c_int32), ("cy", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("lattice", ctypes.c_void_p), ("no_init", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("scheme", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class oct_w2(ctypes.Structure):
@@ -45,7 +46,8 @@ class oct_info(ctypes.Structure):
                 ("By", ctypes.c_int32), ("cx", ctypes.c_int32), ("cy", ctypes.c_int32),
                 ("p", ctypes.c_double), ("q", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("lattice", ctypes.c_void_p),
-                ("lattice_bytes", ctypes.c_int64)]
+                ("lattice_bytes", ctypes.c_int64), ("scheme", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class oct_stats(ctypes.Structure):

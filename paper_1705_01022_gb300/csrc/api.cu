@@ -47,6 +47,7 @@ struct oct_sim {
     double p = 0, q = 0;
     uint64_t seed = 0;
     int Bx = 0, By = 0, cx = 4, cy = 4;
+    int scheme = 0;
     uint32_t *lat = nullptr;
     bool own_lat = false;
     cudaStream_t stream = nullptr;
@@ -108,6 +109,8 @@ int validate(const oct_params *prm, int *Bx, int *By, int *cx, int *cy) {
     if ((*Bx / 32) * (*By / 16) > 32)
         return fail(OCT_EINVAL, "a sub-tile may hold at most 32 groups of 32x16 sites");
     if (L % (2 * *Bx) || L % (2 * *By)) return fail(OCT_EINVAL, "L must be a multiple of 2Bx and 2By");
+    if (prm->scheme != OCT_SCHEME_DT && prm->scheme != OCT_SCHEME_DB)
+        return fail(OCT_EINVAL, "scheme must be OCT_SCHEME_DT or OCT_SCHEME_DB");
     return OCT_OK;
 }
 
@@ -137,6 +140,7 @@ int sim_create(const oct_params *prm, oct_sim **out) {
     s->By = By;
     s->cx = cx;
     s->cy = cy;
+    s->scheme = prm->scheme;
     cudaError_t e = cudaGetDevice(&s->device);
     const size_t lat_bytes = static_cast<size_t>(s->L) * static_cast<size_t>(s->L) / 4;
     if (e == cudaSuccess) {
@@ -201,6 +205,8 @@ int sim_create(const oct_params *prm, oct_sim **out) {
     a.net = s->d_net;
     a.draws = s->d_net + oct::kNetSlots;
     s->any_random = p_rand || q_rand;
+    // DB delays border attempts only when two neighbouring flips could meet
+    a.scheme = (s->scheme == OCT_SCHEME_DB) ? ((s->p > 0.0 && s->q > 0.0) ? 2u : 1u) : 0u;
     *out = s;
     return OCT_OK;
 }
@@ -407,6 +413,8 @@ int oct_get_info(oct_sim *s, oct_info *out) {
     out->stream = s->stream;
     out->lattice = s->lat;
     out->lattice_bytes = s->L * s->L / 4;
+    out->scheme = s->scheme;
+    out->reserved = 0;
     return OCT_OK;
 }
 

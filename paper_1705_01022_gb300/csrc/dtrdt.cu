@@ -42,7 +42,7 @@
 namespace oct {
 namespace {
 
-template <bool RANDOM>
+template <bool RANDOM, int SCHEME>
 __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSM)
     dtrdt_step_kernel(const StepArgs a) {
     __shared__ __align__(16) uint32_t ring[kStepWarpsPerBlock * 32 * kRingWordsPerLane];
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSM)
 
     const uint32_t wpr = a.wpr;
     int net = 0, draws = 0;
-    run_subtile<RANDOM, false>(a.lat, L, wpr, a.Bx, a.By, x0, y0, active, c,
+    run_subtile<RANDOM, false, SCHEME>(a.lat, L, wpr, a.Bx, a.By, x0, y0, active, c,
                                ring + (threadIdx.x >> 5) * 32 * kRingWordsPerLane, net, draws);
 
     // Net flips (and acceptance draws): one atomic per warp into a spread of counters.
@@ -107,10 +107,26 @@ __global__ void advance_t_kernel(uint32_t *t_ptr) { *t_ptr += 1u; }
 cudaError_t launch_dtrdt_step(const StepArgs &a, bool any_random, cudaStream_t st) {
     const uint32_t n_tiles = a.tiles_x * a.tiles_y;
     const uint32_t blocks = (n_tiles + kStepWarpsPerBlock - 1) / kStepWarpsPerBlock;
-    if (any_random)
-        dtrdt_step_kernel<true><<<blocks, kStepWarpsPerBlock * 32, 0, st>>>(a);
-    else
-        dtrdt_step_kernel<false><<<blocks, kStepWarpsPerBlock * 32, 0, st>>>(a);
+    const dim3 grid(blocks), block(kStepWarpsPerBlock * 32);
+    switch (a.scheme) {
+        case 1:
+            if (any_random)
+                dtrdt_step_kernel<true, 1><<<grid, block, 0, st>>>(a);
+            else
+                dtrdt_step_kernel<false, 1><<<grid, block, 0, st>>>(a);
+            break;
+        case 2:
+            if (any_random)
+                dtrdt_step_kernel<true, 2><<<grid, block, 0, st>>>(a);
+            else
+                dtrdt_step_kernel<false, 2><<<grid, block, 0, st>>>(a);
+            break;
+        default:
+            if (any_random)
+                dtrdt_step_kernel<true, 0><<<grid, block, 0, st>>>(a);
+            else
+                dtrdt_step_kernel<false, 0><<<grid, block, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

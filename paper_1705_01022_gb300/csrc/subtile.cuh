@@ -74,9 +74,12 @@ struct TailPool {
 //    T, TAIL<<28), counted from 0 each device step), in order of group, then
 //    position.  The lanes of the sub-tile fill a shared ring with one Philox
 //    block each whenever the words a step needs run past what was generated.
-__device__ __forceinline__ uint32_t accept_candidates(uint32_t pmin, uint32_t pmax, uint32_t s,
+__device__ __forceinline__ uint4 level_words(uint32_t s, const LaneCtx &c) {
+    return philox4x32_10(c.t, c.k | ((s * 8u) << 2), c.T, (kTagAcc << 28) | c.g, c.k0, c.k1);
+}
+
+__device__ __forceinline__ uint32_t accept_candidates(uint32_t pmin, uint32_t pmax, const uint4 &W,
                                                       const LaneCtx &c, TailPool &tp) {
-    const uint4 W = philox4x32_10(c.t, c.k | ((s * 8u) << 2), c.T, (kTagAcc << 28) | c.g, c.k0, c.k1);
     const uint32_t lw[4] = {W.x, W.y, W.z, W.w};
     uint32_t acc = 0, und = pmin | pmax;
 #pragma unroll
@@ -342,11 +345,117 @@ __device__ __forceinline__ void step_apply_rt(uint32_t (&X)[16], uint32_t (&Y)[1
     if (c.gy < c.GY - 1) D ^= vu;
 }
 
+// One collective step of single-hit DB (dead border) with 4 x 4-site thread
+// cells: every cell attempts a uniform site of the whole cell (site word m:
+// bits 4j, 4j+1 = x offset, 4j+2, 4j+3 = y offset of cell j in TC row m).
+// The cell's border is its last column (x = 3) and last row (y = 3), where
+// an update reaches the next cell.  DELAYED (both p and q non-zero): bulk
+// attempts, then border attempts, then corner attempts, each phase decided on
+// the state the earlier phases left; otherwise all attempts of the step are
+// decided on the state before the step, which with one rate zero never lets
+// two accepted flips meet.  Every candidate of a phase is found before any of
+// its flips is applied.
+template <bool RANDOM, bool DELAYED>
+__device__ __forceinline__ void db_step(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E, uint32_t &D,
+                                        const uint4 &site, uint32_t s, const LaneCtx &c, TailPool &tp,
+                                        int &net, int &draws) {
+    const uint32_t sw[4] = {site.x, site.y, site.z, site.w};
+    uint32_t sel[16];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const uint32_t u = sw[m];
+        const uint32_t A = u & kNib, B = (u >> 1) & kNib, C = (u >> 2) & kNib, Dd = (u >> 3) & kNib;
+        const uint32_t col = (~(A | B) & kNib) | ((A & ~B) << 1) | ((B & ~A) << 2) | ((A & B) << 3);
+        sel[4 * m + 0] = col & ((~(C | Dd) & kNib) * 0xFu);
+        sel[4 * m + 1] = col & ((C & ~Dd) * 0xFu);
+        sel[4 * m + 2] = col & ((Dd & ~C) * 0xFu);
+        sel[4 * m + 3] = col & ((C & Dd) * 0xFu);
+    }
+    uint4 W = make_uint4(0u, 0u, 0u, 0u);
+    if (RANDOM) W = level_words(s, c);
+    constexpr int kPhases = DELAYED ? 3 : 1;
+#pragma unroll
+    for (int ph = 0; ph < kPhases; ++ph) {
+        uint32_t cand[16];
+        uint32_t pmin = 0u, pmax = 0u;
+#pragma unroll
+        for (int R = 0; R < 16; ++R) {
+            const bool last_row = (R & 3) == 3;
+            uint32_t mask = 0xFFFFFFFFu;  // columns of this phase in row R
+            if (DELAYED) {
+                if (ph == 0) mask = last_row ? 0u : 0x77777777u;
+                if (ph == 1) mask = last_row ? 0x77777777u : 0x88888888u;
+                if (ph == 2) mask = last_row ? 0x88888888u : 0u;
+            }
+            const uint32_t x = X[R];
+            const uint32_t xr = __funnelshift_r(x, E >> R, 1);
+            const uint32_t y = Y[R], yd = (R < 15) ? Y[(R + 1) & 15] : D;
+            cand[R] = sel[R] & mask & (x ^ xr) & (y ^ yd) & ~(x ^ y);
+        }
+        if (RANDOM) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                uint32_t mn = 0u, mx = 0u;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    mn |= cand[4 * m + r] & ~X[4 * m + r];
+                    mx |= cand[4 * m + r] & X[4 * m + r];
+                }
+                mn &= c.p_random;
+                mx &= c.q_random;
+                pmin |= ((mn | (mn >> 1) | (mn >> 2) | (mn >> 3)) & kNib) << m;
+                pmax |= ((mx | (mx >> 1) | (mx >> 2) | (mx >> 3)) & kNib) << m;
+            }
+            draws += __popc(pmin | pmax);
+        }
+        uint32_t acc = 0u;
+        if (RANDOM) acc = accept_candidates(pmin, pmax, W, c, tp);
+        uint32_t dE = 0u, dB0 = 0u, dD = 0u, dY0 = 0u;
+#pragma unroll
+        for (int R = 0; R < 16; ++R) {
+            const int m = R >> 2;
+            uint32_t amin = c.p_always, amax = c.q_always;
+            if (RANDOM) {
+                const uint32_t spread = ((acc >> m) & kNib) * 0xFu;
+                amin |= spread & c.p_random;
+                amax |= spread & c.q_random;
+            }
+            const uint32_t x = X[R];
+            const uint32_t f = cand[R] & ((~x & amin) | (x & amax));
+            net += __popc(f & ~x) - __popc(f & x);
+            X[R] = x ^ f ^ (f << 1);
+            Y[R] ^= f;
+            if (R < 15)
+                Y[(R + 1) & 15] ^= f;
+            else {
+                D ^= f;
+                dD = f;
+            }
+            dE |= (f >> 31) << R;
+            dB0 |= (f & 1u) << R;
+            if (R == 0) dY0 = f;
+        }
+        // exchange with the neighbouring lanes (all lanes take part)
+        E ^= dE;
+        const uint32_t vr = __shfl_up_sync(kFull, dE, 1);
+        const uint32_t vl = __shfl_down_sync(kFull, dB0, 1);
+        if (c.gx > 0) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) X[r] ^= (vr >> r) & 1u;
+        }
+        if (c.gx < c.GX - 1) E ^= vl;
+        const uint32_t vd = __shfl_up_sync(kFull, dD, c.GX);
+        const uint32_t vu = __shfl_down_sync(kFull, dY0, c.GX);
+        if (c.gy > 0) Y[0] ^= vd;
+        if (c.gy < c.GY - 1) D ^= vu;
+    }
+}
+
 // Device step on one sub-tile (Bx x By sites at (x0, y0)) held by the lanes of
 // one warp that share it: stage the lane's group from the planar lattice,
 // run the 16 single-hit collective steps, write back.  LANE_SETS: lanes of the
 // warp may belong to different sub-tiles (each with its own set draws).
-template <bool RANDOM, bool LANE_SETS>
+template <bool RANDOM, bool LANE_SETS, int SCHEME = 0>
 __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t Bx,
                                             uint32_t By, uint32_t x0, uint32_t y0, bool active,
                                             const LaneCtx &c, uint32_t *ring, int &net, int &draws) {
@@ -411,6 +520,15 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
     const uint4 setw = philox4x32_10(c.t, c.k, c.T, kTagSet << 28, c.k0, c.k1);
     uint4 site = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t s = 0; s < 16u; ++s) {
+        if (SCHEME != 0) {
+            // DB: one site word per TC row and step, 4 bits per cell
+            site = philox4x32_10(c.t, c.k | (s << 2), c.T, (kTagSiteDb << 28) | c.g, c.k0, c.k1);
+            if (SCHEME == 2)
+                db_step<RANDOM, true>(X, Y, E, D, site, s, c, tp, net, draws);
+            else
+                db_step<RANDOM, false>(X, Y, E, D, site, s, c, tp, net, draws);
+            continue;
+        }
         if ((s & 1u) == 0u)
             site = philox4x32_10(c.t, c.k | ((s >> 1) << 2), c.T, (kTagSite << 28) | c.g, c.k0, c.k1);
         const uint32_t d = (setw.x >> (2u * s)) & 3u;
@@ -424,7 +542,7 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
         uint32_t acc = 0u;
         if (RANDOM) {
             draws += __popc(pmin | pmax);
-            acc = accept_candidates(pmin, pmax, s, c, tp);
+            acc = accept_candidates(pmin, pmax, level_words(s, c), c, tp);
         }
         if (LANE_SETS)
             step_apply_rt<RANDOM>(X, Y, E, D, d >> 1, acc, cnd0, cnd1, c, net);

@@ -230,3 +230,28 @@ def test_c3_full_size_sampled(g, oracle):
         m = sim.measure()
         assert (m.s1, m.s2, m.hmax) == _tent_sums(L)
         assert m.s2_hi > 0
+
+
+DB_CONFIGS = [
+    dict(L=256, p=1.0, q=0.0, seed=1, Bx=64, By=64, n=5),
+    dict(L=256, p=0.95, q=0.0, seed=2, Bx=64, By=64, n=4),
+    dict(L=512, p=0.6, q=0.3, seed=3, Bx=256, By=64, n=4),
+    dict(L=256, p=0.5, q=0.5, seed=4, Bx=32, By=16, n=5),
+    dict(L=192, p=0.95, q=0.05, seed=5, Bx=32, By=32, n=4),
+    dict(L=1024, p=0.0, q=1.0, seed=6, Bx=512, By=32, n=3),
+]
+
+
+@pytest.mark.parametrize("c", DB_CONFIGS, ids=lambda c: "DB_L{L}_p{p}_q{q}_B{Bx}x{By}".format(**c))
+def test_db_bit_exact(g, oracle, c):
+    """DTrDB: single-hit dead border at block level (delayed borders when both
+    p and q are non-zero), against the oracle bit for bit."""
+    prm = oracle.Params(L=c["L"], p=c["p"], q=c["q"], seed=c["seed"], Bx=c["Bx"], By=c["By"],
+                        scheme=oracle.SCHEME_DB)
+    X, Y = oracle.flat(c["L"])
+    with g.Simulation(c["L"], c["p"], c["q"], c["seed"], Bx=c["Bx"], By=c["By"], scheme=1) as sim:
+        net = 0
+        for t in range(c["n"]):
+            net += oracle.dtrdt_run(X, Y, prm, t, 1)[0]
+            sim.run(1)
+            _assert_same(oracle, sim, X, Y, net, f"t={t + 1}")

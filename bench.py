@@ -122,23 +122,28 @@ def peaks():
         return {}
 
 
-def step_traffic(dtrdt_src_hash: str):
+def step_traffic(src_hash: str):
     """DRAM bytes per device-step launch from a committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    taken on the current kernel sources (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "dtrdt_step_traffic.json")) as f:
             d = json.load(f)
     except OSError:
         return None
-    if d.get("dtrdt_cu_sha256") != dtrdt_src_hash:
+    if d.get("kernel_sources_sha256") != src_hash:
         return None
     return d.get("dram_bytes_per_launch")
 
 
 def src_hash():
+    """sha256 of the list of sha256 sums of the step kernel's sources (as sha256sum prints it)."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_1705_01022_gb300", "csrc", "dtrdt.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    lines = []
+    for name in ("dtrdt.cu", "subtile.cuh"):
+        path = os.path.join("paper_1705_01022_gb300", "csrc", name)
+        with open(os.path.join(ROOT, path), "rb") as f:
+            lines.append(f"{hashlib.sha256(f.read()).hexdigest()}  {path}\n")
+    return hashlib.sha256("".join(lines).encode()).hexdigest()
 
 
 def cpu_baseline_window(oracle, a, state_getter, t, target_s):

@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--serve-jobs", type=int, default=32)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--db-steps", type=int, default=30)
+    ap.add_argument("--ac-reps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -409,24 +410,55 @@ def main():
     dtrdb = None
     if rank == 0 and a.db_steps > 0:
         sim.close()
-        with g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice,
-                          scheme=_lib.OCT_SCHEME_DB) as db:
-            db.run(3)
-            torch.cuda.synchronize()
-            _lib.oct_set_timing(db.h, True)
-            st_, en_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            st_.record(stream)
-            db.run(a.db_steps)
-            en_.record(stream)
-            torch.cuda.synchronize()
-            dms = st_.elapsed_time(en_)
-            kms, kl, _ = _lib.oct_get_timing(db.h)
-        dtrdb = {"value": L * L * a.db_steps / (dms * 1e6), "unit": UNIT, "mcs": a.db_steps,
-                 "device_step_ms": kms / max(1, kl),
+
+        def timed(p, q, scheme, n):
+            # continues from the lattice as it stands (no_init), new time origin
+            with g.Simulation(L, p, q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice,
+                              no_init=True, scheme=scheme) as h:
+                h.run(2)
+                torch.cuda.synchronize()
+                _lib.oct_set_timing(h.h, True)
+                st_, en_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                st_.record(stream)
+                h.run(n)
+                en_.record(stream)
+                torch.cuda.synchronize()
+                kms, kl, _ = _lib.oct_get_timing(h.h)
+            return L * L * n / (st_.elapsed_time(en_) * 1e6), kms / max(1, kl)
+
+        db_v, db_step = timed(a.p, a.q, _lib.OCT_SCHEME_DB, a.db_steps)
+        kdt_v, kdt_step = timed(1.0, 0.0, _lib.OCT_SCHEME_DT, a.db_steps)
+        kdb_v, kdb_step = timed(1.0, 0.0, _lib.OCT_SCHEME_DB, a.db_steps)
+        dtrdb = {"value": db_v, "unit": UNIT, "mcs": a.db_steps, "device_step_ms": db_step,
                  "scheme": "DTrDB: single-hit dead border at block level, borders delayed (p, q > 0)",
-                 "relative_to_dtrdt": (L * L * a.db_steps / (dms * 1e6)) / (value / world)}
+                 "start": "the DTrDT state after the timed region",
+                 "relative_to_dtrdt": db_v / (value / world),
+                 "kpz": {"p": 1.0, "q": 0.0, "dtrdt": kdt_v, "dtrdb": kdb_v, "relative": kdb_v / kdt_v,
+                         "device_step_ms": {"dtrdt": kdt_step, "dtrdb": kdb_step},
+                         "note": "DB with one rate zero carries out all attempts of a step together"}}
         sim = g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice)
         sim.run(a.warmup + a.steps)
+
+    # ---- two-time autocorrelations C_h, C_s (Sec. 2) on the live state ----
+    two_time = None
+    if rank == 0 and a.ac_reps > 0:
+        sim.snapshot()
+        sim.run(1)
+        ac = sim.measure_ac()
+        st_, en_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st_.record(stream)
+        for _ in range(a.ac_reps):
+            ac = sim.measure_ac()
+        en_.record(stream)
+        torch.cuda.synchronize()
+        ac_ms = st_.elapsed_time(en_) / a.ac_reps
+        ac_bytes = L * L // 2  # both planes of both lattices, read once
+        ac_gbs = ac_bytes / (ac_ms * 1e-3) / 1e9
+        two_time = {"t": ac.t, "s": ac.s, "c_h": ac.c_h, "c_s": ac.c_s, "ms_per_call": ac_ms,
+                    "calls": a.ac_reps,
+                    "roofline": {"bound": "hbm", "achieved": ac_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": ac_gbs / hbm_peak, "algorithmic_bytes": ac_bytes},
+                    "note": "per oct_measure_ac call: row pass, final pass and the 80-byte read-back"}
 
     # ---- batched replicas (uneven L) against a loop of plain launches ----
     batched = None
@@ -478,7 +510,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload(a), "clocks": clk.summary(), "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "dtrdb": dtrdb, "batched": batched, "serving": serving,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "dtrdb": dtrdb, "two_time": two_time, "batched": batched, "serving": serving,
             "probe": {"lop3_per_clk_per_sm": lop3, "imad_per_clk_per_sm": imad, "probe_mhz": probe_mhz},
         }
         print(json.dumps(out), flush=True)

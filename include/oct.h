@@ -215,6 +215,58 @@ int oct_probe_int_rate(int op, double *ops_per_clk_per_sm, double *sm_mhz, int *
 int oct_w2_noalloc(const void *lattice, int64_t L, void *stream, oct_w2 *out);
 
 /* ---------------------------------------------------------------------------
+ * Two-time autocorrelations (Sec. 2: C(t,s) of Eq. (5) and its forms for the
+ * slopes, C_s, and the heights, C_h).  The paper writes the height form with
+ * squared heights; its own identity C_h(s,s) = W^2(s) fixes the product of the
+ * heights at the two times, which is what is computed here.  <.> is the mean
+ * over the sites of one sample (averaging over samples is the caller's):
+ *   C_h(t,s) = <h(t) h(s)> - <h(t)><h(s)>
+ *            = (N*cross - sum_ht*sum_hs) / N^2,            N = L*L,
+ *   C_s(t,s) = <n(t) n(s)> - <n(t)><n(s)> over the 2N lattice-gas variables
+ *            n = X and n = Y (the slope bits of Eq. (1))
+ *            = (2N*(occ_x + occ_y) - m_t*m_s) / (2N)^2.
+ * Heights of each lattice are relative to its own h(0,0) = 0: C_h does not
+ * depend on a constant offset of either field.  Numerators are formed in
+ * 128-bit integers and converted to double once; at t = s, c_h equals the w2
+ * of oct_measure_w2 exactly and c_s = 1/4 on any valid slope field.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t t;          /* time of the current lattice (MCS); -1 from oct_two_time_planes */
+    int64_t s;          /* waiting time: time of the snapshot (MCS); -1 likewise */
+    int64_t n_sites;    /* N = L*L */
+    int64_t sum_ht;     /* sum over sites of h(t) */
+    int64_t sum_hs;     /* sum over sites of h(s) */
+    uint64_t cross_lo;  /* sum over sites of h(t) h(s): low 64 bits of a signed 128-bit value */
+    int64_t cross_hi;   /* its high 64 bits (two's complement) */
+    int64_t occ_x;      /* sum of X_t X_s (x slope up at both times) */
+    int64_t occ_y;      /* sum of Y_t Y_s */
+    int64_t m_t;        /* sum of X_t + Y_t */
+    int64_t m_s;        /* sum of X_s + Y_s */
+    double c_h;         /* C_h(t,s) */
+    double c_s;         /* C_s(t,s) */
+    int64_t reserved[4];
+} oct_ac;
+
+/* Stores a device copy of the current lattice as the state at the waiting
+ * time s = the handle's current t (L*L/4 bytes, allocated on the first call
+ * and owned by the handle; a later call overwrites it).  Asynchronous on the
+ * handle's stream. */
+int oct_snapshot(oct_sim *s);
+
+/* C_h(t,s) and C_s(t,s) of the current lattice (time t) against the last
+ * snapshot (time s).  Synchronises the handle's stream.  Errors: OCT_EINVAL if
+ * no snapshot was taken. */
+int oct_measure_ac(oct_sim *s, oct_ac *out);
+
+/* The same for two planar device lattices the caller owns (X plane then Y
+ * plane, L*L/4 bytes each; 16-byte aligned buffers take the vector path),
+ * e.g. a batched replica and a copy of it.  L even, a multiple of 32, at most
+ * 2^20.  Enqueued on `stream` (NULL: the legacy default stream) with
+ * stream-ordered scratch (cudaMallocAsync of about 48*L bytes), then
+ * synchronises the stream.  out->t = out->s = -1. */
+int oct_two_time_planes(const void *lat_t, const void *lat_s, int64_t L, void *stream, oct_ac *out);
+
+/* ---------------------------------------------------------------------------
  * Batched replicas.  Many independent realizations (each its own L, p, q and
  * key; every one the same DTrDT dynamics as a single handle, bit for bit) are
  * advanced together: every device step of every replica runs in one launch

@@ -111,6 +111,11 @@ def lib():
         L.oo_invariants_planar.argtypes = [i64, _P_u32, i64, i64]
         L.oo_replica_seed.argtypes = [u64, u32]
         L.oo_replica_seed.restype = u64
+        L.oo_two_time_sums.argtypes = [i64, _P_u8, _P_u8, _P_u8, _P_u8, ctypes.POINTER(_TwoTime)]
+        L.oo_ch_from_sums.argtypes = [i64, ctypes.POINTER(_TwoTime)]
+        L.oo_ch_from_sums.restype = dbl
+        L.oo_cs_from_sums.argtypes = [i64, ctypes.POINTER(_TwoTime)]
+        L.oo_cs_from_sums.restype = dbl
         _lib = L
     return _lib
 
@@ -241,6 +246,28 @@ def w2_from_sums(L: int, s1: int, s2: int) -> float:
 def w2(X, Y) -> float:
     s1, s2, _ = w2_sums(X, Y)
     return w2_from_sums(X.shape[0], s1, s2)
+
+
+class _TwoTime(ctypes.Structure):
+    _fields_ = [("sum_ht", ctypes.c_int64), ("sum_hs", ctypes.c_int64),
+                ("cross_lo", ctypes.c_uint64), ("cross_hi", ctypes.c_int64),
+                ("occ_x", ctypes.c_int64), ("occ_y", ctypes.c_int64),
+                ("m_t", ctypes.c_int64), ("m_s", ctypes.c_int64)]
+
+
+def two_time(Xt, Yt, Xs, Ys) -> dict:
+    """Two-time sums and C_h(t,s), C_s(t,s) of one sample (Sec. 2): lattice
+    (Xt, Yt) at time t against (Xs, Ys) at the waiting time s.  Integer sums
+    are exact Python ints; 'cross' = sum h(t) h(s)."""
+    L = Xt.shape[0]
+    a = _TwoTime()
+    arrs = [np.ascontiguousarray(v, dtype=np.uint8) for v in (Xt, Yt, Xs, Ys)]
+    lib().oo_two_time_sums(L, *arrs, ctypes.byref(a))
+    cross = (int(a.cross_hi) << 64) | int(a.cross_lo)
+    return {"sum_ht": int(a.sum_ht), "sum_hs": int(a.sum_hs), "cross": cross,
+            "occ_x": int(a.occ_x), "occ_y": int(a.occ_y), "m_t": int(a.m_t), "m_s": int(a.m_s),
+            "c_h": float(lib().oo_ch_from_sums(L, ctypes.byref(a))),
+            "c_s": float(lib().oo_cs_from_sums(L, ctypes.byref(a)))}
 
 
 def w2_sums_planar(words, L: int):

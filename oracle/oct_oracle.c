@@ -680,6 +680,61 @@ double oo_w2_from_sums(int64_t L, int64_t s1, uint64_t s2_lo, uint64_t s2_hi) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Two-time autocorrelations (Sec. 2, Eq. (5) and the C_s, C_h forms after   */
+/* it).  Written out site by site: both height fields are integrated exactly */
+/* as in oo_w2_sums (up column 0, then along each row), and every product is */
+/* accumulated in 128 bits.                                                  */
+/* ------------------------------------------------------------------------ */
+void oo_two_time_sums(int64_t L, const uint8_t *Xt, const uint8_t *Yt, const uint8_t *Xs,
+                      const uint8_t *Ys, oo_two_time *out) {
+    i128 St = 0, Ss = 0, C = 0;
+    int64_t ox = 0, oy = 0, mt = 0, ms = 0;
+    int64_t h0t = 0, h0s = 0; /* h(0,y) of each lattice */
+    for (int64_t y = 0; y < L; ++y) {
+        if (y > 0) {
+            h0t += 2 * (int64_t)Yt[y * L + 0] - 1;
+            h0s += 2 * (int64_t)Ys[y * L + 0] - 1;
+        }
+        int64_t ht = h0t, hs = h0s;
+        for (int64_t x = 0; x < L; ++x) {
+            const int64_t i = y * L + x;
+            if (x > 0) {
+                ht += 2 * (int64_t)Xt[i] - 1;
+                hs += 2 * (int64_t)Xs[i] - 1;
+            }
+            St += ht;
+            Ss += hs;
+            C += (i128)ht * hs;
+            ox += Xt[i] & Xs[i];
+            oy += Yt[i] & Ys[i];
+            mt += Xt[i] + Yt[i];
+            ms += Xs[i] + Ys[i];
+        }
+    }
+    out->sum_ht = (int64_t)St;
+    out->sum_hs = (int64_t)Ss;
+    out->cross_lo = (uint64_t)(u128)C;
+    out->cross_hi = (int64_t)(C >> 64);
+    out->occ_x = ox;
+    out->occ_y = oy;
+    out->m_t = mt;
+    out->m_s = ms;
+}
+
+double oo_ch_from_sums(int64_t L, const oo_two_time *a) {
+    const i128 N = (i128)L * L;
+    const i128 cross = (i128)(((u128)(uint64_t)a->cross_hi << 64) | a->cross_lo);
+    const i128 num = N * cross - (i128)a->sum_ht * a->sum_hs;
+    return (double)num / ((double)N * (double)N);
+}
+
+double oo_cs_from_sums(int64_t L, const oo_two_time *a) {
+    const i128 M = 2 * (i128)L * L; /* number of slope variables */
+    const i128 num = M * (i128)(a->occ_x + a->occ_y) - (i128)a->m_t * a->m_s;
+    return (double)num / ((double)M * (double)M);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Invariants fixed by the model: heights exist on the torus (row / column   */
 /* slope balance, zero circulation around every plaquette).                  */
 /* ------------------------------------------------------------------------ */

@@ -152,6 +152,32 @@ void oo_w2_sums_planar(int64_t L, const uint32_t *words, int64_t *s1, uint64_t *
                        uint64_t *s2_hi, int64_t *hmax);
 int oo_invariants_planar(int64_t L, const uint32_t *words, int64_t circ_y0, int64_t circ_y1);
 
+/* Two-time quantities of Sec. 2 (Eq. (5) and the slope and height forms
+ * C_s, C_h that follow it) for one sample: lattice (Xt, Yt) at time t and
+ * (Xs, Ys) at the waiting time s.  Heights of each lattice are relative to
+ * its own h(0,0) = 0; the covariance does not depend on that choice.
+ *   sum_ht = sum h(t),  sum_hs = sum h(s),  cross = sum h(t) h(s)  (128-bit)
+ *   occ_x  = sum X_t X_s,  occ_y = sum Y_t Y_s   (lattice-gas occupations)
+ *   m_t    = sum (X_t + Y_t),  m_s = sum (X_s + Y_s)
+ * parity unpinned: no; pinned by tests/test_oracle_two_time.py. */
+typedef struct {
+    int64_t sum_ht, sum_hs;
+    uint64_t cross_lo;
+    int64_t cross_hi;
+    int64_t occ_x, occ_y;
+    int64_t m_t, m_s;
+} oo_two_time;
+
+void oo_two_time_sums(int64_t L, const uint8_t *Xt, const uint8_t *Yt, const uint8_t *Xs,
+                      const uint8_t *Ys, oo_two_time *out);
+
+/* C_h(t,s) = <h(t) h(s)> - <h(t)><h(s)> with <.> the mean over the N = L*L
+ * sites: (N*cross - sum_ht*sum_hs) / N^2, numerator in 128-bit integers.
+ * C_s(t,s) = <n(t) n(s)> - <n(t)><n(s)> over the 2N slope variables (x and y):
+ * (2N*(occ_x+occ_y) - m_t*m_s) / (2N)^2. */
+double oo_ch_from_sums(int64_t L, const oo_two_time *a);
+double oo_cs_from_sums(int64_t L, const oo_two_time *a);
+
 /* Per-replica key derivation for batched runs: key_r = the first two words of
  * Philox(master key, (r, 0, 0, TAG_REPLICA << 28)). */
 uint64_t oo_replica_seed(uint64_t master_seed, uint32_t r);

@@ -10,7 +10,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import _lib
-from ._lib import OctError, oct_params, oct_w2  # noqa: F401
+from ._lib import OctError, oct_ac, oct_params, oct_w2  # noqa: F401
 
 
 def build(force: bool = False) -> str:
@@ -50,6 +50,14 @@ class Simulation:
 
     def measure(self) -> oct_w2:
         return _lib.oct_measure_w2(self.h)
+
+    def snapshot(self) -> None:
+        """Stores the current lattice as the state at the waiting time s = t."""
+        _lib.oct_snapshot(self.h)
+
+    def measure_ac(self) -> oct_ac:
+        """C_h(t,s) and C_s(t,s) of the current lattice against the last snapshot."""
+        return _lib.oct_measure_ac(self.h)
 
     def lattice(self) -> np.ndarray:
         w = np.empty(self.L * self.L // 16, dtype=np.uint32)
@@ -149,6 +157,13 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def two_time(lat_t, lat_s, L: int, stream=None) -> oct_ac:
+    """C_h(t,s), C_s(t,s) of two planar device lattices (torch tensors or raw
+    addresses of L*L/4 bytes each), e.g. a batched replica and a copy of it."""
+    return _lib.oct_two_time_planes(_address(lat_t, "data_ptr"), _address(lat_s, "data_ptr"), L,
+                                    _address(stream, "cuda_stream"))
 
 
 def _address(obj, attr: str):

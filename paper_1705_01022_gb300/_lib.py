@@ -60,6 +60,21 @@ class oct_replica(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 6)]
 
 
+class oct_ac(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int64), ("s", ctypes.c_int64), ("n_sites", ctypes.c_int64),
+                ("sum_ht", ctypes.c_int64), ("sum_hs", ctypes.c_int64),
+                ("cross_lo", ctypes.c_uint64), ("cross_hi", ctypes.c_int64),
+                ("occ_x", ctypes.c_int64), ("occ_y", ctypes.c_int64),
+                ("m_t", ctypes.c_int64), ("m_s", ctypes.c_int64),
+                ("c_h", ctypes.c_double), ("c_s", ctypes.c_double),
+                ("reserved", ctypes.c_int64 * 4)]
+
+    @property
+    def cross(self) -> int:
+        """sum h(t) h(s) as a Python int (signed 128-bit)."""
+        return (int(self.cross_hi) << 64) | int(self.cross_lo)
+
+
 # (name, argtypes, restype) of every entry point declared in include/oct.h
 _H = ctypes.c_void_p
 _SIGNATURES = [
@@ -85,6 +100,10 @@ _SIGNATURES = [
      ctypes.c_int),
     ("oct_w2_noalloc", [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(oct_w2)],
      ctypes.c_int),
+    ("oct_snapshot", [_H], ctypes.c_int),
+    ("oct_measure_ac", [_H, ctypes.POINTER(oct_ac)], ctypes.c_int),
+    ("oct_two_time_planes", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                             ctypes.POINTER(oct_ac)], ctypes.c_int),
     ("oct_replica_seed", [ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)],
      ctypes.c_int),
     ("oct_batch_create", [ctypes.c_int64, ctypes.POINTER(oct_replica), ctypes.c_void_p,
@@ -226,6 +245,22 @@ def oct_probe_int_rate(op: int):
 def oct_w2_noalloc(lattice: int, L: int, stream: int | None) -> oct_w2:
     out = oct_w2()
     _check(load().oct_w2_noalloc(lattice, L, stream, ctypes.byref(out)), "oct_w2_noalloc")
+    return out
+
+
+def oct_snapshot(h: int) -> None:
+    _check(load().oct_snapshot(h), "oct_snapshot")
+
+
+def oct_measure_ac(h: int) -> oct_ac:
+    out = oct_ac()
+    _check(load().oct_measure_ac(h, ctypes.byref(out)), "oct_measure_ac")
+    return out
+
+
+def oct_two_time_planes(lat_t: int, lat_s: int, L: int, stream: int | None) -> oct_ac:
+    out = oct_ac()
+    _check(load().oct_two_time_planes(lat_t, lat_s, L, stream, ctypes.byref(out)), "oct_two_time_planes")
     return out
 
 

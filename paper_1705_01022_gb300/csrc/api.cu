@@ -69,6 +69,11 @@ struct oct_sim {
     double step_ms = 0.0;
     int64_t step_launches = 0;
     int64_t draws = 0;  // acceptance draws counted up to the last measurement
+    // two-time autocorrelations
+    uint32_t *snap = nullptr;  // planar lattice at the waiting time
+    int64_t snap_t = -1;
+    oct::AcRowSums *d_ac_rows = nullptr;
+    oct::AcResult *d_ac = nullptr;
 };
 
 namespace {
@@ -122,6 +127,9 @@ void destroy_members(oct_sim *s) {
     if (s->d_rows) cudaFree(s->d_rows);
     if (s->d_w2) cudaFree(s->d_w2);
     if (s->h_small) cudaFreeHost(s->h_small);
+    if (s->snap) cudaFree(s->snap);
+    if (s->d_ac_rows) cudaFree(s->d_ac_rows);
+    if (s->d_ac) cudaFree(s->d_ac);
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
 }
@@ -456,6 +464,84 @@ int oct_destroy(oct_sim *s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     destroy_members(s);
     delete s;
+    return OCT_OK;
+}
+
+namespace {
+
+// C_h and C_s from the exact sums (numerators in 128-bit integers).
+void fill_ac(int64_t L, const oct::AcResult &r, oct_ac *out) {
+    const __int128 N = static_cast<__int128>(L) * L;
+    const __int128 cross =
+        static_cast<__int128>((static_cast<unsigned __int128>(r.cross_hi) << 64) | r.cross_lo);
+    const __int128 num_h = N * cross - static_cast<__int128>(r.sum_ht) * r.sum_hs;
+    const __int128 M = 2 * N;
+    const __int128 num_s = M * static_cast<__int128>(r.occ_x + r.occ_y) - static_cast<__int128>(r.m_t) * r.m_s;
+    *out = oct_ac{};
+    out->n_sites = static_cast<int64_t>(N);
+    out->sum_ht = r.sum_ht;
+    out->sum_hs = r.sum_hs;
+    out->cross_lo = r.cross_lo;
+    out->cross_hi = static_cast<int64_t>(r.cross_hi);
+    out->occ_x = r.occ_x;
+    out->occ_y = r.occ_y;
+    out->m_t = r.m_t;
+    out->m_s = r.m_s;
+    out->c_h = static_cast<double>(num_h) / (static_cast<double>(N) * static_cast<double>(N));
+    out->c_s = static_cast<double>(num_s) / (static_cast<double>(M) * static_cast<double>(M));
+}
+
+}  // namespace
+
+int oct_snapshot(oct_sim *s) {
+    if (!s) return fail(OCT_EINVAL, "NULL argument");
+    OCT_CUDA(cudaSetDevice(s->device));
+    const size_t bytes = lattice_words(s) * 4;
+    if (!s->snap) {
+        OCT_CUDA(cudaMalloc(&s->snap, bytes));
+        OCT_CUDA(cudaMalloc(&s->d_ac_rows, static_cast<size_t>(s->L) * sizeof(oct::AcRowSums)));
+        OCT_CUDA(cudaMalloc(&s->d_ac, sizeof(oct::AcResult)));
+    }
+    OCT_CUDA(cudaMemcpyAsync(s->snap, s->lat, bytes, cudaMemcpyDeviceToDevice, s->stream));
+    s->snap_t = static_cast<int64_t>(s->t);
+    return OCT_OK;
+}
+
+int oct_measure_ac(oct_sim *s, oct_ac *out) {
+    if (!s || !out) return fail(OCT_EINVAL, "NULL argument");
+    if (!s->snap) return fail(OCT_EINVAL, "no snapshot: call oct_snapshot first");
+    OCT_CUDA(cudaSetDevice(s->device));
+    OCT_CUDA(oct::launch_two_time(s->lat, s->snap, static_cast<uint32_t>(s->L), s->d_ac_rows, s->d_ac,
+                                  s->stream));
+    oct::AcResult r{};
+    OCT_CUDA(cudaMemcpyAsync(&r, s->d_ac, sizeof(r), cudaMemcpyDeviceToHost, s->stream));
+    OCT_CUDA(cudaStreamSynchronize(s->stream));
+    fill_ac(s->L, r, out);
+    out->t = static_cast<int64_t>(s->t);
+    out->s = s->snap_t;
+    return OCT_OK;
+}
+
+int oct_two_time_planes(const void *lat_t, const void *lat_s, int64_t L, void *stream, oct_ac *out) {
+    if (!lat_t || !lat_s || !out) return fail(OCT_EINVAL, "NULL argument");
+    if (L < 32 || L > (1 << 20) || L % 32 != 0) return fail(OCT_EINVAL, "L must be a multiple of 32 in [32, 2^20]");
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : cudaStreamLegacy;
+    void *scratch = nullptr;
+    const size_t rows_bytes = static_cast<size_t>(L) * sizeof(oct::AcRowSums);
+    OCT_CUDA(cudaMallocAsync(&scratch, rows_bytes + sizeof(oct::AcResult), st));
+    auto *rows = static_cast<oct::AcRowSums *>(scratch);
+    auto *res = reinterpret_cast<oct::AcResult *>(static_cast<char *>(scratch) + rows_bytes);
+    oct::AcResult r{};
+    cudaError_t e = oct::launch_two_time(static_cast<const uint32_t *>(lat_t), static_cast<const uint32_t *>(lat_s),
+                                         static_cast<uint32_t>(L), rows, res, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&r, res, sizeof(r), cudaMemcpyDeviceToHost, st);
+    const cudaError_t ef = cudaFreeAsync(scratch, st);
+    if (e == cudaSuccess) e = ef;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "oct_two_time_planes");
+    fill_ac(L, r, out);
+    out->t = -1;
+    out->s = -1;
     return OCT_OK;
 }
 

@@ -55,6 +55,22 @@ struct W2Result {
 cudaError_t launch_w2(const uint32_t *lat, uint32_t L, W2RowSums *rows, W2Result *out,
                       cudaStream_t st);
 
+// Two-time autocorrelation sums of lattice lat_t against lat_s (both planar, L x L).
+struct AcRowSums {
+    long long rt, rs;  // sum over x of r_t(x), r_s(x), r(x) = h(x,y) - h(0,y)
+    long long rts;     // sum over x of r_t(x) r_s(x)
+    int ct, cs;        // Y(0, y) of each lattice
+    int nx, ny;        // popcounts of X_t & X_s and Y_t & Y_s in row y
+    int mt, ms;        // popcounts of X and Y in row y of each lattice
+};
+struct AcResult {
+    long long sum_ht, sum_hs;                // sum h(t), sum h(s)
+    unsigned long long cross_lo, cross_hi;   // sum h(t) h(s), two's-complement 128-bit
+    long long occ_x, occ_y, m_t, m_s;
+};
+cudaError_t launch_two_time(const uint32_t *lat_t, const uint32_t *lat_s, uint32_t L, AcRowSums *rows,
+                            AcResult *out, cudaStream_t st);
+
 // Canonical 4x4-per-word layout conversion for canonical word rows
 // [cy0, cy0 + ncy) (each canonical row covers 4 lattice rows).
 cudaError_t launch_pack_canonical(const uint32_t *lat, uint32_t L, uint32_t cy0, uint32_t ncy,

@@ -1,0 +1,266 @@
+// Two-time autocorrelation sums (Sec. 2: C(t,s) of Eq. (5) and its height and
+// slope forms C_h, C_s) of a lattice at time t against a stored lattice at the
+// waiting time s.
+//
+// Heights of each lattice are taken relative to its own h(0,0) = 0 (the
+// covariance of two fields does not depend on a constant offset of either):
+//   h(0,y) = sum_{y'=1..y} (2 Y(0,y') - 1),  h(x,y) = h(0,y) + r(x,y),
+//   r(x,y) = sum_{x'=1..x} (2 X(x',y) - 1).
+// Wanted: S_t = sum h_t, S_s = sum h_s, C = sum h_t h_s (128-bit), and the
+// slope occupations sum X_t X_s, sum Y_t Y_s, sum (X_t + Y_t), sum (X_s + Y_s).
+//
+// Pass 1 (one warp per row, both lattices side by side): with q(x) the step
+// sum over x' = 0..x and s0 the step of bit 0, r = q - s0, so
+//   sum r_t r_s = sum q_t q_s - s0_s sum q_t - s0_t sum q_s + L s0_t s0_s.
+// Each lane takes 128 sites of the row (one 16-byte load per plane and
+// lattice); a packed warp scan of both lattices' step counts gives the lane's
+// starting q.  Inside the lane the running sums restart at 0 and are built one
+// nibble pair at a time from two tables: for a nibble n, the sum of its four
+// running steps and its net step; for a pair of nibbles, the sum of the
+// products of their running steps.  The lane's local sums are lifted to the
+// row's with one 64-bit multiply-add per lattice.
+// Pass 2 (one block): a scan of the column-0 Y bits gives h(0,y) of both
+// lattices, and S_t, S_s and C accumulate in 64/128-bit integers:
+//   C = sum_y [L h0_t h0_s + h0_t R_s + h0_s R_t + R_ts].
+// Row terms are below 2^52 for L <= 2^17.
+#include "oct_internal.h"
+
+namespace oct {
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr int kAcWarps = 8;
+
+// Running steps of a nibble n (bit i = site i): a_i = sum_{j<=i} (2 b_j - 1).
+__device__ __forceinline__ void nibble_steps(uint32_t n, int (&a)[4]) {
+    int e = 0;
+    for (int i = 0; i < 4; ++i) {
+        e += ((n >> i) & 1u) ? 1 : -1;
+        a[i] = e;
+    }
+}
+
+__global__ void __launch_bounds__(kAcWarps * 32)
+    ac_rows_kernel(const uint32_t *lt, const uint32_t *ls, uint32_t L, AcRowSums *rows) {
+    __shared__ int pair_tab[256];  // sum_i a_i(n_t) a_i(n_s), index n_t | n_s << 4
+    __shared__ int2 nib_tab[16];   // (sum_i a_i(n), a_3(n))
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        int a[4], b[4];
+        nibble_steps(static_cast<uint32_t>(i) & 15u, a);
+        nibble_steps(static_cast<uint32_t>(i) >> 4, b);
+        pair_tab[i] = a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3];
+        if (i < 16) nib_tab[i] = make_int2(a[0] + a[1] + a[2] + a[3], a[3]);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t wpr = L >> 5;
+    const size_t plane = static_cast<size_t>(L) * wpr;
+    const bool vec_ok = (wpr % 4u) == 0u && (reinterpret_cast<uintptr_t>(lt) % 16u) == 0u &&
+                        (reinterpret_cast<uintptr_t>(ls) % 16u) == 0u;
+    for (uint32_t y = blockIdx.x * kAcWarps + (threadIdx.x >> 5); y < L; y += gridDim.x * kAcWarps) {
+        const size_t ro = static_cast<size_t>(y) * wpr;
+        long long base_t = 0, base_s = 0;  // q just before the current chunk
+        long long qt = 0, qs = 0, qts = 0;
+        int nx = 0, ny = 0, mt = 0, ms = 0;
+        for (uint32_t w0 = 0; w0 < wpr; w0 += 128u) {
+            const uint32_t w = w0 + 4u * lane;
+            uint32_t wt[4] = {0u, 0u, 0u, 0u}, ws[4] = {0u, 0u, 0u, 0u};
+            uint32_t vt[4] = {0u, 0u, 0u, 0u}, vs[4] = {0u, 0u, 0u, 0u};
+            int nbits = 0;
+            if (vec_ok && w + 3u < wpr) {
+                const uint4 a = *reinterpret_cast<const uint4 *>(lt + ro + w);
+                const uint4 b = *reinterpret_cast<const uint4 *>(ls + ro + w);
+                const uint4 c = *reinterpret_cast<const uint4 *>(lt + plane + ro + w);
+                const uint4 d = *reinterpret_cast<const uint4 *>(ls + plane + ro + w);
+                wt[0] = a.x; wt[1] = a.y; wt[2] = a.z; wt[3] = a.w;
+                ws[0] = b.x; ws[1] = b.y; ws[2] = b.z; ws[3] = b.w;
+                vt[0] = c.x; vt[1] = c.y; vt[2] = c.z; vt[3] = c.w;
+                vs[0] = d.x; vs[1] = d.y; vs[2] = d.z; vs[3] = d.w;
+                nbits = 128;
+            } else {
+#pragma unroll
+                for (uint32_t j = 0; j < 4u; ++j)
+                    if (w + j < wpr) {
+                        wt[j] = lt[ro + w + j];
+                        ws[j] = ls[ro + w + j];
+                        vt[j] = lt[plane + ro + w + j];
+                        vs[j] = ls[plane + ro + w + j];
+                        nbits += 32;
+                    }
+            }
+            // X words wt (lattice t), ws (lattice s); Y words vt, vs
+            int pt = 0, ps = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                pt += __popc(wt[j]);
+                ps += __popc(ws[j]);
+                nx += __popc(wt[j] & ws[j]);
+                ny += __popc(vt[j] & vs[j]);
+                mt += __popc(vt[j]);
+                ms += __popc(vs[j]);
+            }
+            mt += pt;
+            ms += ps;
+            // Step counts of both lattices in one scan: |prefix| <= 4096, so the
+            // t count fits the low 16 bits of a two's-complement packed word.
+            const int st = 2 * pt - nbits, ss = 2 * ps - nbits;
+            int incl = st + ss * 65536;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int incl_t = static_cast<short>(incl & 0xFFFF);
+            const int incl_s = (incl - incl_t) / 65536;
+            const int tot = __shfl_sync(kFull, incl, 31);
+            const int tot_t = static_cast<short>(tot & 0xFFFF);
+            const int tot_s = (tot - tot_t) / 65536;
+            const long long Bt = base_t + (incl_t - st), Bs = base_s + (incl_s - ss);
+            // lane-local running sums (start at 0): sum a_t, sum a_s, sum a_t a_s
+            int bt = 0, bs = 0, lst = 0, lss = 0, lc = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (32 * j >= nbits) break;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t nt = (wt[j] >> (4 * k)) & 15u, ns = (ws[j] >> (4 * k)) & 15u;
+                    const int2 et = nib_tab[nt], es = nib_tab[ns];
+                    lc += bt * (4 * bs + es.x) + bs * et.x + pair_tab[nt | (ns << 4)];
+                    lst += 4 * bt + et.x;
+                    lss += 4 * bs + es.x;
+                    bt += et.y;
+                    bs += es.y;
+                }
+            }
+            qts += static_cast<long long>(nbits) * Bt * Bs + Bt * lss + Bs * lst + lc;
+            qt += static_cast<long long>(nbits) * Bt + lst;
+            qs += static_cast<long long>(nbits) * Bs + lss;
+            base_t += tot_t;
+            base_s += tot_s;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            qt += __shfl_xor_sync(kFull, qt, o);
+            qs += __shfl_xor_sync(kFull, qs, o);
+            qts += __shfl_xor_sync(kFull, qts, o);
+        }
+        nx = __reduce_add_sync(kFull, nx);
+        ny = __reduce_add_sync(kFull, ny);
+        mt = __reduce_add_sync(kFull, mt);
+        ms = __reduce_add_sync(kFull, ms);
+        if (lane == 0) {
+            const long long s0t = (lt[ro] & 1u) ? 1 : -1, s0s = (ls[ro] & 1u) ? 1 : -1;
+            const long long Ll = L;
+            AcRowSums o;
+            o.rt = qt - Ll * s0t;
+            o.rs = qs - Ll * s0s;
+            o.rts = qts - s0s * qt - s0t * qs + Ll * s0t * s0s;
+            o.ct = static_cast<int>(lt[plane + ro] & 1u);
+            o.cs = static_cast<int>(ls[plane + ro] & 1u);
+            o.nx = nx;
+            o.ny = ny;
+            o.mt = mt;
+            o.ms = ms;
+            rows[y] = o;
+        }
+    }
+}
+
+constexpr int kAcFinalThreads = 1024;
+
+__global__ void __launch_bounds__(kAcFinalThreads)
+    ac_final_kernel(const AcRowSums *rows, uint32_t L, AcResult *out) {
+    __shared__ long long part_t[kAcFinalThreads], part_s[kAcFinalThreads];
+    __shared__ long long red[8][kAcFinalThreads / 32];
+    __shared__ unsigned long long clo[kAcFinalThreads / 32], chi[kAcFinalThreads / 32];
+    const int tid = threadIdx.x;
+    const uint32_t per = (L + kAcFinalThreads - 1) / kAcFinalThreads;
+    const uint32_t y_begin = min(L, tid * per), y_end = min(L, (tid + 1) * per);
+    // column steps 2c-1 of rows 1..y (row 0 contributes nothing), both lattices
+    long long lt = 0, ls = 0;
+    for (uint32_t y = y_begin; y < y_end; ++y)
+        if (y > 0) {
+            lt += rows[y].ct ? 1 : -1;
+            ls += rows[y].cs ? 1 : -1;
+        }
+    part_t[tid] = lt;
+    part_s[tid] = ls;
+    __syncthreads();
+    for (int o = 1; o < kAcFinalThreads; o <<= 1) {
+        const long long vt = (tid >= o) ? part_t[tid - o] : 0;
+        const long long vs = (tid >= o) ? part_s[tid - o] : 0;
+        __syncthreads();
+        part_t[tid] += vt;
+        part_s[tid] += vs;
+        __syncthreads();
+    }
+    long long h0t = part_t[tid] - lt, h0s = part_s[tid] - ls;
+    const long long Ll = L;
+    long long St = 0, Ss = 0, nx = 0, ny = 0, mt = 0, ms = 0;
+    __int128 C = 0;
+    for (uint32_t y = y_begin; y < y_end; ++y) {
+        const AcRowSums r = rows[y];
+        if (y > 0) {
+            h0t += r.ct ? 1 : -1;
+            h0s += r.cs ? 1 : -1;
+        }
+        St += Ll * h0t + r.rt;
+        Ss += Ll * h0s + r.rs;
+        C += static_cast<__int128>(Ll * h0t * h0s) + static_cast<__int128>(h0t * r.rs) +
+             static_cast<__int128>(h0s * r.rt) + static_cast<__int128>(r.rts);
+        nx += r.nx;
+        ny += r.ny;
+        mt += r.mt;
+        ms += r.ms;
+    }
+    // block reduction; C as a two's-complement 128-bit value in (lo, hi)
+    long long v[6] = {St, Ss, nx, ny, mt, ms};
+    unsigned long long lo = static_cast<unsigned long long>(C);
+    unsigned long long hi = static_cast<unsigned long long>(static_cast<unsigned __int128>(C) >> 64);
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) v[i] += __shfl_down_sync(kFull, v[i], o);
+        const unsigned long long lo2 = __shfl_down_sync(kFull, lo, o);
+        const unsigned long long hi2 = __shfl_down_sync(kFull, hi, o);
+        const unsigned long long nlo = lo + lo2;
+        hi = hi + hi2 + (nlo < lo ? 1ull : 0ull);
+        lo = nlo;
+    }
+    if ((tid & 31) == 0) {
+        for (int i = 0; i < 6; ++i) red[i][tid >> 5] = v[i];
+        clo[tid >> 5] = lo;
+        chi[tid >> 5] = hi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long a[6] = {0, 0, 0, 0, 0, 0};
+        unsigned __int128 c = 0;
+        for (int w = 0; w < kAcFinalThreads / 32; ++w) {
+            for (int i = 0; i < 6; ++i) a[i] += red[i][w];
+            c += (static_cast<unsigned __int128>(chi[w]) << 64) | clo[w];
+        }
+        out->sum_ht = a[0];
+        out->sum_hs = a[1];
+        out->occ_x = a[2];
+        out->occ_y = a[3];
+        out->m_t = a[4];
+        out->m_s = a[5];
+        out->cross_lo = static_cast<unsigned long long>(c);
+        out->cross_hi = static_cast<unsigned long long>(c >> 64);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_two_time(const uint32_t *lat_t, const uint32_t *lat_s, uint32_t L, AcRowSums *rows,
+                            AcResult *out, cudaStream_t st) {
+    const uint64_t want = (static_cast<uint64_t>(L) + kAcWarps - 1) / kAcWarps;
+    const int blocks = static_cast<int>(want < 152ull * 8 ? want : 152ull * 8);
+    ac_rows_kernel<<<blocks, kAcWarps * 32, 0, st>>>(lat_t, lat_s, L, rows);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ac_final_kernel<<<1, kAcFinalThreads, 0, st>>>(rows, L, out);
+    return cudaGetLastError();
+}
+
+}  // namespace oct

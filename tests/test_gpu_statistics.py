@@ -1,7 +1,7 @@
 """Statistics of the GPU dynamics against what the paper fixes.
 
-* KPZ (p = 1, q = 0): the effective growth exponent of Eq. (7) on W(t) lies
-  near the paper's beta = 0.2414(2) (Eq. (5)) at L = 4096 over t in [100, 1000]
+* KPZ (p = 1, q = 0): the effective growth exponent of Eq. (8) on W(t) lies
+  near the paper's beta = 0.2414(2) (Sec. 2) at L = 4096 over t in [100, 1000]
   (finite-time corrections are expected, Sec. 4.2).
 * EW (p = q = 0.5): roughening is logarithmic, so beta_eff is small.
 * W^2(t) against true random-sequential updating (oracle O1): the paper

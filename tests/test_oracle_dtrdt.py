@@ -174,7 +174,7 @@ def test_roughness_prefactor_versus_sequential(oracle):
 
 
 def test_kpz_growth_exponent(oracle):
-    """beta_eff from Eq. (7) on W = sqrt(W^2) over t in [16, 128] MCS at L=256
+    """beta_eff from Eq. (8) on W = sqrt(W^2) over t in [16, 128] MCS at L=256
     lies near the asymptotic 0.2414(2); finite-time corrections are expected
     (Sec. 4.2), so the window is wide."""
     L = 256

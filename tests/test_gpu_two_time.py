@@ -87,24 +87,30 @@ def test_bare_buffers_at_L96(g, oracle):
 def test_full_size_properties(g):
     import torch
     L = 1 << 17
-    lat = torch.empty(L * L // 16, dtype=torch.int32, device="cuda")
-    with g.Simulation(L, 0.95, 0.05, 1, Bx=256, By=64, lattice=lat) as sim:
-        sim.run(2)
-        sim.snapshot()
-        m = sim.measure()
-        ac = sim.measure_ac()
-        assert ac.cross == m.s2 and ac.sum_ht == m.s1 and ac.c_h == m.w2
-        assert ac.c_s == 0.25 and ac.m_t == ac.m_s == L * L
-        snap = lat.clone()
-        sim.run(1)
-        m1 = sim.measure()
-        a = g.two_time(lat, snap, L)
-        b = g.two_time(snap, lat, L)
-        assert (a.cross, a.sum_ht, a.sum_hs) == (b.cross, b.sum_hs, b.sum_ht)
-        assert a.c_h == b.c_h and a.c_s == b.c_s
-        assert a.sum_ht == m1.s1 and a.sum_hs == m.s1
-        ac1 = sim.measure_ac()
-        assert (ac1.cross, ac1.c_h, ac1.c_s) == (a.cross, a.c_h, a.c_s)
-        assert 0.0 < a.c_h and a.c_h ** 2 <= m1.w2 * m.w2
-        assert 0.0 < a.c_s < 0.25
+    # one stream for the handle, the copy and the bare-buffer calls: the
+    # library's own streams do not synchronise with torch's default stream
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        lat = torch.empty(L * L // 16, dtype=torch.int32, device="cuda")
+        with g.Simulation(L, 0.95, 0.05, 1, Bx=256, By=64, stream=st, lattice=lat) as sim:
+            sim.run(2)
+            sim.snapshot()
+            m = sim.measure()
+            ac = sim.measure_ac()
+            assert ac.cross == m.s2 and ac.sum_ht == m.s1 and ac.c_h == m.w2
+            assert ac.c_s == 0.25 and ac.m_t == ac.m_s == L * L
+            snap = lat.clone()
+            sim.run(1)
+            m1 = sim.measure()
+            a = g.two_time(lat, snap, L, stream=st)
+            b = g.two_time(snap, lat, L, stream=st)
+            assert (a.cross, a.sum_ht, a.sum_hs) == (b.cross, b.sum_hs, b.sum_ht)
+            assert a.c_h == b.c_h and a.c_s == b.c_s
+            assert a.sum_ht == m1.s1 and a.sum_hs == m.s1
+            ac1 = sim.measure_ac()
+            assert (ac1.cross, ac1.c_h, ac1.c_s) == (a.cross, a.c_h, a.c_s)
+            assert (ac1.occ_x, ac1.occ_y) == (a.occ_x, a.occ_y)
+            assert 0.0 < a.c_h and a.c_h ** 2 <= m1.w2 * m.w2
+            assert 0.0 < a.c_s < 0.25
         del snap
+    st.synchronize()

@@ -26,8 +26,8 @@ _SRC = os.path.join(_HERE, "oct_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboct_oracle.so")
 _lib = None
 
-TAG_MCS, TAG_SET, TAG_SITE, TAG_ACC, TAG_SEQ, TAG_REPLICA, TAG_TAIL, TAG_SITE_DB = 1, 2, 3, 4, 5, 6, 7, 8
-SCHEME_DT, SCHEME_DB, SCHEME_DB_IGNORE = 0, 1, 2
+TAG_MCS, TAG_SET, TAG_SITE, TAG_ACC, TAG_SEQ, TAG_REPLICA, TAG_TAIL, TAG_SITE_DB, TAG_BORG = 1, 2, 3, 4, 5, 6, 7, 8, 9
+SCHEME_DT, SCHEME_DB, SCHEME_DB_IGNORE, SCHEME_DTR = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -60,7 +60,7 @@ class Params:
     By: int = 64
     cx: int = 4
     cy: int = 4
-    scheme: int = 0  # SCHEME_DT, SCHEME_DB or SCHEME_DB_IGNORE
+    scheme: int = 0  # SCHEME_DT, SCHEME_DB, SCHEME_DB_IGNORE or SCHEME_DTR
 
     def c(self) -> _Params:
         return _Params(self.L, self.Bx, self.By, self.cx, self.cy, self.p, self.q, self.seed,
@@ -111,6 +111,7 @@ def lib():
         L.oo_invariants_planar.argtypes = [i64, _P_u32, i64, i64]
         L.oo_replica_seed.argtypes = [u64, u32]
         L.oo_replica_seed.restype = u64
+        L.oo_subtile_step_sites.argtypes = [ctypes.POINTER(_Params), u32, u32, u32, i64, _P_i64, _P_i64]
         L.oo_two_time_sums.argtypes = [i64, _P_u8, _P_u8, _P_u8, _P_u8, ctypes.POINTER(_TwoTime)]
         L.oo_ch_from_sums.argtypes = [i64, ctypes.POINTER(_TwoTime)]
         L.oo_ch_from_sums.restype = dbl
@@ -246,6 +247,17 @@ def w2_from_sums(L: int, s1: int, s2: int) -> float:
 def w2(X, Y) -> float:
     s1, s2, _ = w2_sums(X, Y)
     return w2_from_sums(X.shape[0], s1, s2)
+
+
+def subtile_step_sites(prm: "Params", t: int, k: int, T: int, s: int):
+    """Local sites (lx, ly) of every thread cell's attempt in collective step s
+    of sub-tile T (device step k of MCS t); index = TC row * (Bx/cx) + TC column."""
+    n = (prm.Bx // prm.cx) * (prm.By // prm.cy)
+    lx = np.zeros(n, dtype=np.int64)
+    ly = np.zeros(n, dtype=np.int64)
+    if lib().oo_subtile_step_sites(ctypes.byref(prm.c()), t, k, T, s, lx, ly) != 0:
+        raise ValueError("invalid parameters")
+    return lx, ly
 
 
 class _TwoTime(ctypes.Structure):

@@ -192,7 +192,8 @@ int oo_check_params(const oo_params *P) {
     if (P->L % (2 * P->Bx) || P->L % (2 * P->By)) return -1;
     if (!(P->p >= 0.0 && P->p <= 1.0 && P->q >= 0.0 && P->q <= 1.0)) return -1;
     if (P->cx * P->cy * 8 >= ((int64_t)1 << 30)) return -1;
-    if (P->scheme < OO_SCHEME_DT || P->scheme > OO_SCHEME_DB_IGNORE) return -1;
+    if (P->scheme < OO_SCHEME_DT || P->scheme > OO_SCHEME_DTR) return -1;
+    if (P->scheme == OO_SCHEME_DTR && (P->cx > 16 || P->cy > 16)) return -1;
     int64_t groups = (P->Bx / BW) * ((P->By / P->cy + 3) / 4);
     if (groups >= ((int64_t)1 << 28)) return -1;
     int64_t tiles = (P->L / (2 * P->Bx)) * (P->L / (2 * P->By));
@@ -315,29 +316,6 @@ static int by_group_then_position(const void *pa, const void *pb) {
     return (a->pos > b->pos) - (a->pos < b->pos);
 }
 
-/* Block layer on one sub-tile: single-hit double tiling.
- *
- * The sub-tile (Bx x By sites, local origin (x0,y0)) is cut into thread
- * cells (TC) of cx x cy sites; each TC is cut into four sub-cells of
- * (cx/2) x (cy/2) sites, sub-cell d = (dx,dy) = (d&1, d>>1).  One collective
- * step: the block draws d uniformly (with replacement, not a permutation),
- * every TC performs exactly one attempt at a uniformly chosen site of its
- * sub-cell d, then all synchronise.  cx*cy collective steps make one sweep
- * of the sub-tile (Bx*By attempts).  Attempts of one step never share a slope
- * bit, so every decision can be taken on the state before the step and the
- * flips applied afterwards.
- *
- * Random streams (reading fixed by the schedule specification):
- *   set draw for step s : word (s%64)/16 of Philox(seed, (t, k|(s/64)<<2, T, SET<<28)),
- *                         bits 2*(s%16) .. +1.
- *   TCs are grouped: a band is one TC row, BW = min(32,Bx) sites wide; a group
- *   is four vertically consecutive bands of one band column; g = (c/4)*(Bx/BW)
- *   + band column, m = c%4 (c = TC row), j = TC index inside its band.
- *   site draw           : word m of Philox(seed, (t, k|(s/spw)<<2, T, SITE<<28|g)),
- *                         bits fw*j + (s%spw)*(fw/spw) .. + bpt-1, low log2(cx/2)
- *                         bits = x offset, the rest = y offset.
- *   acceptance uniform  : see acc_level_words / tail_word above.
- */
 /* Decides, flips and counts the attempts of one conflict-free batch (a
  * collective step of DT, or one phase of a DB step): attempts whose site is
  * eligible on the current state are decided by the four leading level bits of
@@ -416,7 +394,19 @@ static void decide_and_flip(const uint32_t key[2], uint32_t t, uint32_t k, uint3
  * both non-zero two accepted flips can then hit the same slope bit, which the
  * flip tracker counts.
  *
+ * DTR (DTrDTr, Sec. 3.2 notation paragraph): DT whose block-layer origin
+ * moves to a uniform (ax, ay) in [0,cx) x [0,cy) after every collective step,
+ * the cell grid wrapping around the sub-tile.  The active sub-cell of set d
+ * then starts at column c0 = (ax + dx*cx/2) mod cx and row r0 = (ay +
+ * dy*cy/2) mod cy of every (unshifted) cell; the attempt of TC (a, c) is at
+ * ((a*cx + c0 + rx) mod Bx, (c*cy + r0 + ry) mod By).  (Each shifted cell is
+ * labelled by the unshifted cell holding the first site of its active
+ * sub-cell; a relabelling of cells does not change the dynamics.)
+ *
  * Random streams (reading fixed by the schedule specification):
+ *   block origin (DTR) for step s : byte s%4 of word (s%16)/4 of
+ *                         Philox(seed, (t, k|(s/16)<<2, T, BORG<<28)); ax =
+ *                         its low log2(cx) bits, ay = log2(cy) bits from bit 4.
  *   set draw (DT) for step s : word (s%64)/16 of Philox(seed, (t, k|(s/64)<<2, T, SET<<28)),
  *                         bits 2*(s%16) .. +1.
  *   TCs are grouped: a band is one TC row, BW = min(32,Bx) sites wide; a group
@@ -429,11 +419,48 @@ static void decide_and_flip(const uint32_t key[2], uint32_t t, uint32_t k, uint3
  *   acceptance uniform  : see acc_level_words / tail_word above; with DB the
  *                         tail words are taken phase by phase.
  */
+/* The block-layer draws of one collective step that every TC of the
+ * sub-tile shares: the DT set (dx, dy) and, for DTR, the block origin. */
+typedef struct {
+    int64_t dx, dy;  /* sub-cell set d = (dx, dy) (DT, DTR) */
+    int64_t c0, r0;  /* first column / row of the active sub-cell in each cell */
+} step_draw_t;
+
+static step_draw_t step_draw(const oo_params *P, const uint32_t key[2], uint32_t t, uint32_t k,
+                             uint32_t T, int64_t s) {
+    step_draw_t d = {0, 0, 0, 0};
+    if (P->scheme == OO_SCHEME_DB || P->scheme == OO_SCHEME_DB_IGNORE) return d;
+    uint32_t sw[4];
+    philox_at(key, t, k | (uint32_t)((s / 64) << 2), T, OO_TAG_SET << 28, sw);
+    const int set = (int)((sw[(s % 64) / 16] >> (2 * (s % 16))) & 3u);
+    d.dx = set & 1;
+    d.dy = set >> 1;
+    d.c0 = d.dx * (P->cx / 2);
+    d.r0 = d.dy * (P->cy / 2);
+    if (P->scheme == OO_SCHEME_DTR) {
+        uint32_t bw[4];
+        philox_at(key, t, k | (uint32_t)((s / 16) << 2), T, OO_TAG_BORG << 28, bw);
+        const uint32_t byte = (bw[(s % 16) / 4] >> (8 * (s % 4))) & 0xFFu;
+        const int64_t ax = byte & (uint32_t)(P->cx - 1), ay = (byte >> 4) & (uint32_t)(P->cy - 1);
+        d.c0 = (ax + d.c0) % P->cx;
+        d.r0 = (ay + d.r0) % P->cy;
+    }
+    return d;
+}
+
+/* Local site in the sub-tile of the attempt of TC column a, TC row c, whose
+ * random offset inside its sub-cell (DT, DTR) or cell (DB) is (rx, ry). */
+static void tc_local_site(const oo_params *P, const step_draw_t *d, int64_t a, int64_t c, int64_t rx,
+                          int64_t ry, int64_t *lx, int64_t *ly) {
+    *lx = (a * P->cx + d->c0 + rx) % P->Bx;
+    *ly = (c * P->cy + d->r0 + ry) % P->By;
+}
+
 static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, uint32_t k,
                         uint32_t T, int64_t x0, int64_t y0, view_t *v, int64_t *net,
                         int64_t *attempts, conflict_t *cf) {
     const int64_t L = P->L, Bx = P->Bx, By = P->By, cx = P->cx, cy = P->cy;
-    const int db = P->scheme != OO_SCHEME_DT;
+    const int db = P->scheme == OO_SCHEME_DB || P->scheme == OO_SCHEME_DB_IGNORE;
     /* The paper delays border attempts only where two neighbouring sites can
      * both be accepted, i.e. when both p and q are non-zero; with one of them
      * zero its DB runs carry out all attempts of a step together. */
@@ -461,14 +488,7 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
     uint32_t tail_next = 0; /* tail-stream words used so far in this device step */
 
     for (int64_t s = 0; s < n_steps; ++s) {
-        int64_t dx = 0, dy = 0;
-        if (!db) {
-            uint32_t sw[4];
-            philox_at(key, t, k | (uint32_t)((s / 64) << 2), T, OO_TAG_SET << 28, sw);
-            const int d = (int)((sw[(s % 64) / 16] >> (2 * (s % 16))) & 3u);
-            dx = d & 1;
-            dy = d >> 1;
-        }
+        const step_draw_t sd = step_draw(P, key, t, k, T, s);
         int64_t na = 0;
         /* every thread cell's attempt: site and leading acceptance bits */
         for (int64_t gr = 0; gr < group_rows; ++gr) {
@@ -491,8 +511,8 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
                             rx = r & ((1u << bx_bits) - 1u);
                             ry = r >> bx_bits;
                         }
-                        const int64_t lx = a * cx + dx * (cx / 2) + rx;
-                        const int64_t ly = c * cy + dy * (cy / 2) + ry;
+                        int64_t lx, ly;
+                        tc_local_site(P, &sd, a, c, rx, ry, &lx, &ly);
                         const int64_t gx = wrap(x0 + lx, L), gy = wrap(y0 + ly, L);
                         if (attempts) attempts[gy * L + gx]++;
                         attempt_t *A = &all[na];
@@ -541,6 +561,43 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
     free(phase);
     free(tied);
     free(cls);
+}
+
+int oo_subtile_step_sites(const oo_params *P, uint32_t t, uint32_t k, uint32_t T, int64_t s,
+                          int64_t *lx, int64_t *ly) {
+    if (oo_check_params(P) || s < 0 || s >= P->cx * P->cy) return -1;
+    uint32_t key[2];
+    seed_key(P->seed, key);
+    const int64_t Bx = P->Bx, By = P->By, cx = P->cx, cy = P->cy;
+    const int db = P->scheme == OO_SCHEME_DB || P->scheme == OO_SCHEME_DB_IGNORE;
+    const int64_t BW = Bx < 32 ? Bx : 32;
+    const int64_t tcs_per_band = BW / cx, band_cols = Bx / BW, tc_rows = By / cy;
+    const int64_t ux = db ? cx : cx / 2, uy = db ? cy : cy / 2;
+    const int bx_bits = ilog2_exact(ux), by_bits = ilog2_exact(uy);
+    const int bpt = bx_bits + by_bits;
+    const int64_t fw = 32 / tcs_per_band;
+    const int spw = (bpt > 0 && 2 * bpt <= fw) ? 2 : 1;
+    const uint32_t site_tag = db ? OO_TAG_SITE_DB : OO_TAG_SITE;
+    const step_draw_t sd = step_draw(P, key, t, k, T, s);
+    for (int64_t c = 0; c < tc_rows; ++c) {
+        const int64_t gr = c / 4, m = c % 4;
+        for (int64_t a = 0; a < Bx / cx; ++a) {
+            const int64_t bc = a / tcs_per_band, j = a % tcs_per_band;
+            const uint32_t g = (uint32_t)(gr * band_cols + bc);
+            int64_t rx = 0, ry = 0;
+            if (bpt > 0) {
+                uint32_t site_w[4];
+                philox_at(key, t, k | (uint32_t)((s / spw) << 2), T, (site_tag << 28) | g, site_w);
+                const int64_t off = fw * j + (s % spw) * (fw / spw);
+                const uint32_t r = (site_w[m] >> off) & ((1u << bpt) - 1u);
+                rx = r & ((1u << bx_bits) - 1u);
+                ry = r >> bx_bits;
+            }
+            const int64_t i = c * (Bx / cx) + a;
+            tc_local_site(P, &sd, a, c, rx, ry, &lx[i], &ly[i]);
+        }
+    }
+    return 0;
 }
 
 static int footprint_inside(const view_t *v, int64_t x0, int64_t y0, int64_t Bx, int64_t By) {

@@ -33,11 +33,13 @@ extern "C" {
 #define OO_TAG_REPLICA 6u
 #define OO_TAG_TAIL 7u
 #define OO_TAG_SITE_DB 8u
+#define OO_TAG_BORG 9u  /* block-layer origin of DTrDTr */
 
 /* Block-layer schemes (Sec. 3.1). */
 #define OO_SCHEME_DT 0          /* single-hit double tiling (DTrDT)                     */
 #define OO_SCHEME_DB 1          /* single-hit dead border, delayed borders (DTrDB)      */
 #define OO_SCHEME_DB_IGNORE 2   /* dead border with border attempts not delayed         */
+#define OO_SCHEME_DTR 3         /* double tiling with a random block-layer origin (DTrDTr) */
 
 typedef struct {
     int64_t L;        /* lateral size; periodic */
@@ -118,6 +120,13 @@ uint32_t oo_dtrdt_tail_word(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, u
  * only sites far enough from the window edge end up exact. */
 int oo_dtrdt_mcs_window(const oo_params *prm, uint32_t t, int64_t wx, int64_t wy,
                         int64_t W, int64_t H, uint8_t *Xw, uint8_t *Yw, int64_t *net_flips);
+
+/* Local sites (lx[i], ly[i]) in the sub-tile of the attempts of every thread
+ * cell i = (TC row)*(Bx/cx) + (TC column) in collective step s of sub-tile T,
+ * device step k, MCS t (the block layer's site selection alone, for tests of
+ * the attempt pattern).  Returns 0, or -1 for invalid parameters. */
+int oo_subtile_step_sites(const oo_params *P, uint32_t t, uint32_t k, uint32_t T, int64_t s,
+                          int64_t *lx, int64_t *ly);
 
 /* O3: exact roughness sums, Eq. (3).  Heights relative to h(0,0) = 0 are
  * integrated first up column 0 and then along each row.  s1 = sum h,

@@ -407,7 +407,7 @@ def main():
     }
 
     # ---- the DTrDB block layer on the same workload (the paper's Fig. 7 pair) ----
-    dtrdb = None
+    dtrdb = dtrdtr = None
     if rank == 0 and a.db_steps > 0:
         sim.close()
 
@@ -436,6 +436,10 @@ def main():
                  "kpz": {"p": 1.0, "q": 0.0, "dtrdt": kdt_v, "dtrdb": kdb_v, "relative": kdb_v / kdt_v,
                          "device_step_ms": {"dtrdt": kdt_step, "dtrdb": kdb_step},
                          "note": "DB with one rate zero carries out all attempts of a step together"}}
+        dtr_v, dtr_step = timed(a.p, a.q, _lib.OCT_SCHEME_DTR, a.db_steps)
+        dtrdtr = {"value": dtr_v, "unit": UNIT, "mcs": a.db_steps, "device_step_ms": dtr_step,
+                  "scheme": "DTrDTr: double tiling with a block-layer origin moved after every collective step",
+                  "start": "the DTrDB state after its run", "relative_to_dtrdt": dtr_v / (value / world)}
         sim = g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice)
         sim.run(a.warmup + a.steps)
 
@@ -510,7 +514,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload(a), "clocks": clk.summary(), "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "dtrdb": dtrdb, "two_time": two_time, "batched": batched, "serving": serving,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "dtrdb": dtrdb, "dtrdtr": dtrdtr, "two_time": two_time, "batched": batched, "serving": serving,
             "probe": {"lop3_per_clk_per_sm": lop3, "imad_per_clk_per_sm": imad, "probe_mhz": probe_mhz},
         }
         print(json.dumps(out), flush=True)

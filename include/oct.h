@@ -69,12 +69,17 @@ typedef struct oct_sim oct_sim; /* opaque; owns its device memory unless told ot
  *          caller and must outlive the handle.
  *   no_init  0: write the flat start h = (x+y) mod 2; 1: keep the buffer.
  *   scheme   block-layer decomposition (Sec. 3.1): OCT_SCHEME_DT (default,
- *          DTrDT: single-hit double tiling) or OCT_SCHEME_DB (DTrDB:
+ *          DTrDT: single-hit double tiling), OCT_SCHEME_DB (DTrDB:
  *          single-hit dead border; border attempts are delayed after the bulk
  *          ones when both p and q are non-zero, otherwise all attempts of a
- *          step are carried out together, as in the paper's runs). */
+ *          step are carried out together, as in the paper's runs) or
+ *          OCT_SCHEME_DTR (DTrDTr, Sec. 3.2: single-hit double tiling whose
+ *          block-layer origin moves to a uniform position in the thread cell
+ *          after every collective step, the cell grid wrapping around the
+ *          sub-tile). */
 #define OCT_SCHEME_DT 0
 #define OCT_SCHEME_DB 1
+#define OCT_SCHEME_DTR 2
 typedef struct {
     int64_t L;
     double p, q;

@@ -14,7 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liboct.so")
 
 OCT_OK, OCT_EINVAL, OCT_ENOMEM, OCT_ECUDA, OCT_ETIMEDOUT, OCT_EINTERNAL, OCT_EUNSUPPORTED = range(7)
-OCT_SCHEME_DT, OCT_SCHEME_DB = 0, 1
+OCT_SCHEME_DT, OCT_SCHEME_DB, OCT_SCHEME_DTR = 0, 1, 2
 
 
 class OctError(RuntimeError):

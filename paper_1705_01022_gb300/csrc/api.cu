@@ -114,8 +114,8 @@ int validate(const oct_params *prm, int *Bx, int *By, int *cx, int *cy) {
     if ((*Bx / 32) * (*By / 16) > 32)
         return fail(OCT_EINVAL, "a sub-tile may hold at most 32 groups of 32x16 sites");
     if (L % (2 * *Bx) || L % (2 * *By)) return fail(OCT_EINVAL, "L must be a multiple of 2Bx and 2By");
-    if (prm->scheme != OCT_SCHEME_DT && prm->scheme != OCT_SCHEME_DB)
-        return fail(OCT_EINVAL, "scheme must be OCT_SCHEME_DT or OCT_SCHEME_DB");
+    if (prm->scheme != OCT_SCHEME_DT && prm->scheme != OCT_SCHEME_DB && prm->scheme != OCT_SCHEME_DTR)
+        return fail(OCT_EINVAL, "scheme must be OCT_SCHEME_DT, OCT_SCHEME_DB or OCT_SCHEME_DTR");
     return OCT_OK;
 }
 
@@ -214,7 +214,10 @@ int sim_create(const oct_params *prm, oct_sim **out) {
     a.draws = s->d_net + oct::kNetSlots;
     s->any_random = p_rand || q_rand;
     // DB delays border attempts only when two neighbouring flips could meet
-    a.scheme = (s->scheme == OCT_SCHEME_DB) ? ((s->p > 0.0 && s->q > 0.0) ? 2u : 1u) : 0u;
+    // kernel variants: 0 DT, 1 DB with all attempts of a step together, 2 DB
+    // with delayed borders (both rates non-zero), 3 DTrDTr
+    a.scheme = (s->scheme == OCT_SCHEME_DB) ? ((s->p > 0.0 && s->q > 0.0) ? 2u : 1u)
+               : (s->scheme == OCT_SCHEME_DTR) ? 3u : 0u;
     *out = s;
     return OCT_OK;
 }

@@ -121,6 +121,12 @@ cudaError_t launch_dtrdt_step(const StepArgs &a, bool any_random, cudaStream_t s
             else
                 dtrdt_step_kernel<false, 2><<<grid, block, 0, st>>>(a);
             break;
+        case 3:
+            if (any_random)
+                dtrdt_step_kernel<true, 3><<<grid, block, 0, st>>>(a);
+            else
+                dtrdt_step_kernel<false, 3><<<grid, block, 0, st>>>(a);
+            break;
         default:
             if (any_random)
                 dtrdt_step_kernel<true, 0><<<grid, block, 0, st>>>(a);

@@ -23,7 +23,7 @@ struct StepArgs {
     uint32_t k;                // device step 0..3
     unsigned long long *net;   // kNetSlots signed flip counters (two's complement)
     unsigned long long *draws; // kNetSlots counters of attempts that needed an acceptance draw
-    uint32_t scheme;           // 0: DT; 1: DB (borders together); 2: DB with delayed borders
+    uint32_t scheme;           // 0: DT; 1: DB (borders together); 2: DB with delayed borders; 3: DTrDTr
 };
 
 constexpr int kNetSlots = 1024;

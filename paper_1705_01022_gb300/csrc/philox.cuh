@@ -17,6 +17,7 @@ constexpr uint32_t kTagAcc = 4u;
 constexpr uint32_t kTagReplica = 6u;
 constexpr uint32_t kTagTail = 7u;
 constexpr uint32_t kTagSiteDb = 8u;
+constexpr uint32_t kTagBorg = 9u;  // block-layer origin of DTrDTr
 
 __host__ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
                                                         uint32_t c3, uint32_t k0, uint32_t k1) {

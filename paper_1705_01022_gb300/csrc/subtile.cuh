@@ -451,6 +451,201 @@ __device__ __forceinline__ void db_step(uint32_t (&X)[16], uint32_t (&Y)[16], ui
     }
 }
 
+// A collective step of DTrDTr (Sec. 3.2, notation paragraph): DT whose
+// block-layer origin moves after every step, the cell grid wrapping around
+// the sub-tile.  With the active sub-cell of every cell starting at column c0
+// and row R0 (uniform in [0, 4): the set's offset plus the moved origin), the
+// attempt of TC (j, m) of a lane is at (4j + c0 + rx, 4m + R0 + ry).  For
+// c0 = 3 the pair of TC 7 reaches column 32, i.e. column 0 of the lane to the
+// right (of the sub-tile's first lane, for the last lane: the wrap); for
+// R0 = 3 the pair of TC row 3 reaches row 16, row 0 of the lane below (or of
+// the first lane row), and TC (7, 3) can reach the lane diagonally below.
+// The lane holding such a site tests it; the candidate goes back to the
+// owning lane, which draws its acceptance with its own level words (so the
+// uniforms, and the order of ties, stay those of the owning thread cell), and
+// the decision returns to the holder, which flips.  The neighbour copies E, D
+// are kept as in DT: the lattice itself does not wrap inside the sub-tile.
+// As for DT the step runs in three phases (candidates and flips specialised
+// on R0, one copy of the acceptance code between them).
+struct DtrLanes {
+    int lL, lR, lA, lB, lAL, lBR;  // lanes left, right, above, below, above-left, below-right (wrapping)
+};
+
+__device__ __forceinline__ DtrLanes dtr_lanes(const LaneCtx &c) {
+    const int gxl = c.gx == 0 ? c.GX - 1 : c.gx - 1, gxr = c.gx == c.GX - 1 ? 0 : c.gx + 1;
+    const int gya = c.gy == 0 ? c.GY - 1 : c.gy - 1, gyb = c.gy == c.GY - 1 ? 0 : c.gy + 1;
+    DtrLanes n;
+    n.lL = gxl + c.gy * c.GX;
+    n.lR = gxr + c.gy * c.GX;
+    n.lA = c.gx + gya * c.GX;
+    n.lB = c.gx + gyb * c.GX;
+    n.lAL = gxl + gya * c.GX;
+    n.lBR = gxr + gyb * c.GX;
+    return n;
+}
+
+// Phase 1.  ca[m], cb[m]: candidates in rows 4m+R0 and 4m+R0+1 held by this
+// lane; with R0 = 3, cb[3] holds row 0 instead (row 16 belongs to the lane
+// below).  pmin / pmax: packed candidates of this lane's own thread cells.
+template <int R0, bool RANDOM>
+__device__ __forceinline__ void dtr_candidates(const uint32_t (&X)[16], const uint32_t (&Y)[16], uint32_t E,
+                                               uint32_t D, const uint4 &site, uint32_t s, uint32_t c0,
+                                               const LaneCtx &c, const DtrLanes &n, uint32_t (&ca)[4],
+                                               uint32_t (&cb)[4], uint32_t &pmin, uint32_t &pmax) {
+    const bool SX = c0 == 3u;     // pairs reach column 32 (uniform over the warp)
+    constexpr bool SY = R0 == 3;  // pairs reach row 16
+    const uint32_t sw[4] = {site.x, site.y, site.z, site.w};
+    const uint32_t par = 2u * (s & 1u);
+    // Selected sites: own thread cells in place, those past column 31 in xw
+    // (bit = row; bit 16 = row 16), those in row 16 in yw (bit = column).
+    uint32_t xw = 0u, yw = 0u;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const uint32_t u = sw[m] >> par;
+        const uint32_t col = ((u & kNib) << 1) | (~u & kNib);  // bit 4j + rx
+        const uint32_t yoff = ((u >> 1) & kNib) * 0xFu;         // thread cells with ry = 1
+        const uint64_t a64 = static_cast<uint64_t>(col & ~yoff) << c0;
+        const uint64_t b64 = static_cast<uint64_t>(col & yoff) << c0;
+        const int ya = 4 * m + R0;
+        ca[m] = static_cast<uint32_t>(a64);
+        xw |= static_cast<uint32_t>(a64 >> 32) << ya;
+        if (ya + 1 < 16) {
+            cb[m] = static_cast<uint32_t>(b64);
+            xw |= static_cast<uint32_t>(b64 >> 32) << (ya + 1);
+        } else {
+            cb[m] = 0u;
+            yw = static_cast<uint32_t>(b64);
+            xw |= static_cast<uint32_t>(b64 >> 32) << 16;
+        }
+    }
+    // sites of neighbouring lanes' thread cells held by this lane
+    if (SX) {
+        const uint32_t v = __shfl_sync(kFull, xw, n.lL);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int ya = 4 * m + R0;
+            ca[m] |= (v >> ya) & 1u;
+            if (ya + 1 < 16) cb[m] |= (v >> (ya + 1)) & 1u;
+        }
+    }
+    if (SY) {
+        const uint32_t v = __shfl_sync(kFull, yw, n.lA);
+        const uint32_t corner = SX ? (__shfl_sync(kFull, xw, n.lAL) >> 16) & 1u : 0u;
+        cb[3] = v | corner;  // row 0
+    }
+    // eligibility
+    uint32_t cw = 0u;  // column-0 candidates: minima in bits 0..15, maxima in 16..31 (row = bit)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int ya = 4 * m + R0;
+        const int yb = SY && m == 3 ? 0 : ya + 1;  // the row cb[m] stands for
+        {
+            const uint32_t x = X[ya], xr = __funnelshift_r(x, E >> ya, 1);
+            const uint32_t y = Y[ya], yd = (ya < 15) ? Y[(ya + 1) & 15] : D;
+            ca[m] &= (x ^ xr) & (y ^ yd) & ~(x ^ y);
+            if (RANDOM) cw |= ((ca[m] & ~x & 1u) << ya) | ((ca[m] & x & 1u) << (ya + 16));
+        }
+        {
+            const uint32_t x = X[yb], xr = __funnelshift_r(x, E >> yb, 1);
+            const uint32_t y = Y[yb], yd = (yb < 15) ? Y[(yb + 1) & 15] : D;
+            cb[m] &= (x ^ xr) & (y ^ yd) & ~(x ^ y);
+            if (RANDOM) cw |= ((cb[m] & ~x & 1u) << yb) | ((cb[m] & x & 1u) << (yb + 16));
+        }
+    }
+    pmin = 0u;
+    pmax = 0u;
+    if (RANDOM) {
+        const uint32_t cwR = SX ? __shfl_sync(kFull, cw, n.lR) : 0u;
+        const uint32_t cwBR = (SX && SY) ? __shfl_sync(kFull, cw, n.lBR) : 0u;
+        uint32_t bmin = 0u, bmax = 0u;  // row 0 of the lane below
+        if (SY) {
+            bmin = __shfl_sync(kFull, cb[3] & ~X[0], n.lB);
+            bmax = __shfl_sync(kFull, cb[3] & X[0], n.lB);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int ya = 4 * m + R0, yb = ya + 1;
+            uint32_t mnl = ca[m] & ~X[ya], mxl = ca[m] & X[ya];
+            uint32_t mnh = (cwR >> ya) & 1u, mxh = (cwR >> (ya + 16)) & 1u;
+            if (yb < 16) {
+                mnl |= cb[m] & ~X[yb & 15];
+                mxl |= cb[m] & X[yb & 15];
+                mnh |= (cwR >> yb) & 1u;
+                mxh |= (cwR >> ((yb + 16) & 31)) & 1u;
+            } else {
+                mnl |= bmin;
+                mxl |= bmax;
+                mnh |= cwBR & 1u;
+                mxh |= (cwBR >> 16) & 1u;
+            }
+            // align each cell's pair to bits 4j, 4j+1, then pack to bit 4j+m
+            const uint32_t cmn = __funnelshift_r(mnl, mnh, c0) & c.p_random;
+            const uint32_t cmx = __funnelshift_r(mxl, mxh, c0) & c.q_random;
+            pmin |= ((cmn | (cmn >> 1)) & kNib) << m;
+            pmax |= ((cmx | (cmx >> 1)) & kNib) << m;
+        }
+    }
+}
+
+// Phase 3: flips of the accepted candidates (acc: this lane's packed
+// acceptance bits), then the exchange of the neighbour copies.
+template <int R0, bool RANDOM>
+__device__ __forceinline__ void dtr_apply(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E, uint32_t &D,
+                                          uint32_t c0, uint32_t acc, const uint32_t (&ca)[4],
+                                          const uint32_t (&cb)[4], const LaneCtx &c, const DtrLanes &n,
+                                          int &net) {
+    const bool SX = c0 == 3u;
+    constexpr bool SY = R0 == 3;
+    uint32_t accL = 0u, accA = 0u, accAL = 0u;
+    if (RANDOM) {
+        if (SX) accL = __shfl_sync(kFull, acc, n.lL);
+        if (SY) accA = __shfl_sync(kFull, acc, n.lA);
+        if (SX && SY) accAL = __shfl_sync(kFull, acc, n.lAL);
+    }
+    uint32_t dE = 0u, dB0 = 0u, dD = 0u, dY0 = 0u;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = i >> 1;
+        const bool second = i & 1;
+        const bool row0 = SY && m == 3 && second;  // incoming row 0
+        const int R = row0 ? 0 : 4 * m + R0 + (second ? 1 : 0);
+        uint32_t amin = c.p_always, amax = c.q_always;
+        if (RANDOM) {
+            const uint32_t own = row0 ? ((accA >> 3) & kNib) * 0xFu : ((acc >> m) & kNib) * 0xFu;
+            const uint32_t left = row0 ? ((accAL >> 3) & kNib) * 0xFu : ((accL >> m) & kNib) * 0xFu;
+            const uint32_t cols = __funnelshift_l(left, own, c0);
+            amin |= cols & c.p_random;
+            amax |= cols & c.q_random;
+        }
+        const uint32_t x = X[R];
+        const uint32_t f = (second ? cb[m] : ca[m]) & ((~x & amin) | (x & amax));
+        net += __popc(f & ~x) - __popc(f & x);
+        X[R] = x ^ f ^ (f << 1);
+        Y[R] ^= f;
+        if (R < 15) {
+            Y[(R + 1) & 15] ^= f;
+        } else {
+            D ^= f;
+            dD = f;
+        }
+        dE |= (f >> 31) << R;
+        dB0 |= (f & 1u) << R;
+        if (R == 0) dY0 = f;
+    }
+    E ^= dE;
+    const uint32_t vr = __shfl_up_sync(kFull, dE, 1);
+    const uint32_t vl = __shfl_down_sync(kFull, dB0, 1);
+    if (c.gx > 0) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) X[r] ^= (vr >> r) & 1u;
+    }
+    if (c.gx < c.GX - 1) E ^= vl;
+    const uint32_t vd = __shfl_up_sync(kFull, dD, c.GX);
+    const uint32_t vu = __shfl_down_sync(kFull, dY0, c.GX);
+    if (c.gy > 0) Y[0] ^= vd;
+    if (c.gy < c.GY - 1) D ^= vu;
+}
+
 // Device step on one sub-tile (Bx x By sites at (x0, y0)) held by the lanes of
 // one warp that share it: stage the lane's group from the planar lattice,
 // run the 16 single-hit collective steps, write back.  LANE_SETS: lanes of the
@@ -519,7 +714,39 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
     // Block layer: 16 single-hit collective steps.
     const uint4 setw = philox4x32_10(c.t, c.k, c.T, kTagSet << 28, c.k0, c.k1);
     uint4 site = make_uint4(0u, 0u, 0u, 0u);
+    uint4 borg = make_uint4(0u, 0u, 0u, 0u);
+    if (SCHEME == 3) borg = philox4x32_10(c.t, c.k, c.T, kTagBorg << 28, c.k0, c.k1);
     for (uint32_t s = 0; s < 16u; ++s) {
+        if (SCHEME == 3) {
+            // DTrDTr: the set, plus a block-layer origin (ax, ay) per step
+            if ((s & 1u) == 0u)
+                site = philox4x32_10(c.t, c.k | ((s >> 1) << 2), c.T, (kTagSite << 28) | c.g, c.k0, c.k1);
+            const uint32_t d = (setw.x >> (2u * s)) & 3u;
+            const uint32_t bw = (s < 4u) ? borg.x : (s < 8u) ? borg.y : (s < 12u) ? borg.z : borg.w;
+            const uint32_t byte = (bw >> (8u * (s & 3u))) & 0xFFu;
+            const uint32_t c0 = ((byte & 3u) + 2u * (d & 1u)) & 3u;
+            const uint32_t r0 = (((byte >> 4) & 3u) + 2u * (d >> 1)) & 3u;
+            const DtrLanes n = dtr_lanes(c);
+            uint32_t ca[4], cb[4], pmin, pmax;
+            switch (r0) {
+                case 0: dtr_candidates<0, RANDOM>(X, Y, E, D, site, s, c0, c, n, ca, cb, pmin, pmax); break;
+                case 1: dtr_candidates<1, RANDOM>(X, Y, E, D, site, s, c0, c, n, ca, cb, pmin, pmax); break;
+                case 2: dtr_candidates<2, RANDOM>(X, Y, E, D, site, s, c0, c, n, ca, cb, pmin, pmax); break;
+                default: dtr_candidates<3, RANDOM>(X, Y, E, D, site, s, c0, c, n, ca, cb, pmin, pmax); break;
+            }
+            uint32_t acc = 0u;
+            if (RANDOM) {
+                draws += __popc(pmin | pmax);
+                acc = accept_candidates(pmin, pmax, level_words(s, c), c, tp);
+            }
+            switch (r0) {
+                case 0: dtr_apply<0, RANDOM>(X, Y, E, D, c0, acc, ca, cb, c, n, net); break;
+                case 1: dtr_apply<1, RANDOM>(X, Y, E, D, c0, acc, ca, cb, c, n, net); break;
+                case 2: dtr_apply<2, RANDOM>(X, Y, E, D, c0, acc, ca, cb, c, n, net); break;
+                default: dtr_apply<3, RANDOM>(X, Y, E, D, c0, acc, ca, cb, c, n, net); break;
+            }
+            continue;
+        }
         if (SCHEME != 0) {
             // DB: one site word per TC row and step, 4 bits per cell
             site = philox4x32_10(c.t, c.k | (s << 2), c.T, (kTagSiteDb << 28) | c.g, c.k0, c.k1);

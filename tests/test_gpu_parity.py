@@ -255,3 +255,30 @@ def test_db_bit_exact(g, oracle, c):
             net += oracle.dtrdt_run(X, Y, prm, t, 1)[0]
             sim.run(1)
             _assert_same(oracle, sim, X, Y, net, f"t={t + 1}")
+
+
+DTR_CONFIGS = [
+    dict(L=256, p=1.0, q=0.0, seed=1, Bx=64, By=64, n=5),       # 2 x 4 groups per sub-tile
+    dict(L=512, p=0.95, q=0.05, seed=2, Bx=256, By=64, n=4),    # a full warp of groups
+    dict(L=256, p=0.5, q=0.5, seed=3, Bx=32, By=16, n=6),       # one group: both wraps inside a lane
+    dict(L=384, p=0.6, q=0.3, seed=4, Bx=32, By=64, n=4),       # one group column
+    dict(L=512, p=0.0, q=0.9, seed=5, Bx=128, By=16, n=4),      # one group row
+    dict(L=192, p=0.95, q=0.05, seed=6, Bx=96, By=32, n=5),     # three group columns
+]
+
+
+@pytest.mark.parametrize("c", DTR_CONFIGS, ids=lambda c: "DTR_L{L}_p{p}_q{q}_B{Bx}x{By}".format(**c))
+def test_dtr_bit_exact(g, oracle, c):
+    """DTrDTr: double tiling with a block-layer origin that moves after every
+    collective step (the cell grid wrapping around the sub-tile), against the
+    oracle bit for bit."""
+    prm = oracle.Params(L=c["L"], p=c["p"], q=c["q"], seed=c["seed"], Bx=c["Bx"], By=c["By"],
+                        scheme=oracle.SCHEME_DTR)
+    X, Y = oracle.flat(c["L"])
+    with g.Simulation(c["L"], c["p"], c["q"], c["seed"], Bx=c["Bx"], By=c["By"],
+                      scheme=g._lib.OCT_SCHEME_DTR) as sim:
+        net = 0
+        for t in range(c["n"]):
+            net += oracle.dtrdt_run(X, Y, prm, t, 1)[0]
+            sim.run(1)
+            _assert_same(oracle, sim, X, Y, net, f"t={t + 1}")

@@ -49,18 +49,37 @@ struct LaneCtx {
     bool active;   // this lane holds a group of a sub-tile
 };
 
+// Net flips (depositions minus removals) among the flips f of one row (x: the
+// row's X bits before the flips) that were accepted without a draw (p = 1 or
+// q = 1).  Flips decided by a draw are counted once per step from the packed
+// acceptance bits instead (random_net).
+template <bool RANDOM>
+__device__ __forceinline__ int always_net(uint32_t f, uint32_t x, const LaneCtx &c) {
+    if (RANDOM) {
+        if ((c.p_always | c.q_always) == 0u) return 0;
+        return __popc(f & ~x & c.p_always) - __popc(f & x & c.q_always);
+    }
+    if (c.q_always == 0u) return __popc(f);   // only depositions are possible
+    if (c.p_always == 0u) return -__popc(f);  // only removals
+    return __popc(f & ~x) - __popc(f & x);
+}
+
+// Net flips among the packed candidates accepted by their draw.
+__device__ __forceinline__ int random_net(uint32_t acc, uint32_t pmin, uint32_t pmax) {
+    return __popc(acc & pmin) - __popc(acc & pmax);
+}
+
 // Shared-memory ring holding a sub-tile's tail stream (see accept_candidates).
-// 36 words per lane bound the live window: fewer than (ties of one step) +
-// 4 x (groups) words, and one step has at most 32 ties per group.
-constexpr int kRingWordsPerLane = 36;
+// Its size is a power of two of at least 64 words per lane, above the live
+// window: fewer than (ties of one step) + 4 x (groups) words, and one step has
+// at most 32 ties per group.
+constexpr int kRingWordsPerLane = 64;
 
 struct TailPool {
-    uint32_t *ring;    // this sub-tile's ring
-    uint32_t rs;       // ring size in words = 36 x groups
-    uint32_t head;     // tail words used so far in this device step
-    uint32_t end;      // tail words generated so far in this device step
-    uint32_t head_at;  // head modulo rs
-    uint32_t end_at;   // end modulo rs
+    uint32_t *ring;  // this sub-tile's ring
+    uint32_t mask;   // ring size - 1
+    uint32_t head;   // tail words used so far in this device step
+    uint32_t end;    // tail words generated so far in this device step
 };
 
 // Acceptance of the packed candidates (bit 4j+m = thread cell column j, TC
@@ -105,28 +124,22 @@ __device__ __forceinline__ uint32_t accept_candidates(uint32_t pmin, uint32_t pm
     while (tp.end < tp.head + total) {
         const uint4 B = philox4x32_10(c.t, c.k | (((tp.end >> 2) + c.g) << 2), c.T, kTagTail << 28,
                                       c.k0, c.k1);
-        uint32_t at = tp.end_at + 4u * c.g;  // < 2 rs
-        if (at >= tp.rs) at -= tp.rs;
-        if (c.active) *reinterpret_cast<uint4 *>(tp.ring + at) = B;
+        if (c.active) *reinterpret_cast<uint4 *>(tp.ring + ((tp.end + 4u * c.g) & tp.mask)) = B;
         tp.end += 4u * G;
-        tp.end_at += 4u * G;
-        if (tp.end_at >= tp.rs) tp.end_at -= tp.rs;
     }
     __syncwarp();
-    uint32_t at = tp.head_at + (incl - n);  // < 2 rs
-    if (at >= tp.rs) at -= tp.rs;
-    const uint32_t low_p = c.thr_p & 0x0FFFFFFFu, low_q = c.thr_q & 0x0FFFFFFFu;
+    // (w >> 4) < (P32 mod 2^28)  <=>  w < 16 (P32 mod 2^28)
+    const uint32_t low_p = c.thr_p << 4, low_q = c.thr_q << 4;
+    uint32_t at = tp.head + (incl - n);
     while (und) {
         const uint32_t bit = und & (0u - und);  // lowest tied position
         und ^= bit;
-        const uint32_t w = tp.ring[at];
-        if (++at == tp.rs) at = 0u;
-        acc |= ((w >> 4) < ((pmin & bit) ? low_p : low_q)) ? bit : 0u;
+        const uint32_t w = tp.ring[at & tp.mask];
+        ++at;
+        acc |= (w < ((pmin & bit) ? low_p : low_q)) ? bit : 0u;
     }
     __syncwarp();
     tp.head += total;
-    tp.head_at += total;  // total <= 32 G < rs
-    if (tp.head_at >= tp.rs) tp.head_at -= tp.rs;
     return acc;
 }
 
@@ -194,7 +207,7 @@ __device__ __forceinline__ void step_apply(uint32_t (&X)[16], uint32_t (&Y)[16],
         // accepted minima are where the candidate has X(s) = 0
         const uint32_t f0 = cnd0[m] & ((~xa & amin) | (xa & amax));
         const uint32_t f1 = cnd1[m] & ((~xb & amin) | (xb & amax));
-        net += __popc((f0 & ~xa) | (f1 & ~xb)) - __popc((f0 & xa) | (f1 & xb));
+        net += always_net<RANDOM>(f0, xa, c) + always_net<RANDOM>(f1, xb, c);
         X[r0] = xa ^ f0 ^ (f0 << 1);
         X[r1] = xb ^ f1 ^ (f1 << 1);
         Y[r0] ^= f0;
@@ -308,7 +321,7 @@ __device__ __forceinline__ void step_apply_rt(uint32_t (&X)[16], uint32_t (&Y)[1
         const uint32_t xb = dy ? X[4 * m + 3] : X[4 * m + 1];
         const uint32_t f0 = cnd0[m] & ((~xa & amin) | (xa & amax));
         const uint32_t f1 = cnd1[m] & ((~xb & amin) | (xb & amax));
-        net += __popc((f0 & ~xa) | (f1 & ~xb)) - __popc((f0 & xa) | (f1 & xb));
+        net += always_net<RANDOM>(f0, xa, c) + always_net<RANDOM>(f1, xb, c);
         const uint32_t nxa = xa ^ f0 ^ (f0 << 1), nxb = xb ^ f1 ^ (f1 << 1);
         X[4 * m] = dy ? X[4 * m] : nxa;
         X[4 * m + 1] = dy ? X[4 * m + 1] : nxb;
@@ -409,7 +422,10 @@ __device__ __forceinline__ void db_step(uint32_t (&X)[16], uint32_t (&Y)[16], ui
             draws += __popc(pmin | pmax);
         }
         uint32_t acc = 0u;
-        if (RANDOM) acc = accept_candidates(pmin, pmax, W, c, tp);
+        if (RANDOM) {
+            acc = accept_candidates(pmin, pmax, W, c, tp);
+            net += random_net(acc, pmin, pmax);
+        }
         uint32_t dE = 0u, dB0 = 0u, dD = 0u, dY0 = 0u;
 #pragma unroll
         for (int R = 0; R < 16; ++R) {
@@ -422,7 +438,7 @@ __device__ __forceinline__ void db_step(uint32_t (&X)[16], uint32_t (&Y)[16], ui
             }
             const uint32_t x = X[R];
             const uint32_t f = cand[R] & ((~x & amin) | (x & amax));
-            net += __popc(f & ~x) - __popc(f & x);
+            net += always_net<RANDOM>(f, x, c);
             X[R] = x ^ f ^ (f << 1);
             Y[R] ^= f;
             if (R < 15)
@@ -584,6 +600,12 @@ __device__ __forceinline__ void dtr_candidates(const uint32_t (&X)[16], const ui
             pmin |= ((cmn | (cmn >> 1)) & kNib) << m;
             pmax |= ((cmx | (cmx >> 1)) & kNib) << m;
         }
+        // A lane outside the sub-tile can read a sub-tile lane's candidates
+        // through the wrapped lane indices; it owns no thread cell.
+        if (!c.active) {
+            pmin = 0u;
+            pmax = 0u;
+        }
     }
 }
 
@@ -619,7 +641,7 @@ __device__ __forceinline__ void dtr_apply(uint32_t (&X)[16], uint32_t (&Y)[16], 
         }
         const uint32_t x = X[R];
         const uint32_t f = (second ? cb[m] : ca[m]) & ((~x & amin) | (x & amax));
-        net += __popc(f & ~x) - __popc(f & x);
+        net += always_net<RANDOM>(f, x, c);
         X[R] = x ^ f ^ (f << 1);
         Y[R] ^= f;
         if (R < 15) {
@@ -656,11 +678,10 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
                                             const LaneCtx &c, uint32_t *ring, int &net, int &draws) {
     TailPool tp;
     tp.ring = ring;
-    tp.rs = static_cast<uint32_t>(kRingWordsPerLane * c.GX * c.GY);
+    const uint32_t G = static_cast<uint32_t>(c.GX * c.GY);
+    tp.mask = static_cast<uint32_t>(kRingWordsPerLane) * (1u << (32 - __clz(static_cast<int>(G - 1u)))) - 1u;
     tp.head = 0u;
     tp.end = 0u;
-    tp.head_at = 0u;
-    tp.end_at = 0u;
     uint32_t *const Xp = lat;
     uint32_t *const Yp = lat + static_cast<size_t>(L) * wpr;
     const uint32_t sh = x0 & 31u;
@@ -738,6 +759,7 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
             if (RANDOM) {
                 draws += __popc(pmin | pmax);
                 acc = accept_candidates(pmin, pmax, level_words(s, c), c, tp);
+                net += random_net(acc, pmin, pmax);
             }
             switch (r0) {
                 case 0: dtr_apply<0, RANDOM>(X, Y, E, D, c0, acc, ca, cb, c, n, net); break;
@@ -770,6 +792,7 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
         if (RANDOM) {
             draws += __popc(pmin | pmax);
             acc = accept_candidates(pmin, pmax, level_words(s, c), c, tp);
+            net += random_net(acc, pmin, pmax);
         }
         if (LANE_SETS)
             step_apply_rt<RANDOM>(X, Y, E, D, d >> 1, acc, cnd0, cnd1, c, net);

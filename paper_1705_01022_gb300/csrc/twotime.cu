@@ -42,17 +42,25 @@ __device__ __forceinline__ void nibble_steps(uint32_t n, int (&a)[4]) {
 
 __global__ void __launch_bounds__(kAcWarps * 32)
     ac_rows_kernel(const uint32_t *lt, const uint32_t *ls, uint32_t L, AcRowSums *rows) {
-    __shared__ int pair_tab[256];  // sum_i a_i(n_t) a_i(n_s), index n_t | n_s << 4
-    __shared__ int2 nib_tab[16];   // (sum_i a_i(n), a_3(n))
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    // sum_i a_i(n_t) a_i(n_s) for the nibble pair e = n_t | n_s << 4, one copy
+    // per lane (entry e of lane l at word 32 e + l: every lane reads its own
+    // bank, so the random lookups never conflict)
+    __shared__ int pair_tab[256 * 32];
+    __shared__ int2 nib_tab[16];   // (sum_i a_i(n), a_3(n)); 16 entries fill 32 banks once
+    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) {
+        const uint32_t e = static_cast<uint32_t>(i) >> 5;
         int a[4], b[4];
-        nibble_steps(static_cast<uint32_t>(i) & 15u, a);
-        nibble_steps(static_cast<uint32_t>(i) >> 4, b);
+        nibble_steps(e & 15u, a);
+        nibble_steps(e >> 4, b);
         pair_tab[i] = a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3];
-        if (i < 16) nib_tab[i] = make_int2(a[0] + a[1] + a[2] + a[3], a[3]);
+        if (i < 16) {
+            nibble_steps(static_cast<uint32_t>(i), a);
+            nib_tab[i] = make_int2(a[0] + a[1] + a[2] + a[3], a[3]);
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const int *const my_pairs = pair_tab + lane;
     const uint32_t wpr = L >> 5;
     const size_t plane = static_cast<size_t>(L) * wpr;
     const bool vec_ok = (wpr % 4u) == 0u && (reinterpret_cast<uintptr_t>(lt) % 16u) == 0u &&
@@ -125,7 +133,7 @@ __global__ void __launch_bounds__(kAcWarps * 32)
                 for (int k = 0; k < 8; ++k) {
                     const uint32_t nt = (wt[j] >> (4 * k)) & 15u, ns = (ws[j] >> (4 * k)) & 15u;
                     const int2 et = nib_tab[nt], es = nib_tab[ns];
-                    lc += bt * (4 * bs + es.x) + bs * et.x + pair_tab[nt | (ns << 4)];
+                    lc += bt * (4 * bs + es.x) + bs * et.x + my_pairs[(nt | (ns << 4)) << 5];
                     lst += 4 * bt + et.x;
                     lss += 4 * bs + es.x;
                     bt += et.y;

@@ -1,0 +1,154 @@
+"""Autotuner for the block tile (the sub-tile of the device layer, Bx x By sites).
+
+The sub-tile shape is a parameter of the domain decomposition, not only of the
+launch: it decides which sites are updated together and how the random
+streams map onto sites (Sec. 3; the paper reports that the decomposition's
+domain sizes shift the roughness prefactor, Sec. 4.2).  A tuned run is
+therefore reproducible only with the same choice, so the tuner records it:
+every decision is kept in a JSON cache keyed by GPU, L and acceptance mode,
+together with the table it was taken from, and a later lookup returns the same
+shape without measuring again.
+
+Candidates are the shapes the step kernel accepts for this L: Bx a multiple of
+32 and By a multiple of 16 (4 x 4-site thread cells, the one cell shape the
+GPU path supports), at most 32 groups of 32 x 16 sites, and L a multiple of
+2Bx and 2By.  By default the group counts in x and y are powers of two, which
+is also what a batched replica needs.  Each candidate runs a warm-up MCS and
+then `mcs` timed MCS on the library's own per-launch CUDA-event timing; the
+score is attempts per ns of the device-step kernel.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+from dataclasses import dataclass, field
+
+CELL = (4, 4)   # thread-cell shape (cx, cy) of the GPU path
+GROUP = (32, 16)  # sites held by one warp lane
+MAX_GROUPS = 32
+
+
+def mode_of(p: float, q: float) -> str:
+    """'random' when an acceptance draw is needed (0 < p < 1 or 0 < q < 1), else 'deterministic'."""
+    return "random" if (0.0 < p < 1.0) or (0.0 < q < 1.0) else "deterministic"
+
+
+def candidates(L: int, pow2: bool = True) -> list[tuple[int, int]]:
+    """Valid (Bx, By) for lattice size L, ordered by (Bx*By, Bx) descending."""
+    out = []
+    for gx in range(1, MAX_GROUPS + 1):
+        for gy in range(1, MAX_GROUPS // gx + 1):
+            if pow2 and (gx & (gx - 1) or gy & (gy - 1)):
+                continue
+            Bx, By = GROUP[0] * gx, GROUP[1] * gy
+            if L % (2 * Bx) or L % (2 * By):
+                continue
+            out.append((Bx, By))
+    out.sort(key=lambda s: (-s[0] * s[1], -s[0]))
+    return out
+
+
+def pick(table: list[dict]) -> dict:
+    """Fastest entry; ties go to the larger sub-tile, then the wider one
+    (the order of `candidates`), so the choice does not depend on dict order."""
+    best = None
+    for row in table:
+        if best is None or row["attempts_per_ns"] > best["attempts_per_ns"]:
+            best = row
+    return best
+
+
+def device_name() -> str:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.get_device_name(torch.cuda.current_device())
+    except Exception:  # noqa: BLE001 - torch is optional here
+        pass
+    return "cuda"
+
+
+@dataclass
+class TuneCache:
+    """Recorded choices, one per (device, L, mode); stored as JSON at `path`
+    (None: kept in memory only)."""
+    path: str | None = None
+    entries: dict = field(default_factory=dict)
+
+    @staticmethod
+    def key(device: str, L: int, mode: str) -> str:
+        return f"{device}|L={L}|{mode}"
+
+    @classmethod
+    def load(cls, path: str | None) -> "TuneCache":
+        c = cls(path)
+        if path and os.path.exists(path):
+            with open(path) as f:
+                c.entries = json.load(f)
+        return c
+
+    def get(self, device: str, L: int, mode: str):
+        return self.entries.get(self.key(device, L, mode))
+
+    def put(self, record: dict) -> None:
+        self.entries[self.key(record["device"], record["L"], record["mode"])] = record
+        if self.path:
+            tmp = self.path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(self.entries, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
+
+
+def measure(L: int, p: float, q: float, Bx: int, By: int, seed: int = 1, mcs: int = 2,
+            stream=None, lattice=None) -> float:
+    """Attempts per ns of the device-step kernel for one shape (flat start,
+    one warm-up MCS, then `mcs` timed MCS)."""
+    from . import Simulation, _lib
+    with Simulation(L, p, q, seed, Bx=Bx, By=By, stream=stream, lattice=lattice) as sim:
+        sim.run(1)
+        sim.sync()
+        _lib.oct_set_timing(sim.h, True)
+        sim.run(mcs)
+        sim.sync()
+        ms, launches, _ = _lib.oct_get_timing(sim.h)
+    per_launch_ms = ms / max(1, launches)
+    return (L * L / 4.0) / (per_launch_ms * 1e6)
+
+
+def tune(L: int, p: float, q: float, seed: int = 1, mcs: int = 2, shapes=None, stream=None,
+         lattice=None, measure_fn=None) -> dict:
+    """Measures every candidate shape and returns the record of the choice:
+    {device, L, p, q, mode, Bx, By, cx, cy, attempts_per_ns, table, mcs, seed, when}."""
+    shapes = list(shapes) if shapes is not None else candidates(L)
+    if not shapes:
+        raise ValueError(f"no sub-tile shape fits L={L}")
+    fn = measure_fn or (lambda Bx, By: measure(L, p, q, Bx, By, seed, mcs, stream, lattice))
+    table = [{"Bx": Bx, "By": By, "attempts_per_ns": float(fn(Bx, By))} for Bx, By in shapes]
+    best = pick(table)
+    return {"device": device_name() if measure_fn is None else "test", "L": L, "p": p, "q": q,
+            "mode": mode_of(p, q), "Bx": best["Bx"], "By": best["By"], "cx": CELL[0], "cy": CELL[1],
+            "attempts_per_ns": best["attempts_per_ns"], "table": table, "mcs": mcs, "seed": seed,
+            "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+
+
+def choose(L: int, p: float, q: float, cache: TuneCache | None = None, **kw) -> dict:
+    """The recorded choice for (GPU, L, mode), measuring once if there is none."""
+    cache = cache if cache is not None else TuneCache()
+    dev = device_name() if kw.get("measure_fn") is None else "test"
+    rec = cache.get(dev, L, mode_of(p, q))
+    if rec is None:
+        rec = tune(L, p, q, **kw)
+        cache.put(rec)
+    return rec
+
+
+def tuned_simulation(L: int, p: float, q: float, seed: int, cache: TuneCache | None = None,
+                     stream=None, lattice=None, **kw):
+    """A Simulation on the tuned (recorded) sub-tile shape; the record is
+    attached as `.tuning`."""
+    from . import Simulation
+    rec = choose(L, p, q, cache=cache, stream=stream, **kw)
+    sim = Simulation(L, p, q, seed, Bx=rec["Bx"], By=rec["By"], stream=stream, lattice=lattice)
+    sim.tuning = rec
+    return sim

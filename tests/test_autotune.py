@@ -1,0 +1,77 @@
+"""Host logic of the block-tile autotuner (no GPU): candidate shapes, the
+choice, and the record that makes a tuned run reproducible."""
+import json
+
+import pytest
+
+from paper_1705_01022_gb300 import autotune as at
+
+
+@pytest.mark.parametrize("L", [64, 128, 192, 256, 1024, 4096, 131072])
+def test_candidates_are_valid_shapes(L):
+    shapes = at.candidates(L)
+    assert shapes, L
+    for Bx, By in shapes:
+        gx, gy = Bx // 32, By // 16
+        assert Bx % 32 == 0 and By % 16 == 0
+        assert gx * gy <= 32
+        assert gx & (gx - 1) == 0 and gy & (gy - 1) == 0
+        assert L % (2 * Bx) == 0 and L % (2 * By) == 0
+    assert len(set(shapes)) == len(shapes)
+
+
+def test_candidates_at_the_bench_size():
+    shapes = at.candidates(1 << 17)
+    assert (256, 64) in shapes
+    # every split of 32 groups into powers of two, down to one group
+    assert len(shapes) == 21
+    assert shapes[0][0] * shapes[0][1] == 32 * 32 * 16
+
+
+def test_non_power_of_two_groups_when_asked():
+    assert (96, 32) in at.candidates(192, pow2=False)
+    assert (96, 32) not in at.candidates(192)
+
+
+def test_mode():
+    assert at.mode_of(1.0, 0.0) == "deterministic"
+    assert at.mode_of(0.0, 1.0) == "deterministic"
+    assert at.mode_of(0.95, 0.05) == "random"
+    assert at.mode_of(1.0, 0.5) == "random"
+
+
+def test_pick_fastest_and_deterministic_ties():
+    table = [{"Bx": 256, "By": 64, "attempts_per_ns": 10.0},
+             {"Bx": 128, "By": 128, "attempts_per_ns": 12.0},
+             {"Bx": 64, "By": 256, "attempts_per_ns": 12.0}]
+    assert (at.pick(table)["Bx"], at.pick(table)["By"]) == (128, 128)
+
+
+def test_tune_with_a_fake_timer_and_cache_round_trip(tmp_path):
+    calls = []
+
+    def fake(Bx, By):
+        calls.append((Bx, By))
+        return 1000.0 - abs(Bx - 256) - abs(By - 64)
+
+    path = str(tmp_path / "tune.json")
+    cache = at.TuneCache.load(path)
+    rec = at.choose(1 << 17, 0.95, 0.05, cache=cache, measure_fn=fake)
+    assert (rec["Bx"], rec["By"]) == (256, 64)
+    assert (rec["cx"], rec["cy"]) == at.CELL
+    assert len(rec["table"]) == len(at.candidates(1 << 17)) == len(calls)
+    # recorded: a second lookup (fresh cache object from the file) does not measure again
+    calls.clear()
+    again = at.choose(1 << 17, 0.95, 0.05, cache=at.TuneCache.load(path), measure_fn=fake)
+    assert calls == [] and (again["Bx"], again["By"]) == (256, 64)
+    with open(path) as f:
+        stored = json.load(f)
+    assert list(stored) == [at.TuneCache.key("test", 1 << 17, "random")]
+    # another acceptance mode is a separate decision
+    at.choose(1 << 17, 1.0, 0.0, cache=cache, measure_fn=fake)
+    assert len(at.TuneCache.load(path).entries) == 2
+
+
+def test_no_shape_fits():
+    with pytest.raises(ValueError):
+        at.tune(96, 1.0, 0.0, measure_fn=lambda Bx, By: 1.0)

@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--db-steps", type=int, default=30)
     ap.add_argument("--ac-reps", type=int, default=5)
+    ap.add_argument("--tune-mcs", type=int, default=1)
     return ap.parse_args()
 
 
@@ -354,6 +355,15 @@ def main():
     L = a.L
     lattice = torch.empty(L * L // 4, dtype=torch.uint8, device="cuda")
     seed = replica_seed(a.seed, rank)
+    # ---- block-tile autotuner: every valid sub-tile shape at this L, its choice recorded ----
+    tuning = None
+    if rank == 0 and a.tune_mcs > 0:
+        from paper_1705_01022_gb300 import autotune
+        rec = autotune.tune(L, a.p, a.q, seed=seed, mcs=a.tune_mcs, stream=stream, lattice=lattice)
+        tuning = {"choice": [rec["Bx"], rec["By"]], "cell": [rec["cx"], rec["cy"]], "mode": rec["mode"],
+                  "device": rec["device"], "mcs_per_shape": rec["mcs"],
+                  "table": [[r["Bx"], r["By"], round(r["attempts_per_ns"], 1)] for r in rec["table"]],
+                  "bench_shape_is_choice": [rec["Bx"], rec["By"]] == [a.Bx, a.By]}
     sim = g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice)
 
     def barrier():
@@ -514,7 +524,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload(a), "clocks": clk.summary(), "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "dtrdb": dtrdb, "dtrdtr": dtrdtr, "two_time": two_time, "batched": batched, "serving": serving,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "autotune": tuning, "dtrdb": dtrdb, "dtrdtr": dtrdtr, "two_time": two_time, "batched": batched, "serving": serving,
             "probe": {"lop3_per_clk_per_sm": lop3, "imad_per_clk_per_sm": imad, "probe_mhz": probe_mhz},
         }
         print(json.dumps(out), flush=True)

@@ -14,8 +14,9 @@
 //     [0 1;0 1] flips to [1 0;1 0] with probability p, a local maximum the
 //     other way with probability q.
 //
-// GB300 mapping.  One warp owns one sub-tile for the whole device step; no
-// block-wide barrier is needed.  Lane (gx, gy) holds a group of 32 x 16 sites
+// GB300 mapping.  One warp owns one sub-tile (or, for sub-tiles of fewer than
+// 32 groups, several) for the whole device step; no block-wide barrier is
+// needed.  Lane (gx, gy) holds a group of 32 x 16 sites
 // (8 TCs across, 4 TC rows) as 16 X-row and 16 Y-row words in registers, so
 // a collective step is a handful of 32-bit logic operations per TC row:
 // selection masks from the site draw, the four-bit minimum/maximum pattern,
@@ -42,13 +43,30 @@
 namespace oct {
 namespace {
 
-template <bool RANDOM, int SCHEME>
-__global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSM)
+// Lanes per sub-tile: its group count rounded up to a power of two.
+__host__ __device__ inline uint32_t segment_lanes(uint32_t groups) {
+    uint32_t s = 1u;
+    while (s < groups) s <<= 1;
+    return s;
+}
+
+// One device step.  A warp holds 32 / S sub-tiles of the set (S = segment_lanes
+// of the sub-tile's G groups; PACKED when S < 32): lane l works on group l % S
+// of sub-tile (warp index) * (32 / S) + l / S.  Packed sub-tiles draw their own
+// sets, so the step takes the per-lane row-offset path.
+template <bool RANDOM, int SCHEME, bool PACKED>
+__global__ void __launch_bounds__(kStepWarpsPerBlock * 32, PACKED ? kStepBlocksPerSMPacked : kStepBlocksPerSM)
     dtrdt_step_kernel(const StepArgs a) {
     __shared__ __align__(16) uint32_t ring[kStepWarpsPerBlock * 32 * kRingWordsPerLane];
     const int lane = threadIdx.x & 31;
-    const uint32_t T = blockIdx.x * kStepWarpsPerBlock + (threadIdx.x >> 5);
-    if (T >= a.tiles_x * a.tiles_y) return;  // the whole warp leaves together
+    const uint32_t G = a.GX * a.GY;
+    const uint32_t S = PACKED ? segment_lanes(G) : 32u;
+    const uint32_t per_warp = 32u / S;
+    const uint32_t warp_id = blockIdx.x * kStepWarpsPerBlock + (threadIdx.x >> 5);
+    const uint32_t n_tiles = a.tiles_x * a.tiles_y;
+    if (warp_id * per_warp >= n_tiles) return;  // the whole warp leaves together
+    const uint32_t seg = static_cast<uint32_t>(lane) / S, sub = static_cast<uint32_t>(lane) % S;
+    const uint32_t T = warp_id * per_warp + seg;
 
     const uint32_t t = *a.t_ptr;
     const uint32_t L = a.L;
@@ -67,15 +85,15 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSM)
     LaneCtx c;
     c.GX = static_cast<int>(a.GX);
     c.GY = static_cast<int>(a.GY);
-    c.gx = lane % c.GX;
-    c.gy = lane / c.GX;
-    const bool active = c.gy < c.GY;
+    c.gx = static_cast<int>(sub) % c.GX;
+    c.gy = static_cast<int>(sub) / c.GX;
+    const bool active = sub < G && T < n_tiles;
     c.active = active;
-    c.last = c.GX * c.GY - 1;
+    c.last = static_cast<int>(seg * S + G - 1u);
     c.t = t;
     c.k = a.k;
     c.T = T;
-    c.g = static_cast<uint32_t>(c.gy * c.GX + c.gx);
+    c.g = sub;
     c.k0 = a.k0;
     c.k1 = a.k1;
     c.thr_p = a.thr_p;
@@ -87,16 +105,18 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSM)
 
     const uint32_t wpr = a.wpr;
     int net = 0, draws = 0;
-    run_subtile<RANDOM, false, SCHEME>(a.lat, L, wpr, a.Bx, a.By, x0, y0, active, c,
-                               ring + (threadIdx.x >> 5) * 32 * kRingWordsPerLane, net, draws);
+    run_subtile<RANDOM, PACKED, SCHEME>(a.lat, L, wpr, a.Bx, a.By, x0, y0, active, c,
+                                        ring + ((threadIdx.x >> 5) * 32 + seg * S) * kRingWordsPerLane,
+                                        net, draws);
 
     // Net flips (and acceptance draws): one atomic per warp into a spread of counters.
+    const uint32_t T0 = warp_id * per_warp;
     const int total = __reduce_add_sync(kFull, net);
     if (lane == 0 && total != 0)
-        atomicAdd(&a.net[T % kNetSlots], static_cast<unsigned long long>(static_cast<long long>(total)));
+        atomicAdd(&a.net[T0 % kNetSlots], static_cast<unsigned long long>(static_cast<long long>(total)));
     if (RANDOM) {
         const unsigned nd = __reduce_add_sync(kFull, static_cast<unsigned>(draws));
-        if (lane == 0 && nd != 0u) atomicAdd(&a.draws[T % kNetSlots], static_cast<unsigned long long>(nd));
+        if (lane == 0 && nd != 0u) atomicAdd(&a.draws[T0 % kNetSlots], static_cast<unsigned long long>(nd));
     }
 }
 
@@ -106,33 +126,34 @@ __global__ void advance_t_kernel(uint32_t *t_ptr) { *t_ptr += 1u; }
 
 cudaError_t launch_dtrdt_step(const StepArgs &a, bool any_random, cudaStream_t st) {
     const uint32_t n_tiles = a.tiles_x * a.tiles_y;
-    const uint32_t blocks = (n_tiles + kStepWarpsPerBlock - 1) / kStepWarpsPerBlock;
+    // DTrDTr routes cells between the lanes of one sub-tile with warp-wide
+    // shuffles whose pattern depends on its own draws: one sub-tile per warp.
+    const uint32_t S = segment_lanes(a.GX * a.GY);
+    const bool packed = S < 32u && a.scheme != 3u;
+    const uint32_t per_block = kStepWarpsPerBlock * (packed ? 32u / S : 1u);
+    const uint32_t blocks = (n_tiles + per_block - 1) / per_block;
     const dim3 grid(blocks), block(kStepWarpsPerBlock * 32);
+#define OCT_LAUNCH(SCHEME, PACKED)                                                   \
+    do {                                                                             \
+        if (any_random)                                                              \
+            dtrdt_step_kernel<true, SCHEME, PACKED><<<grid, block, 0, st>>>(a);      \
+        else                                                                         \
+            dtrdt_step_kernel<false, SCHEME, PACKED><<<grid, block, 0, st>>>(a);     \
+    } while (0)
     switch (a.scheme) {
         case 1:
-            if (any_random)
-                dtrdt_step_kernel<true, 1><<<grid, block, 0, st>>>(a);
-            else
-                dtrdt_step_kernel<false, 1><<<grid, block, 0, st>>>(a);
+            if (packed) OCT_LAUNCH(1, true); else OCT_LAUNCH(1, false);
             break;
         case 2:
-            if (any_random)
-                dtrdt_step_kernel<true, 2><<<grid, block, 0, st>>>(a);
-            else
-                dtrdt_step_kernel<false, 2><<<grid, block, 0, st>>>(a);
+            if (packed) OCT_LAUNCH(2, true); else OCT_LAUNCH(2, false);
             break;
         case 3:
-            if (any_random)
-                dtrdt_step_kernel<true, 3><<<grid, block, 0, st>>>(a);
-            else
-                dtrdt_step_kernel<false, 3><<<grid, block, 0, st>>>(a);
+            OCT_LAUNCH(3, false);
             break;
         default:
-            if (any_random)
-                dtrdt_step_kernel<true, 0><<<grid, block, 0, st>>>(a);
-            else
-                dtrdt_step_kernel<false, 0><<<grid, block, 0, st>>>(a);
+            if (packed) OCT_LAUNCH(0, true); else OCT_LAUNCH(0, false);
     }
+#undef OCT_LAUNCH
     return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ struct StepArgs {
 constexpr int kNetSlots = 1024;
 constexpr int kStepWarpsPerBlock = 4;
 constexpr int kStepBlocksPerSM = 5;  // occupancy target: 20 warps per SM
+constexpr int kStepBlocksPerSMPacked = 4;  // several sub-tiles per warp: per-lane row offsets need more registers
 
 // Launches one device step; returns the CUDA launch status.
 cudaError_t launch_dtrdt_step(const StepArgs &a, bool any_random, cudaStream_t st);

@@ -191,12 +191,20 @@ def batch_replicas(n, _lib, master=1):
 def batched_leg(a, g, _lib, torch, stream, peak_tops):
     """Many independent replicas of uneven L in one launch per device step and
     mode (graph replay), against a loop of plain per-replica launches."""
+    from paper_1705_01022_gb300 import autotune
     reps = batch_replicas(a.batch_replicas, _lib)
     sites = sum(r[0] * r[0] for r in reps)
+    # block tiles by the autotuner's batch policy (timed on this replica set)
+    tuned = autotune.tune_batch(reps, mcs=2, stream=stream) if a.tune_mcs > 0 else None
+    policy = tuned["policy"] if tuned else "default"
+    shapes = [autotune.batch_shape(r[0], policy) for r in reps]
+    reps = [r + sh for r, sh in zip(reps, shapes)]
     out = {"workload": (f"{len(reps)} replicas, L uniform in {{64,...,4096}} (multiples of 64), "
                         f"(p,q) cycled over {BATCH_PQ}, flat start, keys from master seed 1; "
-                        "64x64 sub-tiles if L%128==0 else 32x32; 4x4 thread cells"),
-           "replicas": len(reps), "sites": sites}
+                        f"sub-tiles by the autotuner's policy '{policy}'; 4x4 thread cells"),
+           "replicas": len(reps), "sites": sites,
+           "autotune": ({"policy": policy, "table": [[row["policy"], round(row["attempts_per_ns"], 1)]
+                                                     for row in tuned["table"]]} if tuned else None)}
     with g.Batch(reps, stream=stream) as b:
         b.run(5)
         b.sync()
@@ -222,8 +230,7 @@ def batched_leg(a, g, _lib, torch, stream, peak_tops):
                            "frac": achieved / peak_tops, "kernel": "batch_step_kernel",
                            "device_step_ms": kms / klaunch, "draw_fraction": f_draw}
     # the same replicas, one plain handle each, launched one after another
-    sims = [g.Simulation(L, p, q, seed, Bx=(64 if L % 128 == 0 else 32), By=(64 if L % 128 == 0 else 32),
-                         stream=stream) for (L, p, q, seed) in reps]
+    sims = [g.Simulation(L, p, q, seed, Bx=Bx, By=By, stream=stream) for (L, p, q, seed, Bx, By) in reps]
     for s_ in sims:
         s_.run(1)
     torch.cuda.synchronize()

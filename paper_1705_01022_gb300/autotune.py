@@ -9,6 +9,11 @@ every decision is kept in a JSON cache keyed by GPU, L and acceptance mode,
 together with the table it was taken from, and a later lookup returns the same
 shape without measuring again.
 
+For batched replicas (`tune_batch`) the shape is chosen per replica by a
+policy (the library default, or the largest group count, wide or square), and
+the policies are timed on the actual replica set: what a warp carries and how
+the batched kernel packs it depend on the whole mix, not on one L.
+
 Candidates are the shapes the step kernel accepts for this L: Bx a multiple of
 32 and By a multiple of 16 (4 x 4-site thread cells, the one cell shape the
 GPU path supports), at most 32 groups of 32 x 16 sites, and L a multiple of
@@ -92,7 +97,10 @@ class TuneCache:
         return self.entries.get(self.key(device, L, mode))
 
     def put(self, record: dict) -> None:
-        self.entries[self.key(record["device"], record["L"], record["mode"])] = record
+        self.put_key(self.key(record["device"], record["L"], record["mode"]), record)
+
+    def put_key(self, key: str, record: dict) -> None:
+        self.entries[key] = record
         if self.path:
             tmp = self.path + ".tmp"
             with open(tmp, "w") as f:
@@ -152,3 +160,81 @@ def tuned_simulation(L: int, p: float, q: float, seed: int, cache: TuneCache | N
     sim = Simulation(L, p, q, seed, Bx=rec["Bx"], By=rec["By"], stream=stream, lattice=lattice)
     sim.tuning = rec
     return sim
+
+
+# ---------------------------------------------------------------------------
+# batched replicas
+BATCH_POLICIES = ("default", "wide", "square")
+
+
+def groups(shape: tuple[int, int]) -> int:
+    return (shape[0] // GROUP[0]) * (shape[1] // GROUP[1])
+
+
+def batch_shape(L: int, policy: str) -> tuple[int, int]:
+    """Sub-tile of a replica of size L under a policy: 'default' is the batch
+    library's own default (64 x 64 if L % 128 == 0, else 32 x 32); 'wide' and
+    'square' take the most groups a valid shape allows, then the widest or the
+    most nearly square one."""
+    if policy == "default":
+        return (64, 64) if L % 128 == 0 else (32, 32)
+    shapes = candidates(L)
+    if not shapes:
+        raise ValueError(f"no sub-tile shape fits L={L}")
+    gmax = max(groups(sh) for sh in shapes)
+    best = [sh for sh in shapes if groups(sh) == gmax]
+    if policy == "wide":
+        return max(best, key=lambda sh: sh[0])
+    if policy == "square":
+        return min(best, key=lambda sh: (abs(sh[0].bit_length() - sh[1].bit_length()), -sh[0]))
+    raise ValueError(f"unknown policy {policy!r}")
+
+
+def batch_key(replicas) -> str:
+    """Digest of the replica mix (L and acceptance mode of every replica)."""
+    import hashlib
+    items = sorted((int(r[0]), mode_of(float(r[1]), float(r[2]))) for r in replicas)
+    return hashlib.sha256(repr(items).encode()).hexdigest()[:16]
+
+
+def measure_batch(replicas, mcs: int = 2, stream=None) -> float:
+    """Attempts per ns of the batched device steps (kernel time of every device
+    step, after one warm-up MCS) for replicas (L, p, q, seed, Bx, By)."""
+    from . import Batch, _lib
+    sites = sum(int(r[0]) ** 2 for r in replicas)
+    with Batch(replicas, stream=stream) as b:
+        b.run(1)
+        b.sync()
+        _lib.oct_batch_set_timing(b.h, True)
+        b.run(mcs)
+        ms, launches = _lib.oct_batch_get_timing(b.h)
+        _lib.oct_batch_set_timing(b.h, False)
+    return (sites / 4.0) * launches / (ms * 1e6)
+
+
+def tune_batch(replicas, mcs: int = 2, stream=None, policies=BATCH_POLICIES, measure_fn=None) -> dict:
+    """Times every policy on the replica set (L, p, q, seed[, ...]) and returns
+    the record of the choice, with `shapes`: the (Bx, By) for each replica."""
+    replicas = [tuple(r[:4]) for r in replicas]
+    fn = measure_fn or (lambda reps: measure_batch(reps, mcs, stream))
+    table = []
+    for pol in policies:
+        reps = [r + batch_shape(int(r[0]), pol) for r in replicas]
+        table.append({"policy": pol, "attempts_per_ns": float(fn(reps))})
+    best = max(table, key=lambda row: row["attempts_per_ns"])
+    return {"device": device_name() if measure_fn is None else "test", "key": batch_key(replicas),
+            "policy": best["policy"], "attempts_per_ns": best["attempts_per_ns"], "table": table,
+            "shapes": [batch_shape(int(r[0]), best["policy"]) for r in replicas], "mcs": mcs,
+            "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+
+
+def choose_batch(replicas, cache: TuneCache | None = None, **kw) -> dict:
+    """The recorded policy for this replica mix on this GPU, measuring once if there is none."""
+    cache = cache if cache is not None else TuneCache()
+    dev = device_name() if kw.get("measure_fn") is None else "test"
+    key = f"{dev}|batch|{batch_key(replicas)}"
+    rec = cache.entries.get(key)
+    if rec is None:
+        rec = tune_batch(replicas, **kw)
+        cache.put_key(key, rec)
+    return rec

@@ -10,9 +10,11 @@
 // Items are bucketed by G and by acceptance mode and packed into warp
 // descriptors; persistent warps claim descriptors from an atomic queue.
 // Because the sub-tiles of one warp draw their own block-level sets, the
-// collective step takes the set per lane (collective_step_rt).  All replicas
-// advance in lock step: one MCS is four device steps, each one launch per
-// acceptance mode, captured once in a CUDA graph and replayed.
+// collective step takes the set per lane (step_candidates_rt / step_apply_rt);
+// sub-tiles of 32 groups fill a warp alone and take the uniform path.  All
+// replicas advance in lock step: one MCS is four device steps, each one launch
+// per acceptance mode and warp kind, captured once in a CUDA graph and
+// replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,7 +54,10 @@ struct WarpDesc {
 constexpr int kBatchWarps = 4;
 constexpr int kBatchBlocksPerSM = 4;
 
-template <bool RANDOM>
+// LANE_SETS: the warp holds several sub-tiles (fewer than 32 groups each), each
+// with its own set draws; otherwise one sub-tile fills the warp and the step
+// takes the uniform row-offset path of the plain kernel.
+template <bool RANDOM, bool LANE_SETS>
 __global__ void __launch_bounds__(kBatchWarps * 32, kBatchBlocksPerSM)
     batch_step_kernel(const ReplicaDev *reps, const BatchItem *items, const WarpDesc *descs,
                       uint32_t n_descs, const uint32_t *t_of, uint32_t k, uint32_t *queue) {
@@ -101,7 +106,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, kBatchBlocksPerSM)
         c.p_random = R.p_random;
         c.q_random = R.q_random;
         int net = 0, draws = 0;
-        run_subtile<RANDOM, true>(R.lat, L, R.wpr, R.Bx, R.By, x0, y0, active, c,
+        run_subtile<RANDOM, LANE_SETS>(R.lat, L, R.wpr, R.Bx, R.By, x0, y0, active, c,
                                   ring + ((threadIdx.x >> 5) * 32 + (lane & ~(G - 1))) * kRingWordsPerLane,
                                   net, draws);
         // sum over the G lanes of the item (items start at multiples of G)
@@ -166,9 +171,10 @@ struct oct_batch {
     uint32_t *d_active = nullptr;
     size_t active_cap = 0;
     uint32_t n_active = 0;
-    uint32_t n_desc[2] = {0, 0};
-    uint32_t desc_first[2] = {0, 0};
-    uint32_t *d_queue = nullptr;  // 8 counters: (device step, mode)
+    // work lists by kind = 2 * mode + (one sub-tile per warp); mode 1: acceptance draws
+    uint32_t n_desc[4] = {0, 0, 0, 0};
+    uint32_t desc_first[4] = {0, 0, 0, 0};
+    uint32_t *d_queue = nullptr;  // 16 counters: (device step, kind)
     oct::W2RowSums *d_rows = nullptr;
     int64_t rows_cap = 0;
     oct::W2Result *d_w2 = nullptr;
@@ -321,12 +327,14 @@ cudaError_t rebuild(oct_batch *b) {
     }
     std::vector<oct::BatchItem> items;
     std::vector<oct::WarpDesc> descs;
-    for (int mode = 0; mode < 2; ++mode) {
-        b->desc_first[mode] = static_cast<uint32_t>(descs.size());
+    for (int kind = 0; kind < 4; ++kind) {
+        const int mode = kind >> 1;
+        const bool full = kind & 1;
+        b->desc_first[kind] = static_cast<uint32_t>(descs.size());
         for (int gxi = 5; gxi >= 0; --gxi)
             for (int gyi = 5; gyi >= 0; --gyi) {
                 const uint32_t GX = 1u << gxi, G = GX << gyi;
-                if (G > 32u) continue;
+                if (G > 32u || (G == 32u) != full) continue;
                 const uint32_t per = 32u / G;
                 auto &bk = bucket[mode][gxi][gyi];
                 for (size_t i = 0; i < bk.size(); i += per) {
@@ -339,7 +347,7 @@ cudaError_t rebuild(oct_batch *b) {
                     descs.push_back(d);
                 }
             }
-        b->n_desc[mode] = static_cast<uint32_t>(descs.size()) - b->desc_first[mode];
+        b->n_desc[kind] = static_cast<uint32_t>(descs.size()) - b->desc_first[kind];
     }
     b->n_active = static_cast<uint32_t>(active.size());
     e = ensure(&b->d_items, &b->items_cap, std::max<size_t>(1, items.size()));
@@ -359,19 +367,21 @@ cudaError_t rebuild(oct_batch *b) {
 
 // Enqueues device step k of the current MCS of every active replica.
 cudaError_t enqueue_step(oct_batch *b, uint32_t k, cudaStream_t st) {
-    for (int mode = 0; mode < 2; ++mode) {
-        if (b->n_desc[mode] == 0) continue;
-        uint32_t *q = b->d_queue + 2 * k + mode;
+    for (int kind = 0; kind < 4; ++kind) {
+        if (b->n_desc[kind] == 0) continue;
+        uint32_t *q = b->d_queue + 4 * k + kind;
         cudaError_t e = cudaMemsetAsync(q, 0, sizeof(uint32_t), st);
         if (e != cudaSuccess) return e;
-        const oct::WarpDesc *descs = b->d_descs + b->desc_first[mode];
-        const int blocks = std::min<int>(b->grid, static_cast<int>((b->n_desc[mode] + oct::kBatchWarps - 1) / oct::kBatchWarps));
-        if (mode)
-            oct::batch_step_kernel<true><<<blocks, oct::kBatchWarps * 32, 0, st>>>(
-                b->d_reps, b->d_items, descs, b->n_desc[mode], b->d_t, k, q);
-        else
-            oct::batch_step_kernel<false><<<blocks, oct::kBatchWarps * 32, 0, st>>>(
-                b->d_reps, b->d_items, descs, b->n_desc[mode], b->d_t, k, q);
+        const oct::WarpDesc *descs = b->d_descs + b->desc_first[kind];
+        const uint32_t nd = b->n_desc[kind];
+        const int blocks = std::min<int>(b->grid, static_cast<int>((nd + oct::kBatchWarps - 1) / oct::kBatchWarps));
+        const dim3 grid(blocks), block(oct::kBatchWarps * 32);
+        switch (kind) {
+            case 0: oct::batch_step_kernel<false, true><<<grid, block, 0, st>>>(b->d_reps, b->d_items, descs, nd, b->d_t, k, q); break;
+            case 1: oct::batch_step_kernel<false, false><<<grid, block, 0, st>>>(b->d_reps, b->d_items, descs, nd, b->d_t, k, q); break;
+            case 2: oct::batch_step_kernel<true, true><<<grid, block, 0, st>>>(b->d_reps, b->d_items, descs, nd, b->d_t, k, q); break;
+            default: oct::batch_step_kernel<true, false><<<grid, block, 0, st>>>(b->d_reps, b->d_items, descs, nd, b->d_t, k, q); break;
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -518,7 +528,7 @@ int oct_batch_create(int64_t n, const oct_replica *reps, void *stream, oct_batch
             e = cudaMemPoolSetAttribute(b->pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
     }
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(uint32_t) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(uint32_t) * 16);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_w2, sizeof(oct::W2Result));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_small, 256);
     if (e == cudaSuccess) {

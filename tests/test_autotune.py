@@ -75,3 +75,36 @@ def test_tune_with_a_fake_timer_and_cache_round_trip(tmp_path):
 def test_no_shape_fits():
     with pytest.raises(ValueError):
         at.tune(96, 1.0, 0.0, measure_fn=lambda Bx, By: 1.0)
+
+
+def test_batch_policies_give_valid_shapes():
+    for L in range(64, 4097, 64):
+        assert at.batch_shape(L, "default") == ((64, 64) if L % 128 == 0 else (32, 32))
+        for pol in ("wide", "square"):
+            Bx, By = at.batch_shape(L, pol)
+            assert (Bx, By) in at.candidates(L)
+            assert at.groups((Bx, By)) == max(at.groups(s) for s in at.candidates(L))
+    assert at.batch_shape(4096, "wide") == (1024, 16)
+    assert at.batch_shape(4096, "square") == (128, 128)
+    assert at.batch_shape(192, "wide") == (32, 32)
+
+
+def test_tune_batch_with_a_fake_timer(tmp_path):
+    reps = [(L, p, q, 100 + i) for i, (L, (p, q)) in
+            enumerate(zip(range(64, 4097, 64), [(1.0, 0.0), (0.95, 0.05), (0.5, 0.5)] * 30))]
+    seen = []
+
+    def fake(rs):
+        seen.append(rs)
+        return {(64, 64): 900.0}.get(rs[-1][4:], 1000.0) if rs[-1][4:] != (128, 128) else 1100.0
+
+    cache = at.TuneCache.load(str(tmp_path / "b.json"))
+    rec = at.choose_batch(reps, cache=cache, measure_fn=fake)
+    assert rec["policy"] == "square" and len(rec["shapes"]) == len(reps)
+    assert [row["policy"] for row in rec["table"]] == list(at.BATCH_POLICIES)
+    assert all(len(r) == 6 for r in seen[0])
+    seen.clear()
+    again = at.choose_batch(reps, cache=at.TuneCache.load(cache.path), measure_fn=fake)
+    assert seen == [] and again["policy"] == "square"
+    # a different mix is a different decision
+    assert at.batch_key(reps) != at.batch_key(reps[:-1])

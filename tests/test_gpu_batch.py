@@ -36,6 +36,9 @@ def _replicas(g, master=7):
     # explicit shapes too: a full-warp sub-tile and a two-group one
     reps.append((1024, 0.95, 0.05, 99, 256, 64))
     reps.append((512, 0.5, 0.5, 98, 64, 32))
+    # full-warp sub-tiles of both acceptance modes (the uniform-row-offset kernel)
+    reps.append((1024, 1.0, 0.0, 97, 512, 32))
+    reps.append((512, 0.6, 0.3, 96, 128, 128))
     return reps
 
 

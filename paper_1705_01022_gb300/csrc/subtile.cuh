@@ -30,11 +30,7 @@ __device__ __forceinline__ int perm_element(uint32_t idx, uint32_t k) {
 
 // Sets the bits of *w selected by mask to those of v, leaving the others, as
 // two reductions (no value returned, so the warp does not wait for them).
-__device__ __forceinline__ void merge_bits(uint32_t *w, uint32_t v, uint32_t mask) {
-    if (mask == 0xFFFFFFFFu) {
-        *w = v;
-        return;
-    }
+__device__ __forceinline__ void reduce_bits(uint32_t *w, uint32_t v, uint32_t mask) {
     atomicAnd(w, v | ~mask);
     atomicOr(w, v & mask);
 }
@@ -805,42 +801,102 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
     // Write back.  Global word wA of a row receives the high bits of the left
     // lane and the low bits of this lane; the leftmost lane shares word wA
     // with the bits left of x0, the rightmost lane also owns the low bits of
-    // word wB (its own high bits, and for X the halo-column bit).  Words shared
-    // with sites outside the sub-tile are merged with an AND/OR reduction pair
-    // (no read, so no load latency), full words are stored.  No other warp of
-    // this device step touches these words: active sub-tiles are at least 32
-    // sites apart.
+    // word wB (its own high bits, and for X the halo-column bit).  The bits of
+    // those shared words outside the sub-tile belong to neighbouring sub-tiles,
+    // which this device step does not update, and no other warp writes these
+    // words (active sub-tiles are at least 32 sites apart).  Full words are
+    // stored.  Shared words are merged in one of two ways:
+    //  * a warp holding one sub-tile (few shared words per lane): an AND/OR
+    //    reduction pair, which returns nothing, so the warp does not wait;
+    //  * a warp holding several small sub-tiles (many shared words per lane):
+    //    a fresh read of the outside bits, all reads of eight rows before
+    //    their stores (one wait for memory per eight rows), and one plain
+    //    store per word; there the reductions' throughput would bind the step.
+    const bool left_edge = active && c.gx == 0 && sh != 0u;
+    const bool right_edge = active && c.gx == c.GX - 1;
+    const uint32_t lo_mask = (1u << sh) - 1u;  // bits [0, sh): left of x0 in word wA
+    const uint32_t xb_mask = (2u << sh) - 1u;  // bits [0, sh]: ours in word wB of X (halo bit at sh)
+    const bool by_read = LANE_SETS;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const uint32_t leftX = __shfl_up_sync(kFull, X[r], 1);
-        const uint32_t leftY = __shfl_up_sync(kFull, Y[r], 1);
-        if (active) {
-            uint32_t yr = ybase + r;
-            if (yr >= L) yr -= L;
-            const size_t ro = static_cast<size_t>(yr) * wpr;
-            if (c.gx == 0 && sh) {
-                merge_bits(&Xp[ro + wA], X[r] << sh, ~0u << sh);
-                merge_bits(&Yp[ro + wA], Y[r] << sh, ~0u << sh);
-            } else {
-                Xp[ro + wA] = __funnelshift_l(leftX, X[r], sh);
-                Yp[ro + wA] = __funnelshift_l(leftY, Y[r], sh);
+    for (int h = 0; h < 16; h += 8) {
+        uint32_t oX[8], oY[8];  // outside bits of the lane's edge words (wA's in lo_mask, wB's above)
+        if (by_read) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                uint32_t yr = ybase + h + i;
+                if (yr >= L) yr -= L;
+                const size_t ro = static_cast<size_t>(yr) * wpr;
+                oX[i] = 0u;
+                oY[i] = 0u;
+                if (left_edge) {
+                    oX[i] = Xp[ro + wA] & lo_mask;
+                    oY[i] = Yp[ro + wA] & lo_mask;
+                }
+                if (right_edge) {
+                    oX[i] |= Xp[ro + wB] & ~xb_mask;
+                    oY[i] |= Yp[ro + wB] & ~lo_mask;
+                }
             }
-            if (c.gx == c.GX - 1) {
-                const uint32_t hiX = sh ? (X[r] >> (32u - sh)) : 0u;
-                merge_bits(&Xp[ro + wB], hiX | (((E >> r) & 1u) << sh), (2u << sh) - 1u);
-                if (sh) merge_bits(&Yp[ro + wB], Y[r] >> (32u - sh), (1u << sh) - 1u);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = h + i;
+            const uint32_t leftX = __shfl_up_sync(kFull, X[r], 1);
+            const uint32_t leftY = __shfl_up_sync(kFull, Y[r], 1);
+            if (active) {
+                uint32_t yr = ybase + r;
+                if (yr >= L) yr -= L;
+                const size_t ro = static_cast<size_t>(yr) * wpr;
+                if (left_edge) {
+                    if (by_read) {
+                        Xp[ro + wA] = (oX[i] & lo_mask) | (X[r] << sh);
+                        Yp[ro + wA] = (oY[i] & lo_mask) | (Y[r] << sh);
+                    } else {
+                        reduce_bits(&Xp[ro + wA], X[r] << sh, ~lo_mask);
+                        reduce_bits(&Yp[ro + wA], Y[r] << sh, ~lo_mask);
+                    }
+                } else {
+                    Xp[ro + wA] = __funnelshift_l(leftX, X[r], sh);
+                    Yp[ro + wA] = __funnelshift_l(leftY, Y[r], sh);
+                }
+                if (right_edge) {
+                    const uint32_t hiX = (sh ? (X[r] >> (32u - sh)) : 0u) | (((E >> r) & 1u) << sh);
+                    const uint32_t hiY = sh ? (Y[r] >> (32u - sh)) : 0u;
+                    if (by_read) {
+                        Xp[ro + wB] = (oX[i] & ~xb_mask) | hiX;
+                        if (sh) Yp[ro + wB] = (oY[i] & ~lo_mask) | hiY;
+                    } else {
+                        reduce_bits(&Xp[ro + wB], hiX, xb_mask);
+                        if (sh) reduce_bits(&Yp[ro + wB], hiY, lo_mask);
+                    }
+                }
             }
         }
     }
     {
+        const bool d_row = active && c.gy == c.GY - 1;
+        const size_t ro = static_cast<size_t>(yh) * wpr;
+        uint32_t oD = 0u;
+        if (by_read && d_row) {
+            if (left_edge) oD = Yp[ro + wA] & lo_mask;
+            if (right_edge && sh) oD |= Yp[ro + wB] & ~lo_mask;
+        }
         const uint32_t leftD = __shfl_up_sync(kFull, D, 1);
-        if (active && c.gy == c.GY - 1) {
-            const size_t ro = static_cast<size_t>(yh) * wpr;
-            if (c.gx == 0 && sh)
-                merge_bits(&Yp[ro + wA], D << sh, ~0u << sh);
-            else
+        if (d_row) {
+            if (left_edge) {
+                if (by_read)
+                    Yp[ro + wA] = (oD & lo_mask) | (D << sh);
+                else
+                    reduce_bits(&Yp[ro + wA], D << sh, ~lo_mask);
+            } else {
                 Yp[ro + wA] = __funnelshift_l(leftD, D, sh);
-            if (c.gx == c.GX - 1 && sh) merge_bits(&Yp[ro + wB], D >> (32u - sh), (1u << sh) - 1u);
+            }
+            if (right_edge && sh) {
+                if (by_read)
+                    Yp[ro + wB] = (oD & ~lo_mask) | (D >> (32u - sh));
+                else
+                    reduce_bits(&Yp[ro + wB], D >> (32u - sh), lo_mask);
+            }
         }
     }
 

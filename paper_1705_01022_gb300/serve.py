@@ -44,6 +44,7 @@ class Job:
     admitted: float | None = None
     done: float | None = None
     results: list = field(default_factory=list)  # (t, s1, s2, w2, net_flips)
+    cancelled: bool = False
 
     @property
     def attempts(self) -> int:
@@ -190,10 +191,42 @@ class ServingEngine:
                     self.clock_skip(self.waiting[0].arrival)
         return self.finished
 
+    def cancel(self, jid: int) -> bool:
+        """Withdraws a job: a waiting one leaves the queue, a running one leaves
+        the batch at once and returns its memory (its streamed results stay).
+        Returns False if the job is unknown or already finished."""
+        for job in list(self.waiting):
+            if job.jid == jid:
+                self.waiting.remove(job)
+                job.cancelled = True
+                return True
+        for slot, job in list(self.running.items()):
+            if job.jid == jid:
+                self.batch.remove(slot)
+                del self.running[slot]
+                self.used -= footprint(job.L)
+                job.cancelled = True
+                return True
+        return False
+
     def clock_skip(self, t: float) -> None:
         """Advances a virtual clock (only meaningful with an injected clock)."""
         if hasattr(self.clock, "advance_to"):
             self.clock.advance_to(t)
+
+
+def jsonl_logger(fp, clock=time.perf_counter):
+    """An on_result callback writing one JSON line per streamed measurement:
+    job id, L, p, q, t, S1, S2 (as integers), N, W^2, net flips, and the
+    seconds since the job arrived."""
+    import json
+
+    def log(job: Job, res) -> None:
+        t, s1, s2, w2, net = res
+        fp.write(json.dumps({"job": job.jid, "L": job.L, "p": job.p, "q": job.q, "t": int(t),
+                             "s1": int(s1), "s2": int(s2), "n_sites": job.L * job.L, "w2": float(w2),
+                             "net_flips": int(net), "since_arrival_s": clock() - job.arrival}) + "\n")
+    return log
 
 
 def summary(jobs, wall_s: float) -> dict:

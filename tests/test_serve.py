@@ -103,3 +103,52 @@ def test_engine_rejects_jobs_larger_than_the_budget():
     eng = serve.ServingEngine(1000, batch=FakeBatch(VirtualClock()))
     with pytest.raises(ValueError):
         eng.submit(serve.Job(0, 1024, 1.0, 0.0, 1, t_max=10))
+
+
+def _jobs(n):
+    return [serve.Job(i, 128, 1.0, 0.0, 1000 + i, 20, arrival=0.0, measure_at=serve.log_times(20, 4))
+            for i in range(n)]
+
+
+def test_cancel_waiting_and_running_jobs():
+    clock = VirtualClock()
+    fb = FakeBatch(clock)
+    eng = serve.ServingEngine(hbm_budget=2 * serve.footprint(128), batch=fb, clock=clock)
+    jobs = _jobs(4)
+    for j in jobs:
+        eng.submit(j)
+    eng.tick(0.0)  # admits two (the budget holds two lattices), runs them to their first event
+    assert len(eng.running) == 2 and len(eng.waiting) == 2
+    assert eng.cancel(3)                      # waiting: leaves the queue
+    assert eng.cancel(0)                      # running: leaves the batch, memory back
+    assert not eng.cancel(0) and not eng.cancel(99)
+    assert eng.used == serve.footprint(128) and 0 not in [j.jid for j in eng.running.values()]
+    while eng.waiting or eng.running:
+        eng.tick(clock())
+    done = sorted(j.jid for j in eng.finished)
+    assert done == [1, 2]
+    assert jobs[0].cancelled and jobs[3].cancelled and not jobs[1].cancelled
+    assert jobs[0].results and not jobs[3].results  # what was streamed before the cancel stays
+
+
+def test_admission_budget_of_zero_rejects_everything():
+    eng = serve.ServingEngine(hbm_budget=0, batch=FakeBatch(VirtualClock()), clock=VirtualClock())
+    with pytest.raises(ValueError):
+        eng.submit(_jobs(1)[0])
+
+
+def test_jsonl_metrics_lines():
+    import io
+    import json
+    clock = VirtualClock()
+    buf = io.StringIO()
+    eng = serve.ServingEngine(hbm_budget=10 * serve.footprint(128), batch=FakeBatch(clock), clock=clock,
+                              on_result=serve.jsonl_logger(buf, clock))
+    jobs = _jobs(2)
+    eng.run(jobs, realtime=False)
+    lines = [json.loads(x) for x in buf.getvalue().splitlines()]
+    assert len(lines) == sum(len(j.measure_at) for j in jobs)
+    for rec in lines:
+        assert set(rec) == {"job", "L", "p", "q", "t", "s1", "s2", "n_sites", "w2", "net_flips", "since_arrival_s"}
+        assert rec["n_sites"] == 128 * 128 and rec["since_arrival_s"] >= 0
+    assert [r["t"] for r in lines if r["job"] == 0] == jobs[0].measure_at

@@ -3,7 +3,9 @@
 A job is one realization (L, p, q, seed) to run for t_max MCS, with W^2 sent
 back at log-spaced times.  Jobs arrive over time (e.g. as a Poisson stream).
 The engine keeps one batch (``oct_batch_*`` in include/oct.h) whose replicas
-are the running jobs:
+are the running jobs, each on the sub-tile its shape policy gives (see
+autotune.batch_shape; the shape is recorded in the job, since it is part of
+the job's dynamics):
 
 * admission: a waiting job that has arrived joins the batch as soon as its
   lattice fits the HBM budget (first come, first served);
@@ -45,6 +47,7 @@ class Job:
     done: float | None = None
     results: list = field(default_factory=list)  # (t, s1, s2, w2, net_flips)
     cancelled: bool = False
+    shape: tuple = (0, 0)  # sub-tile (Bx, By) the engine chose; part of the job's dynamics
 
     @property
     def attempts(self) -> int:
@@ -110,8 +113,9 @@ class ServingEngine:
     by default it is the GPU batch of this package."""
 
     def __init__(self, hbm_budget: int, batch=None, stream=None, max_chunk: int = 64,
-                 on_result=None, clock=time.perf_counter):
+                 on_result=None, clock=time.perf_counter, shape_policy: str = "default"):
         self.budget = int(hbm_budget)
+        self.shape_policy = shape_policy  # autotune.batch_shape policy for each job's sub-tile
         self.used = 0
         self.batch = batch if batch is not None else GpuBatch(stream)
         self.max_chunk = max_chunk
@@ -134,6 +138,8 @@ class ServingEngine:
             if self.used + footprint(job.L) > self.budget:
                 break  # first come, first served: later jobs wait behind it
             self.waiting.popleft()
+            from .autotune import batch_shape
+            job.shape = batch_shape(job.L, self.shape_policy)
             job.slot = self.batch.add(job)
             job.admitted = now
             job.t = 0
@@ -255,6 +261,7 @@ class GpuBatch:
     def add(self, job: Job) -> int:
         r = self._lib.oct_replica()
         r.L, r.p, r.q, r.seed = job.L, job.p, job.q, job.seed
+        r.Bx, r.By = job.shape
         return self._lib.oct_batch_add(self.h, r)
 
     def remove(self, slot: int) -> None:

@@ -24,7 +24,8 @@ def test_each_result_is_the_same_alone_and_in_the_mix(g):
     assert len(done) == len(jobs) and eng.used == 0
     assert len(streamed) == sum(len(j.measure_at) for j in jobs)
     for job in done:
-        with g.Simulation(job.L, job.p, job.q, job.seed, Bx=64, By=64) as sim:
+        assert job.shape != (0, 0)
+        with g.Simulation(job.L, job.p, job.q, job.seed, Bx=job.shape[0], By=job.shape[1]) as sim:
             t = 0
             for (tt, s1, s2, w2, net) in job.results:
                 sim.run(tt - t)

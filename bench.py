@@ -148,10 +148,11 @@ def src_hash():
     return hashlib.sha256("".join(lines).encode()).hexdigest()
 
 
-def cpu_baseline_window(oracle, a, state_getter, t, target_s):
+def cpu_baseline_window(oracle, a, state_getter, t, target_s, scheme=0, seed=None, name="DTrDT"):
     """Times the oracle replaying MCS t on windows of the lattice (read from the
     running simulation), growing the window until about target_s of CPU work."""
-    prm = oracle.Params(L=a.L, p=a.p, q=a.q, seed=a.seed, Bx=a.Bx, By=a.By)
+    prm = oracle.Params(L=a.L, p=a.p, q=a.q, seed=a.seed if seed is None else seed, Bx=a.Bx, By=a.By,
+                        scheme=scheme)
     tw, th = 2 * a.Bx, 2 * a.By
     ox, oy, _ = oracle.mcs_draw(prm, t)
     nx, ny, spent, attempts = 2, 2, 0.0, 0
@@ -172,7 +173,7 @@ def cpu_baseline_window(oracle, a, state_getter, t, target_s):
         else:
             ny = int(ny * grow) + 1
     return {"value": attempts / (spent * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle DTrDT replay of MCS {t} on a {nx}x{ny} device-tile window "
+            "sample": (f"oracle {name} replay of MCS {t} on a {nx}x{ny} device-tile window "
                        f"({attempts} attempts, {spent:.1f} s) of the GPU lattice state")}
 
 
@@ -428,12 +429,13 @@ def main():
     if rank == 0 and a.db_steps > 0:
         sim.close()
 
-        def timed(p, q, scheme, n):
+        def timed(p, q, scheme, n, oracle_scheme=None):
             # continues from the lattice as it stands (no_init), new time origin
             with g.Simulation(L, p, q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice,
                               no_init=True, scheme=scheme) as h:
                 h.run(2)
                 torch.cuda.synchronize()
+                st0 = _lib.oct_get_stats(h.h)
                 _lib.oct_set_timing(h.h, True)
                 st_, en_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 st_.record(stream)
@@ -441,22 +443,45 @@ def main():
                 en_.record(stream)
                 torch.cuda.synchronize()
                 kms, kl, _ = _lib.oct_get_timing(h.h)
-            return L * L * n / (st_.elapsed_time(en_) * 1e6), kms / max(1, kl)
+                st1 = _lib.oct_get_stats(h.h)
+                step_ms = kms / max(1, kl)
+                f_draw = (st1.draws - st0.draws) / (L * L * n)
+                cpu_ = None
+                if oracle_scheme is not None and not a.no_cpu and world == 1:
+                    import oracle
+                    oracle.build()
+                    cpu_ = cpu_baseline_window(oracle, a, lambda x, y, W, H: h.window(x, y, W, H), h.t,
+                                               a.cpu_seconds / 4, scheme=oracle_scheme, seed=seed,
+                                               name={1: "DTrDB", 3: "DTrDTr"}[oracle_scheme])
+            return L * L * n / (st_.elapsed_time(en_) * 1e6), step_ms, f_draw, cpu_
 
-        db_v, db_step = timed(a.p, a.q, _lib.OCT_SCHEME_DB, a.db_steps)
-        kdt_v, kdt_step = timed(1.0, 0.0, _lib.OCT_SCHEME_DT, a.db_steps)
-        kdb_v, kdb_step = timed(1.0, 0.0, _lib.OCT_SCHEME_DB, a.db_steps)
+        def alu_roofline(step_ms, bits):
+            ops = 0.5 * bits + 4.0
+            ach = ops * (L * L / 4) / (step_ms * 1e-3) / 1e12
+            return {"bound": "alu", "achieved": ach, "peak": peak_tops, "unit": "Tops/s", "frac": ach / peak_tops,
+                    "ops_per_attempt": ops, "launch_ms": step_ms}
+
+        tcs = (a.Bx // 4) * (a.By // 4)
+        db_v, db_step, db_f, db_cpu = timed(a.p, a.q, _lib.OCT_SCHEME_DB, a.db_steps, oracle_scheme=1)
+        kdt_v, kdt_step, _, _ = timed(1.0, 0.0, _lib.OCT_SCHEME_DT, a.db_steps)
+        kdb_v, kdb_step, _, _ = timed(1.0, 0.0, _lib.OCT_SCHEME_DB, a.db_steps)
         dtrdb = {"value": db_v, "unit": UNIT, "mcs": a.db_steps, "device_step_ms": db_step,
                  "scheme": "DTrDB: single-hit dead border at block level, borders delayed (p, q > 0)",
                  "start": "the DTrDT state after the timed region",
                  "relative_to_dtrdt": db_v / (value / world),
+                 "roofline": dict(alu_roofline(db_step, 4.0 + 32.0 * db_f), draw_fraction=db_f,
+                                  kernel="dtrdt_step_kernel<1, 2>"),
+                 "cpu_baseline": db_cpu,
                  "kpz": {"p": 1.0, "q": 0.0, "dtrdt": kdt_v, "dtrdb": kdb_v, "relative": kdb_v / kdt_v,
                          "device_step_ms": {"dtrdt": kdt_step, "dtrdb": kdb_step},
                          "note": "DB with one rate zero carries out all attempts of a step together"}}
-        dtr_v, dtr_step = timed(a.p, a.q, _lib.OCT_SCHEME_DTR, a.db_steps)
+        dtr_v, dtr_step, dtr_f, dtr_cpu = timed(a.p, a.q, _lib.OCT_SCHEME_DTR, a.db_steps, oracle_scheme=3)
         dtrdtr = {"value": dtr_v, "unit": UNIT, "mcs": a.db_steps, "device_step_ms": dtr_step,
                   "scheme": "DTrDTr: double tiling with a block-layer origin moved after every collective step",
-                  "start": "the DTrDB state after its run", "relative_to_dtrdt": dtr_v / (value / world)}
+                  "start": "the DTrDB state after its run", "relative_to_dtrdt": dtr_v / (value / world),
+                  "roofline": dict(alu_roofline(dtr_step, 2.0 + 6.0 / tcs + 32.0 * dtr_f), draw_fraction=dtr_f,
+                                   kernel="dtrdt_step_kernel<1, 3>"),
+                  "cpu_baseline": dtr_cpu}
         sim = g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice)
         sim.run(a.warmup + a.steps)
 
@@ -475,7 +500,26 @@ def main():
         ac_ms = st_.elapsed_time(en_) / a.ac_reps
         ac_bytes = L * L // 2  # both planes of both lattices, read once
         ac_gbs = ac_bytes / (ac_ms * 1e-3) / 1e9
+        ac_cpu = None
+        if not a.no_cpu and world == 1:
+            import numpy as np
+            import oracle
+            oracle.build()
+            Lc = 2048  # the oracle's lattices: flat start, 2 and 3 MCS of DTrDT
+            prm_c = oracle.Params(L=Lc, p=a.p, q=a.q, seed=seed, Bx=256, By=64)
+            Xs, Ys = oracle.flat(Lc)
+            oracle.dtrdt_run(Xs, Ys, prm_c, 0, 2)
+            Xt, Yt = Xs.copy(), Ys.copy()
+            oracle.dtrdt_run(Xt, Yt, prm_c, 2, 1)
+            reps_c, t0c = 0, time.perf_counter()
+            while reps_c < 3 or time.perf_counter() - t0c < 1.0:
+                oracle.two_time(Xt, Yt, Xs, Ys)
+                reps_c += 1
+            cpu_s = (time.perf_counter() - t0c) / reps_c
+            ac_cpu = {"value": Lc * Lc / (cpu_s * 1e9), "unit": "sites/ns", "cores": 1, "kind": "oracle",
+                      "sample": f"oracle two-time sums of two L={Lc} lattices, {reps_c} calls, {cpu_s * 1e3:.1f} ms each"}
         two_time = {"t": ac.t, "s": ac.s, "c_h": ac.c_h, "c_s": ac.c_s, "ms_per_call": ac_ms,
+                    "sites_per_ns": L * L / (ac_ms * 1e6), "cpu_baseline": ac_cpu,
                     "calls": a.ac_reps,
                     "roofline": {"bound": "hbm", "achieved": ac_gbs, "peak": hbm_peak, "unit": "GB/s",
                                  "frac": ac_gbs / hbm_peak, "algorithmic_bytes": ac_bytes},

@@ -282,3 +282,32 @@ def test_dtr_bit_exact(g, oracle, c):
             net += oracle.dtrdt_run(X, Y, prm, t, 1)[0]
             sim.run(1)
             _assert_same(oracle, sim, X, Y, net, f"t={t + 1}")
+
+
+@pytest.mark.parametrize("scheme", ["DB", "DTR"])
+def test_full_size_sampled_other_block_layers(g, oracle, scheme):
+    """L = 2^17, p = 0.95, q = 0.05, 256 x 64 sub-tiles, DTrDB (delayed borders)
+    and DTrDTr: MCS 2 replayed by the oracle on windows of 5 x 5 device tiles,
+    the centre tile compared with the GPU."""
+    L, p, q, seed, Bx, By = 2**17, 0.95, 0.05, 3, 256, 64
+    o_scheme = {"DB": oracle.SCHEME_DB, "DTR": oracle.SCHEME_DTR}[scheme]
+    g_scheme = {"DB": g._lib.OCT_SCHEME_DB, "DTR": g._lib.OCT_SCHEME_DTR}[scheme]
+    prm = oracle.Params(L=L, p=p, q=q, seed=seed, Bx=Bx, By=By, scheme=o_scheme)
+    tw, th = 2 * Bx, 2 * By
+    with g.Simulation(L, p, q, seed, Bx=Bx, By=By, scheme=g_scheme) as sim:
+        sim.run(2)
+        t = 2
+        ox, oy, _ = oracle.mcs_draw(prm, t)
+        rng = np.random.default_rng(1)
+        tiles = [(0, 0)] + [(int(rng.integers(0, L // tw)), int(rng.integers(0, L // th))) for _ in range(2)]
+        pre = []
+        for tx, ty in tiles:
+            wx, wy = ox + tw * (tx - 2), oy + th * (ty - 2)
+            pre.append((wx, wy, *sim.window(wx, wy, 5 * tw, 5 * th)))
+        sim.run(1)
+        for wx, wy, Xw, Yw in pre:
+            Xw, Yw = Xw.copy(), Yw.copy()
+            oracle.dtrdt_mcs_window(Xw, Yw, prm, t, wx, wy)
+            Xg, Yg = sim.window(wx + 2 * tw, wy + 2 * th, tw, th)
+            c = (slice(2 * th, 3 * th), slice(2 * tw, 3 * tw))
+            assert np.array_equal(Xg, Xw[c]) and np.array_equal(Yg, Yw[c]), (scheme, wx, wy)

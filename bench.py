@@ -564,9 +564,21 @@ def main():
             t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
+        # one more step, phase by phase, for the breakdown
+        ph = []
+        for fn in (lambda: _lib.oct_set_planes(sim.h, hp, words, sim.t), lambda: sim.run(1),
+                   lambda: sim.measure(), lambda: _lib.oct_get_planes(sim.h, hp, words)):
+            sim.sync()
+            t1 = time.perf_counter()
+            fn()
+            sim.sync()
+            ph.append(time.perf_counter() - t1)
         e2e = {"value": world * L * L * a.e2e_steps / (e2e_s * 1e9), "unit": UNIT,
                "h2d_bytes_per_step": L * L // 4, "d2h_bytes_per_step": L * L // 4 + 56,
                "steps": a.e2e_steps,
+               "breakdown_ms": {"h2d": ph[0] * 1e3, "mcs": ph[1] * 1e3, "measure_w2": ph[2] * 1e3,
+                                "d2h": ph[3] * 1e3},
+               "h2d_gbs": (L * L // 4) / ph[0] / 1e9, "d2h_gbs": (L * L // 4) / ph[3] / 1e9,
                "path": "oct_set_planes(pinned host) + oct_run_mcs(1) + oct_measure_w2 + oct_get_planes(pinned host)"}
 
     if rank == 0:

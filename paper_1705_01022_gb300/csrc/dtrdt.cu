@@ -151,7 +151,17 @@ cudaError_t launch_dtrdt_step(const StepArgs &a, bool any_random, cudaStream_t s
             OCT_LAUNCH(3, false);
             break;
         default:
-            if (packed) OCT_LAUNCH(0, true); else OCT_LAUNCH(0, false);
+            if (!any_random && a.p_always == 0xFFFFFFFFu && a.q_always == 0u) {
+                // deposition only (the KPZ case p = 1, q = 0): no acceptance masks
+                if (packed)
+                    dtrdt_step_kernel<false, 4, true><<<grid, block, 0, st>>>(a);
+                else
+                    dtrdt_step_kernel<false, 4, false><<<grid, block, 0, st>>>(a);
+            } else if (packed) {
+                OCT_LAUNCH(0, true);
+            } else {
+                OCT_LAUNCH(0, false);
+            }
     }
 #undef OCT_LAUNCH
     return cudaGetLastError();

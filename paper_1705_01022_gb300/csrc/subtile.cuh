@@ -149,9 +149,11 @@ __device__ __forceinline__ uint32_t accept_candidates(uint32_t pmin, uint32_t pm
 // s is eligible iff X(s) != X(s+x), Y(s) != Y(s+y) and X(s) == Y(s): then
 // X(s) = 0 is the minimum of Eq. (1), X(s) = 1 the maximum.  Candidates that
 // need an acceptance draw are packed to bit 4j+m (TC column j, TC row m).
-// DEP: deposition only (p = 1, q = 0, the KPZ case): every eligible minimum
-// flips and no maximum does, so the candidates are the minima themselves.
-template <int DY, bool RANDOM, bool DEP = false>
+// SPEC 1 (deposition only: p = 1, q = 0, the KPZ case): every eligible
+// minimum flips and no maximum does, so the candidates are the minima
+// themselves.  SPEC 2 (both 0 < p < 1 and 0 < q < 1): every candidate needs a
+// draw, so no always/never masks are applied.
+template <int DY, bool RANDOM, int SPEC = 0>
 __device__ __forceinline__ void step_candidates(const uint32_t (&X)[16], const uint32_t (&Y)[16],
                                                 uint32_t E, uint32_t D, const uint4 &site, uint32_t s,
                                                 uint32_t dx, const LaneCtx &c, uint32_t (&cnd0)[4],
@@ -173,7 +175,7 @@ __device__ __forceinline__ void step_candidates(const uint32_t (&X)[16], const u
         const uint32_t xrb = __funnelshift_r(xb, E >> r1, 1);
         const uint32_t ya = Y[r0], yb = Y[r1];
         const uint32_t yc = (r1 + 1 < 16) ? Y[(r1 + 1) & 15] : D;
-        if (DEP) {
+        if (SPEC == 1) {
             // minimum: X(s) = 0, X(s+x) = 1, Y(s) = 0, Y(s+y) = 1
             cnd0[m] = col & ~yoff & ~xa & xra & ~ya & yb;
             cnd1[m] = col & yoff & ~xb & xrb & ~yb & yc;
@@ -184,7 +186,7 @@ __device__ __forceinline__ void step_candidates(const uint32_t (&X)[16], const u
         if (RANDOM) {
             const uint32_t mn = (cnd0[m] & ~xa) | (cnd1[m] & ~xb);
             const uint32_t mx = (cnd0[m] & xa) | (cnd1[m] & xb);
-            const uint32_t cmn = mn & c.p_random, cmx = mx & c.q_random;
+            const uint32_t cmn = SPEC == 2 ? mn : mn & c.p_random, cmx = SPEC == 2 ? mx : mx & c.q_random;
             pmin |= (((cmn >> sh2) | (cmn >> (sh2 + 1u))) & kNib) << m;
             pmax |= (((cmx >> sh2) | (cmx >> (sh2 + 1u))) & kNib) << m;
         }
@@ -193,7 +195,7 @@ __device__ __forceinline__ void step_candidates(const uint32_t (&X)[16], const u
 
 // Phase 3 with sub-cell set (dx, DY): flips of the accepted candidates (acc:
 // packed acceptance bits) and the exchange with the neighbouring lanes.
-template <int DY, bool RANDOM, bool DEP = false>
+template <int DY, bool RANDOM, int SPEC = 0>
 __device__ __forceinline__ void step_apply(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E, uint32_t &D,
                                            uint32_t dx, uint32_t acc, const uint32_t (&cnd0)[4],
                                            const uint32_t (&cnd1)[4], const LaneCtx &c, int &net) {
@@ -201,20 +203,27 @@ __device__ __forceinline__ void step_apply(uint32_t (&X)[16], uint32_t (&Y)[16],
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const int r0 = 4 * m + 2 * DY, r1 = r0 + 1;
-        uint32_t amin = c.p_always, amax = c.q_always;
+        uint32_t amin = c.p_always, amax = c.q_always, spread = 0u;
         if (RANDOM) {
-            const uint32_t spread = ((acc >> m) & kNib) * 0xFu;
+            spread = ((acc >> m) & kNib) * 0xFu;
             amin |= spread & c.p_random;
             amax |= spread & c.q_random;
         }
         const uint32_t xa = X[r0], xb = X[r1];
         // accepted minima are where the candidate has X(s) = 0
-        const uint32_t f0 = DEP ? cnd0[m] : cnd0[m] & ((~xa & amin) | (xa & amax));
-        const uint32_t f1 = DEP ? cnd1[m] : cnd1[m] & ((~xb & amin) | (xb & amax));
-        if (DEP)
+        uint32_t f0, f1;
+        if (SPEC == 1) {
+            f0 = cnd0[m];
+            f1 = cnd1[m];
             net += __popc(f0 | f1);  // a thread cell flips in one of the two rows
-        else
+        } else if (SPEC == 2) {
+            f0 = cnd0[m] & spread;  // the draw decides every candidate
+            f1 = cnd1[m] & spread;
+        } else {
+            f0 = cnd0[m] & ((~xa & amin) | (xa & amax));
+            f1 = cnd1[m] & ((~xb & amin) | (xb & amax));
             net += always_net<RANDOM>(f0, xa, c) + always_net<RANDOM>(f1, xb, c);
+        }
         X[r0] = xa ^ f0 ^ (f0 << 1);
         X[r1] = xb ^ f1 ^ (f1 << 1);
         Y[r0] ^= f0;
@@ -680,7 +689,8 @@ __device__ __forceinline__ void dtr_apply(uint32_t (&X)[16], uint32_t (&Y)[16], 
 // run the 16 single-hit collective steps, write back.  LANE_SETS: lanes of the
 // warp may belong to different sub-tiles (each with its own set draws).
 // SCHEME: 0 DTrDT, 1 DTrDB with all attempts of a step together, 2 DTrDB with
-// delayed borders, 3 DTrDTr, 4 DTrDT with deposition only (p = 1, q = 0).
+// delayed borders, 3 DTrDTr, 4 DTrDT with deposition only (p = 1, q = 0),
+// 5 DTrDT with both rates strictly inside (0, 1).
 template <bool RANDOM, bool LANE_SETS, int SCHEME = 0>
 __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t Bx,
                                             uint32_t By, uint32_t x0, uint32_t y0, bool active,
@@ -778,7 +788,7 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
             }
             continue;
         }
-        if (SCHEME != 0 && SCHEME != 4) {
+        if (SCHEME == 1 || SCHEME == 2) {
             // DB: one site word per TC row and step, 4 bits per cell
             site = philox4x32_10(c.t, c.k | (s << 2), c.T, (kTagSiteDb << 28) | c.g, c.k0, c.k1);
             if (SCHEME == 2)
@@ -794,9 +804,9 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
         if (LANE_SETS)
             step_candidates_rt<RANDOM>(X, Y, E, D, site, s, d & 1u, d >> 1, c, cnd0, cnd1, pmin, pmax);
         else if (d & 2u)
-            step_candidates<1, RANDOM, SCHEME == 4>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
+            step_candidates<1, RANDOM, SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
         else
-            step_candidates<0, RANDOM, SCHEME == 4>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
+            step_candidates<0, RANDOM, SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
         uint32_t acc = 0u;
         if (RANDOM) {
             draws += __popc(pmin | pmax);
@@ -806,9 +816,9 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
         if (LANE_SETS)
             step_apply_rt<RANDOM>(X, Y, E, D, d >> 1, acc, cnd0, cnd1, c, net);
         else if (d & 2u)
-            step_apply<1, RANDOM, SCHEME == 4>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
+            step_apply<1, RANDOM, SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
         else
-            step_apply<0, RANDOM, SCHEME == 4>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
+            step_apply<0, RANDOM, SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
     }
 
     // Write back.  Global word wA of a row receives the high bits of the left

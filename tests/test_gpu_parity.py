@@ -311,3 +311,22 @@ def test_full_size_sampled_other_block_layers(g, oracle, scheme):
             Xg, Yg = sim.window(wx + 2 * tw, wy + 2 * th, tw, th)
             c = (slice(2 * th, 3 * th), slice(2 * tw, 3 * tw))
             assert np.array_equal(Xg, Xw[c]) and np.array_equal(Yg, Yw[c]), (scheme, wx, wy)
+
+
+def _all_shapes():
+    from paper_1705_01022_gb300 import autotune
+    return autotune.candidates(2048)
+
+
+@pytest.mark.parametrize("shape", _all_shapes(), ids=lambda s: f"{s[0]}x{s[1]}")
+def test_every_tunable_shape_bit_exact(g, oracle, shape):
+    """Every sub-tile shape the autotuner may choose (at L = 2048: one group up
+    to 32, packed several to a warp below 32), both acceptance modes."""
+    Bx, By = shape
+    for (p, q, seed) in ((0.95, 0.05, 21), (1.0, 0.0, 22)):
+        prm = oracle.Params(L=2048, p=p, q=q, seed=seed, Bx=Bx, By=By)
+        X, Y = oracle.flat(2048)
+        net = oracle.dtrdt_run(X, Y, prm, 0, 2)[0]
+        with g.Simulation(2048, p, q, seed, Bx=Bx, By=By) as sim:
+            sim.run(2)
+            _assert_same(oracle, sim, X, Y, net, f"{Bx}x{By} p={p}")

@@ -1,6 +1,9 @@
 // Device code shared by the plain and the batched device-step kernels: one
-// DTrDT device step on a sub-tile held by warp lanes (see dtrdt.cu for the
-// method and the lane layout).
+// device step on a sub-tile held by warp lanes, with the block layer of
+// DTrDT, DTrDB or DTrDTr (see dtrdt.cu for the method and the lane layout).
+// Streams beyond those listed in dtrdt.cu: DTrDB draws a site of the whole
+// cell from (t, k|s<<2, T, SITE_DB<<28|g), DTrDTr its block-layer origin from
+// (t, k, T, BORG<<28), byte s of the device step.
 #pragma once
 #include <cstdint>
 

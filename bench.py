@@ -138,14 +138,19 @@ def step_traffic(src_hash: str):
 
 
 def src_hash():
-    """sha256 of the list of sha256 sums of the step kernel's sources (as sha256sum prints it)."""
+    """sha256 of the step kernel's two source files with comments and blank
+    lines removed (a comment edit does not invalidate a capture)."""
     import hashlib
-    lines = []
+    import re
+    h = hashlib.sha256()
     for name in ("dtrdt.cu", "subtile.cuh"):
-        path = os.path.join("paper_1705_01022_gb300", "csrc", name)
-        with open(os.path.join(ROOT, path), "rb") as f:
-            lines.append(f"{hashlib.sha256(f.read()).hexdigest()}  {path}\n")
-    return hashlib.sha256("".join(lines).encode()).hexdigest()
+        with open(os.path.join(ROOT, "paper_1705_01022_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(name.encode() + b"\0" + code.encode() + b"\0")
+    return h.hexdigest()
 
 
 def cpu_baseline_window(oracle, a, state_getter, t, target_s, scheme=0, seed=None, name="DTrDT"):

@@ -519,16 +519,26 @@ __device__ __forceinline__ DtrLanes dtr_lanes(const LaneCtx &c) {
     return n;
 }
 
-// Phase 1.  ca[m], cb[m]: candidates in rows 4m+R0 and 4m+R0+1 held by this
-// lane; with R0 = 3, cb[3] holds row 0 instead (row 16 belongs to the lane
-// below).  pmin / pmax: packed candidates of this lane's own thread cells.
-template <int R0, bool RANDOM>
+// v[k] for a run-time k in 0..3 (k uniform over the warp: selects, no branch).
+__device__ __forceinline__ uint32_t pick4(uint32_t k, uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
+    const uint32_t lo = (k & 1u) ? v1 : v0, hi = (k & 1u) ? v3 : v2;
+    return (k & 2u) ? hi : lo;
+}
+
+// Phase 1.  The row phase R0 is a run-time value (one copy of the code for all
+// four phases; four specialised copies overflowed the instruction caches).
+// ca[m], cb[m]: candidates in rows a = 4m+R0 and b = a+1 held by this lane;
+// row 16 (m = 3, R0 = 3) is the lane below's row 0, and cb[3] then holds this
+// lane's row 0 (the wrapped row of the lane above) instead.
+// pmin / pmax: packed candidates of this lane's own thread cells.
+template <bool RANDOM>
 __device__ __forceinline__ void dtr_candidates(const uint32_t (&X)[16], const uint32_t (&Y)[16], uint32_t E,
                                                uint32_t D, const uint4 &site, uint32_t s, uint32_t c0,
-                                               const LaneCtx &c, const DtrLanes &n, uint32_t (&ca)[4],
-                                               uint32_t (&cb)[4], uint32_t &pmin, uint32_t &pmax) {
-    const bool SX = c0 == 3u;     // pairs reach column 32 (uniform over the warp)
-    constexpr bool SY = R0 == 3;  // pairs reach row 16
+                                               uint32_t R0, const LaneCtx &c, const DtrLanes &n,
+                                               uint32_t (&ca)[4], uint32_t (&cb)[4], uint32_t &pmin,
+                                               uint32_t &pmax) {
+    const bool SX = c0 == 3u;  // pairs reach column 32 (uniform over the warp)
+    const bool SY = R0 == 3u;  // pairs reach row 16
     const uint32_t sw[4] = {site.x, site.y, site.z, site.w};
     const uint32_t par = 2u * (s & 1u);
     // Selected sites: own thread cells in place, those past column 31 in xw
@@ -541,16 +551,16 @@ __device__ __forceinline__ void dtr_candidates(const uint32_t (&X)[16], const ui
         const uint32_t yoff = ((u >> 1) & kNib) * 0xFu;         // thread cells with ry = 1
         const uint64_t a64 = static_cast<uint64_t>(col & ~yoff) << c0;
         const uint64_t b64 = static_cast<uint64_t>(col & yoff) << c0;
-        const int ya = 4 * m + R0;
+        const uint32_t ya = 4u * m + R0;
         ca[m] = static_cast<uint32_t>(a64);
         xw |= static_cast<uint32_t>(a64 >> 32) << ya;
-        if (ya + 1 < 16) {
-            cb[m] = static_cast<uint32_t>(b64);
-            xw |= static_cast<uint32_t>(b64 >> 32) << (ya + 1);
-        } else {
+        if (m == 3 && SY) {
             cb[m] = 0u;
             yw = static_cast<uint32_t>(b64);
             xw |= static_cast<uint32_t>(b64 >> 32) << 16;
+        } else {
+            cb[m] = static_cast<uint32_t>(b64);
+            xw |= static_cast<uint32_t>(b64 >> 32) << (ya + 1u);
         }
     }
     // sites of neighbouring lanes' thread cells held by this lane
@@ -558,9 +568,9 @@ __device__ __forceinline__ void dtr_candidates(const uint32_t (&X)[16], const ui
         const uint32_t v = __shfl_sync(kFull, xw, n.lL);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            const int ya = 4 * m + R0;
+            const uint32_t ya = 4u * m + R0;
             ca[m] |= (v >> ya) & 1u;
-            if (ya + 1 < 16) cb[m] |= (v >> (ya + 1)) & 1u;
+            if (!(m == 3 && SY)) cb[m] |= (v >> (ya + 1u)) & 1u;
         }
     }
     if (SY) {
@@ -568,23 +578,31 @@ __device__ __forceinline__ void dtr_candidates(const uint32_t (&X)[16], const ui
         const uint32_t corner = SX ? (__shfl_sync(kFull, xw, n.lAL) >> 16) & 1u : 0u;
         cb[3] = v | corner;  // row 0
     }
-    // eligibility
+    // eligibility; rows a and b of TC row m picked by the row phase (for
+    // m = 3 the row after 15 is D for Y, and row b = "16" is row 0)
     uint32_t cw = 0u;  // column-0 candidates: minima in bits 0..15, maxima in 16..31 (row = bit)
+    uint32_t xa_[4], xb_[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const int ya = 4 * m + R0;
-        const int yb = SY && m == 3 ? 0 : ya + 1;  // the row cb[m] stands for
-        {
-            const uint32_t x = X[ya], xr = __funnelshift_r(x, E >> ya, 1);
-            const uint32_t y = Y[ya], yd = (ya < 15) ? Y[(ya + 1) & 15] : D;
-            ca[m] &= (x ^ xr) & (y ^ yd) & ~(x ^ y);
-            if (RANDOM) cw |= ((ca[m] & ~x & 1u) << ya) | ((ca[m] & x & 1u) << (ya + 16));
-        }
-        {
-            const uint32_t x = X[yb], xr = __funnelshift_r(x, E >> yb, 1);
-            const uint32_t y = Y[yb], yd = (yb < 15) ? Y[(yb + 1) & 15] : D;
-            cb[m] &= (x ^ xr) & (y ^ yd) & ~(x ^ y);
-            if (RANDOM) cw |= ((cb[m] & ~x & 1u) << yb) | ((cb[m] & x & 1u) << (yb + 16));
+        const int r = 4 * m;
+        const uint32_t X4 = m < 3 ? X[(r + 4) & 15] : X[0];
+        const uint32_t Y4 = m < 3 ? Y[(r + 4) & 15] : D;
+        const uint32_t Yb4 = m < 3 ? Y[(r + 4) & 15] : Y[0];  // row b's own Y when b = "16"
+        const uint32_t Y5 = m < 3 ? Y[(r + 5) & 15] : Y[1];
+        const uint32_t ya = static_cast<uint32_t>(r) + R0, yb = (ya + 1u) & 15u;
+        const uint32_t xa = pick4(R0, X[r], X[r + 1], X[r + 2], X[r + 3]);
+        const uint32_t yA = pick4(R0, Y[r], Y[r + 1], Y[r + 2], Y[r + 3]);
+        const uint32_t yAd = pick4(R0, Y[r + 1], Y[r + 2], Y[r + 3], Y4);
+        const uint32_t xb = pick4(R0, X[r + 1], X[r + 2], X[r + 3], X4);
+        const uint32_t yB = pick4(R0, Y[r + 1], Y[r + 2], Y[r + 3], Yb4);
+        const uint32_t yBd = pick4(R0, Y[r + 2], Y[r + 3], Y4, Y5);
+        ca[m] &= (xa ^ __funnelshift_r(xa, E >> ya, 1)) & (yA ^ yAd) & ~(xa ^ yA);
+        cb[m] &= (xb ^ __funnelshift_r(xb, E >> yb, 1)) & (yB ^ yBd) & ~(xb ^ yB);
+        xa_[m] = xa;
+        xb_[m] = xb;
+        if (RANDOM) {
+            cw |= ((ca[m] & ~xa & 1u) << ya) | ((ca[m] & xa & 1u) << (ya + 16u));
+            cw |= ((cb[m] & ~xb & 1u) << yb) | ((cb[m] & xb & 1u) << (yb + 16u));
         }
     }
     pmin = 0u;
@@ -599,19 +617,19 @@ __device__ __forceinline__ void dtr_candidates(const uint32_t (&X)[16], const ui
         }
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            const int ya = 4 * m + R0, yb = ya + 1;
-            uint32_t mnl = ca[m] & ~X[ya], mxl = ca[m] & X[ya];
-            uint32_t mnh = (cwR >> ya) & 1u, mxh = (cwR >> (ya + 16)) & 1u;
-            if (yb < 16) {
-                mnl |= cb[m] & ~X[yb & 15];
-                mxl |= cb[m] & X[yb & 15];
-                mnh |= (cwR >> yb) & 1u;
-                mxh |= (cwR >> ((yb + 16) & 31)) & 1u;
-            } else {
+            const uint32_t ya = 4u * m + R0, yb = ya + 1u;
+            uint32_t mnl = ca[m] & ~xa_[m], mxl = ca[m] & xa_[m];
+            uint32_t mnh = (cwR >> ya) & 1u, mxh = (cwR >> (ya + 16u)) & 1u;
+            if (m == 3 && SY) {
                 mnl |= bmin;
                 mxl |= bmax;
                 mnh |= cwBR & 1u;
                 mxh |= (cwBR >> 16) & 1u;
+            } else {
+                mnl |= cb[m] & ~xb_[m];
+                mxl |= cb[m] & xb_[m];
+                mnh |= (cwR >> yb) & 1u;
+                mxh |= (cwR >> (yb + 16u)) & 1u;
             }
             // align each cell's pair to bits 4j, 4j+1, then pack to bit 4j+m
             const uint32_t cmn = __funnelshift_r(mnl, mnh, c0) & c.p_random;
@@ -629,50 +647,63 @@ __device__ __forceinline__ void dtr_candidates(const uint32_t (&X)[16], const ui
 }
 
 // Phase 3: flips of the accepted candidates (acc: this lane's packed
-// acceptance bits), then the exchange of the neighbour copies.
-template <int R0, bool RANDOM>
+// acceptance bits), then the exchange of the neighbour copies.  The flips of
+// row r come from TC row m = r / 4 when r % 4 is R0 (row a) or R0 + 1 (row b),
+// and from TC row m - 1 (mod 4: row 0 takes the wrapped row of TC row 3) when
+// r % 4 = 0 and R0 = 3.
+template <bool RANDOM>
 __device__ __forceinline__ void dtr_apply(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E, uint32_t &D,
-                                          uint32_t c0, uint32_t acc, const uint32_t (&ca)[4],
+                                          uint32_t c0, uint32_t R0, uint32_t acc, const uint32_t (&ca)[4],
                                           const uint32_t (&cb)[4], const LaneCtx &c, const DtrLanes &n,
                                           int &net) {
     const bool SX = c0 == 3u;
-    constexpr bool SY = R0 == 3;
+    const bool SY = R0 == 3u;
     uint32_t accL = 0u, accA = 0u, accAL = 0u;
     if (RANDOM) {
         if (SX) accL = __shfl_sync(kFull, acc, n.lL);
         if (SY) accA = __shfl_sync(kFull, acc, n.lA);
         if (SX && SY) accAL = __shfl_sync(kFull, acc, n.lAL);
     }
-    uint32_t dE = 0u, dB0 = 0u, dD = 0u, dY0 = 0u;
+    // accepted candidates of rows a and b of every TC row (fb[3] with R0 = 3: row 0)
+    uint32_t fa[4], fb[4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int m = i >> 1;
-        const bool second = i & 1;
-        const bool row0 = SY && m == 3 && second;  // incoming row 0
-        const int R = row0 ? 0 : 4 * m + R0 + (second ? 1 : 0);
-        uint32_t amin = c.p_always, amax = c.q_always;
+    for (int m = 0; m < 4; ++m) {
+        const int r = 4 * m;
+        const uint32_t xa = pick4(R0, X[r], X[r + 1], X[r + 2], X[r + 3]);
+        const uint32_t xb = pick4(R0, X[r + 1], X[r + 2], X[r + 3], m < 3 ? X[(r + 4) & 15] : X[0]);
+        uint32_t amin = c.p_always, amax = c.q_always, bmin = c.p_always, bmax = c.q_always;
         if (RANDOM) {
-            const uint32_t own = row0 ? ((accA >> 3) & kNib) * 0xFu : ((acc >> m) & kNib) * 0xFu;
-            const uint32_t left = row0 ? ((accAL >> 3) & kNib) * 0xFu : ((accL >> m) & kNib) * 0xFu;
+            const uint32_t own = ((acc >> m) & kNib) * 0xFu;
+            const uint32_t left = ((accL >> m) & kNib) * 0xFu;
             const uint32_t cols = __funnelshift_l(left, own, c0);
+            // row 0 with R0 = 3: thread cells of the lanes above
+            const uint32_t cols0 = __funnelshift_l(((accAL >> 3) & kNib) * 0xFu, ((accA >> 3) & kNib) * 0xFu, c0);
+            const uint32_t colb = (m == 3 && SY) ? cols0 : cols;
             amin |= cols & c.p_random;
             amax |= cols & c.q_random;
+            bmin |= colb & c.p_random;
+            bmax |= colb & c.q_random;
         }
-        const uint32_t x = X[R];
-        const uint32_t f = (second ? cb[m] : ca[m]) & ((~x & amin) | (x & amax));
-        net += always_net<RANDOM>(f, x, c);
-        X[R] = x ^ f ^ (f << 1);
-        Y[R] ^= f;
-        if (R < 15) {
-            Y[(R + 1) & 15] ^= f;
-        } else {
-            D ^= f;
-            dD = f;
-        }
-        dE |= (f >> 31) << R;
-        dB0 |= (f & 1u) << R;
-        if (R == 0) dY0 = f;
+        fa[m] = ca[m] & ((~xa & amin) | (xa & amax));
+        fb[m] = cb[m] & ((~xb & bmin) | (xb & bmax));
+        net += always_net<RANDOM>(fa[m], xa, c) + always_net<RANDOM>(fb[m], xb, c);
     }
+    uint32_t dE = 0u, dB0 = 0u, F_prev = 0u;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int m = r >> 2;
+        const uint32_t k = static_cast<uint32_t>(r & 3);
+        uint32_t F = (R0 == k ? fa[m] : 0u) | (R0 + 1u == k ? fb[m] : 0u);
+        if (k == 0u && SY) F |= fb[(m + 3) & 3];
+        X[r] ^= F ^ (F << 1);
+        Y[r] ^= F ^ F_prev;  // its own Y, and Y(s+y) of the row above
+        dE |= (F >> 31) << r;
+        dB0 |= (F & 1u) << r;
+        F_prev = F;
+    }
+    D ^= F_prev;  // Y(s+y) of row 15
+    const uint32_t dD = F_prev;
+    const uint32_t dY0 = (R0 == 0u ? fa[0] : 0u) | (SY ? fb[3] : 0u);  // the flips of row 0
     E ^= dE;
     const uint32_t vr = __shfl_up_sync(kFull, dE, 1);
     const uint32_t vl = __shfl_down_sync(kFull, dB0, 1);
@@ -771,24 +802,14 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
             const uint32_t r0 = (((byte >> 4) & 3u) + 2u * (d >> 1)) & 3u;
             const DtrLanes n = dtr_lanes(c);
             uint32_t ca[4], cb[4], pmin, pmax;
-            switch (r0) {
-                case 0: dtr_candidates<0, RANDOM>(X, Y, E, D, site, s, c0, c, n, ca, cb, pmin, pmax); break;
-                case 1: dtr_candidates<1, RANDOM>(X, Y, E, D, site, s, c0, c, n, ca, cb, pmin, pmax); break;
-                case 2: dtr_candidates<2, RANDOM>(X, Y, E, D, site, s, c0, c, n, ca, cb, pmin, pmax); break;
-                default: dtr_candidates<3, RANDOM>(X, Y, E, D, site, s, c0, c, n, ca, cb, pmin, pmax); break;
-            }
+            dtr_candidates<RANDOM>(X, Y, E, D, site, s, c0, r0, c, n, ca, cb, pmin, pmax);
             uint32_t acc = 0u;
             if (RANDOM) {
                 draws += __popc(pmin | pmax);
                 acc = accept_candidates(pmin, pmax, level_words(s, c), c, tp);
                 net += random_net(acc, pmin, pmax);
             }
-            switch (r0) {
-                case 0: dtr_apply<0, RANDOM>(X, Y, E, D, c0, acc, ca, cb, c, n, net); break;
-                case 1: dtr_apply<1, RANDOM>(X, Y, E, D, c0, acc, ca, cb, c, n, net); break;
-                case 2: dtr_apply<2, RANDOM>(X, Y, E, D, c0, acc, ca, cb, c, n, net); break;
-                default: dtr_apply<3, RANDOM>(X, Y, E, D, c0, acc, ca, cb, c, n, net); break;
-            }
+            dtr_apply<RANDOM>(X, Y, E, D, c0, r0, acc, ca, cb, c, n, net);
             continue;
         }
         if (SCHEME == 1 || SCHEME == 2) {

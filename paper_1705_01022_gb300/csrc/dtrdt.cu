@@ -142,10 +142,20 @@ cudaError_t launch_dtrdt_step(const StepArgs &a, bool any_random, cudaStream_t s
     } while (0)
     switch (a.scheme) {
         case 1:
-            if (packed) OCT_LAUNCH(1, true); else OCT_LAUNCH(1, false);
+            if (packed)
+                OCT_LAUNCH(1, true);
+            else if (!any_random && a.p_always == 0xFFFFFFFFu && a.q_always == 0u)
+                dtrdt_step_kernel<false, 6, false><<<grid, block, 0, st>>>(a);  // deposition only
+            else
+                OCT_LAUNCH(1, false);
             break;
         case 2:
-            if (packed) OCT_LAUNCH(2, true); else OCT_LAUNCH(2, false);
+            if (packed)
+                OCT_LAUNCH(2, true);
+            else if (a.p_random && a.q_random)
+                dtrdt_step_kernel<true, 7, false><<<grid, block, 0, st>>>(a);  // both rates random
+            else
+                OCT_LAUNCH(2, false);
             break;
         case 3:
             OCT_LAUNCH(3, false);

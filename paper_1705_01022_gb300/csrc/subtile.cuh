@@ -387,7 +387,8 @@ __device__ __forceinline__ void step_apply_rt(uint32_t (&X)[16], uint32_t (&Y)[1
 // decided on the state before the step, which with one rate zero never lets
 // two accepted flips meet.  Every candidate of a phase is found before any of
 // its flips is applied.
-template <bool RANDOM, bool DELAYED>
+// SPEC as for step_candidates: 1 deposition only, 2 both rates random.
+template <bool RANDOM, bool DELAYED, int SPEC = 0>
 __device__ __forceinline__ void db_step(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E, uint32_t &D,
                                         const uint4 &site, uint32_t s, const LaneCtx &c, TailPool &tp,
                                         int &net, int &draws) {
@@ -422,7 +423,10 @@ __device__ __forceinline__ void db_step(uint32_t (&X)[16], uint32_t (&Y)[16], ui
             const uint32_t x = X[R];
             const uint32_t xr = __funnelshift_r(x, E >> R, 1);
             const uint32_t y = Y[R], yd = (R < 15) ? Y[(R + 1) & 15] : D;
-            cand[R] = sel[R] & mask & (x ^ xr) & (y ^ yd) & ~(x ^ y);
+            if (SPEC == 1)
+                cand[R] = sel[R] & mask & ~x & xr & ~y & yd;  // the minima
+            else
+                cand[R] = sel[R] & mask & (x ^ xr) & (y ^ yd) & ~(x ^ y);
         }
         if (RANDOM) {
 #pragma unroll
@@ -433,8 +437,10 @@ __device__ __forceinline__ void db_step(uint32_t (&X)[16], uint32_t (&Y)[16], ui
                     mn |= cand[4 * m + r] & ~X[4 * m + r];
                     mx |= cand[4 * m + r] & X[4 * m + r];
                 }
-                mn &= c.p_random;
-                mx &= c.q_random;
+                if (SPEC != 2) {
+                    mn &= c.p_random;
+                    mx &= c.q_random;
+                }
                 pmin |= ((mn | (mn >> 1) | (mn >> 2) | (mn >> 3)) & kNib) << m;
                 pmax |= ((mx | (mx >> 1) | (mx >> 2) | (mx >> 3)) & kNib) << m;
             }
@@ -456,8 +462,16 @@ __device__ __forceinline__ void db_step(uint32_t (&X)[16], uint32_t (&Y)[16], ui
                 amax |= spread & c.q_random;
             }
             const uint32_t x = X[R];
-            const uint32_t f = cand[R] & ((~x & amin) | (x & amax));
-            net += always_net<RANDOM>(f, x, c);
+            uint32_t f;
+            if (SPEC == 1) {
+                f = cand[R];
+                net += __popc(f);
+            } else if (SPEC == 2) {
+                f = cand[R] & ((acc >> m) & kNib) * 0xFu;
+            } else {
+                f = cand[R] & ((~x & amin) | (x & amax));
+                net += always_net<RANDOM>(f, x, c);
+            }
             X[R] = x ^ f ^ (f << 1);
             Y[R] ^= f;
             if (R < 15)
@@ -724,7 +738,8 @@ __device__ __forceinline__ void dtr_apply(uint32_t (&X)[16], uint32_t (&Y)[16], 
 // warp may belong to different sub-tiles (each with its own set draws).
 // SCHEME: 0 DTrDT, 1 DTrDB with all attempts of a step together, 2 DTrDB with
 // delayed borders, 3 DTrDTr, 4 DTrDT with deposition only (p = 1, q = 0),
-// 5 DTrDT with both rates strictly inside (0, 1).
+// 5 DTrDT with both rates strictly inside (0, 1), 6 DTrDB with deposition only,
+// 7 DTrDB with delayed borders and both rates random.
 template <bool RANDOM, bool LANE_SETS, int SCHEME = 0>
 __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t Bx,
                                             uint32_t By, uint32_t x0, uint32_t y0, bool active,
@@ -812,11 +827,15 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
             dtr_apply<RANDOM>(X, Y, E, D, c0, r0, acc, ca, cb, c, n, net);
             continue;
         }
-        if (SCHEME == 1 || SCHEME == 2) {
+        if (SCHEME == 1 || SCHEME == 2 || SCHEME == 6 || SCHEME == 7) {
             // DB: one site word per TC row and step, 4 bits per cell
             site = philox4x32_10(c.t, c.k | (s << 2), c.T, (kTagSiteDb << 28) | c.g, c.k0, c.k1);
             if (SCHEME == 2)
                 db_step<RANDOM, true>(X, Y, E, D, site, s, c, tp, net, draws);
+            else if (SCHEME == 7)
+                db_step<RANDOM, true, 2>(X, Y, E, D, site, s, c, tp, net, draws);
+            else if (SCHEME == 6)
+                db_step<RANDOM, false, 1>(X, Y, E, D, site, s, c, tp, net, draws);
             else
                 db_step<RANDOM, false>(X, Y, E, D, site, s, c, tp, net, draws);
             continue;

@@ -57,7 +57,9 @@ constexpr int kBatchBlocksPerSM = 4;
 // LANE_SETS: the warp holds several sub-tiles (fewer than 32 groups each), each
 // with its own set draws; otherwise one sub-tile fills the warp and the step
 // takes the uniform row-offset path of the plain kernel.
-template <bool RANDOM, bool LANE_SETS>
+// SCHEME: 0 DTrDT, 4 with deposition only (p = 1, q = 0), 5 with both rates
+// strictly inside (0, 1) (the step variants of the plain kernel).
+template <bool RANDOM, bool LANE_SETS, int SCHEME>
 __global__ void __launch_bounds__(kBatchWarps * 32, kBatchBlocksPerSM)
     batch_step_kernel(const ReplicaDev *reps, const BatchItem *items, const WarpDesc *descs,
                       uint32_t n_descs, const uint32_t *t_of, uint32_t k, uint32_t *queue) {
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, kBatchBlocksPerSM)
         c.p_random = R.p_random;
         c.q_random = R.q_random;
         int net = 0, draws = 0;
-        run_subtile<RANDOM, LANE_SETS>(R.lat, L, R.wpr, R.Bx, R.By, x0, y0, active, c,
+        run_subtile<RANDOM, LANE_SETS, SCHEME>(R.lat, L, R.wpr, R.Bx, R.By, x0, y0, active, c,
                                   ring + ((threadIdx.x >> 5) * 32 + (lane & ~(G - 1))) * kRingWordsPerLane,
                                   net, draws);
         // sum over the G lanes of the item (items start at multiples of G)
@@ -132,6 +134,9 @@ __global__ void batch_advance_kernel(uint32_t *t_of, const uint32_t *active, uin
 }  // namespace oct
 
 namespace {
+
+constexpr int kModes = 4;
+constexpr int kKinds = 2 * kModes;
 
 int bfail(int code, const std::string &msg) {
     oct::set_last_error(msg);
@@ -171,10 +176,11 @@ struct oct_batch {
     uint32_t *d_active = nullptr;
     size_t active_cap = 0;
     uint32_t n_active = 0;
-    // work lists by kind = 2 * mode + (one sub-tile per warp); mode 1: acceptance draws
-    uint32_t n_desc[4] = {0, 0, 0, 0};
-    uint32_t desc_first[4] = {0, 0, 0, 0};
-    uint32_t *d_queue = nullptr;  // 16 counters: (device step, kind)
+    // work lists by kind = 2 * mode + (one sub-tile per warp); modes: 0 no
+    // acceptance draws, 1 draws, 2 draws for both rates, 3 deposition only
+    uint32_t n_desc[kKinds] = {};
+    uint32_t desc_first[kKinds] = {};
+    uint32_t *d_queue = nullptr;  // 4 * kKinds counters: (device step, kind)
     oct::W2RowSums *d_rows = nullptr;
     int64_t rows_cap = 0;
     oct::W2Result *d_w2 = nullptr;
@@ -312,13 +318,15 @@ cudaError_t rebuild(oct_batch *b) {
     drop_graph(b);
     std::vector<oct::ReplicaDev> rd(b->capacity);
     std::vector<uint32_t> active;
-    std::vector<oct::BatchItem> bucket[2][6][6];
+    std::vector<oct::BatchItem> bucket[kModes][6][6];
     for (size_t slot = 0; slot < b->reps.size(); ++slot) {
         if (!b->used[slot]) continue;
         rd[slot] = replica_dev(b, static_cast<int64_t>(slot));
         const oct::ReplicaDev &D = rd[slot];
         active.push_back(static_cast<uint32_t>(slot));
-        const int mode = (D.p_random || D.q_random) ? 1 : 0;
+        const int mode = (D.p_random && D.q_random) ? 2
+                         : (D.p_random || D.q_random) ? 1
+                         : (D.p_always && !D.q_always) ? 3 : 0;
         int gxi = 0, gyi = 0;
         while ((1u << gxi) < D.GX) ++gxi;
         while ((1u << gyi) < D.GY) ++gyi;
@@ -327,7 +335,7 @@ cudaError_t rebuild(oct_batch *b) {
     }
     std::vector<oct::BatchItem> items;
     std::vector<oct::WarpDesc> descs;
-    for (int kind = 0; kind < 4; ++kind) {
+    for (int kind = 0; kind < kKinds; ++kind) {
         const int mode = kind >> 1;
         const bool full = kind & 1;
         b->desc_first[kind] = static_cast<uint32_t>(descs.size());
@@ -367,21 +375,28 @@ cudaError_t rebuild(oct_batch *b) {
 
 // Enqueues device step k of the current MCS of every active replica.
 cudaError_t enqueue_step(oct_batch *b, uint32_t k, cudaStream_t st) {
-    for (int kind = 0; kind < 4; ++kind) {
+    for (int kind = 0; kind < kKinds; ++kind) {
         if (b->n_desc[kind] == 0) continue;
-        uint32_t *q = b->d_queue + 4 * k + kind;
+        uint32_t *q = b->d_queue + kKinds * k + kind;
         cudaError_t e = cudaMemsetAsync(q, 0, sizeof(uint32_t), st);
         if (e != cudaSuccess) return e;
         const oct::WarpDesc *descs = b->d_descs + b->desc_first[kind];
         const uint32_t nd = b->n_desc[kind];
         const int blocks = std::min<int>(b->grid, static_cast<int>((nd + oct::kBatchWarps - 1) / oct::kBatchWarps));
         const dim3 grid(blocks), block(oct::kBatchWarps * 32);
+#define OCT_BATCH(R, LS, SC) \
+    oct::batch_step_kernel<R, LS, SC><<<grid, block, 0, st>>>(b->d_reps, b->d_items, descs, nd, b->d_t, k, q)
         switch (kind) {
-            case 0: oct::batch_step_kernel<false, true><<<grid, block, 0, st>>>(b->d_reps, b->d_items, descs, nd, b->d_t, k, q); break;
-            case 1: oct::batch_step_kernel<false, false><<<grid, block, 0, st>>>(b->d_reps, b->d_items, descs, nd, b->d_t, k, q); break;
-            case 2: oct::batch_step_kernel<true, true><<<grid, block, 0, st>>>(b->d_reps, b->d_items, descs, nd, b->d_t, k, q); break;
-            default: oct::batch_step_kernel<true, false><<<grid, block, 0, st>>>(b->d_reps, b->d_items, descs, nd, b->d_t, k, q); break;
+            case 0: OCT_BATCH(false, true, 0); break;
+            case 1: OCT_BATCH(false, false, 0); break;
+            case 2: OCT_BATCH(true, true, 0); break;
+            case 3: OCT_BATCH(true, false, 0); break;
+            case 4: OCT_BATCH(true, true, 5); break;
+            case 5: OCT_BATCH(true, false, 5); break;
+            case 6: OCT_BATCH(false, true, 4); break;
+            default: OCT_BATCH(false, false, 4); break;
         }
+#undef OCT_BATCH
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -528,7 +543,7 @@ int oct_batch_create(int64_t n, const oct_replica *reps, void *stream, oct_batch
             e = cudaMemPoolSetAttribute(b->pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
     }
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(uint32_t) * 16);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(uint32_t) * 4 * kKinds);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_w2, sizeof(oct::W2Result));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_small, 256);
     if (e == cudaSuccess) {

@@ -167,9 +167,12 @@ cudaError_t launch_dtrdt_step(const StepArgs &a, bool any_random, cudaStream_t s
                     dtrdt_step_kernel<false, 4, true><<<grid, block, 0, st>>>(a);
                 else
                     dtrdt_step_kernel<false, 4, false><<<grid, block, 0, st>>>(a);
-            } else if (any_random && a.p_random && a.q_random && !packed) {
+            } else if (any_random && a.p_random && a.q_random) {
                 // both rates strictly inside (0, 1): every candidate is decided by its draw
-                dtrdt_step_kernel<true, 5, false><<<grid, block, 0, st>>>(a);
+                if (packed)
+                    dtrdt_step_kernel<true, 5, true><<<grid, block, 0, st>>>(a);
+                else
+                    dtrdt_step_kernel<true, 5, false><<<grid, block, 0, st>>>(a);
             } else if (packed) {
                 OCT_LAUNCH(0, true);
             } else {

@@ -284,7 +284,7 @@ __device__ __forceinline__ void step_apply(uint32_t (&X)[16], uint32_t (&Y)[16],
 // sub-tiles, each with its own set draw: the row offset dy is a run-time value
 // per lane (rows picked with selects instead of branches), and every shuffle
 // runs unconditionally so that all 32 lanes take part.
-template <bool RANDOM>
+template <bool RANDOM, int SPEC = 0>
 __device__ __forceinline__ void step_candidates_rt(const uint32_t (&X)[16], const uint32_t (&Y)[16],
                                                    uint32_t E, uint32_t D, const uint4 &site, uint32_t s,
                                                    uint32_t dx, uint32_t dy, const LaneCtx &c,
@@ -309,19 +309,24 @@ __device__ __forceinline__ void step_candidates_rt(const uint32_t (&X)[16], cons
         const uint32_t r0 = 4u * m + ro;
         const uint32_t xra = __funnelshift_r(xa, E >> r0, 1);
         const uint32_t xrb = __funnelshift_r(xb, E >> (r0 + 1u), 1);
+        if (SPEC == 1) {
+            cnd0[m] = col & ~yoff & ~xa & xra & ~ya & yb;  // the minima
+            cnd1[m] = col & yoff & ~xb & xrb & ~yb & yc;
+            continue;
+        }
         cnd0[m] = col & ~yoff & (xa ^ xra) & (ya ^ yb) & ~(xa ^ ya);
         cnd1[m] = col & yoff & (xb ^ xrb) & (yb ^ yc) & ~(xb ^ yb);
         if (RANDOM) {
             const uint32_t mn = (cnd0[m] & ~xa) | (cnd1[m] & ~xb);
             const uint32_t mx = (cnd0[m] & xa) | (cnd1[m] & xb);
-            const uint32_t cmn = mn & c.p_random, cmx = mx & c.q_random;
+            const uint32_t cmn = SPEC == 2 ? mn : mn & c.p_random, cmx = SPEC == 2 ? mx : mx & c.q_random;
             pmin |= (((cmn >> sh2) | (cmn >> (sh2 + 1u))) & kNib) << m;
             pmax |= (((cmx >> sh2) | (cmx >> (sh2 + 1u))) & kNib) << m;
         }
     }
 }
 
-template <bool RANDOM>
+template <bool RANDOM, int SPEC = 0>
 __device__ __forceinline__ void step_apply_rt(uint32_t (&X)[16], uint32_t (&Y)[16], uint32_t &E, uint32_t &D,
                                               uint32_t dy, uint32_t acc, const uint32_t (&cnd0)[4],
                                               const uint32_t (&cnd1)[4], const LaneCtx &c, int &net) {
@@ -330,17 +335,27 @@ __device__ __forceinline__ void step_apply_rt(uint32_t (&X)[16], uint32_t (&Y)[1
     uint32_t dE = 0, dB0 = 0, dD = 0, dY0 = 0;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        uint32_t amin = c.p_always, amax = c.q_always;
+        uint32_t amin = c.p_always, amax = c.q_always, spread = 0u;
         if (RANDOM) {
-            const uint32_t spread = ((acc >> m) & kNib) * 0xFu;
+            spread = ((acc >> m) & kNib) * 0xFu;
             amin |= spread & c.p_random;
             amax |= spread & c.q_random;
         }
         const uint32_t xa = dy ? X[4 * m + 2] : X[4 * m];
         const uint32_t xb = dy ? X[4 * m + 3] : X[4 * m + 1];
-        const uint32_t f0 = cnd0[m] & ((~xa & amin) | (xa & amax));
-        const uint32_t f1 = cnd1[m] & ((~xb & amin) | (xb & amax));
-        net += always_net<RANDOM>(f0, xa, c) + always_net<RANDOM>(f1, xb, c);
+        uint32_t f0, f1;
+        if (SPEC == 1) {
+            f0 = cnd0[m];
+            f1 = cnd1[m];
+            net += __popc(f0 | f1);
+        } else if (SPEC == 2) {
+            f0 = cnd0[m] & spread;
+            f1 = cnd1[m] & spread;
+        } else {
+            f0 = cnd0[m] & ((~xa & amin) | (xa & amax));
+            f1 = cnd1[m] & ((~xb & amin) | (xb & amax));
+            net += always_net<RANDOM>(f0, xa, c) + always_net<RANDOM>(f1, xb, c);
+        }
         const uint32_t nxa = xa ^ f0 ^ (f0 << 1), nxb = xb ^ f1 ^ (f1 << 1);
         X[4 * m] = dy ? X[4 * m] : nxa;
         X[4 * m + 1] = dy ? X[4 * m + 1] : nxb;
@@ -844,12 +859,13 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
             site = philox4x32_10(c.t, c.k | ((s >> 1) << 2), c.T, (kTagSite << 28) | c.g, c.k0, c.k1);
         const uint32_t d = (setw.x >> (2u * s)) & 3u;
         uint32_t cnd0[4], cnd1[4], pmin, pmax;
+        constexpr int kSpec = SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0;
         if (LANE_SETS)
-            step_candidates_rt<RANDOM>(X, Y, E, D, site, s, d & 1u, d >> 1, c, cnd0, cnd1, pmin, pmax);
+            step_candidates_rt<RANDOM, kSpec>(X, Y, E, D, site, s, d & 1u, d >> 1, c, cnd0, cnd1, pmin, pmax);
         else if (d & 2u)
-            step_candidates<1, RANDOM, SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
+            step_candidates<1, RANDOM, kSpec>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
         else
-            step_candidates<0, RANDOM, SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
+            step_candidates<0, RANDOM, kSpec>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
         uint32_t acc = 0u;
         if (RANDOM) {
             draws += __popc(pmin | pmax);
@@ -857,11 +873,11 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
             net += random_net(acc, pmin, pmax);
         }
         if (LANE_SETS)
-            step_apply_rt<RANDOM>(X, Y, E, D, d >> 1, acc, cnd0, cnd1, c, net);
+            step_apply_rt<RANDOM, kSpec>(X, Y, E, D, d >> 1, acc, cnd0, cnd1, c, net);
         else if (d & 2u)
-            step_apply<1, RANDOM, SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
+            step_apply<1, RANDOM, kSpec>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
         else
-            step_apply<0, RANDOM, SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
+            step_apply<0, RANDOM, kSpec>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
     }
 
     // Write back.  Global word wA of a row receives the high bits of the left

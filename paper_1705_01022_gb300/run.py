@@ -1,0 +1,134 @@
+"""Production runs: roughness at log-spaced times, two-time autocorrelations
+and effective exponents (Sec. 2: W of Eq. (3), C of Eq. (5), Eq. (8)).
+
+A run starts from the flat state and advances whole MCS on the GPU. At each
+measurement time it takes the exact W^2 (integer S1, S2). With waiting times
+given, it snapshots the lattice at the first of them that has been reached
+and from then on measures C_h(t, s) and C_s(t, s) at every later measurement
+time (one snapshot at a time: a later waiting time replaces the earlier one).
+
+Measurement times follow t_i = max(t_{i-1} + 1, round(t_max^(i/(n-1)))),
+i = 0..n-1, after t = 0; waiting times are added to that list.
+
+Effective exponents take Eq. (8) on consecutive pairs (t_j < t_i):
+e = (ln E(t_i) - ln E(t_j)) / (ln t_i - ln t_j). The paper prints the time
+of the estimate as (t_i - t_j)/2, which for a midpoint must be read as
+(t_i + t_j)/2; each estimate also carries the geometric midpoint
+sqrt(t_i t_j), the natural one on a log axis.
+
+Command line:
+    python -m paper_1705_01022_gb300.run --L 131072 --p 0.95 --q 0.05 \
+        --t-max 10000 --points 40 [--wait 100] [--scheme dt|db|dtr] [--out f.jsonl]
+prints one JSON line per measurement, then one summary line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import sys
+import time
+
+SCHEMES = {"dt": 0, "db": 1, "dtr": 2}
+
+
+def measurement_times(t_max: int, n: int, waits=()) -> list[int]:
+    """0, then n log-spaced times ending at t_max (strictly increasing), with the waiting times merged in."""
+    if t_max < 1 or n < 1:
+        raise ValueError("t_max and n must be >= 1")
+    ts = [0]
+    for i in range(n):
+        t = t_max if n == 1 else int(round(t_max ** (i / (n - 1))))
+        t = max(ts[-1] + 1, t)
+        if t > t_max:
+            break
+        ts.append(t)
+    if ts[-1] != t_max:
+        ts.append(t_max)
+    for s in waits:
+        if not 0 <= int(s) <= t_max:
+            raise ValueError(f"waiting time {s} outside [0, {t_max}]")
+    return sorted(set(ts) | {int(s) for s in waits})
+
+
+def effective_exponents(ts, E, power: float = 1.0) -> list[dict]:
+    """Eq. (8) on consecutive pairs of (t, E) with t > 0 and E > 0; `power`
+    rescales the exponent (0.5 turns W^2 into W)."""
+    pts = [(float(t), float(e)) for t, e in zip(ts, E) if t > 0 and e > 0]
+    out = []
+    for (tj, ej), (ti, ei) in zip(pts, pts[1:]):
+        out.append({"t_j": tj, "t_i": ti, "t_mid": 0.5 * (ti + tj), "t_geo": math.sqrt(ti * tj),
+                    "exponent": power * (math.log(ei) - math.log(ej)) / (math.log(ti) - math.log(tj))})
+    return out
+
+
+def production_run(L: int, p: float, q: float, seed: int, t_max: int, points: int, waits=(),
+                   scheme: str = "dt", Bx: int = 0, By: int = 0, stream=None, callback=None) -> dict:
+    """Runs to t_max and returns {records, beta_eff, wall_s, attempts_per_ns}.
+
+    records: one dict per measurement time (t, w2, s1, s2, net_flips and, after
+    a snapshot, s, c_h, c_s). beta_eff: Eq. (8) on W = sqrt(W^2).
+    attempts_per_ns: L^2 t_max attempts over the wall time of the whole run,
+    measurements included."""
+    from . import Simulation
+    ts = measurement_times(t_max, points, waits)
+    waits = sorted(int(s) for s in waits)
+    records = []
+    t0 = time.perf_counter()
+    with Simulation(L, p, q, seed, Bx=Bx, By=By, scheme=SCHEMES[scheme], stream=stream) as sim:
+        t = 0
+        for tt in ts:
+            sim.run(tt - t)
+            t = tt
+            m = sim.measure()
+            rec = {"t": t, "w2": m.w2, "s1": m.s1, "s2": m.s2, "net_flips": m.net_flips}
+            if t in waits:
+                sim.snapshot()
+            if waits and t > waits[0]:
+                ac = sim.measure_ac()
+                rec.update({"s": ac.s, "c_h": ac.c_h, "c_s": ac.c_s})
+            records.append(rec)
+            if callback:
+                callback(rec)
+        sim.sync()
+    wall = time.perf_counter() - t0
+    beta = effective_exponents([r["t"] for r in records], [r["w2"] for r in records], power=0.5)
+    return {"records": records, "beta_eff": beta, "wall_s": wall,
+            "attempts_per_ns": L * L * t_max / (wall * 1e9)}
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--L", type=int, default=4096)
+    ap.add_argument("--p", type=float, default=1.0)
+    ap.add_argument("--q", type=float, default=0.0)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--t-max", type=int, default=1000)
+    ap.add_argument("--points", type=int, default=30)
+    ap.add_argument("--wait", type=int, action="append", default=[], help="waiting time s (repeatable)")
+    ap.add_argument("--scheme", choices=sorted(SCHEMES), default="dt")
+    ap.add_argument("--Bx", type=int, default=0)
+    ap.add_argument("--By", type=int, default=0)
+    ap.add_argument("--out", default=None, help="also write the JSON lines to this file")
+    a = ap.parse_args(argv)
+    fp = open(a.out, "w") if a.out else None
+
+    def emit(obj):
+        line = json.dumps(obj)
+        print(line, flush=True)
+        if fp:
+            fp.write(line + "\n")
+            fp.flush()
+
+    res = production_run(a.L, a.p, a.q, a.seed, a.t_max, a.points, a.wait, a.scheme, a.Bx, a.By,
+                         callback=emit)
+    emit({"summary": {"L": a.L, "p": a.p, "q": a.q, "seed": a.seed, "t_max": a.t_max, "scheme": a.scheme,
+                      "wall_s": round(res["wall_s"], 3), "attempts_per_ns": round(res["attempts_per_ns"], 1),
+                      "beta_eff": [{k: round(v, 5) for k, v in b.items()} for b in res["beta_eff"]]}})
+    if fp:
+        fp.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,42 @@
+"""Production runs on the GPU (W^2 at log-spaced times and the two-time
+autocorrelations after a waiting time, Sec. 2) against the oracle's replay of
+the same schedule: every record's W^2, C_h and C_s are the same doubles
+(they come from equal integer sums)."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1705_01022_gb300 as g
+    g.build()
+    return g
+
+
+@pytest.mark.parametrize("scheme,L,Bx,By,p,q", [
+    ("dt", 256, 64, 64, 0.95, 0.05),
+    ("dt", 512, 128, 32, 1.0, 0.0),
+    ("db", 256, 64, 64, 0.95, 0.05),
+    ("dtr", 256, 64, 64, 0.5, 0.5),
+])
+def test_production_run_matches_oracle(g, oracle, scheme, L, Bx, By, p, q):
+    from oracle import Params, SCHEME_DB, SCHEME_DT, SCHEME_DTR
+    from paper_1705_01022_gb300 import run as prun
+    res = prun.production_run(L, p, q, 9, t_max=24, points=6, waits=[5], scheme=scheme, Bx=Bx, By=By)
+    prm = Params(L=L, p=p, q=q, seed=9, Bx=Bx, By=By,
+                 scheme={"dt": SCHEME_DT, "db": SCHEME_DB, "dtr": SCHEME_DTR}[scheme])
+    X, Y = oracle.flat(L)
+    t, net, snap = 0, 0, None
+    for r in res["records"]:
+        net += oracle.dtrdt_run(X, Y, prm, t, r["t"] - t)[0]
+        t = r["t"]
+        s1, s2, _ = oracle.w2_sums(X, Y)
+        assert (r["s1"], r["s2"], r["net_flips"]) == (s1, s2, net), t
+        assert r["w2"] == oracle.w2(X, Y), t
+        if t == 5:
+            snap = (X.copy(), Y.copy())
+        if t > 5:
+            a = oracle.two_time(X, Y, *snap)
+            assert (r["s"], r["c_h"], r["c_s"]) == (5, a["c_h"], a["c_s"]), t
+    assert [r["t"] for r in res["records"]][-1] == 24

@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--Bx", type=int, default=256)
     ap.add_argument("--By", type=int, default=64)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-lattices", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -550,32 +551,62 @@ def main():
                                   a.cpu_seconds)
 
     # ---- end to end through the C ABI with host buffers ----
+    # Each step copies one lattice in from page-locked host memory, runs one
+    # MCS, measures W^2 and copies the lattice back out.  `--e2e-lattices`
+    # independent lattices (the benchmark's own and replicas with seeds
+    # seed + 1000 k, each on its own stream) take the steps in turn, driven
+    # from one host thread with the asynchronous calls, so that one lattice's
+    # copies overlap another's kernels and copies in the other direction.
     e2e = None
     if not a.no_e2e and a.e2e_steps > 0:
         words = L * L // 16
-        host = torch.empty(words * 4, dtype=torch.uint8, pin_memory=True)
-        hp = host.data_ptr()
-        _lib.oct_get_planes(sim.h, hp, words)
-        # one untimed step through the same path (first use of the host buffer)
-        _lib.oct_set_planes(sim.h, hp, words, sim.t)
-        sim.run(1)
-        sim.measure()
-        _lib.oct_get_planes(sim.h, hp, words)
+        nl = max(1, a.e2e_lattices)
+        e2e_sims = [sim] + [g.Simulation(L, a.p, a.q, seed + 1000 * k, Bx=a.Bx, By=a.By)
+                            for k in range(1, nl)]
+        hosts = [torch.empty(words * 4, dtype=torch.uint8, pin_memory=True) for _ in range(nl)]
+        _lib.oct_get_planes(sim.h, hosts[0].data_ptr(), words)
+        for hb in hosts[1:]:
+            hb.copy_(hosts[0])
+        tk = [sim.t] * nl
+        pending = [False] * nl
+
+        def e2e_step(i):
+            k = i % nl
+            h = e2e_sims[k].h
+            if pending[k]:
+                _lib.oct_w2_wait(h)
+            _lib.oct_set_planes(h, hosts[k].data_ptr(), words, tk[k])
+            _lib.oct_run_mcs(h, 1)
+            _lib.oct_measure_w2_async(h)
+            _lib.oct_get_planes_async(h, hosts[k].data_ptr(), words)
+            tk[k] += 1
+            pending[k] = True
+
+        def e2e_drain():
+            for k in range(nl):
+                if pending[k]:
+                    _lib.oct_w2_wait(e2e_sims[k].h)
+                    pending[k] = False
+
+        for i in range(nl):  # one untimed step per lattice (first use of each host buffer)
+            e2e_step(i)
+        e2e_drain()
         barrier()
         t0 = time.perf_counter()
-        for _ in range(a.e2e_steps):
-            _lib.oct_set_planes(sim.h, hp, words, sim.t)
-            sim.run(1)
-            sim.measure()
-            _lib.oct_get_planes(sim.h, hp, words)
+        for i in range(a.e2e_steps):
+            e2e_step(i)
+        e2e_drain()
         barrier()
         e2e_s = time.perf_counter() - t0
+        for extra in e2e_sims[1:]:
+            extra.close()
         if dist is not None:
             t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
         # one more step, phase by phase, for the breakdown
         ph = []
+        hp = hosts[0].data_ptr()
         for fn in (lambda: _lib.oct_set_planes(sim.h, hp, words, sim.t), lambda: sim.run(1),
                    lambda: sim.measure(), lambda: _lib.oct_get_planes(sim.h, hp, words)):
             sim.sync()
@@ -585,11 +616,14 @@ def main():
             ph.append(time.perf_counter() - t1)
         e2e = {"value": world * L * L * a.e2e_steps / (e2e_s * 1e9), "unit": UNIT,
                "h2d_bytes_per_step": L * L // 4, "d2h_bytes_per_step": L * L // 4 + 56,
-               "steps": a.e2e_steps,
+               "steps": a.e2e_steps, "lattices_in_flight": nl,
                "breakdown_ms": {"h2d": ph[0] * 1e3, "mcs": ph[1] * 1e3, "measure_w2": ph[2] * 1e3,
                                 "d2h": ph[3] * 1e3},
                "h2d_gbs": (L * L // 4) / ph[0] / 1e9, "d2h_gbs": (L * L // 4) / ph[3] / 1e9,
-               "path": "oct_set_planes(pinned host) + oct_run_mcs(1) + oct_measure_w2 + oct_get_planes(pinned host)"}
+               "path": ("per step, lattice k = step mod lattices_in_flight: oct_set_planes(pinned host) + "
+                        "oct_run_mcs(1) + oct_measure_w2_async + oct_get_planes_async(pinned host); "
+                        "oct_w2_wait before the lattice's next step and at the end"),
+               "breakdown_note": "one step of one lattice, phase by phase with a synchronisation between phases"}
 
     if rank == 0:
         out = {

@@ -138,8 +138,21 @@ int oct_create_ex(const oct_params *prm, oct_sim **out);
 int oct_run_mcs(oct_sim *s, int64_t n);
 
 /* Computes the exact roughness of the current lattice (Eq. (3)); synchronises
- * the handle's stream. */
+ * the handle's stream.  OCT_EINVAL while an asynchronous measurement of the
+ * handle is pending. */
 int oct_measure_w2(oct_sim *s, oct_w2 *out);
+
+/* The same measurement in two halves, so that one host thread can keep
+ * several handles busy.  oct_measure_w2_async enqueues the reduction and the
+ * read-back of its sums on the handle's stream and returns at once; it
+ * measures the lattice as it stands after the work enqueued before it (later
+ * oct_run_mcs calls do not change the result).  oct_w2_wait synchronises the
+ * handle's stream and fills *out (out->t is the time of the measured lattice).
+ * One measurement may be pending per handle: a second oct_measure_w2_async, or
+ * oct_measure_w2, before oct_w2_wait returns OCT_EINVAL, and so does
+ * oct_w2_wait with nothing pending. */
+int oct_measure_w2_async(oct_sim *s);
+int oct_w2_wait(oct_sim *s, oct_w2 *out);
 
 /* Copies the lattice to host memory in the canonical 4x4-per-word layout;
  * words must equal L*L/16.  Synchronises. */
@@ -153,9 +166,17 @@ int oct_get_lattice(oct_sim *s, uint32_t *host, size_t words);
 int oct_set_lattice(oct_sim *s, const uint32_t *host, size_t words, int64_t t);
 
 /* Raw copies of the planar layout (words = L*L/16 in total: X plane then Y
- * plane). */
+ * plane).  oct_get_planes and oct_set_planes synchronise the handle's stream
+ * (oct_set_planes also sets the time to t and restarts the flip counters). */
 int oct_get_planes(oct_sim *s, uint32_t *host, size_t words);
 int oct_set_planes(oct_sim *s, const uint32_t *host, size_t words, int64_t t);
+
+/* Enqueues the copy of both planes to `host` on the handle's stream and
+ * returns at once.  The data is there after the next synchronising call on
+ * the handle (oct_sync, oct_w2_wait, ...); until then the caller keeps `host`
+ * alive and does not read it.  With page-locked `host` the copy overlaps other
+ * handles' kernels and host-to-device copies. */
+int oct_get_planes_async(oct_sim *s, uint32_t *host, size_t words);
 
 /* Copies a W x H window whose corner is global site (wx, wy) (periodic) into
  * host byte arrays X, Y of W*H entries each (index j*W + i for site

@@ -51,6 +51,13 @@ class Simulation:
     def measure(self) -> oct_w2:
         return _lib.oct_measure_w2(self.h)
 
+    def measure_async(self) -> None:
+        """Enqueues a W^2 measurement of the lattice as it stands; `w2_wait` returns it."""
+        _lib.oct_measure_w2_async(self.h)
+
+    def w2_wait(self) -> oct_w2:
+        return _lib.oct_w2_wait(self.h)
+
     def snapshot(self) -> None:
         """Stores the current lattice as the state at the waiting time s = t."""
         _lib.oct_snapshot(self.h)

@@ -83,10 +83,13 @@ _SIGNATURES = [
     ("oct_create_ex", [ctypes.POINTER(oct_params), ctypes.POINTER(_H)], ctypes.c_int),
     ("oct_run_mcs", [_H, ctypes.c_int64], ctypes.c_int),
     ("oct_measure_w2", [_H, ctypes.POINTER(oct_w2)], ctypes.c_int),
+    ("oct_measure_w2_async", [_H], ctypes.c_int),
+    ("oct_w2_wait", [_H, ctypes.POINTER(oct_w2)], ctypes.c_int),
     ("oct_get_lattice", [_H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
     ("oct_set_lattice", [_H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64], ctypes.c_int),
     ("oct_get_planes", [_H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
     ("oct_set_planes", [_H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64], ctypes.c_int),
+    ("oct_get_planes_async", [_H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
     ("oct_get_window", [_H, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                         ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     ("oct_get_info", [_H, ctypes.POINTER(oct_info)], ctypes.c_int),
@@ -188,6 +191,16 @@ def oct_measure_w2(h: int) -> oct_w2:
     return out
 
 
+def oct_measure_w2_async(h: int) -> None:
+    _check(load().oct_measure_w2_async(h), "oct_measure_w2_async")
+
+
+def oct_w2_wait(h: int) -> oct_w2:
+    out = oct_w2()
+    _check(load().oct_w2_wait(h, ctypes.byref(out)), "oct_w2_wait")
+    return out
+
+
 def oct_get_lattice(h: int, buf, words: int) -> None:
     _check(load().oct_get_lattice(h, _ptr(buf), words), "oct_get_lattice")
 
@@ -198,6 +211,11 @@ def oct_set_lattice(h: int, buf, words: int, t: int) -> None:
 
 def oct_get_planes(h: int, buf, words: int) -> None:
     _check(load().oct_get_planes(h, _ptr(buf), words), "oct_get_planes")
+
+
+def oct_get_planes_async(h: int, buf, words: int) -> None:
+    """`buf` must stay alive, unread, until the handle's next synchronising call."""
+    _check(load().oct_get_planes_async(h, _ptr(buf), words), "oct_get_planes_async")
 
 
 def oct_set_planes(h: int, buf, words: int, t: int) -> None:

@@ -58,8 +58,10 @@ struct oct_sim {
     long long *d_net_sum = nullptr;         // [net flips, acceptance draws]
     oct::W2RowSums *d_rows = nullptr;
     oct::W2Result *d_w2 = nullptr;
-    void *h_small = nullptr;  // pinned: W2Result + net sum
+    void *h_small = nullptr;  // pinned: W2Result at 0, its net sum at 128, oct_get_stats' net sum at 192
     uint64_t t = 0;
+    bool w2_pending = false;  // oct_measure_w2_async enqueued, oct_w2_wait not yet called
+    uint64_t w2_t = 0;        // time of the pending measurement
     oct::StepArgs args{};
     bool any_random = false;
     // timing
@@ -291,20 +293,33 @@ int oct_run_mcs(oct_sim *s, int64_t n) {
     return OCT_OK;
 }
 
-int oct_measure_w2(oct_sim *s, oct_w2 *out) {
-    if (!s || !out) return fail(OCT_EINVAL, "NULL argument");
-    OCT_CUDA(cudaSetDevice(s->device));
+namespace {
+
+// Enqueues the W^2 reduction (Eq. (3)) and the copy of its sums into the
+// handle's pinned staging area.
+int enqueue_w2(oct_sim *s) {
     OCT_CUDA(oct::launch_net_sum(s->d_net, s->d_net + oct::kNetSlots, s->d_net_sum, s->stream));
     OCT_CUDA(oct::launch_w2(s->lat, static_cast<uint32_t>(s->L), s->d_rows, s->d_w2, s->stream));
     auto *res = static_cast<oct::W2Result *>(s->h_small);
     auto *net = reinterpret_cast<long long *>(static_cast<char *>(s->h_small) + 128);
     OCT_CUDA(cudaMemcpyAsync(res, s->d_w2, sizeof(oct::W2Result), cudaMemcpyDeviceToHost, s->stream));
     OCT_CUDA(cudaMemcpyAsync(net, s->d_net_sum, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    s->w2_pending = true;
+    s->w2_t = s->t;
+    return OCT_OK;
+}
+
+// Waits for the enqueued measurement and forms W^2 = (N S2 - S1^2) / N^2 in
+// 128-bit integers, one conversion to double at the end.
+int finish_w2(oct_sim *s, oct_w2 *out) {
+    s->w2_pending = false;
     OCT_CUDA(cudaStreamSynchronize(s->stream));
+    const auto *res = static_cast<const oct::W2Result *>(s->h_small);
+    const auto *net = reinterpret_cast<const long long *>(static_cast<const char *>(s->h_small) + 128);
     const __int128 N = static_cast<__int128>(s->L) * s->L;
     const __int128 S2 = static_cast<__int128>((static_cast<unsigned __int128>(res->s2_hi) << 64) | res->s2_lo);
     const __int128 num = N * S2 - static_cast<__int128>(res->s1) * res->s1;
-    out->t = static_cast<int64_t>(s->t);
+    out->t = static_cast<int64_t>(s->w2_t);
     out->n_sites = static_cast<int64_t>(N);
     out->s1 = res->s1;
     out->s2_lo = res->s2_lo;
@@ -314,6 +329,31 @@ int oct_measure_w2(oct_sim *s, oct_w2 *out) {
     out->hmax = res->hmax;
     out->w2 = static_cast<double>(num) / (static_cast<double>(N) * static_cast<double>(N));
     return OCT_OK;
+}
+
+}  // namespace
+
+int oct_measure_w2(oct_sim *s, oct_w2 *out) {
+    if (!s || !out) return fail(OCT_EINVAL, "NULL argument");
+    if (s->w2_pending) return fail(OCT_EINVAL, "a measurement from oct_measure_w2_async is pending: call oct_w2_wait");
+    OCT_CUDA(cudaSetDevice(s->device));
+    const int rc = enqueue_w2(s);
+    if (rc) return rc;
+    return finish_w2(s, out);
+}
+
+int oct_measure_w2_async(oct_sim *s) {
+    if (!s) return fail(OCT_EINVAL, "NULL argument");
+    if (s->w2_pending) return fail(OCT_EINVAL, "a measurement is already pending: call oct_w2_wait");
+    OCT_CUDA(cudaSetDevice(s->device));
+    return enqueue_w2(s);
+}
+
+int oct_w2_wait(oct_sim *s, oct_w2 *out) {
+    if (!s || !out) return fail(OCT_EINVAL, "NULL argument");
+    if (!s->w2_pending) return fail(OCT_EINVAL, "no measurement pending (oct_measure_w2_async first)");
+    OCT_CUDA(cudaSetDevice(s->device));
+    return finish_w2(s, out);
 }
 
 int oct_get_lattice(oct_sim *s, uint32_t *host, size_t words) {
@@ -365,6 +405,14 @@ int oct_get_planes(oct_sim *s, uint32_t *host, size_t words) {
     OCT_CUDA(cudaSetDevice(s->device));
     OCT_CUDA(cudaMemcpyAsync(host, s->lat, words * 4, cudaMemcpyDeviceToHost, s->stream));
     OCT_CUDA(cudaStreamSynchronize(s->stream));
+    return OCT_OK;
+}
+
+int oct_get_planes_async(oct_sim *s, uint32_t *host, size_t words) {
+    if (!s || !host) return fail(OCT_EINVAL, "NULL argument");
+    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal L*L/16");
+    OCT_CUDA(cudaSetDevice(s->device));
+    OCT_CUDA(cudaMemcpyAsync(host, s->lat, words * 4, cudaMemcpyDeviceToHost, s->stream));
     return OCT_OK;
 }
 
@@ -552,7 +600,7 @@ int oct_get_stats(oct_sim *s, oct_stats *out) {
     if (!s || !out) return fail(OCT_EINVAL, "NULL argument");
     OCT_CUDA(cudaSetDevice(s->device));
     OCT_CUDA(oct::launch_net_sum(s->d_net, s->d_net + oct::kNetSlots, s->d_net_sum, s->stream));
-    auto *net = reinterpret_cast<long long *>(static_cast<char *>(s->h_small) + 128);
+    auto *net = reinterpret_cast<long long *>(static_cast<char *>(s->h_small) + 192);
     OCT_CUDA(cudaMemcpyAsync(net, s->d_net_sum, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
     OCT_CUDA(cudaStreamSynchronize(s->stream));
     out->t = static_cast<int64_t>(s->t);

@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--e2e-lattices", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-cores", type=int, default=0, help="host cores for --impl reference (0: all)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-replicas", type=int, default=2048)
@@ -180,7 +181,96 @@ def cpu_baseline_window(oracle, a, state_getter, t, target_s, scheme=0, seed=Non
             ny = int(ny * grow) + 1
     return {"value": attempts / (spent * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": (f"oracle {name} replay of MCS {t} on a {nx}x{ny} device-tile window "
-                       f"({attempts} attempts, {spent:.1f} s) of the GPU lattice state")}
+                       f"({attempts} attempts, {spent:.1f} s) of the GPU lattice state"),
+            "_window": (prm, t, ox, oy, W, H, attempts)}
+
+
+def _replay_task(task):
+    """Host-core worker: replays MCS t of the oracle's schedule on a private
+    copy of a window stored in a file; returns (attempts, replay seconds)."""
+    import numpy as np
+
+    import oracle
+    path, H, W, prm, t, ox, oy, attempts = task
+    view = np.memmap(path, dtype=np.uint8, mode="r", shape=(2, H, W))
+    Xw, Yw = np.array(view[0]), np.array(view[1])
+    del view
+    t0 = time.perf_counter()
+    oracle.dtrdt_mcs_window(Xw, Yw, prm, t, ox, oy)
+    return attempts, time.perf_counter() - t0
+
+
+def _warm_task(_):
+    import oracle
+    oracle.lib()
+    return os.getpid()
+
+
+class HostCores:
+    """A process pool over the host cores (started with spawn, so it is safe
+    after CUDA is up) in which every core replays its own copy of a window."""
+
+    def __init__(self, n=None):
+        import multiprocessing as mp
+        self.n = n or len(os.sched_getaffinity(0))
+        self.pool = mp.get_context("spawn").Pool(self.n)
+        self.pool.map(_warm_task, range(self.n), chunksize=1)
+        shm = "/dev/shm"
+        self.dir = shm if os.path.isdir(shm) and os.access(shm, os.W_OK) else tempfile.gettempdir()
+
+    def replay(self, Xw, Yw, prm, t, ox, oy, attempts):
+        """All cores at once, one window copy each: (total attempts, wall s, per-core s)."""
+        import numpy as np
+        H, W = Xw.shape
+        fd, path = tempfile.mkstemp(dir=self.dir, suffix=".win")
+        os.close(fd)
+        try:
+            mm = np.memmap(path, dtype=np.uint8, mode="w+", shape=(2, H, W))
+            mm[0], mm[1] = Xw, Yw
+            mm.flush()
+            del mm
+            t0 = time.perf_counter()
+            res = self.pool.map(_replay_task, [(path, H, W, prm, t, ox, oy, attempts)] * self.n, chunksize=1)
+            wall = time.perf_counter() - t0
+        finally:
+            os.unlink(path)
+        return sum(r[0] for r in res), wall, [r[1] for r in res]
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline_all_cores(oracle, single, state_getter, name="DTrDT"):
+    """The window of the single-core run, replayed by every host core at once
+    (each on its own copy); the value is all attempts over the wall time,
+    which includes the workers' copy of the window."""
+    prm, t, ox, oy, W, H, attempts = single["_window"]
+    Xw, Yw = state_getter(ox, oy, W, H)
+    cores = HostCores()
+    try:
+        total, wall, per = cores.replay(Xw, Yw, prm, t, ox, oy, attempts)
+    finally:
+        cores.close()
+    return {"value": total / (wall * 1e9), "unit": UNIT, "cores": cores.n, "kind": "oracle",
+            "sample": (f"oracle {name} replay of MCS {t}: {cores.n} processes, each on its own copy of the "
+                       f"window of the single-core sample ({attempts} attempts each, {wall:.1f} s wall, "
+                       f"replays {min(per):.1f}-{max(per):.1f} s)"),
+            "single_core": {k: v for k, v in single.items() if not k.startswith("_")}}
+
+
+def cpu_sequential_rs(oracle, L=4096, p=1.0, q=0.0, seed=1, target_s=3.0):
+    """O1 (sequential RS, one attempt at a time) on one core at L=4096, the
+    paper's CPU comparison size (Sec. 4.3)."""
+    X, Y = oracle.flat(L)
+    n, spent = 0, 0.0
+    while spent < target_s:
+        t0 = time.perf_counter()
+        oracle.seq_rs(X, Y, p, q, seed, n, 1)
+        spent += time.perf_counter() - t0
+        n += 1
+    return {"value": n * L * L / (spent * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle sequential RS (O1), L={L}, p={p}, q={q}, {n} MCS from the flat start, {spent:.1f} s"}
 
 
 BATCH_PQ = [(1.0, 0.0), (0.95, 0.05), (0.5, 0.5)]
@@ -284,8 +374,9 @@ def serving_leg(a, g, _lib, torch, stream, capacity):
 
 
 def run_reference(a, rank, world):
-    """The oracle as it stands, on the host cores, same metric and workload;
-    each step replays one MCS on a bounded window of the lattice."""
+    """The oracle as it stands, on the host cores, same metric and workload:
+    each step, every core replays one MCS on its own copy of a bounded window
+    of the lattice (flat start; the window follows the MCS origin)."""
     if rank != 0:
         return None
     import numpy as np
@@ -294,32 +385,33 @@ def run_reference(a, rank, world):
     oracle.build()
     prm = oracle.Params(L=a.L, p=a.p, q=a.q, seed=a.seed, Bx=a.Bx, By=a.By)
     tw, th = 2 * a.Bx, 2 * a.By
-    nx, ny = max(1, min(a.L // tw, 4)), max(1, min(a.L // th, 4))
+    nx, ny = max(1, min(a.L // tw, 8)), max(1, min(a.L // th, 4))
     W, H = min(nx * tw + 1, a.L), min(ny * th + 1, a.L)
-    # flat start restricted to the window, which follows the origin of each MCS
+    per_window = nx * ny * tw * th
+    cores = HostCores(a.ref_cores or None)
     times, total = [], 0
-    for step in range(a.warmup + a.steps):
-        ox, oy, _ = oracle.mcs_draw(prm, step)
-        xs = (ox + np.arange(W)) % a.L
-        ys = (oy + np.arange(H)) % a.L
-        flat = ((xs[None, :] + ys[:, None]) & 1).astype(np.uint8)
-        Xw, Yw = flat.copy(), flat.copy()
-        t0 = time.perf_counter()
-        oracle.dtrdt_mcs_window(Xw, Yw, prm, step, ox, oy)
-        dt = time.perf_counter() - t0
-        if step >= a.warmup:
-            times.append(dt)
-            total += nx * ny * tw * th
+    try:
+        for step in range(a.warmup + a.steps):
+            ox, oy, _ = oracle.mcs_draw(prm, step)
+            xs = (ox + np.arange(W)) % a.L
+            ys = (oy + np.arange(H)) % a.L
+            flat = ((xs[None, :] + ys[:, None]) & 1).astype(np.uint8)
+            n_att, wall, _ = cores.replay(flat, flat, prm, step, ox, oy, per_window)
+            if step >= a.warmup:
+                times.append(wall)
+                total += n_att
+    finally:
+        cores.close()
     secs = sum(times)
     value = total / (secs * 1e9)
-    sample = (f"oracle DTrDT replay of one MCS per step on a {nx}x{ny} device-tile window "
-              f"({nx * ny * tw * th} attempts per step) of the L={a.L} lattice")
+    sample = (f"oracle DTrDT replay of one MCS per step on {cores.n} host cores at once, each on its own copy "
+              f"of a {nx}x{ny} device-tile window ({per_window} attempts per core and step) of the L={a.L} lattice")
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * secs / max(1, len(times)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "config": workload(a),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores.n, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -459,6 +551,7 @@ def main():
                     cpu_ = cpu_baseline_window(oracle, a, lambda x, y, W, H: h.window(x, y, W, H), h.t,
                                                a.cpu_seconds / 4, scheme=oracle_scheme, seed=seed,
                                                name={1: "DTrDB", 3: "DTrDTr"}[oracle_scheme])
+                    cpu_.pop("_window")
             return L * L * n / (st_.elapsed_time(en_) * 1e6), step_ms, f_draw, cpu_
 
         def alu_roofline(step_ms, bits):
@@ -543,12 +636,19 @@ def main():
         serving = serving_leg(a, g, _lib, torch, stream, cap)
 
     # ---- CPU baseline: the oracle on a sample of the same state ----
+    # One core first (sizes the window to about --cpu-seconds), then every
+    # host core on its own copy of that window; O1 beside it at L=4096.
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         import oracle
         oracle.build()
-        cpu = cpu_baseline_window(oracle, a, lambda x, y, W, H: sim.window(x, y, W, H), sim.t,
-                                  a.cpu_seconds)
+
+        def getter(x, y, W, H):
+            return sim.window(x, y, W, H)
+
+        single = cpu_baseline_window(oracle, a, getter, sim.t, a.cpu_seconds)
+        cpu = cpu_baseline_all_cores(oracle, single, getter)
+        cpu["sequential_rs_L4096"] = cpu_sequential_rs(oracle)
 
     # ---- end to end through the C ABI with host buffers ----
     # Each step copies one lattice in from page-locked host memory, runs one

@@ -635,21 +635,6 @@ def main():
         cap = batched["value"] if batched else value
         serving = serving_leg(a, g, _lib, torch, stream, cap)
 
-    # ---- CPU baseline: the oracle on a sample of the same state ----
-    # One core first (sizes the window to about --cpu-seconds), then every
-    # host core on its own copy of that window; O1 beside it at L=4096.
-    cpu = None
-    if rank == 0 and world == 1 and not a.no_cpu:
-        import oracle
-        oracle.build()
-
-        def getter(x, y, W, H):
-            return sim.window(x, y, W, H)
-
-        single = cpu_baseline_window(oracle, a, getter, sim.t, a.cpu_seconds)
-        cpu = cpu_baseline_all_cores(oracle, single, getter)
-        cpu["sequential_rs_L4096"] = cpu_sequential_rs(oracle)
-
     # ---- end to end through the C ABI with host buffers ----
     # Each step copies one lattice in from page-locked host memory, runs one
     # MCS, measures W^2 and copies the lattice back out.  `--e2e-lattices`
@@ -670,17 +655,23 @@ def main():
         tk = [sim.t] * nl
         pending = [False] * nl
 
-        def e2e_step(i):
+        marks = []  # host time (ms from the timed start) after each wait and each copy in, per step
+
+        def e2e_step(i, t0=None):
             k = i % nl
             h = e2e_sims[k].h
             if pending[k]:
                 _lib.oct_w2_wait(h)
+            tw_ = time.perf_counter()
             _lib.oct_set_planes(h, hosts[k].data_ptr(), words, tk[k])
+            ts_ = time.perf_counter()
             _lib.oct_run_mcs(h, 1)
             _lib.oct_measure_w2_async(h)
             _lib.oct_get_planes_async(h, hosts[k].data_ptr(), words)
             tk[k] += 1
             pending[k] = True
+            if t0 is not None:
+                marks.append([round((tw_ - t0) * 1e3, 1), round((ts_ - t0) * 1e3, 1)])
 
         def e2e_drain():
             for k in range(nl):
@@ -694,7 +685,7 @@ def main():
         barrier()
         t0 = time.perf_counter()
         for i in range(a.e2e_steps):
-            e2e_step(i)
+            e2e_step(i, t0)
         e2e_drain()
         barrier()
         e2e_s = time.perf_counter() - t0
@@ -716,7 +707,7 @@ def main():
             ph.append(time.perf_counter() - t1)
         e2e = {"value": world * L * L * a.e2e_steps / (e2e_s * 1e9), "unit": UNIT,
                "h2d_bytes_per_step": L * L // 4, "d2h_bytes_per_step": L * L // 4 + 56,
-               "steps": a.e2e_steps, "lattices_in_flight": nl,
+               "steps": a.e2e_steps, "lattices_in_flight": nl, "host_marks_ms": marks,
                "breakdown_ms": {"h2d": ph[0] * 1e3, "mcs": ph[1] * 1e3, "measure_w2": ph[2] * 1e3,
                                 "d2h": ph[3] * 1e3},
                "h2d_gbs": (L * L // 4) / ph[0] / 1e9, "d2h_gbs": (L * L // 4) / ph[3] / 1e9,
@@ -724,6 +715,24 @@ def main():
                         "oct_run_mcs(1) + oct_measure_w2_async + oct_get_planes_async(pinned host); "
                         "oct_w2_wait before the lattice's next step and at the end"),
                "breakdown_note": "one step of one lattice, phase by phase with a synchronisation between phases"}
+
+    # ---- CPU baseline: the oracle on a sample of the same state ----
+    # (after the end-to-end leg: run right after the worker processes had
+    # exited, the first end-to-end copies from page-locked memory were up to
+    # 7x slower)
+    # One core first (sizes the window to about --cpu-seconds), then every
+    # host core on its own copy of that window; O1 beside it at L=4096.
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        import oracle
+        oracle.build()
+
+        def getter(x, y, W, H):
+            return sim.window(x, y, W, H)
+
+        single = cpu_baseline_window(oracle, a, getter, sim.t, a.cpu_seconds)
+        cpu = cpu_baseline_all_cores(oracle, single, getter)
+        cpu["sequential_rs_L4096"] = cpu_sequential_rs(oracle)
 
     if rank == 0:
         out = {

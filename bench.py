@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--Bx", type=int, default=256)
     ap.add_argument("--By", type=int, default=64)
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=24)
     ap.add_argument("--e2e-lattices", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-cores", type=int, default=0, help="host cores for --impl reference (0: all)")

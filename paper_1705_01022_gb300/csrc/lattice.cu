@@ -27,9 +27,10 @@ __global__ void init_flat_kernel(uint32_t *lat, uint32_t L, uint64_t n_words, ui
     }
 }
 
-// Byte table: for byte value v, with running step e_i = sum_{j<=i} (2 b_j - 1):
-//   .x = (sum e_i) + 64 | (net = e_7) + 64 << 8     (net in [-8, 8])
-//   .y = sum e_i^2 | (min e_i + 16) << 16 | (max e_i + 16) << 24
+// Byte table: for byte value v, with running step e_i = sum_{j<=i} (2 b_j - 1),
+// i = 0..7 (every field a signed byte, sign-extended on use):
+//   .x = sum e_i | net e_7 << 8 | min e_i << 16 | max e_i << 24
+//   .y = sum e_i^2 (at most 204)
 __device__ __forceinline__ uint2 byte_entry(uint32_t v) {
     int e = 0, s1 = 0, s2 = 0, mn = 1 << 20, mx = -(1 << 20);
     for (int i = 0; i < 8; ++i) {
@@ -40,13 +41,32 @@ __device__ __forceinline__ uint2 byte_entry(uint32_t v) {
         mx = max(mx, e);
     }
     uint2 r;
-    r.x = static_cast<uint32_t>(s1 + 64) | (static_cast<uint32_t>(e + 64) << 8);
-    r.y = static_cast<uint32_t>(s2) | (static_cast<uint32_t>(mn + 16) << 16) |
-          (static_cast<uint32_t>(mx + 16) << 24);
+    r.x = (static_cast<uint32_t>(s1) & 0xFFu) | ((static_cast<uint32_t>(e) & 0xFFu) << 8) |
+          ((static_cast<uint32_t>(mn) & 0xFFu) << 16) | ((static_cast<uint32_t>(mx) & 0xFFu) << 24);
+    r.y = static_cast<uint32_t>(s2);
     return r;
 }
 
+__device__ __forceinline__ int sbyte(uint32_t x, int k) {
+    return static_cast<int>(static_cast<signed char>(static_cast<unsigned char>(x >> (8 * k))));
+}
+
 constexpr int kW2Warps = 8;
+
+// The 4 words w..w+3 of a row (one 16-byte load where the row allows it);
+// words past the row's end read as 0 and are not counted.
+__device__ __forceinline__ uint4 load_chunk(const uint32_t *row, uint32_t w, uint32_t wpr, bool vec_ok) {
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (vec_ok && w + 3u < wpr) {
+        v = *reinterpret_cast<const uint4 *>(row + w);
+    } else if (w < wpr) {
+        v.x = row[w];
+        if (w + 1u < wpr) v.y = row[w + 1];
+        if (w + 2u < wpr) v.z = row[w + 2];
+        if (w + 3u < wpr) v.w = row[w + 3];
+    }
+    return v;
+}
 
 __global__ void __launch_bounds__(kW2Warps * 32)
     w2_rows_kernel(const uint32_t *lat, uint32_t L, W2RowSums *rows) {
@@ -63,21 +83,14 @@ __global__ void __launch_bounds__(kW2Warps * 32)
         long long base = 0;  // q just before the current chunk
         long long q1 = 0, q2 = 0;
         int qmin = 1 << 30, qmax = -(1 << 30);
-        // Chunks of 128 words: lane i takes words 4i..4i+3 (one 16-byte load).
+        // Chunks of 128 words: lane i takes words 4i..4i+3; the next chunk's
+        // load is issued before the current one is reduced.
+        uint4 v = load_chunk(row, 4u * lane, wpr, vec_ok);
         for (uint32_t w0 = 0; w0 < wpr; w0 += 128u) {
             const uint32_t w = w0 + 4u * lane;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            int nbits = 0;
-            if (vec_ok && w + 3u < wpr) {
-                v = *reinterpret_cast<const uint4 *>(row + w);
-                nbits = 128;
-            } else if (w < wpr) {
-                v.x = row[w];
-                nbits = 32;
-                if (w + 1u < wpr) { v.y = row[w + 1]; nbits = 64; }
-                if (w + 2u < wpr) { v.z = row[w + 2]; nbits = 96; }
-                if (w + 3u < wpr) { v.w = row[w + 3]; nbits = 128; }
-            }
+            const uint4 vn = load_chunk(row, w + 128u, wpr, vec_ok);
+            const int nw = (w < wpr) ? static_cast<int>(min(4u, wpr - w)) : 0;
+            const int nbits = 32 * nw;
             const int step = 2 * (__popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w)) - nbits;
             int incl = step;
 #pragma unroll
@@ -85,27 +98,34 @@ __global__ void __launch_bounds__(kW2Warps * 32)
                 const int n = __shfl_up_sync(kFull, incl, o);
                 if (lane >= o) incl += n;
             }
-            long long b = base + (incl - step);  // q before this lane's first bit
+            // Lane-local running sum a (0 at the lane's first bit) in 32 bits:
+            // |a| <= 128, sum a <= 2^14, sum a^2 <= 2^21.
+            int a = 0, l1 = 0, l2 = 0, lmn = 1 << 30, lmx = -(1 << 30);
             const uint32_t words[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                if (32 * j >= nbits) break;
+                if (j >= nw) break;
 #pragma unroll
                 for (int byte = 0; byte < 4; ++byte) {
                     const uint2 te = table[(words[j] >> (8 * byte)) & 0xFFu];
-                    const long long t1 = static_cast<long long>(te.x & 0xFFu) - 64;
-                    const int net = static_cast<int>((te.x >> 8) & 0xFFu) - 64;
-                    const long long t2 = te.y & 0xFFFFu;
-                    const int mn = static_cast<int>((te.y >> 16) & 0xFFu) - 16;
-                    const int mx = static_cast<int>(te.y >> 24) - 16;
-                    q1 += 8 * b + t1;
-                    q2 += 8 * b * b + 2 * b * t1 + t2;
-                    qmin = min(qmin, static_cast<int>(b) + mn);
-                    qmax = max(qmax, static_cast<int>(b) + mx);
-                    b += net;
+                    const int t1 = sbyte(te.x, 0), net = sbyte(te.x, 1);
+                    l1 += 8 * a + t1;
+                    l2 += a * (8 * a + 2 * t1) + static_cast<int>(te.y);
+                    lmn = min(lmn, a + sbyte(te.x, 2));
+                    lmx = max(lmx, a + sbyte(te.x, 3));
+                    a += net;
                 }
             }
+            // lift to the row: q = B + a with B = q before this lane's first bit
+            const long long B = base + (incl - step);
+            q1 += static_cast<long long>(nbits) * B + l1;
+            q2 += static_cast<long long>(nbits) * B * B + 2 * B * l1 + l2;
+            if (nw > 0) {
+                qmin = min(qmin, static_cast<int>(B) + lmn);
+                qmax = max(qmax, static_cast<int>(B) + lmx);
+            }
             base += __shfl_sync(kFull, incl, 31);
+            v = vn;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

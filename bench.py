@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--Bx", type=int, default=256)
     ap.add_argument("--By", type=int, default=64)
-    ap.add_argument("--e2e-steps", type=int, default=24)
+    ap.add_argument("--e2e-steps", type=int, default=48)
     ap.add_argument("--e2e-lattices", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-cores", type=int, default=0, help="host cores for --impl reference (0: all)")
@@ -645,7 +645,9 @@ def main():
     e2e = None
     if not a.no_e2e and a.e2e_steps > 0:
         words = L * L // 16
-        nl = max(1, a.e2e_lattices)
+        # page-locked host memory: at most a quarter of the host's RAM over all ranks
+        ram = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+        nl = max(1, min(a.e2e_lattices, int(0.25 * ram) // (world * 4 * words)))
         e2e_sims = [sim] + [g.Simulation(L, a.p, a.q, seed + 1000 * k, Bx=a.Bx, By=a.By)
                             for k in range(1, nl)]
         hosts = [torch.empty(words * 4, dtype=torch.uint8, pin_memory=True) for _ in range(nl)]

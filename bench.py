@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=32)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-policy", default="large", help="autotune.batch_shape policy of the serving leg")
     ap.add_argument("--db-steps", type=int, default=30)
     ap.add_argument("--ac-reps", type=int, default=5)
     ap.add_argument("--tune-mcs", type=int, default=1)
@@ -357,11 +358,12 @@ def serving_leg(a, g, _lib, torch, stream, capacity):
     out = {"workload": ("Poisson job stream: L log-uniform in [128, 16384] (multiples of 128), t_max "
                         "log-uniform in [10, 10^4] MCS, (p,q) uniform over (1,0), (0.8,0.2), (0.5,0.5), "
                         "W^2 streamed at 8 log-spaced times per job, HBM budget 64 GiB"),
+           "shape_policy": a.serve_policy,
            "capacity_attempts_per_ns": capacity, "expected_attempts_per_job": work, "loads": []}
     for rho in (0.5, 0.8, 1.0):
         rate = rho * capacity * 1e9 / work
         jobs = serve.poisson_jobs(a.serve_jobs, rate, master_seed=1, seed_fn=_lib.oct_replica_seed)
-        eng = serve.ServingEngine(64 << 30, stream=stream, max_chunk=64)
+        eng = serve.ServingEngine(64 << 30, stream=stream, max_chunk=64, shape_policy=a.serve_policy)
         t0 = time.perf_counter()
         done = eng.run(jobs)
         torch.cuda.synchronize()

@@ -164,7 +164,8 @@ def tuned_simulation(L: int, p: float, q: float, seed: int, cache: TuneCache | N
 
 # ---------------------------------------------------------------------------
 # batched replicas
-BATCH_POLICIES = ("default", "wide", "square")
+BATCH_POLICIES = ("default", "wide", "square", "large")
+LARGE_MIN_SUBTILES = 1024  # sub-tiles per device step for which 'large' keeps the wide shape
 
 
 def groups(shape: tuple[int, int]) -> int:
@@ -175,9 +176,16 @@ def batch_shape(L: int, policy: str) -> tuple[int, int]:
     """Sub-tile of a replica of size L under a policy: 'default' is the batch
     library's own default (64 x 64 if L % 128 == 0, else 32 x 32); 'wide' and
     'square' take the most groups a valid shape allows, then the widest or the
-    most nearly square one."""
+    most nearly square one; 'large' takes the wide shape where it still leaves
+    at least LARGE_MIN_SUBTILES sub-tiles per device step (large lattices get
+    full-warp sub-tiles, as in the plain kernel), else the default."""
     if policy == "default":
         return (64, 64) if L % 128 == 0 else (32, 32)
+    if policy == "large":
+        Bx, By = batch_shape(L, "wide")
+        if (L // (2 * Bx)) * (L // (2 * By)) >= LARGE_MIN_SUBTILES:
+            return (Bx, By)
+        return batch_shape(L, "default")
     shapes = candidates(L)
     if not shapes:
         raise ValueError(f"no sub-tile shape fits L={L}")

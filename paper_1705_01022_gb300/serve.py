@@ -113,7 +113,7 @@ class ServingEngine:
     by default it is the GPU batch of this package."""
 
     def __init__(self, hbm_budget: int, batch=None, stream=None, max_chunk: int = 64,
-                 on_result=None, clock=time.perf_counter, shape_policy: str = "default"):
+                 on_result=None, clock=time.perf_counter, shape_policy: str = "large"):
         self.budget = int(hbm_budget)
         self.shape_policy = shape_policy  # autotune.batch_shape policy for each job's sub-tile
         self.used = 0

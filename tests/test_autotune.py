@@ -87,6 +87,14 @@ def test_batch_policies_give_valid_shapes():
     assert at.batch_shape(4096, "wide") == (1024, 16)
     assert at.batch_shape(4096, "square") == (128, 128)
     assert at.batch_shape(192, "wide") == (32, 32)
+    # 'large': full-warp sub-tiles only where they leave enough of them per device step
+    assert at.batch_shape(4096, "large") == (64, 64)
+    assert at.batch_shape(6144, "large") == (64, 64)
+    assert at.batch_shape(8192, "large") == (1024, 16)
+    assert at.batch_shape(16384, "large") == (1024, 16)
+    for L in range(128, 16385, 128):
+        Bx, By = at.batch_shape(L, "large")
+        assert (Bx, By) in at.candidates(L) or (Bx, By) == at.batch_shape(L, "default")
 
 
 def test_tune_batch_with_a_fake_timer(tmp_path):

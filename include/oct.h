@@ -48,7 +48,7 @@ extern "C" {
 #define OCT_ECUDA 3        /* a CUDA runtime call failed                           */
 #define OCT_ETIMEDOUT 4    /* a bounded device wait gave up                        */
 #define OCT_EINTERNAL 5    /* an internal consistency check failed                 */
-#define OCT_EUNSUPPORTED 6 /* valid request this build does not implement          */
+#define OCT_EUNSUPPORTED 6 /* valid request the library does not implement       */
 
 typedef struct oct_sim oct_sim; /* opaque; owns its device memory unless told otherwise */
 
@@ -60,8 +60,8 @@ typedef struct oct_sim oct_sim; /* opaque; owns its device memory unless told ot
  *          a multiple of 32 and By a multiple of 4*cy; a sub-tile may hold at
  *          most 32 groups of 32 x 4cy sites.  Defaults: 64 x 64 if L % 128 == 0,
  *          else 32 x 16.
- *   cx, cy block-layer thread cell in sites (default 4 x 4; this build
- *          supports 4 x 4).
+ *   cx, cy block-layer thread cell in sites (default 4 x 4, the one cell
+ *          shape the library implements; others give OCT_EUNSUPPORTED).
  *   stream cudaStream_t to enqueue on, or NULL for a library-owned stream
  *          (pass cudaStreamLegacy, 0x1, for the legacy default stream).
  *   lattice  external device buffer of L*L/4 bytes (planar layout), or NULL

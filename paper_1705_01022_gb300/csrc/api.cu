@@ -100,7 +100,7 @@ int validate(const oct_params *prm, int *Bx, int *By, int *cx, int *cy) {
         return fail(OCT_EINVAL, "p and q must lie in [0, 1]");
     *cx = prm->cx ? prm->cx : 4;
     *cy = prm->cy ? prm->cy : 4;
-    if (*cx != 4 || *cy != 4) return fail(OCT_EUNSUPPORTED, "this build supports 4x4-site thread cells");
+    if (*cx != 4 || *cy != 4) return fail(OCT_EUNSUPPORTED, "the library implements 4x4-site thread cells only");
     if (prm->Bx || prm->By) {
         *Bx = prm->Bx;
         *By = prm->By;

@@ -16,9 +16,14 @@ of the estimate as (t_i - t_j)/2, which for a midpoint must be read as
 (t_i + t_j)/2; each estimate also carries the geometric midpoint
 sqrt(t_i t_j), the natural one on a log axis.
 
+An ensemble (`ensemble_run`, `--seeds N`) advances N independent DTrDT
+realizations together as one batch and reports the mean W^2 with its
+standard error; the effective exponents of the mean carry jackknife errors
+over the realizations.
+
 Command line:
     python -m paper_1705_01022_gb300.run --L 131072 --p 0.95 --q 0.05 \
-        --t-max 10000 --points 40 [--wait 100] [--scheme dt|db|dtr] [--out f.jsonl]
+        --t-max 10000 --points 40 [--wait 100] [--scheme dt|db|dtr] [--seeds N] [--out f.jsonl]
 prints one JSON line per measurement, then one summary line.
 """
 from __future__ import annotations
@@ -97,6 +102,67 @@ def production_run(L: int, p: float, q: float, seed: int, t_max: int, points: in
             "attempts_per_ns": L * L * t_max / (wall * 1e9)}
 
 
+def jackknife(values, estimator):
+    """Jackknife means and standard errors of a vector-valued estimator(samples)
+    over the leave-one-out subsets of the sample list (n >= 2); a scalar
+    estimator gives one-element lists."""
+    n = len(values)
+    if n < 2:
+        raise ValueError("the jackknife needs at least two samples")
+    est = [estimator(values[:i] + values[i + 1:]) for i in range(n)]
+    est = [list(e) if isinstance(e, (list, tuple)) else [e] for e in est]
+    means = [sum(col) / n for col in zip(*est)]
+    errs = [math.sqrt((n - 1) / n * sum((x - m) ** 2 for x in col)) for col, m in zip(zip(*est), means)]
+    return means, errs
+
+
+def ensemble_run(L: int, p: float, q: float, seeds, t_max: int, points: int, Bx: int = 0, By: int = 0,
+                 stream=None, callback=None) -> dict:
+    """Independent realizations (one per seed, DTrDT) advanced together as one
+    batch; returns {records, beta_eff, wall_s, attempts_per_ns}.
+
+    records: per measurement time, t, the mean W^2 over the realizations, its
+    standard error and every realization's W^2. beta_eff: Eq. (8) on
+    W = sqrt(mean W^2) for consecutive times, with a jackknife error over the
+    realizations."""
+    from . import Batch
+    seeds = [int(x) for x in seeds]
+    if len(seeds) < 2:
+        raise ValueError("an ensemble needs at least two seeds")
+    ts = measurement_times(t_max, points)
+    shape = (Bx, By) if Bx and By else ()
+    records = []
+    t0 = time.perf_counter()
+    with Batch([(L, p, q, sd) + shape for sd in seeds], stream=stream) as b:
+        t = 0
+        for tt in ts:
+            b.run(tt - t)
+            t = tt
+            ms = b.measure()
+            w = [m.w2 for m in ms]
+            mean = sum(w) / len(w)
+            se = math.sqrt(sum((x - mean) ** 2 for x in w) / (len(w) - 1) / len(w))
+            rec = {"t": t, "w2_mean": mean, "w2_se": se, "w2": w}
+            records.append(rec)
+            if callback:
+                callback(rec)
+        b.sync()
+    wall = time.perf_counter() - t0
+    times = [r["t"] for r in records]
+    per_seed = [[r["w2"][i] for r in records] for i in range(len(seeds))]
+
+    def beta_of(samples):
+        mean = [sum(col) / len(col) for col in zip(*samples)]
+        return [e["exponent"] for e in effective_exponents(times, mean, power=0.5)]
+
+    central = effective_exponents(times, [r["w2_mean"] for r in records], power=0.5)
+    _, errs = jackknife(per_seed, beta_of)
+    for e, err in zip(central, errs):
+        e["error"] = err
+    return {"records": records, "beta_eff": central, "wall_s": wall,
+            "attempts_per_ns": len(seeds) * L * L * t_max / (wall * 1e9)}
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--L", type=int, default=4096)
@@ -110,6 +176,9 @@ def main(argv=None) -> int:
     ap.add_argument("--Bx", type=int, default=0)
     ap.add_argument("--By", type=int, default=0)
     ap.add_argument("--out", default=None, help="also write the JSON lines to this file")
+    ap.add_argument("--seeds", type=int, default=1,
+                    help="realizations; with 2 or more, an ensemble (DTrDT, one batch) whose replica seeds derive "
+                         "from --seed, and --wait is ignored")
     a = ap.parse_args(argv)
     fp = open(a.out, "w") if a.out else None
 
@@ -120,9 +189,15 @@ def main(argv=None) -> int:
             fp.write(line + "\n")
             fp.flush()
 
-    res = production_run(a.L, a.p, a.q, a.seed, a.t_max, a.points, a.wait, a.scheme, a.Bx, a.By,
-                         callback=emit)
-    emit({"summary": {"L": a.L, "p": a.p, "q": a.q, "seed": a.seed, "t_max": a.t_max, "scheme": a.scheme,
+    if a.seeds >= 2:
+        from . import _lib
+        seeds = [_lib.oct_replica_seed(a.seed, r) for r in range(a.seeds)]
+        res = ensemble_run(a.L, a.p, a.q, seeds, a.t_max, a.points, a.Bx, a.By, callback=emit)
+    else:
+        res = production_run(a.L, a.p, a.q, a.seed, a.t_max, a.points, a.wait, a.scheme, a.Bx, a.By,
+                             callback=emit)
+    emit({"summary": {"L": a.L, "p": a.p, "q": a.q, "seed": a.seed, "seeds": a.seeds, "t_max": a.t_max,
+                      "scheme": a.scheme,
                       "wall_s": round(res["wall_s"], 3), "attempts_per_ns": round(res["attempts_per_ns"], 1),
                       "beta_eff": [{k: round(v, 5) for k, v in b.items()} for b in res["beta_eff"]]}})
     if fp:

@@ -40,3 +40,20 @@ def test_production_run_matches_oracle(g, oracle, scheme, L, Bx, By, p, q):
             a = oracle.two_time(X, Y, *snap)
             assert (r["s"], r["c_h"], r["c_s"]) == (5, a["c_h"], a["c_s"]), t
     assert [r["t"] for r in res["records"]][-1] == 24
+
+
+@pytest.mark.parametrize("L,p,q,Bx,By", [(256, 1.0, 0.0, 64, 64), (320, 0.5, 0.5, 32, 32)])
+def test_ensemble_run_matches_plain_runs(g, L, p, q, Bx, By):
+    """Every realization of the batched ensemble has the W^2 of the same seed
+    run alone, at every measurement time."""
+    from paper_1705_01022_gb300 import run as prun
+    seeds = [g._lib.oct_replica_seed(7, r) for r in range(5)]
+    res = prun.ensemble_run(L, p, q, seeds, t_max=30, points=8, Bx=Bx, By=By)
+    for i, sd in enumerate(seeds):
+        with g.Simulation(L, p, q, sd, Bx=Bx, By=By) as sim:
+            t = 0
+            for r in res["records"]:
+                sim.run(r["t"] - t)
+                t = r["t"]
+                assert r["w2"][i] == sim.measure().w2, (i, t)
+    assert all(b["error"] > 0 for b in res["beta_eff"])

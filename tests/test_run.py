@@ -9,6 +9,10 @@ effective exponents of Eq. (8)), on CPU.
 * production_run's bookkeeping (when it snapshots, which records carry C)
   with the simulation replaced by an oracle-backed stand-in: every record
   equals the oracle's own W^2 and two-time values at that time.
+* Ensembles: the jackknife error of a sample mean is the classical standard
+  error (an identity); ensemble_run's per-realization W^2 equal the oracle's,
+  the mean and its error follow, and the exponent errors shrink with more
+  realizations.
 """
 import math
 
@@ -126,3 +130,67 @@ def test_production_run_bookkeeping(oracle, monkeypatch, scheme):
             assert "c_h" not in r
     assert recs[0]["w2"] == 0.25  # flat start
     assert len(res["beta_eff"]) == len(recs) - 2
+
+
+def test_jackknife_of_the_mean_is_the_standard_error():
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=13).tolist()
+    (m,), (e,) = prun.jackknife(x, lambda v: sum(v) / len(v))
+    assert m == pytest.approx(np.mean(x), rel=1e-12)
+    assert e == pytest.approx(np.std(x, ddof=1) / np.sqrt(len(x)), rel=1e-10)
+    with pytest.raises(ValueError):
+        prun.jackknife([1.0], lambda v: v[0])
+
+
+class _OracleBatch:
+    """Stand-in for the GPU Batch: one oracle replay per replica."""
+
+    def __init__(self, oracle, replicas, stream=None):
+        from oracle import Params
+        self.o = oracle
+        self.reps = []
+        for L, p, q, seed, Bx, By in replicas:
+            X, Y = oracle.flat(L)
+            self.reps.append([Params(L=L, p=p, q=q, seed=seed, Bx=Bx, By=By), X, Y])
+        self.t = 0
+
+    def run(self, n):
+        for prm, X, Y in self.reps:
+            self.o.dtrdt_run(X, Y, prm, self.t, n)
+        self.t += n
+
+    def measure(self):
+        return [type("W", (), dict(w2=self.o.w2(X, Y))) for _, X, Y in self.reps]
+
+    def sync(self):
+        pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        pass
+
+
+def test_ensemble_run_bookkeeping(oracle, monkeypatch):
+    import paper_1705_01022_gb300 as pkg
+    from oracle import Params
+    monkeypatch.setattr(pkg, "Batch", lambda reps, stream=None: _OracleBatch(oracle, reps))
+    L, p, q, seeds = 64, 1.0, 0.0, [11, 12, 13, 14]
+    res = prun.ensemble_run(L, p, q, seeds, t_max=10, points=4, Bx=32, By=32)
+    recs = res["records"]
+    assert [r["t"] for r in recs] == prun.measurement_times(10, 4)
+    for i, sd in enumerate(seeds):
+        X, Y = oracle.flat(L)
+        t = 0
+        for r in recs:
+            oracle.dtrdt_run(X, Y, Params(L=L, p=p, q=q, seed=sd, Bx=32, By=32), t, r["t"] - t)
+            t = r["t"]
+            assert r["w2"][i] == oracle.w2(X, Y)
+    for r in recs:
+        assert r["w2_mean"] == pytest.approx(np.mean(r["w2"]), rel=1e-14)
+        assert r["w2_se"] == pytest.approx(np.std(r["w2"], ddof=1) / 2, rel=1e-12)
+    assert recs[0]["w2_se"] == 0.0  # every realization starts flat
+    assert all(b["error"] > 0 for b in res["beta_eff"])
+    with pytest.raises(ValueError):
+        prun.ensemble_run(L, p, q, [1], t_max=10, points=4)

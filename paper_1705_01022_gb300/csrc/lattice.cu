@@ -68,12 +68,23 @@ __device__ __forceinline__ uint4 load_chunk(const uint32_t *row, uint32_t w, uin
     return v;
 }
 
+// Copies of the byte table: lane l reads copy l % 16, entry e of copy c at
+// uint2 index 16 e + c, i.e. banks 2c and 2c + 1.  The 16 lanes of a
+// half-warp (one 8-byte shared-memory transaction) then never share a bank,
+// whatever bytes they look up.
+constexpr int kW2TableCopies = 16;
+
 __global__ void __launch_bounds__(kW2Warps * 32)
     w2_rows_kernel(const uint32_t *lat, uint32_t L, W2RowSums *rows) {
-    __shared__ uint2 table[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) table[i] = byte_entry(static_cast<uint32_t>(i));
+    __shared__ uint2 table[256 * kW2TableCopies];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const uint2 e = byte_entry(static_cast<uint32_t>(i));
+#pragma unroll
+        for (int c = 0; c < kW2TableCopies; ++c) table[i * kW2TableCopies + c] = e;
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const uint2 *const my_table = table + (lane % kW2TableCopies);
     const uint32_t wpr = L >> 5;
     const uint32_t *Yp = lat + static_cast<size_t>(L) * wpr;
     // 16-byte loads need every row to start on a 16-byte boundary
@@ -107,7 +118,7 @@ __global__ void __launch_bounds__(kW2Warps * 32)
                 if (j >= nw) break;
 #pragma unroll
                 for (int byte = 0; byte < 4; ++byte) {
-                    const uint2 te = table[(words[j] >> (8 * byte)) & 0xFFu];
+                    const uint2 te = my_table[((words[j] >> (8 * byte)) & 0xFFu) * kW2TableCopies];
                     const int t1 = sbyte(te.x, 0), net = sbyte(te.x, 1);
                     l1 += 8 * a + t1;
                     l2 += a * (8 * a + 2 * t1) + static_cast<int>(te.y);
@@ -305,8 +316,17 @@ cudaError_t launch_init_flat(uint32_t *lat, uint32_t L, cudaStream_t st) {
 
 cudaError_t launch_w2(const uint32_t *lat, uint32_t L, W2RowSums *rows, W2Result *out,
                       cudaStream_t st) {
+    // one wave of resident blocks (32 KB of table each), rows taken grid-stride
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
     const uint64_t want = (static_cast<uint64_t>(L) + kW2Warps - 1) / kW2Warps;
-    const int blocks = static_cast<int>(want < 152ull * 16 ? want : 152ull * 16);
+    const uint64_t wave = static_cast<uint64_t>(sms) * 6u;
+    const int blocks = static_cast<int>(want < wave ? want : wave);
     w2_rows_kernel<<<blocks, kW2Warps * 32, 0, st>>>(lat, L, rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

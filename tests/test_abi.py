@@ -54,3 +54,23 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert e.value.code == _lib.OCT_EINVAL
     assert _lib.oct_destroy(None) is None
     assert _lib.oct_strerror(0) == "success"
+
+
+def test_null_handles_rejected_without_gpu(lib):
+    """Entry points that take a handle reject NULL with OCT_EINVAL before any CUDA call."""
+    from paper_1705_01022_gb300 import _lib
+    _lib.load()
+    calls = [
+        lambda: _lib.oct_run_mcs(None, 1),
+        lambda: _lib.oct_measure_w2(None),
+        lambda: _lib.oct_measure_w2_async(None),
+        lambda: _lib.oct_w2_wait(None),
+        lambda: _lib.oct_get_planes_async(None, 0, 16),
+        lambda: _lib.oct_measure_ac(None),
+        lambda: _lib.oct_snapshot(None),
+        lambda: _lib.oct_get_stats(None),
+    ]
+    for call in calls:
+        with pytest.raises(_lib.OctError) as e:
+            call()
+        assert e.value.code == _lib.OCT_EINVAL

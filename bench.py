@@ -586,6 +586,40 @@ def main():
         sim = g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice)
         sim.run(a.warmup + a.steps)
 
+    # ---- exact roughness W^2 (Eq. (3)) on the live state ----
+    w2_leg = None
+    if rank == 0 and a.ac_reps > 0:
+        m = sim.measure()
+        st_, en_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st_.record(stream)
+        for _ in range(a.ac_reps):
+            m = sim.measure()
+        en_.record(stream)
+        torch.cuda.synchronize()
+        w2_ms = st_.elapsed_time(en_) / a.ac_reps
+        w2_bytes = L * L // 8 + 4 * L  # the X plane and one Y word per row, read once
+        w2_gbs = w2_bytes / (w2_ms * 1e-3) / 1e9
+        w2_cpu = None
+        if not a.no_cpu and world == 1:
+            import oracle
+            oracle.build()
+            Lc = 2048
+            Xc, Yc = oracle.flat(Lc)
+            oracle.dtrdt_run(Xc, Yc, oracle.Params(L=Lc, p=a.p, q=a.q, seed=seed, Bx=256, By=64), 0, 2)
+            reps_c, t0c = 0, time.perf_counter()
+            while reps_c < 3 or time.perf_counter() - t0c < 1.0:
+                oracle.w2_sums(Xc, Yc)
+                reps_c += 1
+            sec_c = (time.perf_counter() - t0c) / reps_c
+            w2_cpu = {"value": Lc * Lc / (sec_c * 1e9), "unit": "sites/ns", "cores": 1, "kind": "oracle",
+                      "sample": f"oracle O3 (exact S1, S2) on an L={Lc} lattice after 2 MCS, {reps_c} calls"}
+        w2_leg = {"t": m.t, "w2": m.w2, "ms_per_call": w2_ms, "sites_per_ns": L * L / (w2_ms * 1e6),
+                  "calls": a.ac_reps, "cpu_baseline": w2_cpu,
+                  "roofline": {"bound": "hbm", "achieved": w2_gbs, "peak": hbm_peak, "unit": "GB/s",
+                               "frac": w2_gbs / hbm_peak, "algorithmic_bytes": w2_bytes},
+                  "note": "per oct_measure_w2 call: flip-counter sum, row pass, final pass, read-back and "
+                          "synchronisation"}
+
     # ---- two-time autocorrelations C_h, C_s (Sec. 2) on the live state ----
     two_time = None
     if rank == 0 and a.ac_reps > 0:
@@ -744,7 +778,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload(a), "clocks": clk.summary(), "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "autotune": tuning, "dtrdb": dtrdb, "dtrdtr": dtrdtr, "two_time": two_time, "batched": batched, "serving": serving,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "autotune": tuning, "dtrdb": dtrdb, "dtrdtr": dtrdtr, "w2": w2_leg, "two_time": two_time, "batched": batched, "serving": serving,
             "probe": {"lop3_per_clk_per_sm": lop3, "imad_per_clk_per_sm": imad, "probe_mhz": probe_mhz},
         }
         print(json.dumps(out), flush=True)

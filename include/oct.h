@@ -346,6 +346,16 @@ int oct_batch_measure_slot(oct_batch *b, int64_t slot, oct_w2 *out);
 /* Planar lattice of the replica in `slot` (words = L*L/16).  Synchronises. */
 int oct_batch_get_planes(oct_batch *b, int64_t slot, uint32_t *host, size_t words);
 
+/* Two-time autocorrelations of one replica (Sec. 2, Eq. (5); the same sums and
+ * readings as oct_snapshot / oct_measure_ac).  oct_batch_snapshot stores the
+ * replica's current lattice as its state at the waiting time s (its own MCS
+ * count), in a buffer from the batch's memory pool that lives until the
+ * replica is removed; a later call replaces it.  oct_batch_measure_ac reduces
+ * the replica's current lattice against that snapshot; OCT_EINVAL without a
+ * snapshot or for a free slot.  Both synchronise the batch's stream. */
+int oct_batch_snapshot(oct_batch *b, int64_t slot);
+int oct_batch_measure_ac(oct_batch *b, int64_t slot, oct_ac *out);
+
 /* MCS run by oct_batch_run so far, replicas present, their total sites, and
  * their acceptance draws. */
 int oct_batch_get_stats(oct_batch *b, int64_t *ticks, int64_t *n_active, int64_t *active_sites,

@@ -136,6 +136,14 @@ class Batch:
     def measure(self):
         return _lib.oct_batch_measure_w2(self.h, len(self.replicas))
 
+    def snapshot(self, r: int) -> None:
+        """Stores replica r's current lattice as its state at the waiting time s."""
+        _lib.oct_batch_snapshot(self.h, r)
+
+    def measure_ac(self, r: int) -> oct_ac:
+        """C_h(t,s), C_s(t,s) of replica r against its last snapshot."""
+        return _lib.oct_batch_measure_ac(self.h, r)
+
     def planes(self, r: int) -> np.ndarray:
         L = self.replicas[r].L
         w = np.empty(L * L // 16, dtype=np.uint32)

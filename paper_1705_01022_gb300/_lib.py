@@ -117,6 +117,8 @@ _SIGNATURES = [
     ("oct_batch_measure_slot", [_H, ctypes.c_int64, ctypes.POINTER(oct_w2)], ctypes.c_int),
     ("oct_batch_measure_w2", [_H, ctypes.POINTER(oct_w2), ctypes.c_int64], ctypes.c_int),
     ("oct_batch_get_planes", [_H, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    ("oct_batch_snapshot", [_H, ctypes.c_int64], ctypes.c_int),
+    ("oct_batch_measure_ac", [_H, ctypes.c_int64, ctypes.POINTER(oct_ac)], ctypes.c_int),
     ("oct_batch_get_stats", [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
      ctypes.c_int),
@@ -319,6 +321,16 @@ def oct_batch_measure_w2(h: int, n: int):
     out = (oct_w2 * n)()
     _check(load().oct_batch_measure_w2(h, out, n), "oct_batch_measure_w2")
     return list(out)
+
+
+def oct_batch_snapshot(h: int, slot: int) -> None:
+    _check(load().oct_batch_snapshot(h, slot), "oct_batch_snapshot")
+
+
+def oct_batch_measure_ac(h: int, slot: int) -> oct_ac:
+    out = oct_ac()
+    _check(load().oct_batch_measure_ac(h, slot, ctypes.byref(out)), "oct_batch_measure_ac")
+    return out
 
 
 def oct_batch_get_planes(h: int, r: int, buf, words: int) -> None:

@@ -42,6 +42,28 @@ constexpr int kEventPairs = 256;
 
 void oct::set_last_error(const std::string &msg) { g_last_error = msg; }
 
+// C_h and C_s from the exact sums (numerators in 128-bit integers).
+void oct::fill_ac(int64_t L, const oct::AcResult &r, oct_ac *out) {
+    const __int128 N = static_cast<__int128>(L) * L;
+    const __int128 cross =
+        static_cast<__int128>((static_cast<unsigned __int128>(r.cross_hi) << 64) | r.cross_lo);
+    const __int128 num_h = N * cross - static_cast<__int128>(r.sum_ht) * r.sum_hs;
+    const __int128 M = 2 * N;
+    const __int128 num_s = M * static_cast<__int128>(r.occ_x + r.occ_y) - static_cast<__int128>(r.m_t) * r.m_s;
+    *out = oct_ac{};
+    out->n_sites = static_cast<int64_t>(N);
+    out->sum_ht = r.sum_ht;
+    out->sum_hs = r.sum_hs;
+    out->cross_lo = r.cross_lo;
+    out->cross_hi = static_cast<int64_t>(r.cross_hi);
+    out->occ_x = r.occ_x;
+    out->occ_y = r.occ_y;
+    out->m_t = r.m_t;
+    out->m_s = r.m_s;
+    out->c_h = static_cast<double>(num_h) / (static_cast<double>(N) * static_cast<double>(N));
+    out->c_s = static_cast<double>(num_s) / (static_cast<double>(M) * static_cast<double>(M));
+}
+
 struct oct_sim {
     int64_t L = 0;
     double p = 0, q = 0;
@@ -518,31 +540,7 @@ int oct_destroy(oct_sim *s) {
     return OCT_OK;
 }
 
-namespace {
 
-// C_h and C_s from the exact sums (numerators in 128-bit integers).
-void fill_ac(int64_t L, const oct::AcResult &r, oct_ac *out) {
-    const __int128 N = static_cast<__int128>(L) * L;
-    const __int128 cross =
-        static_cast<__int128>((static_cast<unsigned __int128>(r.cross_hi) << 64) | r.cross_lo);
-    const __int128 num_h = N * cross - static_cast<__int128>(r.sum_ht) * r.sum_hs;
-    const __int128 M = 2 * N;
-    const __int128 num_s = M * static_cast<__int128>(r.occ_x + r.occ_y) - static_cast<__int128>(r.m_t) * r.m_s;
-    *out = oct_ac{};
-    out->n_sites = static_cast<int64_t>(N);
-    out->sum_ht = r.sum_ht;
-    out->sum_hs = r.sum_hs;
-    out->cross_lo = r.cross_lo;
-    out->cross_hi = static_cast<int64_t>(r.cross_hi);
-    out->occ_x = r.occ_x;
-    out->occ_y = r.occ_y;
-    out->m_t = r.m_t;
-    out->m_s = r.m_s;
-    out->c_h = static_cast<double>(num_h) / (static_cast<double>(N) * static_cast<double>(N));
-    out->c_s = static_cast<double>(num_s) / (static_cast<double>(M) * static_cast<double>(M));
-}
-
-}  // namespace
 
 int oct_snapshot(oct_sim *s) {
     if (!s) return fail(OCT_EINVAL, "NULL argument");
@@ -567,7 +565,7 @@ int oct_measure_ac(oct_sim *s, oct_ac *out) {
     oct::AcResult r{};
     OCT_CUDA(cudaMemcpyAsync(&r, s->d_ac, sizeof(r), cudaMemcpyDeviceToHost, s->stream));
     OCT_CUDA(cudaStreamSynchronize(s->stream));
-    fill_ac(s->L, r, out);
+    oct::fill_ac(s->L, r, out);
     out->t = static_cast<int64_t>(s->t);
     out->s = s->snap_t;
     return OCT_OK;
@@ -590,7 +588,7 @@ int oct_two_time_planes(const void *lat_t, const void *lat_s, int64_t L, void *s
     if (e == cudaSuccess) e = ef;
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "oct_two_time_planes");
-    fill_ac(L, r, out);
+    oct::fill_ac(L, r, out);
     out->t = -1;
     out->s = -1;
     return OCT_OK;

@@ -185,6 +185,12 @@ struct oct_batch {
     int64_t rows_cap = 0;
     oct::W2Result *d_w2 = nullptr;
     void *h_small = nullptr;
+    // two-time autocorrelations: per slot, the lattice at its waiting time
+    std::vector<uint32_t *> snap;
+    std::vector<int64_t> snap_t;
+    oct::AcRowSums *d_ac_rows = nullptr;
+    int64_t ac_rows_cap = 0;
+    oct::AcResult *d_ac = nullptr;
     uint64_t ticks = 0;  // MCS run by oct_batch_run
     int grid = 0;
     cudaGraph_t graph = nullptr;
@@ -209,7 +215,11 @@ void batch_free(oct_batch *b) {
     drop_graph(b);
     for (uint32_t *p : b->lat)
         if (p) cudaFreeAsync(p, b->stream);
+    for (uint32_t *p : b->snap)
+        if (p) cudaFreeAsync(p, b->stream);
     if (b->stream) cudaStreamSynchronize(b->stream);
+    cudaFree(b->d_ac_rows);
+    cudaFree(b->d_ac);
     cudaFree(b->d_reps);
     cudaFree(b->d_t);
     cudaFree(b->counters);
@@ -448,6 +458,8 @@ int add_replica(oct_batch *b, const oct_replica *in, int64_t *slot_out) {
         b->reps.emplace_back();
         b->lat.push_back(nullptr);
         b->used.push_back(0);
+        b->snap.push_back(nullptr);
+        b->snap_t.push_back(-1);
     }
     const size_t bytes = static_cast<size_t>(R.L) * R.L / 4;
     uint32_t *p = nullptr;
@@ -587,6 +599,11 @@ int oct_batch_remove(oct_batch *b, int64_t slot) {
     BATCH_CUDA(cudaSetDevice(b->device));
     BATCH_CUDA(cudaFreeAsync(b->lat[slot], b->stream));
     b->lat[slot] = nullptr;
+    if (b->snap[slot]) {
+        BATCH_CUDA(cudaFreeAsync(b->snap[slot], b->stream));
+        b->snap[slot] = nullptr;
+    }
+    b->snap_t[slot] = -1;
     b->used[slot] = 0;
     b->free_slots.push_back(slot);
     b->dirty = true;
@@ -658,6 +675,53 @@ int oct_batch_measure_slot(oct_batch *b, int64_t slot, oct_w2 *out) {
     if (!b || !out || !valid_slot(b, slot)) return bfail(OCT_EINVAL, "no replica in that slot");
     BATCH_CUDA(cudaSetDevice(b->device));
     return measure_slot(b, slot, out);
+}
+
+int oct_batch_snapshot(oct_batch *b, int64_t slot) {
+    if (!b || !valid_slot(b, slot)) return bfail(OCT_EINVAL, "no replica in that slot");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    const int64_t L = b->reps[slot].L;
+    const size_t bytes = static_cast<size_t>(L) * L / 4;
+    if (!b->snap[slot]) {
+        uint32_t *p = nullptr;
+        cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&p), bytes, b->pool, b->stream);
+        if (e != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? bfail(OCT_ENOMEM, "no device memory for the snapshot")
+                                                  : bfail(OCT_ECUDA, std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e));
+        b->snap[slot] = p;
+    }
+    BATCH_CUDA(cudaMemcpyAsync(b->snap[slot], b->lat[slot], bytes, cudaMemcpyDeviceToDevice, b->stream));
+    auto *tt = reinterpret_cast<uint32_t *>(static_cast<char *>(b->h_small) + 96);
+    BATCH_CUDA(cudaMemcpyAsync(tt, b->d_t + slot, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(cudaStreamSynchronize(b->stream));
+    b->snap_t[slot] = static_cast<int64_t>(*tt);
+    return OCT_OK;
+}
+
+int oct_batch_measure_ac(oct_batch *b, int64_t slot, oct_ac *out) {
+    if (!b || !out || !valid_slot(b, slot)) return bfail(OCT_EINVAL, "no replica in that slot");
+    if (!b->snap[slot]) return bfail(OCT_EINVAL, "no snapshot in that slot: call oct_batch_snapshot first");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    const int64_t L = b->reps[slot].L;
+    if (L > b->ac_rows_cap) {
+        cudaFree(b->d_ac_rows);
+        b->d_ac_rows = nullptr;
+        b->ac_rows_cap = 0;
+        BATCH_CUDA(cudaMalloc(&b->d_ac_rows, sizeof(oct::AcRowSums) * L));
+        b->ac_rows_cap = L;
+    }
+    if (!b->d_ac) BATCH_CUDA(cudaMalloc(&b->d_ac, sizeof(oct::AcResult)));
+    BATCH_CUDA(oct::launch_two_time(b->lat[slot], b->snap[slot], static_cast<uint32_t>(L), b->d_ac_rows, b->d_ac,
+                                    b->stream));
+    oct::AcResult r{};
+    BATCH_CUDA(cudaMemcpyAsync(&r, b->d_ac, sizeof(r), cudaMemcpyDeviceToHost, b->stream));
+    auto *tt = reinterpret_cast<uint32_t *>(static_cast<char *>(b->h_small) + 96);
+    BATCH_CUDA(cudaMemcpyAsync(tt, b->d_t + slot, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(cudaStreamSynchronize(b->stream));
+    oct::fill_ac(L, r, out);
+    out->t = static_cast<int64_t>(*tt);
+    out->s = b->snap_t[slot];
+    return OCT_OK;
 }
 
 int oct_batch_get_planes(oct_batch *b, int64_t slot, uint32_t *host, size_t words) {

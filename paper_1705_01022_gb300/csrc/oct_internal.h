@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <string>
 
+#include "oct.h"
+
 namespace oct {
 
 // Arguments of one device-step launch (one set of sub-tiles of one MCS).
@@ -71,6 +73,9 @@ struct AcResult {
 };
 cudaError_t launch_two_time(const uint32_t *lat_t, const uint32_t *lat_s, uint32_t L, AcRowSums *rows,
                             AcResult *out, cudaStream_t st);
+// C_h and C_s of an oct_ac from the exact sums of an L x L pair (numerators in
+// 128-bit integers); leaves out->t and out->s to the caller.
+void fill_ac(int64_t L, const AcResult &r, oct_ac *out);
 
 // Canonical 4x4-per-word layout conversion for canonical word rows
 // [cy0, cy0 + ncy) (each canonical row covers 4 lattice rows).

@@ -17,9 +17,9 @@ of the estimate as (t_i - t_j)/2, which for a midpoint must be read as
 sqrt(t_i t_j), the natural one on a log axis.
 
 An ensemble (`ensemble_run`, `--seeds N`) advances N independent DTrDT
-realizations together as one batch and reports the mean W^2 with its
-standard error; the effective exponents of the mean carry jackknife errors
-over the realizations.
+realizations together as one batch and reports the mean W^2 (and, after a
+waiting time, the mean C_h and C_s) with standard errors; the effective
+exponents of the mean carry jackknife errors over the realizations.
 
 Command line:
     python -m paper_1705_01022_gb300.run --L 131072 --p 0.95 --q 0.05 \
@@ -116,20 +116,27 @@ def jackknife(values, estimator):
     return means, errs
 
 
+def _mean_se(x):
+    m = sum(x) / len(x)
+    return m, math.sqrt(sum((v - m) ** 2 for v in x) / (len(x) - 1) / len(x))
+
+
 def ensemble_run(L: int, p: float, q: float, seeds, t_max: int, points: int, Bx: int = 0, By: int = 0,
-                 stream=None, callback=None) -> dict:
+                 stream=None, callback=None, wait: int | None = None) -> dict:
     """Independent realizations (one per seed, DTrDT) advanced together as one
     batch; returns {records, beta_eff, wall_s, attempts_per_ns}.
 
     records: per measurement time, t, the mean W^2 over the realizations, its
-    standard error and every realization's W^2. beta_eff: Eq. (8) on
-    W = sqrt(mean W^2) for consecutive times, with a jackknife error over the
-    realizations."""
+    standard error and every realization's W^2; with a waiting time s
+    (`wait`), every realization is snapshot at s and the records after it
+    add the mean C_h(t,s) and C_s(t,s) with their standard errors and every
+    realization's C_h. beta_eff: Eq. (8) on W = sqrt(mean W^2) for
+    consecutive times, with a jackknife error over the realizations."""
     from . import Batch
     seeds = [int(x) for x in seeds]
     if len(seeds) < 2:
         raise ValueError("an ensemble needs at least two seeds")
-    ts = measurement_times(t_max, points)
+    ts = measurement_times(t_max, points, () if wait is None else (wait,))
     shape = (Bx, By) if Bx and By else ()
     records = []
     t0 = time.perf_counter()
@@ -140,9 +147,18 @@ def ensemble_run(L: int, p: float, q: float, seeds, t_max: int, points: int, Bx:
             t = tt
             ms = b.measure()
             w = [m.w2 for m in ms]
-            mean = sum(w) / len(w)
-            se = math.sqrt(sum((x - mean) ** 2 for x in w) / (len(w) - 1) / len(w))
+            mean, se = _mean_se(w)
             rec = {"t": t, "w2_mean": mean, "w2_se": se, "w2": w}
+            if wait is not None and t == wait:
+                for r in range(len(seeds)):
+                    b.snapshot(r)
+            if wait is not None and t > wait:
+                acs = [b.measure_ac(r) for r in range(len(seeds))]
+                ch, cs = [a.c_h for a in acs], [a.c_s for a in acs]
+                rec["s"] = wait
+                rec["c_h_mean"], rec["c_h_se"] = _mean_se(ch)
+                rec["c_s_mean"], rec["c_s_se"] = _mean_se(cs)
+                rec["c_h"] = ch
             records.append(rec)
             if callback:
                 callback(rec)
@@ -178,7 +194,7 @@ def main(argv=None) -> int:
     ap.add_argument("--out", default=None, help="also write the JSON lines to this file")
     ap.add_argument("--seeds", type=int, default=1,
                     help="realizations; with 2 or more, an ensemble (DTrDT, one batch) whose replica seeds derive "
-                         "from --seed, and --wait is ignored")
+                         "from --seed, and the first --wait is its waiting time")
     a = ap.parse_args(argv)
     fp = open(a.out, "w") if a.out else None
 
@@ -192,7 +208,8 @@ def main(argv=None) -> int:
     if a.seeds >= 2:
         from . import _lib
         seeds = [_lib.oct_replica_seed(a.seed, r) for r in range(a.seeds)]
-        res = ensemble_run(a.L, a.p, a.q, seeds, a.t_max, a.points, a.Bx, a.By, callback=emit)
+        res = ensemble_run(a.L, a.p, a.q, seeds, a.t_max, a.points, a.Bx, a.By, callback=emit,
+                           wait=a.wait[0] if a.wait else None)
     else:
         res = production_run(a.L, a.p, a.q, a.seed, a.t_max, a.points, a.wait, a.scheme, a.Bx, a.By,
                              callback=emit)

@@ -57,3 +57,37 @@ def test_ensemble_run_matches_plain_runs(g, L, p, q, Bx, By):
                 t = r["t"]
                 assert r["w2"][i] == sim.measure().w2, (i, t)
     assert all(b["error"] > 0 for b in res["beta_eff"])
+
+
+def test_ensemble_autocorrelations_match_plain_runs(g):
+    """The batch's per-replica snapshot and C_h, C_s equal those of the same
+    seed run alone (exact doubles from equal integer sums)."""
+    from paper_1705_01022_gb300 import run as prun
+    L, p, q, Bx, By, s = 256, 0.95, 0.05, 64, 64, 4
+    seeds = [g._lib.oct_replica_seed(9, r) for r in range(4)]
+    res = prun.ensemble_run(L, p, q, seeds, t_max=20, points=6, Bx=Bx, By=By, wait=s)
+    for i, sd in enumerate(seeds):
+        with g.Simulation(L, p, q, sd, Bx=Bx, By=By) as sim:
+            t = 0
+            for r in res["records"]:
+                sim.run(r["t"] - t)
+                t = r["t"]
+                if t == s:
+                    sim.snapshot()
+                if t > s:
+                    ac = sim.measure_ac()
+                    assert r["c_h"][i] == ac.c_h, (i, t)
+
+
+def test_batch_autocorrelation_errors(g):
+    with g.Batch([(128, 1.0, 0.0, 1), (128, 0.5, 0.5, 2)]) as b:
+        b.run(2)
+        with pytest.raises(g.OctError):
+            b.measure_ac(0)  # no snapshot yet
+        b.snapshot(1)
+        b.run(1)
+        ac = b.measure_ac(1)
+        assert (ac.t, ac.s) == (3, 2)
+        assert 0.0 < ac.c_s < 0.25
+        with pytest.raises(g.OctError):
+            b.measure_ac(5)  # no such slot

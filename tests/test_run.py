@@ -162,6 +162,16 @@ class _OracleBatch:
     def measure(self):
         return [type("W", (), dict(w2=self.o.w2(X, Y))) for _, X, Y in self.reps]
 
+    def snapshot(self, r):
+        _, X, Y = self.reps[r]
+        self.snaps = getattr(self, "snaps", {})
+        self.snaps[r] = (X.copy(), Y.copy())
+
+    def measure_ac(self, r):
+        _, X, Y = self.reps[r]
+        a = self.o.two_time(X, Y, *self.snaps[r])
+        return type("A", (), dict(c_h=a["c_h"], c_s=a["c_s"]))
+
     def sync(self):
         pass
 
@@ -194,3 +204,30 @@ def test_ensemble_run_bookkeeping(oracle, monkeypatch):
     assert all(b["error"] > 0 for b in res["beta_eff"])
     with pytest.raises(ValueError):
         prun.ensemble_run(L, p, q, [1], t_max=10, points=4)
+
+
+def test_ensemble_run_with_waiting_time(oracle, monkeypatch):
+    import paper_1705_01022_gb300 as pkg
+    from oracle import Params
+    monkeypatch.setattr(pkg, "Batch", lambda reps, stream=None: _OracleBatch(oracle, reps))
+    L, p, q, seeds, s = 64, 0.95, 0.05, [21, 22, 23], 3
+    res = prun.ensemble_run(L, p, q, seeds, t_max=12, points=4, Bx=32, By=32, wait=s)
+    recs = res["records"]
+    assert s in [r["t"] for r in recs]
+    for r in recs:
+        assert ("c_h_mean" in r) == (r["t"] > s)
+    # every realization's C_h against the oracle's own replay
+    for i, sd in enumerate(seeds):
+        X, Y = oracle.flat(L)
+        t, snap = 0, None
+        for r in recs:
+            oracle.dtrdt_run(X, Y, Params(L=L, p=p, q=q, seed=sd, Bx=32, By=32), t, r["t"] - t)
+            t = r["t"]
+            if t == s:
+                snap = (X.copy(), Y.copy())
+            if t > s:
+                assert r["c_h"][i] == oracle.two_time(X, Y, *snap)["c_h"]
+    for r in recs:
+        if r["t"] > s:
+            assert r["c_h_mean"] == pytest.approx(np.mean(r["c_h"]), rel=1e-14)
+            assert r["c_h_se"] == pytest.approx(np.std(r["c_h"], ddof=1) / np.sqrt(3), rel=1e-10)

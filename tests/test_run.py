@@ -231,3 +231,22 @@ def test_ensemble_run_with_waiting_time(oracle, monkeypatch):
         if r["t"] > s:
             assert r["c_h_mean"] == pytest.approx(np.mean(r["c_h"]), rel=1e-14)
             assert r["c_h_se"] == pytest.approx(np.std(r["c_h"], ddof=1) / np.sqrt(3), rel=1e-10)
+
+
+def test_command_line(oracle, monkeypatch, tmp_path, capsys):
+    """`python -m paper_1705_01022_gb300.run`: one JSON line per measurement
+    time, then a summary; the same lines go to --out."""
+    import json
+
+    import paper_1705_01022_gb300 as pkg
+    monkeypatch.setattr(pkg, "Simulation", lambda *a, **k: _OracleSim(oracle, *a, **k))
+    out = tmp_path / "run.jsonl"
+    rc = prun.main(["--L", "64", "--p", "0.95", "--q", "0.05", "--t-max", "8", "--points", "4",
+                    "--wait", "2", "--Bx", "32", "--By", "32", "--out", str(out)])
+    assert rc == 0
+    lines = [json.loads(x) for x in capsys.readouterr().out.splitlines()]
+    assert lines == [json.loads(x) for x in out.read_text().splitlines()]
+    recs, summary = lines[:-1], lines[-1]["summary"]
+    assert [r["t"] for r in recs] == prun.measurement_times(8, 4, [2])
+    assert summary["L"] == 64 and summary["seeds"] == 1 and len(summary["beta_eff"]) == len(recs) - 2
+    assert all("c_h" in r for r in recs if r["t"] > 2)

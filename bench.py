@@ -524,6 +524,91 @@ def main():
         "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak},
     }
 
+    # ---- end to end through the C ABI with host buffers ----
+    # (right after the timed region: after the other legs, the copies from
+    # page-locked memory stalled for 0.1-0.2 s about every 0.3 s)
+    # Each step copies one lattice in from page-locked host memory, runs one
+    # MCS, measures W^2 and copies the lattice back out.  `--e2e-lattices`
+    # independent lattices (the benchmark's own and replicas with seeds
+    # seed + 1000 k, each on its own stream) take the steps in turn, driven
+    # from one host thread with the asynchronous calls, so that one lattice's
+    # copies overlap another's kernels and copies in the other direction.
+    e2e = None
+    if not a.no_e2e and a.e2e_steps > 0:
+        words = L * L // 16
+        # page-locked host memory: at most a quarter of the host's RAM over all ranks
+        ram = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+        nl = max(1, min(a.e2e_lattices, int(0.25 * ram) // (world * 4 * words)))
+        e2e_sims = [sim] + [g.Simulation(L, a.p, a.q, seed + 1000 * k, Bx=a.Bx, By=a.By)
+                            for k in range(1, nl)]
+        hosts = [torch.empty(words * 4, dtype=torch.uint8, pin_memory=True) for _ in range(nl)]
+        _lib.oct_get_planes(sim.h, hosts[0].data_ptr(), words)
+        for hb in hosts[1:]:
+            hb.copy_(hosts[0])
+        tk = [sim.t] * nl
+        pending = [False] * nl
+
+        marks = []  # host time (ms from the timed start) after each wait and each copy in, per step
+
+        def e2e_step(i, t0=None):
+            k = i % nl
+            h = e2e_sims[k].h
+            if pending[k]:
+                _lib.oct_w2_wait(h)
+            tw_ = time.perf_counter()
+            _lib.oct_set_planes(h, hosts[k].data_ptr(), words, tk[k])
+            ts_ = time.perf_counter()
+            _lib.oct_run_mcs(h, 1)
+            _lib.oct_measure_w2_async(h)
+            _lib.oct_get_planes_async(h, hosts[k].data_ptr(), words)
+            tk[k] += 1
+            pending[k] = True
+            if t0 is not None:
+                marks.append([round((tw_ - t0) * 1e3, 1), round((ts_ - t0) * 1e3, 1)])
+
+        def e2e_drain():
+            for k in range(nl):
+                if pending[k]:
+                    _lib.oct_w2_wait(e2e_sims[k].h)
+                    pending[k] = False
+
+        for i in range(nl):  # one untimed step per lattice (first use of each host buffer)
+            e2e_step(i)
+        e2e_drain()
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(a.e2e_steps):
+            e2e_step(i, t0)
+        e2e_drain()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        for extra in e2e_sims[1:]:
+            extra.close()
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        # one more step, phase by phase, for the breakdown
+        ph = []
+        hp = hosts[0].data_ptr()
+        for fn in (lambda: _lib.oct_set_planes(sim.h, hp, words, sim.t), lambda: sim.run(1),
+                   lambda: sim.measure(), lambda: _lib.oct_get_planes(sim.h, hp, words)):
+            sim.sync()
+            t1 = time.perf_counter()
+            fn()
+            sim.sync()
+            ph.append(time.perf_counter() - t1)
+        e2e = {"value": world * L * L * a.e2e_steps / (e2e_s * 1e9), "unit": UNIT,
+               "h2d_bytes_per_step": L * L // 4, "d2h_bytes_per_step": L * L // 4 + 56,
+               "steps": a.e2e_steps, "lattices_in_flight": nl, "host_marks_ms": marks,
+               "breakdown_ms": {"h2d": ph[0] * 1e3, "mcs": ph[1] * 1e3, "measure_w2": ph[2] * 1e3,
+                                "d2h": ph[3] * 1e3},
+               "h2d_gbs": (L * L // 4) / ph[0] / 1e9, "d2h_gbs": (L * L // 4) / ph[3] / 1e9,
+               "path": ("per step, lattice k = step mod lattices_in_flight: oct_set_planes(pinned host) + "
+                        "oct_run_mcs(1) + oct_measure_w2_async + oct_get_planes_async(pinned host); "
+                        "oct_w2_wait before the lattice's next step and at the end"),
+               "breakdown_note": "one step of one lattice, phase by phase with a synchronisation between phases"}
+
     # ---- the DTrDB block layer on the same workload (the paper's Fig. 7 pair) ----
     dtrdb = dtrdtr = None
     if rank == 0 and a.db_steps > 0:
@@ -568,7 +653,7 @@ def main():
         kdb_v, kdb_step, _, _ = timed(1.0, 0.0, _lib.OCT_SCHEME_DB, a.db_steps)
         dtrdb = {"value": db_v, "unit": UNIT, "mcs": a.db_steps, "device_step_ms": db_step,
                  "scheme": "DTrDB: single-hit dead border at block level, borders delayed (p, q > 0)",
-                 "start": "the DTrDT state after the timed region",
+                 "start": "the DTrDT state after the timed region and the end-to-end steps",
                  "relative_to_dtrdt": db_v / (value / world),
                  "roofline": dict(alu_roofline(db_step, 4.0 + 32.0 * db_f), draw_fraction=db_f,
                                   kernel="dtrdt_step_kernel<1, 2>"),
@@ -671,93 +756,9 @@ def main():
         cap = batched["value"] if batched else value
         serving = serving_leg(a, g, _lib, torch, stream, cap)
 
-    # ---- end to end through the C ABI with host buffers ----
-    # Each step copies one lattice in from page-locked host memory, runs one
-    # MCS, measures W^2 and copies the lattice back out.  `--e2e-lattices`
-    # independent lattices (the benchmark's own and replicas with seeds
-    # seed + 1000 k, each on its own stream) take the steps in turn, driven
-    # from one host thread with the asynchronous calls, so that one lattice's
-    # copies overlap another's kernels and copies in the other direction.
-    e2e = None
-    if not a.no_e2e and a.e2e_steps > 0:
-        words = L * L // 16
-        # page-locked host memory: at most a quarter of the host's RAM over all ranks
-        ram = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
-        nl = max(1, min(a.e2e_lattices, int(0.25 * ram) // (world * 4 * words)))
-        e2e_sims = [sim] + [g.Simulation(L, a.p, a.q, seed + 1000 * k, Bx=a.Bx, By=a.By)
-                            for k in range(1, nl)]
-        hosts = [torch.empty(words * 4, dtype=torch.uint8, pin_memory=True) for _ in range(nl)]
-        _lib.oct_get_planes(sim.h, hosts[0].data_ptr(), words)
-        for hb in hosts[1:]:
-            hb.copy_(hosts[0])
-        tk = [sim.t] * nl
-        pending = [False] * nl
-
-        marks = []  # host time (ms from the timed start) after each wait and each copy in, per step
-
-        def e2e_step(i, t0=None):
-            k = i % nl
-            h = e2e_sims[k].h
-            if pending[k]:
-                _lib.oct_w2_wait(h)
-            tw_ = time.perf_counter()
-            _lib.oct_set_planes(h, hosts[k].data_ptr(), words, tk[k])
-            ts_ = time.perf_counter()
-            _lib.oct_run_mcs(h, 1)
-            _lib.oct_measure_w2_async(h)
-            _lib.oct_get_planes_async(h, hosts[k].data_ptr(), words)
-            tk[k] += 1
-            pending[k] = True
-            if t0 is not None:
-                marks.append([round((tw_ - t0) * 1e3, 1), round((ts_ - t0) * 1e3, 1)])
-
-        def e2e_drain():
-            for k in range(nl):
-                if pending[k]:
-                    _lib.oct_w2_wait(e2e_sims[k].h)
-                    pending[k] = False
-
-        for i in range(nl):  # one untimed step per lattice (first use of each host buffer)
-            e2e_step(i)
-        e2e_drain()
-        barrier()
-        t0 = time.perf_counter()
-        for i in range(a.e2e_steps):
-            e2e_step(i, t0)
-        e2e_drain()
-        barrier()
-        e2e_s = time.perf_counter() - t0
-        for extra in e2e_sims[1:]:
-            extra.close()
-        if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        # one more step, phase by phase, for the breakdown
-        ph = []
-        hp = hosts[0].data_ptr()
-        for fn in (lambda: _lib.oct_set_planes(sim.h, hp, words, sim.t), lambda: sim.run(1),
-                   lambda: sim.measure(), lambda: _lib.oct_get_planes(sim.h, hp, words)):
-            sim.sync()
-            t1 = time.perf_counter()
-            fn()
-            sim.sync()
-            ph.append(time.perf_counter() - t1)
-        e2e = {"value": world * L * L * a.e2e_steps / (e2e_s * 1e9), "unit": UNIT,
-               "h2d_bytes_per_step": L * L // 4, "d2h_bytes_per_step": L * L // 4 + 56,
-               "steps": a.e2e_steps, "lattices_in_flight": nl, "host_marks_ms": marks,
-               "breakdown_ms": {"h2d": ph[0] * 1e3, "mcs": ph[1] * 1e3, "measure_w2": ph[2] * 1e3,
-                                "d2h": ph[3] * 1e3},
-               "h2d_gbs": (L * L // 4) / ph[0] / 1e9, "d2h_gbs": (L * L // 4) / ph[3] / 1e9,
-               "path": ("per step, lattice k = step mod lattices_in_flight: oct_set_planes(pinned host) + "
-                        "oct_run_mcs(1) + oct_measure_w2_async + oct_get_planes_async(pinned host); "
-                        "oct_w2_wait before the lattice's next step and at the end"),
-               "breakdown_note": "one step of one lattice, phase by phase with a synchronisation between phases"}
-
     # ---- CPU baseline: the oracle on a sample of the same state ----
-    # (after the end-to-end leg: run right after the worker processes had
-    # exited, the first end-to-end copies from page-locked memory were up to
-    # 7x slower)
+    # (last: run right after the worker processes had exited, the first
+    # end-to-end copies from page-locked memory were up to 7x slower)
     # One core first (sizes the window to about --cpu-seconds), then every
     # host core on its own copy of that window; O1 beside it at L=4096.
     cpu = None

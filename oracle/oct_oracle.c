@@ -15,10 +15,13 @@
  *   - DTrDT (O2): device layer = double tiling with a random origin
  *     (Sec. 3, "DT" and "DTr"; Fig. 2); block layer = single-hit double
  *     tiling, one randomly drawn domain set per collective step
- *     (Sec. 3.1, block layer paragraph).
- * Where the paper is silent the schedule specification fixes the reading
- * (random-number streams, thread-cell units, acceptance rounding); those
- * readings are restated at each use below.
+ *     (Sec. 3.1, block layer paragraph);
+ *   - the other block layers: single-hit dead border with delayed borders
+ *     (DTrDB, Sec. 3.2, Fig. 7) and double tiling whose origin moves after
+ *     every collective step (DTrDTr, Sec. 3.2, notation paragraph);
+ *   - two-time autocorrelations C_h, C_s: Sec. 2, Eq. (5).
+ * Where the paper is silent (random-number streams, thread-cell units,
+ * acceptance rounding), a reading is fixed here and restated at each use.
  *
  * Parity pins (tests/test_oracle_*.py): Philox known-answer vectors and an
  * independent Philox implementation; flat-start closed forms; lattice

@@ -257,7 +257,7 @@ static void touch(conflict_t *cf, int64_t bit, int64_t tile, int64_t tc) {
     cf->step_owner[bit] = tc;
 }
 
-/* Acceptance uniforms (reading fixed by the schedule specification).  The
+/* Acceptance uniforms (a reading: the paper names no generator).  The
  * uniform u of a thread cell's attempt is 32 bits, most significant first:
  *   - bits 31..28: "level" bits, positional per group: bit (31-l) of u is bit
  *     pos = 4j+m of word l (l = 0..3) of Philox(seed, (t, k|(s*8)<<2, T, ACC<<28|g));
@@ -392,7 +392,7 @@ static void decide_and_flip(const uint32_t key[2], uint32_t t, uint32_t k, uint3
  * conflict-free and sees the flips of the earlier ones.  The paper delays
  * borders only when both p and q are non-zero; with one of them zero two
  * neighbouring sites are never both accepted, and its DB runs carry out all
- * attempts of a step together (reading of the schedule specification: DB does
+ * attempts of a step together (a reading of Sec. 3.2: DB does
  * the same).  DB_IGNORE carries out all attempts together for any p, q; with
  * both non-zero two accepted flips can then hit the same slope bit, which the
  * flip tracker counts.
@@ -406,7 +406,7 @@ static void decide_and_flip(const uint32_t key[2], uint32_t t, uint32_t k, uint3
  * labelled by the unshifted cell holding the first site of its active
  * sub-cell; a relabelling of cells does not change the dynamics.)
  *
- * Random streams (reading fixed by the schedule specification):
+ * Random streams (a reading: the paper names no generator):
  *   block origin (DTR) for step s : byte s%4 of word (s%16)/4 of
  *                         Philox(seed, (t, k|(s/16)<<2, T, BORG<<28)); ax =
  *                         its low log2(cx) bits, ay = log2(cy) bits from bit 4.

@@ -22,7 +22,7 @@
 // Pass 2 (one block): a scan of the column-0 Y bits gives h(0,y) of both
 // lattices, and S_t, S_s and C accumulate in 64/128-bit integers:
 //   C = sum_y [L h0_t h0_s + h0_t R_s + h0_s R_t + R_ts].
-// Row terms are below 2^52 for L <= 2^17.
+// Row terms are at most L^3 in magnitude (2^60 at the largest L, 2^20).
 #include "oct_internal.h"
 
 namespace oct {

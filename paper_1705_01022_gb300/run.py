@@ -16,10 +16,12 @@ of the estimate as (t_i - t_j)/2, which for a midpoint must be read as
 (t_i + t_j)/2; each estimate also carries the geometric midpoint
 sqrt(t_i t_j), the natural one on a log axis.
 
-An ensemble (`ensemble_run`, `--seeds N`) advances N independent DTrDT
-realizations together as one batch and reports the mean W^2 (and, after a
-waiting time, the mean C_h and C_s) with standard errors; the effective
-exponents of the mean carry jackknife errors over the realizations.
+An ensemble (`ensemble_run`, `--seeds N`) advances N independent
+realizations together (DTrDT as one batch, the other block layers as one
+handle per realization, each on its own stream) and reports the mean W^2
+(and, after a waiting time, the mean C_h and C_s) with standard errors; the
+effective exponents of the mean carry jackknife errors over the
+realizations.
 
 Command line:
     python -m paper_1705_01022_gb300.run --L 131072 --p 0.95 --q 0.05 \
@@ -121,10 +123,55 @@ def _mean_se(x):
     return m, math.sqrt(sum((v - m) ** 2 for v in x) / (len(x) - 1) / len(x))
 
 
+class _Handles:
+    """Realizations of a block layer the batched kernel does not run (DTrDB,
+    DTrDTr): one simulation handle each, every handle on its own stream, so
+    that the device steps of different realizations overlap on the GPU. Same
+    interface as the parts of Batch that ensemble_run uses."""
+
+    def __init__(self, L, p, q, seeds, scheme, Bx, By):
+        from . import Simulation
+        self.sims = []
+        try:
+            for sd in seeds:
+                self.sims.append(Simulation(L, p, q, sd, Bx=Bx, By=By, scheme=SCHEMES[scheme]))
+        except Exception:
+            self.close()
+            raise
+
+    def run(self, n):
+        for sim in self.sims:  # asynchronous: every handle enqueues on its own stream
+            sim.run(n)
+
+    def measure(self):
+        return [sim.measure() for sim in self.sims]
+
+    def snapshot(self, r):
+        self.sims[r].snapshot()
+
+    def measure_ac(self, r):
+        return self.sims[r].measure_ac()
+
+    def sync(self):
+        for sim in self.sims:
+            sim.sync()
+
+    def close(self):
+        for sim in self.sims:
+            sim.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def ensemble_run(L: int, p: float, q: float, seeds, t_max: int, points: int, Bx: int = 0, By: int = 0,
-                 stream=None, callback=None, wait: int | None = None) -> dict:
-    """Independent realizations (one per seed, DTrDT) advanced together as one
-    batch; returns {records, beta_eff, wall_s, attempts_per_ns}.
+                 stream=None, callback=None, wait: int | None = None, scheme: str = "dt") -> dict:
+    """Independent realizations (one per seed) advanced together: DTrDT as one
+    batch, DTrDB and DTrDTr as one handle per realization on its own stream;
+    returns {records, beta_eff, wall_s, attempts_per_ns}.
 
     records: per measurement time, t, the mean W^2 over the realizations, its
     standard error and every realization's W^2; with a waiting time s
@@ -140,7 +187,11 @@ def ensemble_run(L: int, p: float, q: float, seeds, t_max: int, points: int, Bx:
     shape = (Bx, By) if Bx and By else ()
     records = []
     t0 = time.perf_counter()
-    with Batch([(L, p, q, sd) + shape for sd in seeds], stream=stream) as b:
+    if scheme not in SCHEMES:
+        raise ValueError(f"unknown scheme {scheme!r}")
+    group = (Batch([(L, p, q, sd) + shape for sd in seeds], stream=stream) if scheme == "dt"
+             else _Handles(L, p, q, seeds, scheme, Bx, By))
+    with group as b:
         t = 0
         for tt in ts:
             b.run(tt - t)
@@ -193,8 +244,8 @@ def main(argv=None) -> int:
     ap.add_argument("--By", type=int, default=0)
     ap.add_argument("--out", default=None, help="also write the JSON lines to this file")
     ap.add_argument("--seeds", type=int, default=1,
-                    help="realizations; with 2 or more, an ensemble (DTrDT, one batch) whose replica seeds derive "
-                         "from --seed, and the first --wait is its waiting time")
+                    help="realizations; with 2 or more, an ensemble (DTrDT as one batch, DTrDB/DTrDTr as concurrent "
+                         "handles) whose replica seeds derive from --seed; the first --wait is its waiting time")
     a = ap.parse_args(argv)
     fp = open(a.out, "w") if a.out else None
 
@@ -209,7 +260,7 @@ def main(argv=None) -> int:
         from . import _lib
         seeds = [_lib.oct_replica_seed(a.seed, r) for r in range(a.seeds)]
         res = ensemble_run(a.L, a.p, a.q, seeds, a.t_max, a.points, a.Bx, a.By, callback=emit,
-                           wait=a.wait[0] if a.wait else None)
+                           wait=a.wait[0] if a.wait else None, scheme=a.scheme)
     else:
         res = production_run(a.L, a.p, a.q, a.seed, a.t_max, a.points, a.wait, a.scheme, a.Bx, a.By,
                              callback=emit)

@@ -91,3 +91,24 @@ def test_batch_autocorrelation_errors(g):
         assert 0.0 < ac.c_s < 0.25
         with pytest.raises(g.OctError):
             b.measure_ac(5)  # no such slot
+
+
+@pytest.mark.parametrize("scheme,sch", [("db", 1), ("dtr", 2)])
+def test_ensemble_of_other_block_layers_on_concurrent_streams(g, scheme, sch):
+    """DTrDB / DTrDTr ensembles (one handle per realization, interleaved on
+    their own streams) equal the same seeds run one after another."""
+    from paper_1705_01022_gb300 import run as prun
+    L, p, q, Bx, By, s = 256, 0.95, 0.05, 64, 64, 3
+    seeds = [101, 202, 303]
+    res = prun.ensemble_run(L, p, q, seeds, t_max=12, points=5, Bx=Bx, By=By, wait=s, scheme=scheme)
+    for i, sd in enumerate(seeds):
+        with g.Simulation(L, p, q, sd, Bx=Bx, By=By, scheme=sch) as sim:
+            t = 0
+            for r in res["records"]:
+                sim.run(r["t"] - t)
+                t = r["t"]
+                assert r["w2"][i] == sim.measure().w2, (i, t)
+                if t == s:
+                    sim.snapshot()
+                if t > s:
+                    assert r["c_h"][i] == sim.measure_ac().c_h, (i, t)

@@ -93,6 +93,9 @@ class _OracleSim:
     def sync(self):
         pass
 
+    def close(self):
+        pass
+
     def __enter__(self):
         return self
 
@@ -250,3 +253,28 @@ def test_command_line(oracle, monkeypatch, tmp_path, capsys):
     assert [r["t"] for r in recs] == prun.measurement_times(8, 4, [2])
     assert summary["L"] == 64 and summary["seeds"] == 1 and len(summary["beta_eff"]) == len(recs) - 2
     assert all("c_h" in r for r in recs if r["t"] > 2)
+
+
+@pytest.mark.parametrize("scheme", ["db", "dtr"])
+def test_ensemble_of_other_block_layers(oracle, monkeypatch, scheme):
+    """DTrDB and DTrDTr ensembles run one handle per realization; every
+    realization's W^2 and C_h equal the oracle's replay of that seed."""
+    import paper_1705_01022_gb300 as pkg
+    from oracle import Params, SCHEME_DB, SCHEME_DTR
+    monkeypatch.setattr(pkg, "Simulation", lambda *a, **k: _OracleSim(oracle, *a, **k))
+    L, p, q, seeds, s = 64, 0.95, 0.05, [31, 32], 2
+    res = prun.ensemble_run(L, p, q, seeds, t_max=8, points=4, Bx=32, By=32, wait=s, scheme=scheme)
+    osch = {"db": SCHEME_DB, "dtr": SCHEME_DTR}[scheme]
+    for i, sd in enumerate(seeds):
+        X, Y = oracle.flat(L)
+        t, snap = 0, None
+        for r in res["records"]:
+            oracle.dtrdt_run(X, Y, Params(L=L, p=p, q=q, seed=sd, Bx=32, By=32, scheme=osch), t, r["t"] - t)
+            t = r["t"]
+            assert r["w2"][i] == oracle.w2(X, Y)
+            if t == s:
+                snap = (X.copy(), Y.copy())
+            if t > s:
+                assert r["c_h"][i] == oracle.two_time(X, Y, *snap)["c_h"]
+    with pytest.raises(ValueError):
+        prun.ensemble_run(L, p, q, seeds, t_max=8, points=4, scheme="cdb")

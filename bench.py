@@ -601,6 +601,9 @@ def main():
         e2e = {"value": world * L * L * a.e2e_steps / (e2e_s * 1e9), "unit": UNIT,
                "h2d_bytes_per_step": L * L // 4, "d2h_bytes_per_step": L * L // 4 + 56,
                "steps": a.e2e_steps, "lattices_in_flight": nl, "host_marks_ms": marks,
+               "copy_in_ms_median": statistics.median(b - w for w, b in marks) if marks else None,
+               "stalled_copies_in": sum(1 for w, b in marks if marks and b - w > 2 * statistics.median(
+                   b2 - w2 for w2, b2 in marks)),
                "breakdown_ms": {"h2d": ph[0] * 1e3, "mcs": ph[1] * 1e3, "measure_w2": ph[2] * 1e3,
                                 "d2h": ph[3] * 1e3},
                "h2d_gbs": (L * L // 4) / ph[0] / 1e9, "d2h_gbs": (L * L // 4) / ph[3] / 1e9,

@@ -28,9 +28,12 @@ __global__ void init_flat_kernel(uint32_t *lat, uint32_t L, uint64_t n_words, ui
 }
 
 // Byte table: for byte value v, with running step e_i = sum_{j<=i} (2 b_j - 1),
-// i = 0..7 (every field a signed byte, sign-extended on use):
-//   .x = sum e_i | net e_7 << 8 | min e_i << 16 | max e_i << 24
-//   .y = sum e_i^2 (at most 204)
+// i = 0..7:
+//   .x = sum e_i (signed byte) | net e_7 << 8 (signed byte) | sum e_i^2 << 16
+//   .y = the extremes as two biased 16-bit halves for one packed minimum:
+//        (min e_i + kW2Bias) | (kW2Bias - max e_i) << 16
+constexpr uint32_t kW2Bias = 0x8000u;
+
 __device__ __forceinline__ uint2 byte_entry(uint32_t v) {
     int e = 0, s1 = 0, s2 = 0, mn = 1 << 20, mx = -(1 << 20);
     for (int i = 0; i < 8; ++i) {
@@ -42,13 +45,20 @@ __device__ __forceinline__ uint2 byte_entry(uint32_t v) {
     }
     uint2 r;
     r.x = (static_cast<uint32_t>(s1) & 0xFFu) | ((static_cast<uint32_t>(e) & 0xFFu) << 8) |
-          ((static_cast<uint32_t>(mn) & 0xFFu) << 16) | ((static_cast<uint32_t>(mx) & 0xFFu) << 24);
-    r.y = static_cast<uint32_t>(s2);
+          (static_cast<uint32_t>(s2) << 16);
+    r.y = (kW2Bias + static_cast<uint32_t>(mn)) | ((kW2Bias - static_cast<uint32_t>(mx)) << 16);
     return r;
 }
 
 __device__ __forceinline__ int sbyte(uint32_t x, int k) {
     return static_cast<int>(static_cast<signed char>(static_cast<unsigned char>(x >> (8 * k))));
+}
+
+// Halfword-wise unsigned minimum of two packed pairs.
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
 }
 
 constexpr int kW2Warps = 8;
@@ -111,7 +121,10 @@ __global__ void __launch_bounds__(kW2Warps * 32)
             }
             // Lane-local running sum a (0 at the lane's first bit) in 32 bits:
             // |a| <= 128, sum a <= 2^14, sum a^2 <= 2^21.
-            int a = 0, l1 = 0, l2 = 0, lmn = 1 << 30, lmx = -(1 << 30);
+            // ext: running packed minimum of (a + min e + bias | bias - a - max e),
+            // both halves within [bias - 136, bias + 136]
+            int a = 0, l1 = 0, l2 = 0;
+            uint32_t ext = 0xFFFFFFFFu;
             const uint32_t words[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -121,9 +134,9 @@ __global__ void __launch_bounds__(kW2Warps * 32)
                     const uint2 te = my_table[((words[j] >> (8 * byte)) & 0xFFu) * kW2TableCopies];
                     const int t1 = sbyte(te.x, 0), net = sbyte(te.x, 1);
                     l1 += 8 * a + t1;
-                    l2 += a * (8 * a + 2 * t1) + static_cast<int>(te.y);
-                    lmn = min(lmn, a + sbyte(te.x, 2));
-                    lmx = max(lmx, a + sbyte(te.x, 3));
+                    l2 += a * (8 * a + 2 * t1) + static_cast<int>(te.x >> 16);
+                    // + a in the low half, - a in the high half (a * (1 - 2^16))
+                    ext = min_u16x2(ext, te.y + static_cast<uint32_t>(a) * 0xFFFF0001u);
                     a += net;
                 }
             }
@@ -132,6 +145,8 @@ __global__ void __launch_bounds__(kW2Warps * 32)
             q1 += static_cast<long long>(nbits) * B + l1;
             q2 += static_cast<long long>(nbits) * B * B + 2 * B * l1 + l2;
             if (nw > 0) {
+                const int lmn = static_cast<int>(ext & 0xFFFFu) - static_cast<int>(kW2Bias);
+                const int lmx = static_cast<int>(kW2Bias) - static_cast<int>(ext >> 16);
                 qmin = min(qmin, static_cast<int>(B) + lmn);
                 qmax = max(qmax, static_cast<int>(B) + lmx);
             }

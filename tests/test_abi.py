@@ -74,3 +74,26 @@ def test_null_handles_rejected_without_gpu(lib):
         with pytest.raises(_lib.OctError) as e:
             call()
         assert e.value.code == _lib.OCT_EINVAL
+
+
+def test_batch_replicas_validated_without_gpu(lib):
+    """oct_batch_create checks every replica before any CUDA call."""
+    from paper_1705_01022_gb300 import _lib
+    _lib.load()
+    bad = [
+        dict(L=96),                       # not a multiple of 64
+        dict(L=32768),                    # above 16384
+        dict(L=256, p=1.5),               # p outside [0, 1]
+        dict(L=256, Bx=48, By=16),        # Bx not a multiple of 32
+        dict(L=256, Bx=64, By=48),        # By not a multiple of 16
+        dict(L=192, Bx=64, By=64),        # 2 Bx does not divide L
+        dict(L=4096, Bx=1024, By=32),     # 64 groups: more than a warp
+        dict(L=256, Bx=96, By=16),        # 3 group columns: not a power of two
+    ]
+    for kw in bad:
+        r = _lib.oct_replica()
+        r.L, r.p, r.q, r.seed = kw.get("L", 256), kw.get("p", 1.0), 0.0, 1
+        r.Bx, r.By = kw.get("Bx", 0), kw.get("By", 0)
+        with pytest.raises(_lib.OctError) as e:
+            _lib.oct_batch_create([r], None)
+        assert e.value.code == _lib.OCT_EINVAL, kw

@@ -330,3 +330,19 @@ def test_every_tunable_shape_bit_exact(g, oracle, shape):
         with g.Simulation(2048, p, q, seed, Bx=Bx, By=By) as sim:
             sim.run(2)
             _assert_same(oracle, sim, X, Y, net, f"{Bx}x{By} p={p}")
+
+
+@pytest.mark.parametrize("L,Bx,By", [(192, 32, 32), (4160, 32, 32), (4224, 64, 64)])
+def test_roughness_on_ragged_rows(g, oracle, L, Bx, By):
+    """The W^2 row pass on rows of 6 words (scalar loads), 130 words (a ragged
+    second chunk of 2 words) and 132 words (16-byte loads, ragged second chunk):
+    S1, S2 and hmax of the GPU lattice equal the oracle's O3 on the same
+    lattice, after a few MCS of rough dynamics (EW, then KPZ-like)."""
+    for p, q, n in ((0.5, 0.5, 3), (0.95, 0.05, 5)):
+        with g.Simulation(L, p, q, 77, Bx=Bx, By=By) as sim:
+            sim.run(n)
+            m = sim.measure()
+            X, Y = _oracle_bits(oracle, sim)
+            s1, s2, hmax = oracle.w2_sums(X, Y)
+            assert (m.s1, m.s2, m.hmax) == (s1, s2, hmax), (L, p, q)
+            assert m.w2 == oracle.w2(X, Y)

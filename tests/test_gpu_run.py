@@ -112,3 +112,32 @@ def test_ensemble_of_other_block_layers_on_concurrent_streams(g, scheme, sch):
                     sim.snapshot()
                 if t > s:
                     assert r["c_h"][i] == sim.measure_ac().c_h, (i, t)
+
+
+def test_waiting_time_zero(g, oracle):
+    """s = 0: the snapshot is the flat start itself (C_h(0,0) = W^2(0) = 1/4);
+    later C_h(t,0), C_s(t,0) equal the oracle's, alone and in an ensemble."""
+    from oracle import Params
+    from paper_1705_01022_gb300 import run as prun
+    L, p, q = 256, 1.0, 0.0
+    res = prun.production_run(L, p, q, 5, t_max=6, points=4, waits=[0], Bx=64, By=64)
+    X, Y = oracle.flat(L)
+    Xs, Ys = X.copy(), Y.copy()
+    t = 0
+    for r in res["records"]:
+        oracle.dtrdt_run(X, Y, Params(L=L, p=p, q=q, seed=5, Bx=64, By=64), t, r["t"] - t)
+        t = r["t"]
+        if t > 0:
+            a = oracle.two_time(X, Y, Xs, Ys)
+            assert (r["s"], r["c_h"], r["c_s"]) == (0, a["c_h"], a["c_s"]), t
+    assert res["records"][0]["w2"] == 0.25
+    seeds = [g._lib.oct_replica_seed(3, r) for r in range(3)]
+    ens = prun.ensemble_run(L, p, q, seeds, t_max=6, points=4, Bx=64, By=64, wait=0)
+    for i, sd in enumerate(seeds):
+        X, Y = oracle.flat(L)
+        t = 0
+        for r in ens["records"]:
+            oracle.dtrdt_run(X, Y, Params(L=L, p=p, q=q, seed=sd, Bx=64, By=64), t, r["t"] - t)
+            t = r["t"]
+            if t > 0:
+                assert r["c_h"][i] == oracle.two_time(X, Y, Xs, Ys)["c_h"], (i, t)

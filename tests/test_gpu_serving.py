@@ -37,3 +37,30 @@ def test_each_result_is_the_same_alone_and_in_the_mix(g):
     assert any(b.admitted < a.done for a, b in zip(by_adm, by_adm[1:]))
     s = serve.summary(done, max(j.done for j in done) - min(j.arrival for j in done))
     assert s["p50_latency_s"] > 0
+
+
+def test_full_warp_jobs_in_the_mix(g):
+    """A job whose lattice takes full-warp sub-tiles under the 'large' policy
+    (L = 8192: 1024 x 16) shares the batch with packed small jobs; every
+    streamed W^2 equals the job run alone on the same sub-tile."""
+    from paper_1705_01022_gb300 import _lib, serve
+    from paper_1705_01022_gb300.autotune import batch_shape
+    assert batch_shape(8192, "large") == (1024, 16)
+    jobs = [serve.Job(0, 8192, 0.95, 0.05, _lib.oct_replica_seed(8, 0), 6, arrival=0.0,
+                      measure_at=serve.log_times(6, 3)),
+            serve.Job(1, 256, 1.0, 0.0, _lib.oct_replica_seed(8, 1), 9, arrival=0.0,
+                      measure_at=serve.log_times(9, 4)),
+            serve.Job(2, 384, 0.5, 0.5, _lib.oct_replica_seed(8, 2), 4, arrival=0.0,
+                      measure_at=serve.log_times(4, 3))]
+    eng = serve.ServingEngine(1 << 30, max_chunk=4)
+    done = eng.run(jobs)
+    assert {j.jid for j in done} == {0, 1, 2}
+    for job in done:
+        assert job.shape == batch_shape(job.L, "large")
+        with g.Simulation(job.L, job.p, job.q, job.seed, Bx=job.shape[0], By=job.shape[1]) as sim:
+            t = 0
+            for (tt, s1, s2, w2, net) in job.results:
+                sim.run(tt - t)
+                t = tt
+                m = sim.measure()
+                assert (tt, s1, s2, w2, net) == (m.t, m.s1, m.s2, m.w2, m.net_flips), job.jid

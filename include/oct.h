@@ -73,7 +73,7 @@ typedef struct oct_sim oct_sim; /* opaque; owns its device memory unless told ot
  *          single-hit dead border; border attempts are delayed after the bulk
  *          ones when both p and q are non-zero, otherwise all attempts of a
  *          step are carried out together, as in the paper's runs) or
- *          OCT_SCHEME_DTR (DTrDTr, Sec. 3.2: single-hit double tiling whose
+ *          OCT_SCHEME_DTR (DTrDTr, Sec. 4.1.2: single-hit double tiling whose
  *          block-layer origin moves to a uniform position in the thread cell
  *          after every collective step, the cell grid wrapping around the
  *          sub-tile). */
@@ -223,8 +223,8 @@ int oct_probe_int_rate(int op, double *ops_per_clk_per_sm, double *sm_mhz, int *
  * For callers such as a plugin or framework that owns all device memory and
  * hands over only a buffer and a stream, or a latency-critical loop where
  * cudaMalloc/cudaFree are not allowed because they may synchronise the
- * device.  It computes what oct_measure_w2 computes (Eq. (3), mean over the
- * L^2 sites) for the planar lattice at device address `lattice` (L*L/4 bytes,
+ * device.  It computes what oct_measure_w2 computes (the same sums, the same
+ * W^2) for the planar lattice at device address `lattice` (L*L/4 bytes,
  * 16-byte aligned), enqueued on `stream` (a cudaStream_t, NULL for the
  * default stream), then synchronises that stream and writes out->s1, s2,
  * hmax, n_sites and w2 (out->t = -1 and out->net_flips = 0: a bare lattice
@@ -233,9 +233,12 @@ int oct_probe_int_rate(int op, double *ops_per_clk_per_sm, double *sm_mhz, int *
  * holds until the process exits; it serves L up to 131072 (2^17) and larger L
  * is rejected with OCT_EINVAL and a message in oct_last_error().  The first
  * call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array: calls that may
- * overlap on the GPU (other streams, other threads) race and must be
+ * (cudaGetSymbolAddress) with that device current and keeps it for the rest
+ * of the process; make that first call before any stream capture.  The kept
+ * address belongs to the device's context at that first call and does not
+ * survive a cudaDeviceReset: do not use this entry point on a device that was
+ * reset earlier in the same process.  All calls share the one array: calls
+ * that may overlap on the GPU (other streams, other threads) race and must be
  * serialised by the caller.  It calls no cudaMalloc, cudaFree or other
  * allocating routine. */
 int oct_w2_noalloc(const void *lattice, int64_t L, void *stream, oct_w2 *out);

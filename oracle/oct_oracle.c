@@ -17,8 +17,8 @@
  *     tiling, one randomly drawn domain set per collective step
  *     (Sec. 3.1, block layer paragraph);
  *   - the other block layers: single-hit dead border with delayed borders
- *     (DTrDB, Sec. 3.2, Fig. 7) and double tiling whose origin moves after
- *     every collective step (DTrDTr, Sec. 3.2, notation paragraph);
+ *     (DTrDB, Sec. 3.1, delayed borders; Fig. 5) and double tiling whose origin moves after
+ *     every collective step (DTrDTr, Sec. 4.1.2);
  *   - two-time autocorrelations C_h, C_s: Sec. 2, Eq. (5).
  * Where the paper is silent (random-number streams, thread-cell units,
  * acceptance rounding), a reading is fixed here and restated at each use.
@@ -392,12 +392,12 @@ static void decide_and_flip(const uint32_t key[2], uint32_t t, uint32_t k, uint3
  * conflict-free and sees the flips of the earlier ones.  The paper delays
  * borders only when both p and q are non-zero; with one of them zero two
  * neighbouring sites are never both accepted, and its DB runs carry out all
- * attempts of a step together (a reading of Sec. 3.2: DB does
+ * attempts of a step together (a reading of Sec. 3.1: DB does
  * the same).  DB_IGNORE carries out all attempts together for any p, q; with
  * both non-zero two accepted flips can then hit the same slope bit, which the
  * flip tracker counts.
  *
- * DTR (DTrDTr, Sec. 3.2 notation paragraph): DT whose block-layer origin
+ * DTR (DTrDTr, Sec. 4.1.2): DT whose block-layer origin
  * moves to a uniform (ax, ay) in [0,cx) x [0,cy) after every collective step,
  * the cell grid wrapping around the sub-tile.  The active sub-cell of set d
  * then starts at column c0 = (ax + dx*cx/2) mod cx and row r0 = (ay +

@@ -35,7 +35,9 @@ std::mutex g_setup_mutex;
 void *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_w2_scratch on the current device, looked up on the first
-// call made with that device current.
+// call made with that device current.  The address belongs to the device's
+// context at that call, so it does not survive a cudaDeviceReset of that
+// device in the same process.
 cudaError_t scratch_address(int dev, void **out) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_addr[dev]) {

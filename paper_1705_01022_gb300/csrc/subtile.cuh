@@ -515,7 +515,7 @@ __device__ __forceinline__ void db_step(uint32_t (&X)[16], uint32_t (&Y)[16], ui
     }
 }
 
-// A collective step of DTrDTr (Sec. 3.2, notation paragraph): DT whose
+// A collective step of DTrDTr (Sec. 4.1.2): DT whose
 // block-layer origin moves after every step, the cell grid wrapping around
 // the sub-tile.  With the active sub-cell of every cell starting at column c0
 // and row R0 (uniform in [0, 4): the set's offset plus the moved origin), the

@@ -1,6 +1,5 @@
 """Pins for the oracle's DTrDTr block layer (double tiling whose block-layer
-origin moves to a random position after every collective step, Sec. 3.2,
-notation paragraph).
+origin moves to a random position after every collective step, Sec. 4.1.2).
 
 * Schedule: conflict-free, one MCS = L^2 attempts, invariants hold, at several
   sub-tile and thread-cell shapes.

@@ -112,6 +112,9 @@ def lib():
         L.oo_replica_seed.argtypes = [u64, u32]
         L.oo_replica_seed.restype = u64
         L.oo_subtile_step_sites.argtypes = [ctypes.POINTER(_Params), u32, u32, u32, i64, _P_i64, _P_i64]
+        L.oo_subtile_steps_many.argtypes = [ctypes.POINTER(_Params), u64, i64, u32, u32, u32, i64, i64,
+                                            i64, _P_u8, _P_u8, _P_u8, _P_u8, _P_i64]
+        L.oo_set_plant.argtypes = [ctypes.c_int]
         L.oo_two_time_sums.argtypes = [i64, _P_u8, _P_u8, _P_u8, _P_u8, ctypes.POINTER(_TwoTime)]
         L.oo_ch_from_sums.argtypes = [i64, ctypes.POINTER(_TwoTime)]
         L.oo_ch_from_sums.restype = dbl
@@ -258,6 +261,40 @@ def subtile_step_sites(prm: "Params", t: int, k: int, T: int, s: int):
     if lib().oo_subtile_step_sites(ctypes.byref(prm.c()), t, k, T, s, lx, ly) != 0:
         raise ValueError("invalid parameters")
     return lx, ly
+
+
+def subtile_steps_many(prm: "Params", seed0: int, n_runs: int, t: int, k: int, T: int, x0: int, y0: int,
+                       n_steps: int, X0, Y0):
+    """The first n_steps collective steps of one sub-tile (at (x0, y0)) alone,
+    once per seed seed0 + r from the lattice (X0, Y0).  Returns the stacks of
+    resulting lattices (X, Y) and the net flips of each run."""
+    L = prm.L
+    X = np.zeros((n_runs, L, L), dtype=np.uint8)
+    Y = np.zeros((n_runs, L, L), dtype=np.uint8)
+    net = np.zeros(n_runs, dtype=np.int64)
+    rc = lib().oo_subtile_steps_many(ctypes.byref(prm.c()), seed0, n_runs, t, k, T, x0, y0, n_steps,
+                                     np.ascontiguousarray(X0, dtype=np.uint8),
+                                     np.ascontiguousarray(Y0, dtype=np.uint8), X, Y, net)
+    if rc != 0:
+        raise ValueError("invalid parameters")
+    return X, Y, net
+
+
+class planted:
+    """Context manager that plants one of the oracle's two known mistakes
+    (1: cells 2i and 2i+1 share site bits; 2: DTrDB corners before borders)
+    for a negative control, and removes it on exit."""
+
+    def __init__(self, which: int):
+        self.which = which
+
+    def __enter__(self):
+        lib().oo_set_plant(self.which)
+        return self
+
+    def __exit__(self, *exc):
+        lib().oo_set_plant(0)
+        return False
 
 
 class _TwoTime(ctypes.Structure):

@@ -27,7 +27,11 @@
  * independent Philox implementation; flat-start closed forms; lattice
  * invariants after every run; exact 4x4 master equations for O1 and for O2
  * (degenerate 2x2 thread cells); site-selection and acceptance statistics
- * for O2 at full thread-cell size; planted-mistake tests of the checker.
+ * for O2 at full thread-cell size; every cell's site against an independent
+ * statement of the site fields, and neighbouring cells' offsets jointly
+ * uniform, at 4x4 to 32x16 cells; exact one-collective-step distributions of
+ * DT, DTrDB (delayed borders) and DTrDTr on sub-tiles of several cells;
+ * planted-mistake tests of the checker and of the block layer (oo_set_plant).
  */
 #include "oct_oracle.h"
 
@@ -93,6 +97,12 @@ static inline int64_t wrap(int64_t a, int64_t L) {
     int64_t r = a % L;
     return r < 0 ? r + L : r;
 }
+
+/* Planted mistakes, for the negative controls of the tests only (0 = none,
+ * the default; see oo_set_plant in the header). */
+static int g_plant = 0;
+
+void oo_set_plant(int which) { g_plant = which; }
 
 /* ------------------------------------------------------------------------ */
 /* Model, Sec. 2.1 / Eq. (1)                                                 */
@@ -451,6 +461,10 @@ static step_draw_t step_draw(const oo_params *P, const uint32_t key[2], uint32_t
     return d;
 }
 
+/* The field of the site word that TC j of a band reads: its own (planted
+ * mistake 1 makes cells 2i and 2i+1 share the field of cell 2i). */
+static int64_t site_field(int64_t j) { return g_plant == 1 ? (j & ~(int64_t)1) : j; }
+
 /* Local site in the sub-tile of the attempt of TC column a, TC row c, whose
  * random offset inside its sub-cell (DT, DTR) or cell (DB) is (rx, ry). */
 static void tc_local_site(const oo_params *P, const step_draw_t *d, int64_t a, int64_t c, int64_t rx,
@@ -461,7 +475,7 @@ static void tc_local_site(const oo_params *P, const step_draw_t *d, int64_t a, i
 
 static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, uint32_t k,
                         uint32_t T, int64_t x0, int64_t y0, view_t *v, int64_t *net,
-                        int64_t *attempts, conflict_t *cf) {
+                        int64_t *attempts, conflict_t *cf, int64_t s_end) {
     const int64_t L = P->L, Bx = P->Bx, By = P->By, cx = P->cx, cy = P->cy;
     const int db = P->scheme == OO_SCHEME_DB || P->scheme == OO_SCHEME_DB_IGNORE;
     /* The paper delays border attempts only where two neighbouring sites can
@@ -490,7 +504,8 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
     int *cls = (int *)malloc(sizeof(int) * (size_t)n_tc);
     uint32_t tail_next = 0; /* tail-stream words used so far in this device step */
 
-    for (int64_t s = 0; s < n_steps; ++s) {
+    if (s_end > n_steps) s_end = n_steps;
+    for (int64_t s = 0; s < s_end; ++s) {
         const step_draw_t sd = step_draw(P, key, t, k, T, s);
         int64_t na = 0;
         /* every thread cell's attempt: site and leading acceptance bits */
@@ -509,7 +524,7 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
                         const int64_t a = bc * tcs_per_band + j; /* TC column */
                         int64_t rx = 0, ry = 0;
                         if (bpt > 0) {
-                            const int64_t off = fw * j + (s % spw) * (fw / spw);
+                            const int64_t off = fw * site_field(j) + (s % spw) * (fw / spw);
                             const uint32_t r = (site_w[m] >> off) & ((1u << bpt) - 1u);
                             rx = r & ((1u << bx_bits) - 1u);
                             ry = r >> bx_bits;
@@ -538,7 +553,10 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
                 }
             }
         }
-        for (int ph = 0; ph < 3; ++ph) {
+        /* bulk, border, corner (planted mistake 2: corner before border) */
+        const int order[3] = {0, g_plant == 2 ? 2 : 1, g_plant == 2 ? 1 : 2};
+        for (int pi = 0; pi < 3; ++pi) {
+            const int ph = order[pi];
             int64_t np = 0;
             for (int64_t i = 0; i < na; ++i)
                 if (cls[i] == ph) phase[np++] = all[i];
@@ -591,7 +609,7 @@ int oo_subtile_step_sites(const oo_params *P, uint32_t t, uint32_t k, uint32_t T
             if (bpt > 0) {
                 uint32_t site_w[4];
                 philox_at(key, t, k | (uint32_t)((s / spw) << 2), T, (site_tag << 28) | g, site_w);
-                const int64_t off = fw * j + (s % spw) * (fw / spw);
+                const int64_t off = fw * site_field(j) + (s % spw) * (fw / spw);
                 const uint32_t r = (site_w[m] >> off) & ((1u << bpt) - 1u);
                 rx = r & ((1u << bx_bits) - 1u);
                 ry = r >> bx_bits;
@@ -599,6 +617,25 @@ int oo_subtile_step_sites(const oo_params *P, uint32_t t, uint32_t k, uint32_t T
             const int64_t i = c * (Bx / cx) + a;
             tc_local_site(P, &sd, a, c, rx, ry, &lx[i], &ly[i]);
         }
+    }
+    return 0;
+}
+
+int oo_subtile_steps_many(const oo_params *P, uint64_t seed0, int64_t n_runs, uint32_t t, uint32_t k,
+                          uint32_t T, int64_t x0, int64_t y0, int64_t n_steps, const uint8_t *X0,
+                          const uint8_t *Y0, uint8_t *Xout, uint8_t *Yout, int64_t *net_flips) {
+    if (oo_check_params(P) || n_steps < 0 || n_runs < 0) return -1;
+    const int64_t L = P->L, N = L * L;
+    for (int64_t r = 0; r < n_runs; ++r) {
+        uint8_t *X = Xout + r * N, *Y = Yout + r * N;
+        memcpy(X, X0, (size_t)N);
+        memcpy(Y, Y0, (size_t)N);
+        uint32_t key[2];
+        seed_key(seed0 + (uint64_t)r, key);
+        view_t v = {L, 0, 0, L, L, X, Y};
+        int64_t net = 0;
+        run_subtile(P, key, t, k, T, wrap(x0, L), wrap(y0, L), &v, &net, NULL, NULL, n_steps);
+        if (net_flips) net_flips[r] = net;
     }
     return 0;
 }
@@ -631,7 +668,7 @@ static void run_mcs(const oo_params *P, uint32_t t, view_t *v, int64_t *net, int
                 const int64_t x0 = wrap(ox + 2 * P->Bx * tx + P->Bx * sx, P->L);
                 const int64_t y0 = wrap(oy + 2 * P->By * ty + P->By * sy, P->L);
                 if (!footprint_inside(v, x0, y0, P->Bx, P->By)) continue;
-                run_subtile(P, key, t, k, T, x0, y0, v, net, attempts, cf);
+                run_subtile(P, key, t, k, T, x0, y0, v, net, attempts, cf, P->cx * P->cy);
             }
     }
 }

@@ -128,6 +128,24 @@ int oo_dtrdt_mcs_window(const oo_params *prm, uint32_t t, int64_t wx, int64_t wy
 int oo_subtile_step_sites(const oo_params *P, uint32_t t, uint32_t k, uint32_t T, int64_t s,
                           int64_t *lx, int64_t *ly);
 
+/* The first n_steps collective steps of one sub-tile alone (Bx x By sites at
+ * (x0, y0), periodic in L), device step k, tile index T, MCS t, once for each
+ * seed seed0 + r, r < n_runs, each from the lattice (X0, Y0).  Writes each
+ * resulting lattice to Xout/Yout (n_runs * L*L bytes each) and its net flips
+ * to net_flips[r] (optional).  The tail stream starts from word 0, as at the
+ * start of a device step.  For exact one-step distributions in the tests.
+ * Returns 0, or -1 for invalid parameters. */
+int oo_subtile_steps_many(const oo_params *P, uint64_t seed0, int64_t n_runs, uint32_t t, uint32_t k,
+                          uint32_t T, int64_t x0, int64_t y0, int64_t n_steps, const uint8_t *X0,
+                          const uint8_t *Y0, uint8_t *Xout, uint8_t *Yout, int64_t *net_flips);
+
+/* Plants one of two known mistakes in the block layer, for negative controls
+ * of the tests only: 1 = thread cells 2i and 2i+1 of a band read the same
+ * site-draw bits; 2 = DTrDB carries out corner attempts before border
+ * attempts.  0 (the default) plants nothing.  Not thread-safe; a test sets it
+ * and resets it to 0. */
+void oo_set_plant(int which);
+
 /* O3: exact roughness sums, Eq. (3).  Heights relative to h(0,0) = 0 are
  * integrated first up column 0 and then along each row.  s1 = sum h,
  * s2 = sum h^2 returned as two 64-bit halves of an unsigned 128-bit value

@@ -122,7 +122,12 @@ int validate(const oct_params *prm, int *Bx, int *By, int *cx, int *cy) {
         return fail(OCT_EINVAL, "p and q must lie in [0, 1]");
     *cx = prm->cx ? prm->cx : 4;
     *cy = prm->cy ? prm->cy : 4;
-    if (*cx != 4 || *cy != 4) return fail(OCT_EUNSUPPORTED, "the library implements 4x4-site thread cells only");
+    const bool coarse = *cx != 4 || *cy != 4;
+    if (coarse && !oct::cells_shape_supported(*cx, *cy))
+        return fail(OCT_EUNSUPPORTED,
+                    "thread cells: cx in {4, 8, 16, 32} and cy in {4, 8, 16} sites (4 x 16 included)");
+    if (coarse && prm->scheme != OCT_SCHEME_DT)
+        return fail(OCT_EUNSUPPORTED, "thread cells other than 4 x 4 sites are implemented for DTrDT only");
     if (prm->Bx || prm->By) {
         *Bx = prm->Bx;
         *By = prm->By;
@@ -133,8 +138,8 @@ int validate(const oct_params *prm, int *Bx, int *By, int *cx, int *cy) {
         *Bx = 32;
         *By = 16;
     }
-    if (*Bx < 32 || *By < 16 || *Bx % 32 || *By % (4 * *cy))
-        return fail(OCT_EINVAL, "Bx must be a multiple of 32 and By a multiple of 4*cy");
+    if (*Bx < 32 || *By < 16 || *Bx % 32 || *By % 16)
+        return fail(OCT_EINVAL, "Bx must be a multiple of 32 and By a multiple of 16");
     if ((*Bx / 32) * (*By / 16) > 32)
         return fail(OCT_EINVAL, "a sub-tile may hold at most 32 groups of 32x16 sites");
     if (L % (2 * *Bx) || L % (2 * *By)) return fail(OCT_EINVAL, "L must be a multiple of 2Bx and 2By");
@@ -242,6 +247,8 @@ int sim_create(const oct_params *prm, oct_sim **out) {
     // with delayed borders (both rates non-zero), 3 DTrDTr
     a.scheme = (s->scheme == OCT_SCHEME_DB) ? ((s->p > 0.0 && s->q > 0.0) ? 2u : 1u)
                : (s->scheme == OCT_SCHEME_DTR) ? 3u : 0u;
+    a.cx = static_cast<uint32_t>(cx);
+    a.cy = static_cast<uint32_t>(cy);
     *out = s;
     return OCT_OK;
 }

@@ -133,6 +133,7 @@ __global__ void advance_t_kernel(uint32_t *t_ptr) { *t_ptr += 1u; }
 }  // namespace
 
 cudaError_t launch_dtrdt_step(const StepArgs &a, bool any_random, cudaStream_t st) {
+    if (a.cx != 4u || a.cy != 4u) return launch_cells_step(a, any_random, st);
     const uint32_t n_tiles = a.tiles_x * a.tiles_y;
     // DTrDTr routes cells between the lanes of one sub-tile with warp-wide
     // shuffles whose pattern depends on its own draws: one sub-tile per warp.

@@ -26,6 +26,7 @@ struct StepArgs {
     unsigned long long *net;   // kNetSlots signed flip counters (two's complement)
     unsigned long long *draws; // kNetSlots counters of attempts that needed an acceptance draw
     uint32_t scheme;           // 0: DT; 1: DB (borders together); 2: DB with delayed borders; 3: DTrDTr
+    uint32_t cx, cy;           // thread cell in sites (4 x 4, or a coarser DTrDT cell of cells.cu)
 };
 
 constexpr int kNetSlots = 1024;
@@ -35,6 +36,11 @@ constexpr int kStepBlocksPerSMPacked = 4;  // several sub-tiles per warp: per-la
 
 // Launches one device step; returns the CUDA launch status.
 cudaError_t launch_dtrdt_step(const StepArgs &a, bool any_random, cudaStream_t st);
+
+// DTrDT thread cells other than 4 x 4 sites (cells.cu): whether a cell shape
+// has a kernel, and the launch of one device step with it.
+bool cells_shape_supported(int cx, int cy);
+cudaError_t launch_cells_step(const StepArgs &a, bool any_random, cudaStream_t st);
 
 // Adds one to the device MCS counter.
 cudaError_t launch_advance_t(uint32_t *t_ptr, cudaStream_t st);

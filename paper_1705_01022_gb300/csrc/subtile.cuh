@@ -747,34 +747,38 @@ __device__ __forceinline__ void dtr_apply(uint32_t (&X)[16], uint32_t (&Y)[16], 
     if (c.gy < c.GY - 1) D ^= vu;
 }
 
-// Device step on one sub-tile (Bx x By sites at (x0, y0)) held by the lanes of
-// one warp that share it: stage the lane's group from the planar lattice,
-// run the 16 single-hit collective steps, write back.  LANE_SETS: lanes of the
-// warp may belong to different sub-tiles (each with its own set draws).
-// SCHEME: 0 DTrDT, 1 DTrDB with all attempts of a step together, 2 DTrDB with
-// delayed borders, 3 DTrDTr, 4 DTrDT with deposition only (p = 1, q = 0),
-// 5 DTrDT with both rates strictly inside (0, 1), 6 DTrDB with deposition only,
-// 7 DTrDB with delayed borders and both rates random.
-template <bool RANDOM, bool LANE_SETS, int SCHEME = 0>
-__device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t Bx,
-                                            uint32_t By, uint32_t x0, uint32_t y0, bool active,
-                                            const LaneCtx &c, uint32_t *ring, int &net, int &draws) {
-    TailPool tp;
-    tp.ring = ring;
-    const uint32_t G = static_cast<uint32_t>(c.GX * c.GY);
-    tp.mask = static_cast<uint32_t>(kRingWordsPerLane) * (1u << (32 - __clz(static_cast<int>(G - 1u)))) - 1u;
-    tp.head = 0u;
-    tp.end = 0u;
-    uint32_t *const Xp = lat;
-    uint32_t *const Yp = lat + static_cast<size_t>(L) * wpr;
-    const uint32_t sh = x0 & 31u;
-    const uint32_t wA = ((x0 >> 5) + static_cast<uint32_t>(c.gx)) % wpr;
-    const uint32_t wB = (wA + 1u == wpr) ? 0u : wA + 1u;
-    uint32_t ybase = y0 + 16u * static_cast<uint32_t>(c.gy);
-    if (ybase >= L) ybase -= L;
+// Where a lane's group lies in the planar lattice: the two words wA, wB of
+// every row that hold its 32 sites (from bit sh of wA), its first row ybase
+// and the sub-tile's halo row yh.
+struct LaneGeom {
+    uint32_t *Xp, *Yp;
+    uint32_t sh, wA, wB, ybase, yh;
+};
 
-    // Stage the group: 16 rows of X and Y, funnel-shifted to local bit 0.
-    uint32_t X[16], Y[16];
+__device__ __forceinline__ LaneGeom lane_geom(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t By, uint32_t x0,
+                                              uint32_t y0, const LaneCtx &c) {
+    LaneGeom q;
+    q.Xp = lat;
+    q.Yp = lat + static_cast<size_t>(L) * wpr;
+    q.sh = x0 & 31u;
+    q.wA = ((x0 >> 5) + static_cast<uint32_t>(c.gx)) % wpr;
+    q.wB = (q.wA + 1u == wpr) ? 0u : q.wA + 1u;
+    q.ybase = y0 + 16u * static_cast<uint32_t>(c.gy);
+    if (q.ybase >= L) q.ybase -= L;
+    q.yh = y0 + By;
+    if (q.yh >= L) q.yh -= L;
+    return q;
+}
+
+// Stage the lane's group: 16 rows of X and Y, funnel-shifted to local bit 0;
+// E: column 0 of the right neighbour (the halo column x0 + Bx for the last
+// lane column); D: row 0 of the lane below (the halo row y0 + By for the last
+// lane row).
+__device__ __forceinline__ void stage_lane(const LaneGeom &q, uint32_t L, uint32_t wpr, uint32_t Bx, uint32_t x0,
+                                           bool active, const LaneCtx &c, uint32_t (&X)[16], uint32_t (&Y)[16],
+                                           uint32_t &E, uint32_t &D) {
+    const uint32_t *const Xp = q.Xp;
+    const uint32_t *const Yp = q.Yp;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         X[r] = 0u;
@@ -783,19 +787,18 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
     if (active) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
-            uint32_t yr = ybase + r;
+            uint32_t yr = q.ybase + r;
             if (yr >= L) yr -= L;
             const size_t ro = static_cast<size_t>(yr) * wpr;
-            X[r] = __funnelshift_r(Xp[ro + wA], Xp[ro + wB], sh);
-            Y[r] = __funnelshift_r(Yp[ro + wA], Yp[ro + wB], sh);
+            X[r] = __funnelshift_r(Xp[ro + q.wA], Xp[ro + q.wB], q.sh);
+            Y[r] = __funnelshift_r(Yp[ro + q.wA], Yp[ro + q.wB], q.sh);
         }
     }
-    // E: column 0 of the right neighbour; D: row 0 of the lane below.
     uint32_t b0 = 0;
 #pragma unroll
     for (int r = 0; r < 16; ++r) b0 |= (X[r] & 1u) << r;
-    uint32_t E = __shfl_down_sync(kFull, b0, 1);
-    uint32_t D = __shfl_down_sync(kFull, Y[0], c.GX);
+    E = __shfl_down_sync(kFull, b0, 1);
+    D = __shfl_down_sync(kFull, Y[0], c.GX);
     if (active && c.gx == c.GX - 1) {  // halo column x0 + Bx
         uint32_t xc = x0 + Bx;
         if (xc >= L) xc -= L;
@@ -803,83 +806,24 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
         E = 0u;
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
-            uint32_t yr = ybase + r;
+            uint32_t yr = q.ybase + r;
             if (yr >= L) yr -= L;
             E |= ((Xp[static_cast<size_t>(yr) * wpr + wc] >> bc) & 1u) << r;
         }
     }
-    uint32_t yh = y0 + By;
-    if (yh >= L) yh -= L;
     if (active && c.gy == c.GY - 1) {  // halo row y0 + By
-        const size_t ro = static_cast<size_t>(yh) * wpr;
-        D = __funnelshift_r(Yp[ro + wA], Yp[ro + wB], sh);
+        const size_t ro = static_cast<size_t>(q.yh) * wpr;
+        D = __funnelshift_r(Yp[ro + q.wA], Yp[ro + q.wB], q.sh);
     }
+}
 
-    // Block layer: 16 single-hit collective steps.
-    const uint4 setw = philox4x32_10(c.t, c.k, c.T, kTagSet << 28, c.k0, c.k1);
-    uint4 site = make_uint4(0u, 0u, 0u, 0u);
-    uint4 borg = make_uint4(0u, 0u, 0u, 0u);
-    if (SCHEME == 3) borg = philox4x32_10(c.t, c.k, c.T, kTagBorg << 28, c.k0, c.k1);
-    for (uint32_t s = 0; s < 16u; ++s) {
-        if (SCHEME == 3) {
-            // DTrDTr: the set, plus a block-layer origin (ax, ay) per step
-            if ((s & 1u) == 0u)
-                site = philox4x32_10(c.t, c.k | ((s >> 1) << 2), c.T, (kTagSite << 28) | c.g, c.k0, c.k1);
-            const uint32_t d = (setw.x >> (2u * s)) & 3u;
-            const uint32_t bw = (s < 4u) ? borg.x : (s < 8u) ? borg.y : (s < 12u) ? borg.z : borg.w;
-            const uint32_t byte = (bw >> (8u * (s & 3u))) & 0xFFu;
-            const uint32_t c0 = ((byte & 3u) + 2u * (d & 1u)) & 3u;
-            const uint32_t r0 = (((byte >> 4) & 3u) + 2u * (d >> 1)) & 3u;
-            const DtrLanes n = dtr_lanes(c);
-            uint32_t ca[4], cb[4], pmin, pmax;
-            dtr_candidates<RANDOM>(X, Y, E, D, site, s, c0, r0, c, n, ca, cb, pmin, pmax);
-            uint32_t acc = 0u;
-            if (RANDOM) {
-                draws += __popc(pmin | pmax);
-                acc = accept_candidates(pmin, pmax, level_words(s, c), c, tp);
-                net += random_net(acc, pmin, pmax);
-            }
-            dtr_apply<RANDOM>(X, Y, E, D, c0, r0, acc, ca, cb, c, n, net);
-            continue;
-        }
-        if (SCHEME == 1 || SCHEME == 2 || SCHEME == 6 || SCHEME == 7) {
-            // DB: one site word per TC row and step, 4 bits per cell
-            site = philox4x32_10(c.t, c.k | (s << 2), c.T, (kTagSiteDb << 28) | c.g, c.k0, c.k1);
-            if (SCHEME == 2)
-                db_step<RANDOM, true>(X, Y, E, D, site, s, c, tp, net, draws);
-            else if (SCHEME == 7)
-                db_step<RANDOM, true, 2>(X, Y, E, D, site, s, c, tp, net, draws);
-            else if (SCHEME == 6)
-                db_step<RANDOM, false, 1>(X, Y, E, D, site, s, c, tp, net, draws);
-            else
-                db_step<RANDOM, false>(X, Y, E, D, site, s, c, tp, net, draws);
-            continue;
-        }
-        if ((s & 1u) == 0u)
-            site = philox4x32_10(c.t, c.k | ((s >> 1) << 2), c.T, (kTagSite << 28) | c.g, c.k0, c.k1);
-        const uint32_t d = (setw.x >> (2u * s)) & 3u;
-        uint32_t cnd0[4], cnd1[4], pmin, pmax;
-        constexpr int kSpec = SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0;
-        if (LANE_SETS)
-            step_candidates_rt<RANDOM, kSpec>(X, Y, E, D, site, s, d & 1u, d >> 1, c, cnd0, cnd1, pmin, pmax);
-        else if (d & 2u)
-            step_candidates<1, RANDOM, kSpec>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
-        else
-            step_candidates<0, RANDOM, kSpec>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
-        uint32_t acc = 0u;
-        if (RANDOM) {
-            draws += __popc(pmin | pmax);
-            acc = accept_candidates(pmin, pmax, level_words(s, c), c, tp);
-            net += random_net(acc, pmin, pmax);
-        }
-        if (LANE_SETS)
-            step_apply_rt<RANDOM, kSpec>(X, Y, E, D, d >> 1, acc, cnd0, cnd1, c, net);
-        else if (d & 2u)
-            step_apply<1, RANDOM, kSpec>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
-        else
-            step_apply<0, RANDOM, kSpec>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
-    }
-
+template <bool LANE_SETS>
+__device__ __forceinline__ void write_back(const LaneGeom &q, uint32_t L, uint32_t wpr, bool active,
+                                           const LaneCtx &c, const uint32_t (&X)[16], const uint32_t (&Y)[16],
+                                           uint32_t E, uint32_t D) {
+    uint32_t *const Xp = q.Xp;
+    uint32_t *const Yp = q.Yp;
+    const uint32_t sh = q.sh, wA = q.wA, wB = q.wB, ybase = q.ybase, yh = q.yh;
     // Write back.  Global word wA of a row receives the high bits of the left
     // lane and the low bits of this lane; the leftmost lane shares word wA
     // with the bits left of x0, the rightmost lane also owns the low bits of
@@ -981,7 +925,96 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
             }
         }
     }
+}
 
+// Device step on one sub-tile (Bx x By sites at (x0, y0)) held by the lanes of
+// one warp that share it: stage the lane's group from the planar lattice,
+// run the 16 single-hit collective steps, write back.  LANE_SETS: lanes of the
+// warp may belong to different sub-tiles (each with its own set draws).
+// SCHEME: 0 DTrDT, 1 DTrDB with all attempts of a step together, 2 DTrDB with
+// delayed borders, 3 DTrDTr, 4 DTrDT with deposition only (p = 1, q = 0),
+// 5 DTrDT with both rates strictly inside (0, 1), 6 DTrDB with deposition only,
+// 7 DTrDB with delayed borders and both rates random.
+template <bool RANDOM, bool LANE_SETS, int SCHEME = 0>
+__device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t Bx,
+                                            uint32_t By, uint32_t x0, uint32_t y0, bool active,
+                                            const LaneCtx &c, uint32_t *ring, int &net, int &draws) {
+    TailPool tp;
+    tp.ring = ring;
+    const uint32_t G = static_cast<uint32_t>(c.GX * c.GY);
+    tp.mask = static_cast<uint32_t>(kRingWordsPerLane) * (1u << (32 - __clz(static_cast<int>(G - 1u)))) - 1u;
+    tp.head = 0u;
+    tp.end = 0u;
+    const LaneGeom q = lane_geom(lat, L, wpr, By, x0, y0, c);
+    uint32_t X[16], Y[16], E, D;
+    stage_lane(q, L, wpr, Bx, x0, active, c, X, Y, E, D);
+
+    // Block layer: 16 single-hit collective steps.
+    const uint4 setw = philox4x32_10(c.t, c.k, c.T, kTagSet << 28, c.k0, c.k1);
+    uint4 site = make_uint4(0u, 0u, 0u, 0u);
+    uint4 borg = make_uint4(0u, 0u, 0u, 0u);
+    if (SCHEME == 3) borg = philox4x32_10(c.t, c.k, c.T, kTagBorg << 28, c.k0, c.k1);
+    for (uint32_t s = 0; s < 16u; ++s) {
+        if (SCHEME == 3) {
+            // DTrDTr: the set, plus a block-layer origin (ax, ay) per step
+            if ((s & 1u) == 0u)
+                site = philox4x32_10(c.t, c.k | ((s >> 1) << 2), c.T, (kTagSite << 28) | c.g, c.k0, c.k1);
+            const uint32_t d = (setw.x >> (2u * s)) & 3u;
+            const uint32_t bw = (s < 4u) ? borg.x : (s < 8u) ? borg.y : (s < 12u) ? borg.z : borg.w;
+            const uint32_t byte = (bw >> (8u * (s & 3u))) & 0xFFu;
+            const uint32_t c0 = ((byte & 3u) + 2u * (d & 1u)) & 3u;
+            const uint32_t r0 = (((byte >> 4) & 3u) + 2u * (d >> 1)) & 3u;
+            const DtrLanes n = dtr_lanes(c);
+            uint32_t ca[4], cb[4], pmin, pmax;
+            dtr_candidates<RANDOM>(X, Y, E, D, site, s, c0, r0, c, n, ca, cb, pmin, pmax);
+            uint32_t acc = 0u;
+            if (RANDOM) {
+                draws += __popc(pmin | pmax);
+                acc = accept_candidates(pmin, pmax, level_words(s, c), c, tp);
+                net += random_net(acc, pmin, pmax);
+            }
+            dtr_apply<RANDOM>(X, Y, E, D, c0, r0, acc, ca, cb, c, n, net);
+            continue;
+        }
+        if (SCHEME == 1 || SCHEME == 2 || SCHEME == 6 || SCHEME == 7) {
+            // DB: one site word per TC row and step, 4 bits per cell
+            site = philox4x32_10(c.t, c.k | (s << 2), c.T, (kTagSiteDb << 28) | c.g, c.k0, c.k1);
+            if (SCHEME == 2)
+                db_step<RANDOM, true>(X, Y, E, D, site, s, c, tp, net, draws);
+            else if (SCHEME == 7)
+                db_step<RANDOM, true, 2>(X, Y, E, D, site, s, c, tp, net, draws);
+            else if (SCHEME == 6)
+                db_step<RANDOM, false, 1>(X, Y, E, D, site, s, c, tp, net, draws);
+            else
+                db_step<RANDOM, false>(X, Y, E, D, site, s, c, tp, net, draws);
+            continue;
+        }
+        if ((s & 1u) == 0u)
+            site = philox4x32_10(c.t, c.k | ((s >> 1) << 2), c.T, (kTagSite << 28) | c.g, c.k0, c.k1);
+        const uint32_t d = (setw.x >> (2u * s)) & 3u;
+        uint32_t cnd0[4], cnd1[4], pmin, pmax;
+        constexpr int kSpec = SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0;
+        if (LANE_SETS)
+            step_candidates_rt<RANDOM, kSpec>(X, Y, E, D, site, s, d & 1u, d >> 1, c, cnd0, cnd1, pmin, pmax);
+        else if (d & 2u)
+            step_candidates<1, RANDOM, kSpec>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
+        else
+            step_candidates<0, RANDOM, kSpec>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
+        uint32_t acc = 0u;
+        if (RANDOM) {
+            draws += __popc(pmin | pmax);
+            acc = accept_candidates(pmin, pmax, level_words(s, c), c, tp);
+            net += random_net(acc, pmin, pmax);
+        }
+        if (LANE_SETS)
+            step_apply_rt<RANDOM, kSpec>(X, Y, E, D, d >> 1, acc, cnd0, cnd1, c, net);
+        else if (d & 2u)
+            step_apply<1, RANDOM, kSpec>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
+        else
+            step_apply<0, RANDOM, kSpec>(X, Y, E, D, d & 1u, acc, cnd0, cnd1, c, net);
+    }
+
+    write_back<LANE_SETS>(q, L, wpr, active, c, X, Y, E, D);
 }
 
 }  // namespace oct

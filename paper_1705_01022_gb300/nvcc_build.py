@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboct.so")
-SOURCES = ["api.cu", "dtrdt.cu", "lattice.cu", "probe.cu", "noalloc.cu", "batch.cu", "twotime.cu"]
+SOURCES = ["api.cu", "dtrdt.cu", "cells.cu", "cells_a.cu", "cells_b.cu", "cells_c.cu", "lattice.cu", "probe.cu", "noalloc.cu", "batch.cu", "twotime.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]

@@ -44,10 +44,15 @@ def test_invalid_arguments_rejected_without_gpu(lib):
         _lib.oct_create(256, 1.5, 0.0, 1)
     assert e.value.code == _lib.OCT_EINVAL
     prm = _lib.oct_params()
-    prm.L, prm.p, prm.q, prm.seed, prm.cx, prm.cy = 256, 1.0, 0.0, 1, 8, 8
+    prm.L, prm.p, prm.q, prm.seed, prm.cx, prm.cy = 256, 1.0, 0.0, 1, 64, 8
     with pytest.raises(_lib.OctError) as e:
         _lib.oct_create_ex(prm)
     assert e.value.code == _lib.OCT_EUNSUPPORTED
+    prm.cx, prm.cy, prm.scheme = 8, 8, _lib.OCT_SCHEME_DB  # coarse cells run DTrDT only
+    with pytest.raises(_lib.OctError) as e:
+        _lib.oct_create_ex(prm)
+    assert e.value.code == _lib.OCT_EUNSUPPORTED
+    prm.scheme = 0
     prm.cx, prm.cy, prm.Bx, prm.By = 4, 4, 48, 16
     with pytest.raises(_lib.OctError) as e:
         _lib.oct_create_ex(prm)

@@ -4,11 +4,16 @@
   near the paper's beta = 0.2414(2) (Sec. 2) at L = 4096 over t in [100, 1000]
   (finite-time corrections are expected, Sec. 4.2).
 * EW (p = q = 0.5): roughening is logarithmic, so beta_eff is small.
-* W^2(t) against true random-sequential updating (oracle O1): the paper
-  reports that fine decomposition lowers the roughness prefactor (Sec. 4.2);
-  with 4 x 4 thread cells the GPU's W^2 sits a few percent below RS at every
-  t.  The test requires that band and prints the z-scores rather than
-  requiring |z| < 3, which the method does not satisfy at high statistics.
+* W^2(t) against true random-sequential updating (oracle O1), KPZ, L = 512,
+  t = 4, 16, 48 MCS, 48 realizations on each side.  The paper reports that
+  finer block-layer domains lower the roughness prefactor (Sec. 4.2) and that
+  runs with coarse decomposition are indistinguishable from sequential ones
+  (Sec. 5).  So: at the coarsest cells the GPU implements (32 x 16 sites,
+  the paper's TC=3,2) W^2 agrees with RS within 3 sigma at t = 16 and 48 and
+  lies within 0.5 % of it at t = 4 (z there is printed: about -5); the
+  GPU/RS ratio rises with the cell size (4x4 < 8x8 < 16x16 < 32x16); and at
+  4 x 4 cells the GPU does not agree with RS within 3 sigma, a known
+  deviation of the method at fine cells (strict xfail, z printed).
 """
 import math
 
@@ -57,18 +62,72 @@ def test_ew_roughening_is_logarithmic(g):
     assert 0.5 < d2 / d1 < 1.5, (d1, d2)
 
 
-def test_roughness_against_sequential_rs(g, oracle):
-    L, n, ts = 512, 16, [4, 16, 48]
-    gpu = _w2_series(g, L, 1.0, 0.0, range(100, 100 + n), ts)
-    rs = np.zeros((n, len(ts)))
-    for i in range(n):
-        X, Y = oracle.flat(L)
-        t = 0
-        for j, tt in enumerate(ts):
-            oracle.seq_rs(X, Y, 1.0, 0.0, 5000 + i, t, tt - t)
-            t = tt
-            rs[i, j] = oracle.w2(X, Y)
+L_RS, N_RS, TS_RS = 512, 48, [4, 16, 48]
+
+
+def _rs_job(i):
+    import oracle
+    oracle.build()
+    X, Y = oracle.flat(L_RS)
+    out, t = [], 0
+    for tt in TS_RS:
+        oracle.seq_rs(X, Y, 1.0, 0.0, 5000 + i, t, tt - t)
+        t = tt
+        out.append(oracle.w2(X, Y))
+    return out
+
+
+@pytest.fixture(scope="module")
+def rs_w2():
+    """W^2(t) of N_RS sequential-RS realizations (O1) on all host cores."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as pool:
+        return np.array(pool.map(_rs_job, range(N_RS)))
+
+
+def _gpu_w2(g, cx, cy):
+    out = np.zeros((N_RS, len(TS_RS)))
+    for i in range(N_RS):
+        with g.Simulation(L_RS, 1.0, 0.0, 100 + i, Bx=64, By=64, cx=cx, cy=cy) as sim:
+            t = 0
+            for j, tt in enumerate(TS_RS):
+                sim.run(tt - t)
+                t = tt
+                out[i, j] = sim.measure().w2
+    return out
+
+
+def _z(gpu, rs):
     ratio = gpu.mean(0) / rs.mean(0)
-    z = (gpu.mean(0) - rs.mean(0)) / np.sqrt(gpu.var(0, ddof=1) / n + rs.var(0, ddof=1) / n)
-    print("t", ts, "GPU/RS W^2 ratio", np.round(ratio, 4), "z", np.round(z, 2))
-    assert np.all((ratio > 0.92) & (ratio < 1.0)), ratio
+    z = (gpu.mean(0) - rs.mean(0)) / np.sqrt(gpu.var(0, ddof=1) / len(gpu) + rs.var(0, ddof=1) / len(rs))
+    return ratio, z
+
+
+def test_coarse_cells_agree_with_sequential_rs(g, rs_w2):
+    """32 x 16-site cells: |z| < 3 in the growth regime (t = 16, 48).  At
+    t = 4, where 48 realizations resolve W^2 to 0.05 %, the GPU lies 0.26 %
+    below RS (z = -5.0): the prefactor shift of Sec. 4.2 has not vanished at
+    these cells, only shrunk; it must stay below 0.5 %."""
+    ratio, z = _z(_gpu_w2(g, 32, 16), rs_w2)
+    print("TC 32x16: t", TS_RS, "GPU/RS W^2", np.round(ratio, 4), "z", np.round(z, 2))
+    assert np.all(np.abs(z[1:]) < 3.0), (ratio, z)
+    assert abs(ratio[0] - 1.0) < 0.005, (ratio, z)
+
+
+def test_prefactor_rises_with_cell_size(g, rs_w2):
+    ratios = []
+    for cx, cy in ((4, 4), (8, 8), (16, 16), (32, 16)):
+        ratio, z = _z(_gpu_w2(g, cx, cy), rs_w2)
+        print(f"TC {cx}x{cy}: t", TS_RS, "GPU/RS W^2", np.round(ratio, 4), "z", np.round(z, 2))
+        ratios.append(ratio)
+    r = np.array(ratios)
+    assert np.all(r[:-1] < r[1:]), r  # monotone in the cell size at every t
+    assert np.all((r[0] > 0.92) & (r[0] < 1.0)), r[0]
+
+
+@pytest.mark.xfail(strict=True, reason="4x4-site cells lower the W^2 prefactor by about 3.5 % against RS "
+                   "(z about -20 at 48 realizations): the finer-domain effect of Sec. 4.2")
+def test_fine_cells_agree_with_sequential_rs(g, rs_w2):
+    ratio, z = _z(_gpu_w2(g, 4, 4), rs_w2)
+    print("TC 4x4: t", TS_RS, "GPU/RS W^2", np.round(ratio, 4), "z", np.round(z, 2))
+    assert np.all(np.abs(z) < 3.0), (ratio, z)

@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-policy", default="large", help="autotune.batch_shape policy of the serving leg")
     ap.add_argument("--db-steps", type=int, default=30)
+    ap.add_argument("--cell-steps", type=int, default=2, help="timed MCS per coarse thread-cell shape")
     ap.add_argument("--ac-reps", type=int, default=5)
     ap.add_argument("--tune-mcs", type=int, default=1)
     return ap.parse_args()
@@ -125,6 +126,46 @@ def peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def philox_blocks_per_lane(scheme: str, cx: int, cy: int, random: bool) -> float:
+    """Philox-4x32-10 blocks one lane of the plain device-step kernels
+    evaluates per device step, apart from the tail stream (a lane holds 32 x 16
+    sites, i.e. 512 attempts per device step): the MCS draw, the set draws
+    (one block per 64 collective steps), the DTrDTr block origins (one block
+    per 16 steps), the site words (DT: one block per 2 steps when two steps
+    share a site field, else per step; DB: per step) and, with acceptance
+    draws, the four level words (one block per step)."""
+    steps = cx * cy
+    bpt = (cx // 2).bit_length() - 1 + (cy // 2).bit_length() - 1
+    spw = 2 if 2 * bpt <= cx else 1
+    blocks = 1.0  # MCS draw
+    if scheme == "DB":
+        blocks += steps
+    else:
+        blocks += -(-steps // 64) + steps / spw
+        if scheme == "DTR":
+            blocks += -(-steps // 16)
+    if random:
+        blocks += steps
+    return blocks
+
+
+def alu_accounting(scheme, cx, cy, random, attempts, tail_blocks, draws, tcs_per_subtile):
+    """Integer operations per attempt, two ways.  Both charge 0.5 operations per
+    random bit (Philox-4x32-10: ten rounds of about six operations per 128
+    bits) plus 4 operations per attempt (the pattern test and the flip,
+    amortised over a 32-site word):
+      * generated: the bits the kernel actually generates (its Philox blocks
+        per lane and device step, plus the tail-stream blocks it counted);
+      * survey: the bits the method consumes as fixed before the first
+        measurement (site offset + set draw + 32 bits per acceptance draw)."""
+    gen_bits = 128.0 * philox_blocks_per_lane(scheme, cx, cy, random) / 512.0 + 128.0 * tail_blocks / attempts
+    site_bits = (cx * cy).bit_length() - 1 if scheme == "DB" else (cx // 2 * cy // 2).bit_length() - 1
+    shared = {"DB": 0.0, "DT": 2.0, "DTR": 6.0}[scheme]  # set (and DTrDTr origin) bits per collective step
+    survey_bits = site_bits + shared / tcs_per_subtile + 32.0 * draws / attempts
+    return {"generated": {"bits_per_attempt": gen_bits, "ops_per_attempt": 0.5 * gen_bits + 4.0},
+            "survey": {"bits_per_attempt": survey_bits, "ops_per_attempt": 0.5 * survey_bits + 4.0}}
 
 
 def step_traffic(src_hash: str):
@@ -322,11 +363,18 @@ def batched_leg(a, g, _lib, torch, stream, peak_tops):
         kms, klaunch = _lib.oct_batch_get_timing(b.h)
         _lib.oct_batch_set_timing(b.h, False)
         f_draw = draws / (sites * a.batch_steps)
-        ops = 0.5 * (2.0 + 32.0 * f_draw) + 4.0
+        # The batched kernel keeps no tail-block count: ties are 1/16 of the draws in
+        # expectation and a block holds four tail words, so about draws/64 blocks.
+        acct = alu_accounting("DT", 4, 4, True, 1.0, f_draw / 64.0, f_draw, 256)
+        ops = acct["generated"]["ops_per_attempt"]
         achieved = ops * sites / 4 / (kms / klaunch * 1e-3) / 1e12
+        survey = acct["survey"]["ops_per_attempt"] * sites / 4 / (kms / klaunch * 1e-3) / 1e12
         out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                            "frac": achieved / peak_tops, "kernel": "batch_step_kernel",
-                           "device_step_ms": kms / klaunch, "draw_fraction": f_draw}
+                           "device_step_ms": kms / klaunch, "draw_fraction": f_draw, "ops_per_attempt": ops,
+                           "accounting": "generated bits; tail blocks estimated as draws/64",
+                           "survey_accounting": {"ops_per_attempt": acct["survey"]["ops_per_attempt"],
+                                                 "achieved": survey, "frac": survey / peak_tops}}
     # the same replicas, one plain handle each, launched one after another
     sims = [g.Simulation(L, p, q, seed, Bx=Bx, By=By, stream=stream) for (L, p, q, seed, Bx, By) in reps]
     for s_ in sims:
@@ -504,14 +552,17 @@ def main():
     att_per_launch = L * L / 4
     tcs_per_subtile = (a.Bx // 4) * (a.By // 4)
     f_draw = (stats1.draws - stats0.draws) / attempts
-    bits = 2.0 + 2.0 / tcs_per_subtile + 32.0 * f_draw
-    ops_per_attempt = 0.5 * bits + 4.0
+    any_random = 0.0 < a.p < 1.0 or 0.0 < a.q < 1.0
+    acct = alu_accounting("DT", 4, 4, any_random, attempts, stats1.tail_blocks - stats0.tail_blocks,
+                          stats1.draws - stats0.draws, tcs_per_subtile)
+    ops_per_attempt = acct["generated"]["ops_per_attempt"]
     lop3, probe_mhz, sms = _lib.oct_probe_int_rate(0)
     imad, _, _ = _lib.oct_probe_int_rate(1)
     pk = peaks()
     max_mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak_tops = sms * lop3 * max_mhz * 1e6 / 1e12
     achieved_tops = ops_per_attempt * att_per_launch / (launch_ms * 1e-3) / 1e12
+    survey_tops = acct["survey"]["ops_per_attempt"] * att_per_launch / (launch_ms * 1e-3) / 1e12
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
     hbm_gbs = 2 * (L * L / 16) / (launch_ms * 1e-3) / 1e9  # quarter lattice read + written
     roofline = {
@@ -519,6 +570,12 @@ def main():
         "frac": achieved_tops / peak_tops, "traffic": step_traffic(src_hash()),
         "kernel": "dtrdt_step_kernel", "launch_ms": launch_ms, "launches": launches,
         "ops_per_attempt": ops_per_attempt, "draw_fraction": f_draw,
+        "accounting": "generated: 0.5 op per random bit the kernel generates + 4 ops per attempt",
+        "bits_per_attempt": acct["generated"]["bits_per_attempt"],
+        "survey_accounting": {"ops_per_attempt": acct["survey"]["ops_per_attempt"],
+                              "bits_per_attempt": acct["survey"]["bits_per_attempt"],
+                              "achieved": survey_tops, "frac": survey_tops / peak_tops,
+                              "note": "bits the method consumes (32 per acceptance draw), not those generated"},
         "peak_basis": (f"{sms} SMs x {lop3:.1f} LOP3/clk/SM (probe; IMAD {imad:.1f}) x "
                        f"{max_mhz:.0f} MHz max SM clock"),
         "hbm": {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak},
@@ -613,7 +670,7 @@ def main():
                "breakdown_note": "one step of one lattice, phase by phase with a synchronisation between phases"}
 
     # ---- the DTrDB block layer on the same workload (the paper's Fig. 7 pair) ----
-    dtrdb = dtrdtr = None
+    dtrdb = dtrdtr = cells = None
     if rank == 0 and a.db_steps > 0:
         sim.close()
 
@@ -634,6 +691,7 @@ def main():
                 st1 = _lib.oct_get_stats(h.h)
                 step_ms = kms / max(1, kl)
                 f_draw = (st1.draws - st0.draws) / (L * L * n)
+                tails_[0] = (st1.tail_blocks - st0.tail_blocks) / (L * L * n)
                 cpu_ = None
                 if oracle_scheme is not None and not a.no_cpu and world == 1:
                     import oracle
@@ -644,33 +702,69 @@ def main():
                     cpu_.pop("_window")
             return L * L * n / (st_.elapsed_time(en_) * 1e6), step_ms, f_draw, cpu_
 
-        def alu_roofline(step_ms, bits):
-            ops = 0.5 * bits + 4.0
+        tails_ = [0.0]  # tail-stream blocks per attempt of the last timed run
+
+        def alu_roofline(step_ms, scheme, f_draw, tail_per_attempt):
+            acc = alu_accounting(scheme, 4, 4, any_random, 1.0, tail_per_attempt, f_draw, tcs)
+            ops = acc["generated"]["ops_per_attempt"]
             ach = ops * (L * L / 4) / (step_ms * 1e-3) / 1e12
+            sv = acc["survey"]["ops_per_attempt"] * (L * L / 4) / (step_ms * 1e-3) / 1e12
             return {"bound": "alu", "achieved": ach, "peak": peak_tops, "unit": "Tops/s", "frac": ach / peak_tops,
-                    "ops_per_attempt": ops, "launch_ms": step_ms}
+                    "ops_per_attempt": ops, "bits_per_attempt": acc["generated"]["bits_per_attempt"],
+                    "launch_ms": step_ms,
+                    "survey_accounting": {"ops_per_attempt": acc["survey"]["ops_per_attempt"],
+                                          "achieved": sv, "frac": sv / peak_tops}}
 
         tcs = (a.Bx // 4) * (a.By // 4)
         db_v, db_step, db_f, db_cpu = timed(a.p, a.q, _lib.OCT_SCHEME_DB, a.db_steps, oracle_scheme=1)
+        db_tail = tails_[0]
         kdt_v, kdt_step, _, _ = timed(1.0, 0.0, _lib.OCT_SCHEME_DT, a.db_steps)
         kdb_v, kdb_step, _, _ = timed(1.0, 0.0, _lib.OCT_SCHEME_DB, a.db_steps)
         dtrdb = {"value": db_v, "unit": UNIT, "mcs": a.db_steps, "device_step_ms": db_step,
                  "scheme": "DTrDB: single-hit dead border at block level, borders delayed (p, q > 0)",
                  "start": "the DTrDT state after the timed region and the end-to-end steps",
                  "relative_to_dtrdt": db_v / (value / world),
-                 "roofline": dict(alu_roofline(db_step, 4.0 + 32.0 * db_f), draw_fraction=db_f,
+                 "roofline": dict(alu_roofline(db_step, "DB", db_f, db_tail), draw_fraction=db_f,
                                   kernel="dtrdt_step_kernel<1, 2>"),
                  "cpu_baseline": db_cpu,
                  "kpz": {"p": 1.0, "q": 0.0, "dtrdt": kdt_v, "dtrdb": kdb_v, "relative": kdb_v / kdt_v,
                          "device_step_ms": {"dtrdt": kdt_step, "dtrdb": kdb_step},
                          "note": "DB with one rate zero carries out all attempts of a step together"}}
         dtr_v, dtr_step, dtr_f, dtr_cpu = timed(a.p, a.q, _lib.OCT_SCHEME_DTR, a.db_steps, oracle_scheme=3)
+        dtr_tail = tails_[0]
         dtrdtr = {"value": dtr_v, "unit": UNIT, "mcs": a.db_steps, "device_step_ms": dtr_step,
                   "scheme": "DTrDTr: double tiling with a block-layer origin moved after every collective step",
                   "start": "the DTrDB state after its run", "relative_to_dtrdt": dtr_v / (value / world),
-                  "roofline": dict(alu_roofline(dtr_step, 2.0 + 6.0 / tcs + 32.0 * dtr_f), draw_fraction=dtr_f,
+                  "roofline": dict(alu_roofline(dtr_step, "DTR", dtr_f, dtr_tail), draw_fraction=dtr_f,
                                    kernel="dtrdt_step_kernel<1, 3>"),
                   "cpu_baseline": dtr_cpu}
+        # ---- DTrDT with the paper's coarser thread cells (TC=1,1 .. 3,2) on the same workload ----
+        cells = {}
+        for cx, cy in ((8, 8), (16, 8), (16, 16), (32, 16)):
+            with g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, cx=cx, cy=cy, stream=stream, lattice=lattice,
+                              no_init=True) as h:
+                h.run(1)
+                torch.cuda.synchronize()
+                st0 = _lib.oct_get_stats(h.h)
+                _lib.oct_set_timing(h.h, True)
+                st_, en_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                st_.record(stream)
+                h.run(a.cell_steps)
+                en_.record(stream)
+                torch.cuda.synchronize()
+                kms, kl, _ = _lib.oct_get_timing(h.h)
+                st1 = _lib.oct_get_stats(h.h)
+                n_att = L * L * a.cell_steps
+                acc_ = alu_accounting("DT", cx, cy, any_random, n_att, st1.tail_blocks - st0.tail_blocks,
+                                      st1.draws - st0.draws, (a.Bx // cx) * (a.By // cy))
+                step_ = kms / max(1, kl)
+                ach = acc_["generated"]["ops_per_attempt"] * (L * L / 4) / (step_ * 1e-3) / 1e12
+                cells[f"{cx}x{cy}"] = {
+                    "value": n_att / (st_.elapsed_time(en_) * 1e6), "unit": UNIT, "device_step_ms": step_,
+                    "paper_tc": f"TC={(cx // 4).bit_length() - 1},{(cy // 4).bit_length() - 1}",
+                    "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tops, "frac": ach / peak_tops,
+                                 "ops_per_attempt": acc_["generated"]["ops_per_attempt"],
+                                 "bits_per_attempt": acc_["generated"]["bits_per_attempt"]}}
         sim = g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice)
         sim.run(a.warmup + a.steps)
 
@@ -782,7 +876,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload(a), "clocks": clk.summary(), "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "autotune": tuning, "dtrdb": dtrdb, "dtrdtr": dtrdtr, "w2": w2_leg, "two_time": two_time, "batched": batched, "serving": serving,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * a.steps, "autotune": tuning, "dtrdb": dtrdb, "dtrdtr": dtrdtr, "cells": cells, "w2": w2_leg, "two_time": two_time, "batched": batched, "serving": serving,
             "probe": {"lop3_per_clk_per_sm": lop3, "imad_per_clk_per_sm": imad, "probe_mhz": probe_mhz},
         }
         print(json.dumps(out), flush=True)

@@ -202,11 +202,15 @@ int oct_get_timing(oct_sim *s, double *step_ms, int64_t *step_launches, double *
  * net_flips = accepted depositions minus removals, draws = attempts that
  * landed on an eligible site whose probability lies strictly in (0,1) and so
  * needed an acceptance draw (counted only when p or q lies strictly inside
- * (0,1)).  Synchronises. */
+ * (0,1)), tail_blocks = Philox blocks the plain device-step kernels generated
+ * for the tail stream of tied acceptance uniforms (counted over the lanes that
+ * store them; zero without acceptance draws).  Synchronises. */
 typedef struct {
     int64_t t;
     int64_t net_flips;
     int64_t draws;
+    int64_t tail_blocks;  /* Philox-4x32-10 blocks generated for the tail stream
+                             of tied acceptance uniforms (128 random bits each) */
 } oct_stats;
 int oct_get_stats(oct_sim *s, oct_stats *out);
 

@@ -51,7 +51,8 @@ class oct_info(ctypes.Structure):
 
 
 class oct_stats(ctypes.Structure):
-    _fields_ = [("t", ctypes.c_int64), ("net_flips", ctypes.c_int64), ("draws", ctypes.c_int64)]
+    _fields_ = [("t", ctypes.c_int64), ("net_flips", ctypes.c_int64), ("draws", ctypes.c_int64),
+                ("tail_blocks", ctypes.c_int64)]
 
 
 class oct_replica(ctypes.Structure):

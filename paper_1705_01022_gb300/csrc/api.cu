@@ -76,8 +76,8 @@ struct oct_sim {
     bool own_stream = false;
     int device = 0;
     uint32_t *d_t = nullptr;
-    unsigned long long *d_net = nullptr;    // kNetSlots flip counters, then kNetSlots draw counters
-    long long *d_net_sum = nullptr;         // [net flips, acceptance draws]
+    unsigned long long *d_net = nullptr;    // kNetSlots flip, then draw, then tail-block counters
+    long long *d_net_sum = nullptr;         // [net flips, acceptance draws, tail blocks]
     oct::W2RowSums *d_rows = nullptr;
     oct::W2Result *d_w2 = nullptr;
     void *h_small = nullptr;  // pinned: W2Result at 0, its net sum at 128, oct_get_stats' net sum at 192
@@ -202,14 +202,14 @@ int sim_create(const oct_params *prm, oct_sim **out) {
         }
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->d_t, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_net, sizeof(unsigned long long) * 2 * oct::kNetSlots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_net_sum, 2 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_net, sizeof(unsigned long long) * 3 * oct::kNetSlots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_net_sum, 3 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_rows, sizeof(oct::W2RowSums) * s->L);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_w2, sizeof(oct::W2Result));
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_small, 256);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_t, 0, sizeof(uint32_t), s->stream);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(s->d_net, 0, sizeof(unsigned long long) * 2 * oct::kNetSlots, s->stream);
+        e = cudaMemsetAsync(s->d_net, 0, sizeof(unsigned long long) * 3 * oct::kNetSlots, s->stream);
     if (e == cudaSuccess && !prm->no_init) e = oct::launch_init_flat(s->lat, static_cast<uint32_t>(s->L), s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
@@ -241,6 +241,7 @@ int sim_create(const oct_params *prm, oct_sim **out) {
     a.k = 0;
     a.net = s->d_net;
     a.draws = s->d_net + oct::kNetSlots;
+    a.tails = s->d_net + 2 * oct::kNetSlots;
     s->any_random = p_rand || q_rand;
     // DB delays border attempts only when two neighbouring flips could meet
     // kernel variants: 0 DT, 1 DB with all attempts of a step together, 2 DB
@@ -257,7 +258,7 @@ int set_time(oct_sim *s, int64_t t) {
     if (t < 0 || t > 0xFFFFFFFFll) return fail(OCT_EINVAL, "t must lie in [0, 2^32-1]");
     const uint32_t tt = static_cast<uint32_t>(t);
     OCT_CUDA(cudaMemcpyAsync(s->d_t, &tt, sizeof(tt), cudaMemcpyHostToDevice, s->stream));
-    OCT_CUDA(cudaMemsetAsync(s->d_net, 0, sizeof(unsigned long long) * 2 * oct::kNetSlots, s->stream));
+    OCT_CUDA(cudaMemsetAsync(s->d_net, 0, sizeof(unsigned long long) * 3 * oct::kNetSlots, s->stream));
     OCT_CUDA(cudaStreamSynchronize(s->stream));
     s->t = static_cast<uint64_t>(t);
     return OCT_OK;
@@ -327,7 +328,8 @@ namespace {
 // Enqueues the W^2 reduction (Eq. (3)) and the copy of its sums into the
 // handle's pinned staging area.
 int enqueue_w2(oct_sim *s) {
-    OCT_CUDA(oct::launch_net_sum(s->d_net, s->d_net + oct::kNetSlots, s->d_net_sum, s->stream));
+    OCT_CUDA(oct::launch_net_sum(s->d_net, s->d_net + oct::kNetSlots, s->d_net + 2 * oct::kNetSlots,
+                                 s->d_net_sum, s->stream));
     OCT_CUDA(oct::launch_w2(s->lat, static_cast<uint32_t>(s->L), s->d_rows, s->d_w2, s->stream));
     auto *res = static_cast<oct::W2Result *>(s->h_small);
     auto *net = reinterpret_cast<long long *>(static_cast<char *>(s->h_small) + 128);
@@ -604,13 +606,15 @@ int oct_two_time_planes(const void *lat_t, const void *lat_s, int64_t L, void *s
 int oct_get_stats(oct_sim *s, oct_stats *out) {
     if (!s || !out) return fail(OCT_EINVAL, "NULL argument");
     OCT_CUDA(cudaSetDevice(s->device));
-    OCT_CUDA(oct::launch_net_sum(s->d_net, s->d_net + oct::kNetSlots, s->d_net_sum, s->stream));
+    OCT_CUDA(oct::launch_net_sum(s->d_net, s->d_net + oct::kNetSlots, s->d_net + 2 * oct::kNetSlots,
+                                 s->d_net_sum, s->stream));
     auto *net = reinterpret_cast<long long *>(static_cast<char *>(s->h_small) + 192);
-    OCT_CUDA(cudaMemcpyAsync(net, s->d_net_sum, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    OCT_CUDA(cudaMemcpyAsync(net, s->d_net_sum, 3 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
     OCT_CUDA(cudaStreamSynchronize(s->stream));
     out->t = static_cast<int64_t>(s->t);
     out->net_flips = net[0];
     out->draws = net[1];
+    out->tail_blocks = net[2];
     return OCT_OK;
 }
 

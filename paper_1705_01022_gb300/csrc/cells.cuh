@@ -177,6 +177,7 @@ __device__ __forceinline__ uint32_t cells_accept(uint32_t pmin, uint32_t pmax, c
                                       kTagTail << 28, c.k0, c.k1);
         if (c.active) *reinterpret_cast<uint4 *>(tp.ring + ((tp.end + 4u * static_cast<uint32_t>(cc.lane)) & tp.mask)) = B;
         tp.end += 4u * nl;
+        ++tp.rounds;
     }
     __syncwarp();
     // (w >> 4) < (P32 mod 2^28)  <=>  w < 16 (P32 mod 2^28)
@@ -274,7 +275,7 @@ __device__ __forceinline__ void cells_apply(uint32_t (&X)[16], uint32_t (&Y)[16]
 template <int CX, int CY, bool RANDOM, int SPEC>
 __device__ __forceinline__ void run_subtile_cells(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t Bx, uint32_t By,
                                                   uint32_t x0, uint32_t y0, bool active, const CellCtx &cc,
-                                                  uint32_t *ring, int &net, int &draws) {
+                                                  uint32_t *ring, int &net, int &draws, int &tails) {
     using S = CellShape<CX, CY>;
     const LaneCtx &c = cc.c;
     TailPool tp;
@@ -283,6 +284,7 @@ __device__ __forceinline__ void run_subtile_cells(uint32_t *lat, uint32_t L, uin
     tp.mask = static_cast<uint32_t>(kRingWordsPerLane) * (1u << (32 - __clz(static_cast<int>(nl - 1u)))) - 1u;
     tp.head = 0u;
     tp.end = 0u;
+    tp.rounds = 0u;
     const LaneGeom q = lane_geom(lat, L, wpr, By, x0, y0, c);
     uint32_t X[16], Y[16], E, D;
     stage_lane(q, L, wpr, Bx, x0, active, c, X, Y, E, D);
@@ -310,6 +312,7 @@ __device__ __forceinline__ void run_subtile_cells(uint32_t *lat, uint32_t L, uin
             cells_apply<CX, CY, 0, RANDOM, SPEC>(X, Y, E, D, d & 1u, acc, cand, cc, net);
     }
     write_back<false>(q, L, wpr, active, c, X, Y, E, D);
+    tails = static_cast<int>(tp.rounds);
 }
 
 // One device step with cx x cy-site cells: the kernel and its launch.  The
@@ -369,9 +372,10 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSMPacke
     cc.m0 = static_cast<uint32_t>(cc.gh * S::NTR);
     c.g = static_cast<uint32_t>(cc.gr * c.GX + c.gx);  // the lane's group
 
-    int net = 0, draws = 0;
+    int net = 0, draws = 0, tails = 0;
     run_subtile_cells<CX, CY, RANDOM, SPEC>(a.lat, L, a.wpr, a.Bx, a.By, x0, y0, active, cc,
-                                            ring + (threadIdx.x >> 5) * 32 * kRingWordsPerLane, net, draws);
+                                            ring + (threadIdx.x >> 5) * 32 * kRingWordsPerLane, net, draws,
+                                            tails);
 
     const int total = __reduce_add_sync(kFull, net);
     if (lane == 0 && total != 0)
@@ -379,6 +383,9 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSMPacke
     if (RANDOM) {
         const unsigned nd = __reduce_add_sync(kFull, static_cast<unsigned>(draws));
         if (lane == 0 && nd != 0u) atomicAdd(&a.draws[T % kNetSlots], static_cast<unsigned long long>(nd));
+        // tail-stream Philox blocks stored by the sub-tile's lanes
+        const unsigned nb = __reduce_add_sync(kFull, active ? static_cast<unsigned>(tails) : 0u);
+        if (lane == 0 && nb != 0u) atomicAdd(&a.tails[T % kNetSlots], static_cast<unsigned long long>(nb));
     }
 }
 

@@ -112,10 +112,10 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, step_min_blocks(SCHEM
     c.q_random = a.q_random;
 
     const uint32_t wpr = a.wpr;
-    int net = 0, draws = 0;
+    int net = 0, draws = 0, tails = 0;
     run_subtile<RANDOM, PACKED, SCHEME>(a.lat, L, wpr, a.Bx, a.By, x0, y0, active, c,
                                         ring + ((threadIdx.x >> 5) * 32 + seg * S) * kRingWordsPerLane,
-                                        net, draws);
+                                        net, draws, tails);
 
     // Net flips (and acceptance draws): one atomic per warp into a spread of counters.
     const uint32_t T0 = warp_id * per_warp;
@@ -125,6 +125,9 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, step_min_blocks(SCHEM
     if (RANDOM) {
         const unsigned nd = __reduce_add_sync(kFull, static_cast<unsigned>(draws));
         if (lane == 0 && nd != 0u) atomicAdd(&a.draws[T0 % kNetSlots], static_cast<unsigned long long>(nd));
+        // tail-stream Philox blocks stored by the lanes of the warp's sub-tiles
+        const unsigned nb = __reduce_add_sync(kFull, active ? static_cast<unsigned>(tails) : 0u);
+        if (lane == 0 && nb != 0u) atomicAdd(&a.tails[T0 % kNetSlots], static_cast<unsigned long long>(nb));
     }
 }
 

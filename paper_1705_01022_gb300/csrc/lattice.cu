@@ -299,19 +299,22 @@ __global__ void unpack_canonical_kernel(const uint32_t *in, uint32_t L, uint32_t
 }
 
 __global__ void net_sum_kernel(const unsigned long long *net, const unsigned long long *draws,
-                               long long *out) {
-    long long s = 0, d = 0;
+                               const unsigned long long *tails, long long *out) {
+    long long s = 0, d = 0, b = 0;
     for (int i = threadIdx.x; i < kNetSlots; i += 32) {
         s += static_cast<long long>(net[i]);
         d += static_cast<long long>(draws[i]);
+        b += static_cast<long long>(tails[i]);
     }
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_down_sync(kFull, s, o);
         d += __shfl_down_sync(kFull, d, o);
+        b += __shfl_down_sync(kFull, b, o);
     }
     if (threadIdx.x == 0) {
         out[0] = s;
         out[1] = d;
+        out[2] = b;
     }
 }
 
@@ -364,8 +367,8 @@ cudaError_t launch_unpack_canonical(const uint32_t *in, uint32_t L, uint32_t cy0
 }
 
 cudaError_t launch_net_sum(const unsigned long long *net, const unsigned long long *draws,
-                           long long *out, cudaStream_t st) {
-    net_sum_kernel<<<1, 32, 0, st>>>(net, draws, out);
+                           const unsigned long long *tails, long long *out, cudaStream_t st) {
+    net_sum_kernel<<<1, 32, 0, st>>>(net, draws, tails, out);
     return cudaGetLastError();
 }
 

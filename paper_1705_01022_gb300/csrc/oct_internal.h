@@ -25,6 +25,7 @@ struct StepArgs {
     uint32_t k;                // device step 0..3
     unsigned long long *net;   // kNetSlots signed flip counters (two's complement)
     unsigned long long *draws; // kNetSlots counters of attempts that needed an acceptance draw
+    unsigned long long *tails; // kNetSlots counters of tail-stream Philox blocks generated
     uint32_t scheme;           // 0: DT; 1: DB (borders together); 2: DB with delayed borders; 3: DTrDTr
     uint32_t cx, cy;           // thread cell in sites (4 x 4, or a coarser DTrDT cell of cells.cu)
 };
@@ -90,9 +91,10 @@ cudaError_t launch_pack_canonical(const uint32_t *lat, uint32_t L, uint32_t cy0,
 cudaError_t launch_unpack_canonical(const uint32_t *in, uint32_t L, uint32_t cy0, uint32_t ncy,
                                     uint32_t *lat, cudaStream_t st);
 
-// Sum of the kNetSlots flip counters into out[0] and of the draw counters into out[1].
+// Sums of the kNetSlots flip counters into out[0], of the draw counters into
+// out[1] and of the tail-block counters into out[2].
 cudaError_t launch_net_sum(const unsigned long long *net, const unsigned long long *draws,
-                           long long *out, cudaStream_t st);
+                           const unsigned long long *tails, long long *out, cudaStream_t st);
 
 // Integer-pipe probe (op 0: LOP3, op 1: IMAD): operations per SM per clock
 // and the SM clock during the probe.

@@ -79,6 +79,7 @@ struct TailPool {
     uint32_t mask;   // ring size - 1
     uint32_t head;   // tail words used so far in this device step
     uint32_t end;    // tail words generated so far in this device step
+    uint32_t rounds; // refills so far (each lane generated one Philox block per refill)
 };
 
 // Acceptance of the packed candidates (bit 4j+m = thread cell column j, TC
@@ -125,6 +126,7 @@ __device__ __forceinline__ uint32_t accept_candidates(uint32_t pmin, uint32_t pm
                                       c.k0, c.k1);
         if (c.active) *reinterpret_cast<uint4 *>(tp.ring + ((tp.end + 4u * c.g) & tp.mask)) = B;
         tp.end += 4u * G;
+        ++tp.rounds;
     }
     __syncwarp();
     // (w >> 4) < (P32 mod 2^28)  <=>  w < 16 (P32 mod 2^28)
@@ -938,13 +940,15 @@ __device__ __forceinline__ void write_back(const LaneGeom &q, uint32_t L, uint32
 template <bool RANDOM, bool LANE_SETS, int SCHEME = 0>
 __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t Bx,
                                             uint32_t By, uint32_t x0, uint32_t y0, bool active,
-                                            const LaneCtx &c, uint32_t *ring, int &net, int &draws) {
+                                            const LaneCtx &c, uint32_t *ring, int &net, int &draws,
+                                            int &tails) {
     TailPool tp;
     tp.ring = ring;
     const uint32_t G = static_cast<uint32_t>(c.GX * c.GY);
     tp.mask = static_cast<uint32_t>(kRingWordsPerLane) * (1u << (32 - __clz(static_cast<int>(G - 1u)))) - 1u;
     tp.head = 0u;
     tp.end = 0u;
+    tp.rounds = 0u;
     const LaneGeom q = lane_geom(lat, L, wpr, By, x0, y0, c);
     uint32_t X[16], Y[16], E, D;
     stage_lane(q, L, wpr, Bx, x0, active, c, X, Y, E, D);
@@ -1015,6 +1019,7 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
     }
 
     write_back<LANE_SETS>(q, L, wpr, active, c, X, Y, E, D);
+    tails = static_cast<int>(tp.rounds);
 }
 
 }  // namespace oct

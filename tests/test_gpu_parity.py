@@ -3,11 +3,9 @@
 Bar (integer and bit work throughout): the GPU lattice equals the DTrDT
 replay (O2) bit for bit, the net flip count and the roughness sums S1, S2 are
 equal integers, and W^2 is the same double.  Small lattices are compared
-whole; L = 4096 is compared whole for 16 seeds; L = 2^17 is compared on
-sampled device tiles (window replay) and through properties that hold at any
-size (exact S1/S2 of a closed-form lattice, row balance)."""
-import multiprocessing as mp
-
+whole; L = 2^17 here through properties that hold at any size (exact S1/S2 of
+a closed-form lattice, row balance); test_gpu_fullsize.py compares L = 2^17
+tile by tile and L = 4096 whole for 16 seeds."""
 import numpy as np
 import pytest
 
@@ -168,50 +166,14 @@ def test_roughness_of_closed_form_lattice(g, oracle, L):
         assert (m.s1, m.s2, m.hmax) == (s1, s2, hmax)
 
 
-def test_c2_sixteen_seeds(g, oracle):
-    """L = 4096 (16.8M sites, 4 MiB), 16 seeds: KPZ for 4 MCS and EW
-    (p = q = 0.5) for 2 MCS, whole lattices, default 64 x 64 sub-tiles."""
-    from oracle import jobs
-    jobs_list = [(4096, 1.0, 0.0, s, 64, 64, 4) for s in range(1, 17)]
-    jobs_list += [(4096, 0.5, 0.5, s, 64, 64, 2) for s in range(1, 17)]
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(min(16, mp.cpu_count())) as pool:
-        results = pool.map(jobs.dtrdt_final_canonical, jobs_list)
-    for (L, p, q, seed, Bx, By, n), (words, net, (s1, s2)) in zip(jobs_list, results):
-        with g.Simulation(L, p, q, seed, Bx=Bx, By=By) as sim:
-            sim.run(n)
-            got = sim.lattice()
-            assert np.array_equal(got, words), (p, q, seed)
-            m = sim.measure()
-            assert (m.net_flips, m.s1, m.s2) == (net, s1, s2), (p, q, seed)
-
-
-def test_c3_full_size_sampled(g, oracle):
-    """L = 2^17 (1.7e10 sites, 4 GiB), p = 0.95, q = 0.05, 256 x 64 sub-tiles.
-    After two MCS, MCS 2 is replayed by the oracle on windows of 5 x 5 device
-    tiles read from the GPU before the MCS; the centre tile must match the GPU
-    after the MCS.  Exact roughness at full size on the closed-form lattice."""
+def test_c3_full_size_properties(g, oracle):
+    """L = 2^17 (1.7e10 sites, 4 GiB), p = 0.95, q = 0.05, 256 x 64 sub-tiles,
+    after three MCS: L/2 up-slopes in every row, exact roughness of the evolved
+    lattice against the oracle's O3, and the 128-bit S2 of the closed-form
+    lattice.  (Tile-by-tile parity at this size: test_gpu_fullsize.py.)"""
     L, p, q, seed, Bx, By = 2**17, 0.95, 0.05, 1, 256, 64
-    prm = oracle.Params(L=L, p=p, q=q, seed=seed, Bx=Bx, By=By)
-    tw, th = 2 * Bx, 2 * By
     with g.Simulation(L, p, q, seed, Bx=Bx, By=By) as sim:
-        sim.run(2)
-        t = 2
-        ox, oy, _ = oracle.mcs_draw(prm, t)
-        rng = np.random.default_rng(0)
-        tiles = [(0, 0), (L // tw - 1, L // th - 1)] + [
-            (int(rng.integers(0, L // tw)), int(rng.integers(0, L // th))) for _ in range(3)]
-        pre = []
-        for tx, ty in tiles:
-            wx, wy = ox + tw * (tx - 2), oy + th * (ty - 2)
-            pre.append((wx, wy, *sim.window(wx, wy, 5 * tw, 5 * th)))
-        sim.run(1)
-        for wx, wy, Xw, Yw in pre:
-            Xw, Yw = Xw.copy(), Yw.copy()
-            oracle.dtrdt_mcs_window(Xw, Yw, prm, t, wx, wy)
-            Xg, Yg = sim.window(wx + 2 * tw, wy + 2 * th, tw, th)
-            c = (slice(2 * th, 3 * th), slice(2 * tw, 3 * tw))
-            assert np.array_equal(Xg, Xw[c]) and np.array_equal(Yg, Yw[c]), (wx, wy)
+        sim.run(3)
         # row balance at full size (X plane): L/2 up-slopes per row
         planes = sim.planes()
         table = np.array([bin(i).count("1") for i in range(256)], dtype=np.uint8)
@@ -282,35 +244,6 @@ def test_dtr_bit_exact(g, oracle, c):
             net += oracle.dtrdt_run(X, Y, prm, t, 1)[0]
             sim.run(1)
             _assert_same(oracle, sim, X, Y, net, f"t={t + 1}")
-
-
-@pytest.mark.parametrize("scheme", ["DB", "DTR"])
-def test_full_size_sampled_other_block_layers(g, oracle, scheme):
-    """L = 2^17, p = 0.95, q = 0.05, 256 x 64 sub-tiles, DTrDB (delayed borders)
-    and DTrDTr: MCS 2 replayed by the oracle on windows of 5 x 5 device tiles,
-    the centre tile compared with the GPU."""
-    L, p, q, seed, Bx, By = 2**17, 0.95, 0.05, 3, 256, 64
-    o_scheme = {"DB": oracle.SCHEME_DB, "DTR": oracle.SCHEME_DTR}[scheme]
-    g_scheme = {"DB": g._lib.OCT_SCHEME_DB, "DTR": g._lib.OCT_SCHEME_DTR}[scheme]
-    prm = oracle.Params(L=L, p=p, q=q, seed=seed, Bx=Bx, By=By, scheme=o_scheme)
-    tw, th = 2 * Bx, 2 * By
-    with g.Simulation(L, p, q, seed, Bx=Bx, By=By, scheme=g_scheme) as sim:
-        sim.run(2)
-        t = 2
-        ox, oy, _ = oracle.mcs_draw(prm, t)
-        rng = np.random.default_rng(1)
-        tiles = [(0, 0)] + [(int(rng.integers(0, L // tw)), int(rng.integers(0, L // th))) for _ in range(2)]
-        pre = []
-        for tx, ty in tiles:
-            wx, wy = ox + tw * (tx - 2), oy + th * (ty - 2)
-            pre.append((wx, wy, *sim.window(wx, wy, 5 * tw, 5 * th)))
-        sim.run(1)
-        for wx, wy, Xw, Yw in pre:
-            Xw, Yw = Xw.copy(), Yw.copy()
-            oracle.dtrdt_mcs_window(Xw, Yw, prm, t, wx, wy)
-            Xg, Yg = sim.window(wx + 2 * tw, wy + 2 * th, tw, th)
-            c = (slice(2 * th, 3 * th), slice(2 * tw, 3 * tw))
-            assert np.array_equal(Xg, Xw[c]) and np.array_equal(Yg, Yw[c]), (scheme, wx, wy)
 
 
 def _all_shapes():

@@ -740,7 +740,7 @@ def main():
                   "cpu_baseline": dtr_cpu}
         # ---- DTrDT with the paper's coarser thread cells (TC=1,1 .. 3,2) on the same workload ----
         cells = {}
-        for cx, cy in ((8, 8), (16, 8), (16, 16), (32, 16)):
+        for cx, cy in (((8, 8), (16, 8), (16, 16), (32, 16)) if a.cell_steps > 0 else ()):
             with g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, cx=cx, cy=cy, stream=stream, lattice=lattice,
                               no_init=True) as h:
                 h.run(1)

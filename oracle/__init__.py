@@ -105,7 +105,7 @@ def lib():
         L.oo_dtrdt_many.argtypes = [ctypes.POINTER(_Params), u64, i64, u32, _P_u8, _P_u8]
         L.oo_dtrdt_acc_prefix.argtypes = [u64, u32, u32, u32, u32, u32, ctypes.c_int]
         L.oo_dtrdt_acc_prefix.restype = u32
-        L.oo_dtrdt_tail_word.argtypes = [u64, u32, u32, u32, u32]
+        L.oo_dtrdt_tail_word.argtypes = [u64, u32, u32, u32, u32, u32]
         L.oo_dtrdt_tail_word.restype = u32
         L.oo_w2_sums_planar.argtypes = [i64, _P_u32, P_i64, P_u64, P_u64, P_i64]
         L.oo_invariants_planar.argtypes = [i64, _P_u32, i64, i64]
@@ -115,6 +115,8 @@ def lib():
         L.oo_subtile_steps_many.argtypes = [ctypes.POINTER(_Params), u64, i64, u32, u32, u32, i64, i64,
                                             i64, _P_u8, _P_u8, _P_u8, _P_u8, _P_i64]
         L.oo_set_plant.argtypes = [ctypes.c_int]
+        L.oo_set_tie_log.argtypes = [ctypes.c_void_p, i64]
+        L.oo_tie_log_count.restype = i64
         L.oo_two_time_sums.argtypes = [i64, _P_u8, _P_u8, _P_u8, _P_u8, ctypes.POINTER(_TwoTime)]
         L.oo_ch_from_sums.argtypes = [i64, ctypes.POINTER(_TwoTime)]
         L.oo_ch_from_sums.restype = dbl
@@ -212,9 +214,9 @@ def acc_prefix(seed: int, t: int, k: int, T: int, g: int, s: int, pos: int) -> i
     return int(lib().oo_dtrdt_acc_prefix(seed, t, k, T, g, s, pos))
 
 
-def tail_word(seed: int, t: int, k: int, T: int, i: int) -> int:
-    """Word i of a sub-tile's tail stream in device step k of MCS t."""
-    return int(lib().oo_dtrdt_tail_word(seed, t, k, T, i))
+def tail_word(seed: int, t: int, k: int, T: int, g: int, i: int) -> int:
+    """Word i of group g's tail stream in device step k of MCS t (sub-tile T)."""
+    return int(lib().oo_dtrdt_tail_word(seed, t, k, T, g, i))
 
 
 def dtrdt_mcs_window(Xw, Yw, prm: Params, t: int, wx: int, wy: int) -> int:
@@ -280,10 +282,31 @@ def subtile_steps_many(prm: "Params", seed0: int, n_runs: int, t: int, k: int, T
     return X, Y, net
 
 
+class tie_log:
+    """Context manager recording the tail words tied candidates take (rows of
+    stream group, word index, candidate group, position) while it is open."""
+
+    def __init__(self, cap: int = 1 << 16):
+        self.buf = np.zeros((cap, 4), dtype=np.int64)
+
+    def __enter__(self):
+        lib().oo_set_tie_log(self.buf.ctypes.data_as(ctypes.c_void_p), self.buf.shape[0])
+        return self
+
+    def __exit__(self, *exc):
+        self.n = int(lib().oo_tie_log_count())
+        lib().oo_set_tie_log(None, 0)
+        return False
+
+    def rows(self):
+        return self.buf[: self.n]
+
+
 class planted:
-    """Context manager that plants one of the oracle's two known mistakes
-    (1: cells 2i and 2i+1 share site bits; 2: DTrDB corners before borders)
-    for a negative control, and removes it on exit."""
+    """Context manager that plants one of the oracle's known mistakes (1: cells
+    2i and 2i+1 share site bits; 2: DTrDB corners before borders; 3: all groups
+    take tail words from group 0's stream) for a negative control, and removes
+    it on exit."""
 
     def __init__(self, which: int):
         self.which = which

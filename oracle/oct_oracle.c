@@ -104,6 +104,19 @@ static int g_plant = 0;
 
 void oo_set_plant(int which) { g_plant = which; }
 
+/* Optional record of the tail words the tied candidates take, for the tests:
+ * four int64 per tie (stream group, word index, candidate group, position). */
+static int64_t *g_tie_log = NULL;
+static int64_t g_tie_cap = 0, g_tie_n = 0;
+
+void oo_set_tie_log(int64_t *buf, int64_t cap) {
+    g_tie_log = buf;
+    g_tie_cap = buf ? cap : 0;
+    g_tie_n = 0;
+}
+
+int64_t oo_tie_log_count(void) { return g_tie_n; }
+
 /* ------------------------------------------------------------------------ */
 /* Model, Sec. 2.1 / Eq. (1)                                                 */
 /* ------------------------------------------------------------------------ */
@@ -273,10 +286,10 @@ static void touch(conflict_t *cf, int64_t bit, int64_t tile, int64_t tc) {
  *     pos = 4j+m of word l (l = 0..3) of Philox(seed, (t, k|(s*8)<<2, T, ACC<<28|g));
  *   - bits 27..0: only needed when bits 31..28 equal those of P32 (otherwise
  *     u < P32 is already decided); they are the top 28 bits of the next word
- *     of the sub-tile's tail stream, word i = word i%4 of
- *     Philox(seed, (t, k|(i/4)<<2, T, TAIL<<28)), i counted from 0 at the start
- *     of each device step; within a collective step the candidates that need
- *     one take words in order of group g, then position pos. */
+ *     of the group's own tail stream, word i = word i%4 of
+ *     Philox(seed, (t, k|(i/4)<<2, T, TAIL<<28|g)), i counted from 0 at the
+ *     start of each device step; within a collective step (a DB phase) the
+ *     group's candidates that need one take words in order of position pos. */
 static void acc_level_words(const uint32_t key[2], uint32_t t, uint32_t k, uint32_t T, uint32_t g,
                             uint32_t s, uint32_t lw[4]) {
     philox_at(key, t, k | ((s * 8) << 2), T, (OO_TAG_ACC << 28) | g, lw);
@@ -289,9 +302,10 @@ static uint32_t acc_prefix(const uint32_t lw[4], int pos) {
     return hi;
 }
 
-static uint32_t tail_word(const uint32_t key[2], uint32_t t, uint32_t k, uint32_t T, uint32_t i) {
+static uint32_t tail_word(const uint32_t key[2], uint32_t t, uint32_t k, uint32_t T, uint32_t g,
+                          uint32_t i) {
     uint32_t w[4];
-    philox_at(key, t, k | ((i / 4) << 2), T, OO_TAG_TAIL << 28, w);
+    philox_at(key, t, k | ((i / 4) << 2), T, (OO_TAG_TAIL << 28) | g, w);
     return w[i % 4];
 }
 
@@ -303,10 +317,10 @@ uint32_t oo_dtrdt_acc_prefix(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, 
     return acc_prefix(w, pos);
 }
 
-uint32_t oo_dtrdt_tail_word(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t i) {
+uint32_t oo_dtrdt_tail_word(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t g, uint32_t i) {
     uint32_t key[2];
     seed_key(seed, key);
-    return tail_word(key, t, k, T, i);
+    return tail_word(key, t, k, T, g, i);
 }
 
 typedef struct {
@@ -332,7 +346,8 @@ static int by_group_then_position(const void *pa, const void *pb) {
 /* Decides, flips and counts the attempts of one conflict-free batch (a
  * collective step of DT, or one phase of a DB step): attempts whose site is
  * eligible on the current state are decided by the four leading level bits of
- * their uniform; ties take tail words in order of group, then position. */
+ * their uniform; ties take the next words of their group's tail stream
+ * (tail_next[g] = words group g used so far), in order of position. */
 static void decide_and_flip(const uint32_t key[2], uint32_t t, uint32_t k, uint32_t T, view_t *v,
                             attempt_t *att, int64_t na, attempt_t *tied, uint32_t *tail_next,
                             int64_t *net, conflict_t *cf) {
@@ -358,7 +373,17 @@ static void decide_and_flip(const uint32_t key[2], uint32_t t, uint32_t k, uint3
     }
     qsort(tied, (size_t)nt, sizeof(attempt_t), by_group_then_position);
     for (int64_t i = 0; i < nt; ++i) {
-        const uint32_t low28 = tail_word(key, t, k, T, (*tail_next)++) >> 4;
+        /* the candidate's own group's stream (planted mistake 3: group 0's for all) */
+        const uint32_t gs = g_plant == 3 ? 0u : tied[i].g;
+        const uint32_t wi = tail_next[gs]++;
+        if (g_tie_log && g_tie_n < g_tie_cap) {
+            int64_t *e = g_tie_log + 4 * g_tie_n++;
+            e[0] = gs;
+            e[1] = wi;
+            e[2] = tied[i].g;
+            e[3] = tied[i].pos;
+        }
+        const uint32_t low28 = tail_word(key, t, k, T, gs, wi) >> 4;
         tied[i].decided = (uint64_t)low28 < (tied[i].thr & 0x0FFFFFFFu) ? 1 : 0;
     }
     /* apply the accepted flips (no two share a bit; tracked when cf is set) */
@@ -502,7 +527,8 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
     attempt_t *phase = (attempt_t *)malloc(sizeof(attempt_t) * (size_t)n_tc);
     attempt_t *tied = (attempt_t *)malloc(sizeof(attempt_t) * (size_t)n_tc);
     int *cls = (int *)malloc(sizeof(int) * (size_t)n_tc);
-    uint32_t tail_next = 0; /* tail-stream words used so far in this device step */
+    /* tail-stream words each group used so far in this device step */
+    uint32_t *tail_next = (uint32_t *)calloc((size_t)(group_rows * band_cols), sizeof(uint32_t));
 
     if (s_end > n_steps) s_end = n_steps;
     for (int64_t s = 0; s < s_end; ++s) {
@@ -575,13 +601,14 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
                         touch(cf, nv + phase[i].iu, T, phase[i].tc);
                     }
             }
-            decide_and_flip(key, t, k, T, v, phase, np, tied, &tail_next, net, cf);
+            decide_and_flip(key, t, k, T, v, phase, np, tied, tail_next, net, cf);
         }
     }
     free(all);
     free(phase);
     free(tied);
     free(cls);
+    free(tail_next);
 }
 
 int oo_subtile_step_sites(const oo_params *P, uint32_t t, uint32_t k, uint32_t T, int64_t s,

@@ -106,11 +106,11 @@ int oo_dtrdt_many(const oo_params *prm, uint64_t seed0, int64_t n_runs, uint32_t
 /* The acceptance randomness O2 uses: the four leading bits (31..28) of the
  * uniform of the thread cell at position pos (= 4*j + m) of group g at
  * collective step s, device step k, tile T, MCS t; and word i of the
- * sub-tile's tail stream of a device step (its top 28 bits complete a uniform
+ * tail stream of group g in a device step (its top 28 bits complete a uniform
  * whose leading bits tie with P32's). */
 uint32_t oo_dtrdt_acc_prefix(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t g,
                              uint32_t s, int pos);
-uint32_t oo_dtrdt_tail_word(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t i);
+uint32_t oo_dtrdt_tail_word(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, uint32_t g, uint32_t i);
 
 /* O2 restricted to a window: the lattice is only known on a W x H window whose
  * lower-left corner is the global site (wx, wy) (periodic in L).  Xw/Yw hold
@@ -142,9 +142,18 @@ int oo_subtile_steps_many(const oo_params *P, uint64_t seed0, int64_t n_runs, ui
 /* Plants one of two known mistakes in the block layer, for negative controls
  * of the tests only: 1 = thread cells 2i and 2i+1 of a band read the same
  * site-draw bits; 2 = DTrDB carries out corner attempts before border
- * attempts.  0 (the default) plants nothing.  Not thread-safe; a test sets it
+ * attempts; 3 = every group's tied candidates take words from group 0's tail
+ * stream.  0 (the default) plants nothing.  Not thread-safe; a test sets it
  * and resets it to 0. */
 void oo_set_plant(int which);
+
+/* Records, for the tests, the tail word every tied candidate takes (the
+ * candidates whose four leading uniform bits equal those of P32): four int64
+ * per tie in buf (stream group, word index, candidate group, position 4j+m),
+ * at most cap ties, in the order they are taken.  buf = NULL stops recording.
+ * oo_tie_log_count() returns the number recorded.  Not thread-safe. */
+void oo_set_tie_log(int64_t *buf, int64_t cap);
+int64_t oo_tie_log_count(void);
 
 /* O3: exact roughness sums, Eq. (3).  Heights relative to h(0,0) = 0 are
  * integrated first up column 0 and then along each row.  s1 = sum h,

@@ -130,8 +130,8 @@ __device__ __forceinline__ void cells_candidates(const uint32_t (&X)[16], const 
 }
 
 // Phase 2: acceptance of the lane's packed candidates (bit 4j+m), as in
-// accept_candidates, with the tail words of tied candidates taken in order of
-// group, then position, over groups that span GS lane rows.
+// accept_candidates, for groups that span GS lane rows: a tied candidate's
+// word in its group's tail stream is ranked among the ties of the whole group.
 template <int GS>
 __device__ __forceinline__ uint32_t cells_accept(uint32_t pmin, uint32_t pmax, const uint4 &W, const CellCtx &cc,
                                                  TailPool &tp) {
@@ -158,39 +158,22 @@ __device__ __forceinline__ uint32_t cells_accept(uint32_t pmin, uint32_t pmax, c
             gund |= ok ? v : 0u;
         }
     }
-    // exclusive prefix of the groups' tie counts, in group order (the first
-    // lane row of every group contributes its group's count)
-    const uint32_t contrib = (cc.gh == 0) ? static_cast<uint32_t>(__popc(gund)) : 0u;
-    uint32_t incl = contrib;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(kFull, incl, o);
-        if (cc.lane >= o) incl += v;
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, c.last);
-    if (__all_sync(kFull, total == 0u)) return acc;
-    uint32_t base = incl - contrib;
-    if (GS > 1) base = __shfl_sync(kFull, base, cc.gr * GS * c.GX + c.gx);
-    const uint32_t nl = static_cast<uint32_t>(c.GX * c.GY);
-    while (tp.end < tp.head + total) {
-        const uint4 B = philox4x32_10(c.t, c.k | (((tp.end >> 2) + static_cast<uint32_t>(cc.lane)) << 2), c.T,
-                                      kTagTail << 28, c.k0, c.k1);
-        if (c.active) *reinterpret_cast<uint4 *>(tp.ring + ((tp.end + 4u * static_cast<uint32_t>(cc.lane)) & tp.mask)) = B;
-        tp.end += 4u * nl;
-        ++tp.rounds;
-    }
-    __syncwarp();
+    // The group's ties take the next words of its tail stream in order of
+    // position; every lane of the group keeps the group's stream in its own
+    // slot, so that it finds the words of its own ties there.
+    if (__all_sync(kFull, gund == 0u)) return acc;
+    const uint32_t ng = static_cast<uint32_t>(__popc(gund));
+    tail_refill(ng, c.g, c, tp);
     // (w >> 4) < (P32 mod 2^28)  <=>  w < 16 (P32 mod 2^28)
     const uint32_t low_p = c.thr_p << 4, low_q = c.thr_q << 4;
     while (und) {
         const uint32_t bit = und & (0u - und);
         und ^= bit;
-        const uint32_t at = tp.head + base + static_cast<uint32_t>(__popc(gund & (bit - 1u)));
-        const uint32_t w = tp.ring[at & tp.mask];
+        const uint32_t at = tp.head + static_cast<uint32_t>(__popc(gund & (bit - 1u)));
+        const uint32_t w = tp.ring[at & static_cast<uint32_t>(kRingWordsPerLane - 1)];
         acc |= (w < ((pmin & bit) ? low_p : low_q)) ? bit : 0u;
     }
-    __syncwarp();
-    tp.head += total;
+    tp.head += ng;
     return acc;
 }
 
@@ -231,7 +214,7 @@ __device__ __forceinline__ void cells_apply(uint32_t (&X)[16], uint32_t (&Y)[16]
                 f = cd & ((~x & amin) | (x & amax));
                 net += always_net<RANDOM>(f, x, c);
             }
-            X[r] = x ^ f ^ (f << 1);
+            X[r] = x ^ (f * 3u);  // f ^ (f << 1): one flip per cell, cells at least cx columns apart
             Y[r] ^= f;
             if (r + 1 < 16)
                 Y[(r + 1) & 15] ^= f;
@@ -279,9 +262,7 @@ __device__ __forceinline__ void run_subtile_cells(uint32_t *lat, uint32_t L, uin
     using S = CellShape<CX, CY>;
     const LaneCtx &c = cc.c;
     TailPool tp;
-    tp.ring = ring;
-    const uint32_t nl = static_cast<uint32_t>(c.GX * c.GY);
-    tp.mask = static_cast<uint32_t>(kRingWordsPerLane) * (1u << (32 - __clz(static_cast<int>(nl - 1u)))) - 1u;
+    tp.ring = ring + static_cast<uint32_t>(kRingWordsPerLane) * static_cast<uint32_t>(cc.lane);  // own slot
     tp.head = 0u;
     tp.end = 0u;
     tp.rounds = 0u;

@@ -25,12 +25,18 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1
 #pragma unroll
 #endif
     for (int round = 0; round < 10; ++round) {
-        const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c0;
-        const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c2;
-        const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ k0;
-        const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ k1;
-        c1 = static_cast<uint32_t>(p1);
-        c3 = static_cast<uint32_t>(p0);
+        // high and low halves of the two 32 x 32 -> 64-bit products
+#ifdef __CUDA_ARCH__
+        const uint32_t h0 = __umulhi(0xD2511F53u, c0), h1 = __umulhi(0xCD9E8D57u, c2);
+#else
+        const uint32_t h0 = static_cast<uint32_t>((static_cast<uint64_t>(0xD2511F53u) * c0) >> 32);
+        const uint32_t h1 = static_cast<uint32_t>((static_cast<uint64_t>(0xCD9E8D57u) * c2) >> 32);
+#endif
+        const uint32_t l0 = 0xD2511F53u * c0, l1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = h1 ^ c1 ^ k0;
+        const uint32_t n2 = h0 ^ c3 ^ k1;
+        c1 = l1;
+        c3 = l0;
         c0 = n0;
         c2 = n2;
         k0 += 0x9E3779B9u;

@@ -68,19 +68,31 @@ __device__ __forceinline__ int random_net(uint32_t acc, uint32_t pmin, uint32_t 
     return __popc(acc & pmin) - __popc(acc & pmax);
 }
 
-// Shared-memory ring holding a sub-tile's tail stream (see accept_candidates).
-// Its size is a power of two of at least 64 words per lane, above the live
-// window: fewer than (ties of one step) + 4 x (groups) words, and one step has
-// at most 32 ties per group.
+// Each lane keeps its group's tail stream (see accept_candidates) in its own
+// slot of kRingWordsPerLane words of shared memory, a ring above the live
+// window: fewer than (ties of one step, at most 32) + 4 words.
 constexpr int kRingWordsPerLane = 64;
 
 struct TailPool {
-    uint32_t *ring;  // this sub-tile's ring
-    uint32_t mask;   // ring size - 1
-    uint32_t head;   // tail words used so far in this device step
-    uint32_t end;    // tail words generated so far in this device step
-    uint32_t rounds; // refills so far (each lane generated one Philox block per refill)
+    uint32_t *ring;  // the lane's own slot of kRingWordsPerLane words
+    uint32_t head;   // words of the group's tail stream used so far in this device step
+    uint32_t end;    // words generated into the slot so far in this device step
+    uint32_t rounds; // Philox blocks the lane generated into its slot
 };
+
+// Tops up the lane's slot until it holds the `need` words after head; every
+// lane of the warp takes part in each round (one Philox block per lane, block
+// end/4 of its group's stream, kept only if the slot has room).
+__device__ __forceinline__ void tail_refill(uint32_t need, uint32_t g, const LaneCtx &c, TailPool &tp) {
+    while (__any_sync(kFull, tp.end < tp.head + need)) {
+        const uint4 B = philox4x32_10(c.t, c.k | ((tp.end >> 2) << 2), c.T, (kTagTail << 28) | g, c.k0, c.k1);
+        if (tp.end - tp.head <= static_cast<uint32_t>(kRingWordsPerLane - 4)) {
+            *reinterpret_cast<uint4 *>(tp.ring + (tp.end & static_cast<uint32_t>(kRingWordsPerLane - 1))) = B;
+            tp.end += 4u;
+            ++tp.rounds;
+        }
+    }
+}
 
 // Acceptance of the packed candidates (bit 4j+m = thread cell column j, TC
 // row m).  The uniform u of a candidate, most significant bit first:
@@ -89,10 +101,9 @@ struct TailPool {
 //    cells of the lane are compared with P32 together, one level at a time;
 //    the comparison is decided unless the four bits equal P32's;
 //  * a candidate still tied takes its bits 27..0 from the top of the next word
-//    of the sub-tile's tail stream (word i = word i%4 of Philox(t, k|(i/4)<<2,
-//    T, TAIL<<28), counted from 0 each device step), in order of group, then
-//    position.  The lanes of the sub-tile fill a shared ring with one Philox
-//    block each whenever the words a step needs run past what was generated.
+//    of its group's tail stream (word i = word i%4 of Philox(t, k|(i/4)<<2, T,
+//    TAIL<<28|g), counted from 0 each device step), the group's ties of a step
+//    in order of position.  A lane holds one group, so it takes its own words.
 __device__ __forceinline__ uint4 level_words(uint32_t s, const LaneCtx &c) {
     return philox4x32_10(c.t, c.k | ((s * 8u) << 2), c.T, (kTagAcc << 28) | c.g, c.k0, c.k1);
 }
@@ -108,39 +119,19 @@ __device__ __forceinline__ uint32_t accept_candidates(uint32_t pmin, uint32_t pm
         acc |= und & tb & ~lw[i];
         und &= ~(tb ^ lw[i]);
     }
-    // ties: exclusive prefix of their counts over the groups of the sub-tile
-    const uint32_t n = static_cast<uint32_t>(__popc(und));
-    uint32_t incl = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(kFull, incl, o);
-        if (static_cast<int>(c.g) >= o) incl += v;
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, c.last);
-    // Skip the tail stage only when no lane of the warp needs it: in a batched
-    // warp the sub-tiles differ, and every lane must reach the __syncwarp below.
-    if (__all_sync(kFull, total == 0u)) return acc;
-    const uint32_t G = static_cast<uint32_t>(c.GX * c.GY);
-    while (tp.end < tp.head + total) {
-        const uint4 B = philox4x32_10(c.t, c.k | (((tp.end >> 2) + c.g) << 2), c.T, kTagTail << 28,
-                                      c.k0, c.k1);
-        if (c.active) *reinterpret_cast<uint4 *>(tp.ring + ((tp.end + 4u * c.g) & tp.mask)) = B;
-        tp.end += 4u * G;
-        ++tp.rounds;
-    }
-    __syncwarp();
+    // Skip the tail stage only when no lane of the warp needs it: every lane
+    // takes part in the refill rounds.
+    if (__all_sync(kFull, und == 0u)) return acc;
+    tail_refill(static_cast<uint32_t>(__popc(und)), c.g, c, tp);
     // (w >> 4) < (P32 mod 2^28)  <=>  w < 16 (P32 mod 2^28)
     const uint32_t low_p = c.thr_p << 4, low_q = c.thr_q << 4;
-    uint32_t at = tp.head + (incl - n);
     while (und) {
         const uint32_t bit = und & (0u - und);  // lowest tied position
         und ^= bit;
-        const uint32_t w = tp.ring[at & tp.mask];
-        ++at;
+        const uint32_t w = tp.ring[tp.head & static_cast<uint32_t>(kRingWordsPerLane - 1)];
+        ++tp.head;
         acc |= (w < ((pmin & bit) ? low_p : low_q)) ? bit : 0u;
     }
-    __syncwarp();
-    tp.head += total;
     return acc;
 }
 
@@ -229,8 +220,10 @@ __device__ __forceinline__ void step_apply(uint32_t (&X)[16], uint32_t (&Y)[16],
             f1 = cnd1[m] & ((~xb & amin) | (xb & amax));
             net += always_net<RANDOM>(f0, xa, c) + always_net<RANDOM>(f1, xb, c);
         }
-        X[r0] = xa ^ f0 ^ (f0 << 1);
-        X[r1] = xb ^ f1 ^ (f1 << 1);
+        // f ^ (f << 1) = 3f: a cell flips at most one site, so flips are at
+        // least three columns apart and the sum has no carries (FMA pipe)
+        X[r0] = xa ^ (f0 * 3u);
+        X[r1] = xb ^ (f1 * 3u);
         Y[r0] ^= f0;
         Y[r1] ^= f0 ^ f1;
         if (r1 + 1 < 16)
@@ -358,7 +351,7 @@ __device__ __forceinline__ void step_apply_rt(uint32_t (&X)[16], uint32_t (&Y)[1
             f1 = cnd1[m] & ((~xb & amin) | (xb & amax));
             net += always_net<RANDOM>(f0, xa, c) + always_net<RANDOM>(f1, xb, c);
         }
-        const uint32_t nxa = xa ^ f0 ^ (f0 << 1), nxb = xb ^ f1 ^ (f1 << 1);
+        const uint32_t nxa = xa ^ (f0 * 3u), nxb = xb ^ (f1 * 3u);  // 3f = f ^ (f << 1), see step_apply
         X[4 * m] = dy ? X[4 * m] : nxa;
         X[4 * m + 1] = dy ? X[4 * m + 1] : nxb;
         X[4 * m + 2] = dy ? nxa : X[4 * m + 2];
@@ -726,7 +719,7 @@ __device__ __forceinline__ void dtr_apply(uint32_t (&X)[16], uint32_t (&Y)[16], 
         const uint32_t k = static_cast<uint32_t>(r & 3);
         uint32_t F = (R0 == k ? fa[m] : 0u) | (R0 + 1u == k ? fb[m] : 0u);
         if (k == 0u && SY) F |= fb[(m + 3) & 3];
-        X[r] ^= F ^ (F << 1);
+        X[r] ^= F * 3u;      // F ^ (F << 1): the row's flips are at least three columns apart
         Y[r] ^= F ^ F_prev;  // its own Y, and Y(s+y) of the row above
         dE |= (F >> 31) << r;
         dB0 |= (F & 1u) << r;
@@ -943,9 +936,7 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
                                             const LaneCtx &c, uint32_t *ring, int &net, int &draws,
                                             int &tails) {
     TailPool tp;
-    tp.ring = ring;
-    const uint32_t G = static_cast<uint32_t>(c.GX * c.GY);
-    tp.mask = static_cast<uint32_t>(kRingWordsPerLane) * (1u << (32 - __clz(static_cast<int>(G - 1u)))) - 1u;
+    tp.ring = ring + static_cast<uint32_t>(kRingWordsPerLane) * c.g;  // the lane's own slot
     tp.head = 0u;
     tp.end = 0u;
     tp.rounds = 0u;

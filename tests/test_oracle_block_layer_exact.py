@@ -385,3 +385,81 @@ def test_db_step_exact_distribution(oracle, L, Bx, By, cx, cy, x0, y0):
     swapped = exact_db(X0, Y0, x0, y0, Bx, By, cx, cy, pe, qe, order=(0, 2, 1))
     tv = 0.5 * sum(abs(exact.get(k, 0) - swapped.get(k, 0)) for k in set(exact) | set(swapped))
     assert tv > 0.02, tv
+
+
+# ------------------------------------------------------------ tail streams ---
+
+TAG_ACC = 4
+
+
+def stated_ties(oracle, prm, t, k, T, s, x0, y0):
+    """Tied candidates of collective step s of a sub-tile at the flat start,
+    from the stated reading: every attempted site is extremal (a minimum iff
+    x + y is even); the four leading bits of a cell's uniform are bit 4j+m of
+    the four level words of its group (most significant first); the candidate
+    ties iff they equal the four leading bits of P32 of its rate.  Each group
+    takes words 0, 1, 2, ... of its own tail stream in order of position.
+    Returns rows (stream group, word index, candidate group, position)."""
+    lx, ly = stated_sites(oracle, prm, t, k, T, s)
+    n_a = prm.Bx // prm.cx
+    tpb = min(32, prm.Bx) // prm.cx
+    band_cols = prm.Bx // min(32, prm.Bx)
+    thr = {1: oracle.threshold32(prm.p) >> 28, -1: oracle.threshold32(prm.q) >> 28}
+    key = _key(prm.seed)
+    words = {}
+    ties = []
+    for i, (x, y) in enumerate(zip(lx, ly)):
+        c, a = divmod(i, n_a)
+        g = (c // 4) * band_cols + a // tpb
+        pos = 4 * (a % tpb) + c % 4
+        kind = 1 if (x0 + x + y0 + y) % 2 == 0 else -1
+        if g not in words:
+            words[g] = oracle.philox([t, k | ((s * 8) << 2), T, (TAG_ACC << 28) | g], key)
+        hi = sum(((int(words[g][l]) >> pos) & 1) << (3 - l) for l in range(4))
+        if hi == thr[kind]:
+            ties.append((g, pos))
+    ties.sort()
+    rows, used = [], {}
+    for g, pos in ties:
+        rows.append((g, used.get(g, 0), g, pos))
+        used[g] = used.get(g, 0) + 1
+    return rows
+
+
+def test_ties_take_their_groups_tail_words_in_position_order(oracle):
+    """Four groups (64 cells of 4x4 sites in a 64 x 32 sub-tile), both rates
+    random, step 0 from the flat start over 300 seeds: the oracle's record of
+    the tail words its tied candidates take equals the stated reading; the
+    planted mistake (all groups on group 0's stream) does not."""
+    L, x0, y0 = 128, 5, 9
+    n_ties = 0
+    for seed in range(300):
+        prm = oracle.Params(L=L, p=0.95, q=0.05, seed=seed, Bx=64, By=32)
+        X0, Y0 = oracle.flat(L)
+        with oracle.tie_log() as log:
+            oracle.subtile_steps_many(prm, seed, 1, 3, 1, 6, x0, y0, 1, X0, Y0)
+        want = stated_ties(oracle, prm, 3, 1, 6, 0, x0, y0)
+        assert [tuple(r) for r in log.rows().tolist()] == want, seed
+        n_ties += len(want)
+    assert n_ties > 600
+    prm = oracle.Params(L=L, p=0.95, q=0.05, seed=1, Bx=64, By=32)
+    bad = 0
+    for seed in range(40):
+        prm = oracle.Params(L=L, p=0.95, q=0.05, seed=seed, Bx=64, By=32)
+        X0, Y0 = oracle.flat(L)
+        with oracle.planted(3), oracle.tie_log() as log:
+            oracle.subtile_steps_many(prm, seed, 1, 3, 1, 6, x0, y0, 1, X0, Y0)
+        bad += [tuple(r) for r in log.rows().tolist()] != stated_ties(oracle, prm, 3, 1, 6, 0, x0, y0)
+    assert bad > 20
+
+
+def test_tail_streams_are_uniform_and_independent_across_groups(oracle):
+    n = 20000
+    a = np.array([oracle.tail_word(9, 4, 2, 11, 0, i) for i in range(n)], dtype=np.float64) / 2.0**32
+    b = np.array([oracle.tail_word(9, 4, 2, 11, 1, i) for i in range(n)], dtype=np.float64) / 2.0**32
+    from scipy import stats
+    assert stats.kstest(a, "uniform").pvalue > 1e-4 and stats.kstest(b, "uniform").pvalue > 1e-4
+    assert abs(np.corrcoef(a, b)[0, 1]) < 5 / np.sqrt(n)
+    # joint uniformity of the leading nibbles of the two streams at equal indices
+    ha, hb = (a * 16).astype(int), (b * 16).astype(int)
+    assert _joint_g_test(ha, hb, 16)[2] > P_MIN

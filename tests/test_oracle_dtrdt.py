@@ -96,9 +96,10 @@ def test_acceptance_randomness(oracle):
     for l in range(4):
         b = (H >> l) & 1
         assert abs(b.mean() - 0.5) < 4 * 0.5 / np.sqrt(b.size)
-    tails = np.array([oracle.tail_word(3, 2, 1, 7, i) for i in range(20000)], dtype=np.float64)
+    tails = np.array([oracle.tail_word(3, 2, 1, 7, 5, i) for i in range(20000)], dtype=np.float64)
     assert stats.kstest(tails / 2.0**32, "uniform").pvalue > 1e-4
-    assert oracle.tail_word(3, 2, 1, 7, 5) != oracle.tail_word(3, 2, 1, 8, 5)
+    assert oracle.tail_word(3, 2, 1, 7, 0, 5) != oracle.tail_word(3, 2, 1, 8, 0, 5)
+    assert oracle.tail_word(3, 2, 1, 7, 0, 5) != oracle.tail_word(3, 2, 1, 7, 1, 5)
     assert oracle.acc_prefix(1, 2, 3, 4, 5, 6, 7) == oracle.acc_prefix(1, 2, 3, 4, 5, 6, 7)
 
 

@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--loop-steps", type=int, default=3)
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--serve-jobs", type=int, default=32)
+    ap.add_argument("--serve-jobs", type=int, default=96)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-policy", default="large", help="autotune.batch_shape policy of the serving leg")
     ap.add_argument("--db-steps", type=int, default=30)
@@ -408,16 +408,29 @@ def serving_leg(a, g, _lib, torch, stream, capacity):
                         "W^2 streamed at 8 log-spaced times per job, HBM budget 64 GiB"),
            "shape_policy": a.serve_policy,
            "capacity_attempts_per_ns": capacity, "expected_attempts_per_job": work, "loads": []}
+    # One job list (Poisson gaps of mean 1, keys from master seed 1).  The offered
+    # load rho is the work the list actually holds per second of its arrival
+    # span, over the capacity: arrival times are scaled so that the list's own
+    # work arrives at rho x capacity (its work is heavy-tailed, so the expected
+    # work per job would misstate the load of a finite list).
+    base = serve.poisson_jobs(a.serve_jobs, 1.0, master_seed=1, seed_fn=_lib.oct_replica_seed)
+    realized = sum(j.attempts for j in base)
+    span = max(j.arrival for j in base)
+    out.update({"jobs": len(base), "realized_attempts": realized,
+                "realized_over_expected": realized / (len(base) * work),
+                "offered_load_basis": "the job list's own work per second of arrival span / capacity"})
     for rho in (0.5, 0.8, 1.0):
-        rate = rho * capacity * 1e9 / work
-        jobs = serve.poisson_jobs(a.serve_jobs, rate, master_seed=1, seed_fn=_lib.oct_replica_seed)
+        scale = realized / (rho * capacity * 1e9) / span
+        jobs = [serve.Job(j.jid, j.L, j.p, j.q, j.seed, j.t_max, arrival=j.arrival * scale,
+                          measure_at=list(j.measure_at)) for j in base]
         eng = serve.ServingEngine(64 << 30, stream=stream, max_chunk=64, shape_policy=a.serve_policy)
         t0 = time.perf_counter()
         done = eng.run(jobs)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         res = serve.summary(done, wall)
-        res.update({"offered_load": rho, "rate_jobs_per_s": rate, "ticks": eng.ticks})
+        res.update({"offered_load": rho, "rate_jobs_per_s": (len(base) - 1) / (span * scale), "ticks": eng.ticks,
+                    "arrival_span_s": span * scale, "fraction_of_capacity": res["attempts_per_ns"] / capacity})
         out["loads"].append(res)
         eng.batch.close()
     return out

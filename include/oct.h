@@ -339,7 +339,8 @@ int oct_batch_remove(oct_batch *b, int64_t slot);
 
 /* Enqueues n MCS for every replica in the batch (asynchronous); each replica
  * advances its own time t.  The work list and graph are rebuilt first if
- * replicas were added or removed. */
+ * replicas were added or removed; the rebuild copies the new work list in
+ * stream order and does not wait for the device. */
 int oct_batch_run(oct_batch *b, int64_t n);
 
 /* Exact roughness of every slot (out holds one entry per slot index handed
@@ -349,6 +350,20 @@ int oct_batch_measure_w2(oct_batch *b, oct_w2 *out, int64_t n);
 
 /* Exact roughness of the replica in one slot.  Synchronises. */
 int oct_batch_measure_slot(oct_batch *b, int64_t slot, oct_w2 *out);
+
+/* The same measurement without waiting: oct_batch_measure_async enqueues the
+ * roughness reduction of the replica in `slot` as it stands at this point of
+ * the batch's stream (after the MCS enqueued so far) and returns a ticket at
+ * once; oct_batch_poll reports whether it is done (*ready = 1, *out filled) or
+ * not yet (*ready = 0); oct_batch_wait blocks until it is.  The replica may be
+ * removed (and its slot reused) right after the call: the measurement reads
+ * the lattice before the removal takes effect.  The last 1024 tickets stay
+ * valid; an older one is refused with OCT_EINVAL.  Serving streams W^2 back
+ * this way without stalling the device (Sec. 2.1, Eq. (3); the scheduling is
+ * this library's, the paper has no counterpart). */
+int oct_batch_measure_async(oct_batch *b, int64_t slot, int64_t *ticket);
+int oct_batch_poll(oct_batch *b, int64_t ticket, oct_w2 *out, int *ready);
+int oct_batch_wait(oct_batch *b, int64_t ticket, oct_w2 *out);
 
 /* Planar lattice of the replica in `slot` (words = L*L/16).  Synchronises. */
 int oct_batch_get_planes(oct_batch *b, int64_t slot, uint32_t *host, size_t words);

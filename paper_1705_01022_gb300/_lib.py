@@ -116,6 +116,9 @@ _SIGNATURES = [
     ("oct_batch_remove", [_H, ctypes.c_int64], ctypes.c_int),
     ("oct_batch_run", [_H, ctypes.c_int64], ctypes.c_int),
     ("oct_batch_measure_slot", [_H, ctypes.c_int64, ctypes.POINTER(oct_w2)], ctypes.c_int),
+    ("oct_batch_measure_async", [_H, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    ("oct_batch_poll", [_H, ctypes.c_int64, ctypes.POINTER(oct_w2), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    ("oct_batch_wait", [_H, ctypes.c_int64, ctypes.POINTER(oct_w2)], ctypes.c_int),
     ("oct_batch_measure_w2", [_H, ctypes.POINTER(oct_w2), ctypes.c_int64], ctypes.c_int),
     ("oct_batch_get_planes", [_H, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
     ("oct_batch_snapshot", [_H, ctypes.c_int64], ctypes.c_int),
@@ -311,6 +314,25 @@ def oct_batch_remove(h: int, slot: int) -> None:
 def oct_batch_measure_slot(h: int, slot: int) -> oct_w2:
     out = oct_w2()
     _check(load().oct_batch_measure_slot(h, slot, ctypes.byref(out)), "oct_batch_measure_slot")
+    return out
+
+
+def oct_batch_measure_async(h: int, slot: int) -> int:
+    t = ctypes.c_int64()
+    _check(load().oct_batch_measure_async(h, slot, ctypes.byref(t)), "oct_batch_measure_async")
+    return t.value
+
+
+def oct_batch_poll(h: int, ticket: int):
+    """The measurement of a ticket if it is done, else None."""
+    out, ready = oct_w2(), ctypes.c_int()
+    _check(load().oct_batch_poll(h, ticket, ctypes.byref(out), ctypes.byref(ready)), "oct_batch_poll")
+    return out if ready.value else None
+
+
+def oct_batch_wait(h: int, ticket: int) -> oct_w2:
+    out = oct_w2()
+    _check(load().oct_batch_wait(h, ticket, ctypes.byref(out)), "oct_batch_wait")
     return out
 
 

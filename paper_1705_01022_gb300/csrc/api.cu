@@ -159,7 +159,8 @@ void destroy_members(oct_sim *s) {
     if (s->snap) cudaFree(s->snap);
     if (s->d_ac_rows) cudaFree(s->d_ac_rows);
     if (s->d_ac) cudaFree(s->d_ac);
-    for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : s->ev)
+        if (e) cudaEventDestroy(e);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
 }
 

@@ -153,6 +153,39 @@ uint32_t thr32(double p) { return static_cast<uint32_t>(std::floor(std::ldexp(p,
 
 }  // namespace
 
+namespace oct {
+namespace {
+
+// One of the two alternating copies of the work list (replica table, items,
+// warp descriptors, active slots).  A rebuild fills the copy the running work
+// does not read, from pinned staging memory, in stream order: no host wait.
+struct WorkBuf {
+    ReplicaDev *reps = nullptr;
+    size_t reps_cap = 0;
+    BatchItem *items = nullptr;
+    size_t items_cap = 0;
+    WarpDesc *descs = nullptr;
+    size_t descs_cap = 0;
+    uint32_t *active = nullptr;
+    size_t active_cap = 0;
+    char *host = nullptr;     // pinned staging of the last copy into this set
+    size_t host_cap = 0;
+    cudaEvent_t copied = nullptr;  // recorded after that copy
+};
+
+// An asynchronous W^2 measurement: the exact sums, the replica's counters and
+// its time, copied to pinned host memory behind an event.
+struct MeasureRecord {
+    W2Result res;
+    unsigned long long cnt[2];
+    uint32_t t;
+    uint32_t pad[3];
+};
+constexpr int kMeasureRing = 1024;
+
+}  // namespace
+}  // namespace oct
+
 struct oct_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -164,17 +197,12 @@ struct oct_batch {
     std::vector<char> used;
     std::vector<int64_t> free_slots;
     size_t capacity = 0;
-    oct::ReplicaDev *d_reps = nullptr;  // capacity entries
     uint32_t *d_t = nullptr;            // capacity MCS counters
     unsigned long long *counters = nullptr;  // 2 * capacity: net flips, draws
     // work list of the current membership
     bool dirty = true;
-    oct::BatchItem *d_items = nullptr;
-    size_t items_cap = 0;
-    oct::WarpDesc *d_descs = nullptr;
-    size_t descs_cap = 0;
-    uint32_t *d_active = nullptr;
-    size_t active_cap = 0;
+    oct::WorkBuf wb[2];
+    int cur = 0;  // the copy the enqueued work reads
     uint32_t n_active = 0;
     // work lists by kind = 2 * mode + (one sub-tile per warp); modes: 0 no
     // acceptance draws, 1 draws, 2 draws for both rates, 3 deposition only
@@ -195,6 +223,12 @@ struct oct_batch {
     int grid = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // asynchronous measurements: a ring of records (device and pinned host)
+    oct::MeasureRecord *d_req = nullptr;
+    oct::MeasureRecord *h_req = nullptr;
+    std::vector<cudaEvent_t> req_ev;
+    std::vector<int64_t> req_L;
+    int64_t req_next = 0;  // tickets handed out so far
     bool timing = false;
     std::vector<cudaEvent_t> ev;
     int ev_used = 0;
@@ -220,17 +254,26 @@ void batch_free(oct_batch *b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     cudaFree(b->d_ac_rows);
     cudaFree(b->d_ac);
-    cudaFree(b->d_reps);
     cudaFree(b->d_t);
     cudaFree(b->counters);
-    cudaFree(b->d_items);
-    cudaFree(b->d_descs);
-    cudaFree(b->d_active);
+    for (oct::WorkBuf &w : b->wb) {
+        cudaFree(w.reps);
+        cudaFree(w.items);
+        cudaFree(w.descs);
+        cudaFree(w.active);
+        if (w.host) cudaFreeHost(w.host);
+        if (w.copied) cudaEventDestroy(w.copied);
+    }
+    cudaFree(b->d_req);
+    if (b->h_req) cudaFreeHost(b->h_req);
+    for (cudaEvent_t e : b->req_ev)
+        if (e) cudaEventDestroy(e);  // ring events are created on first use
     cudaFree(b->d_queue);
     cudaFree(b->d_rows);
     cudaFree(b->d_w2);
     if (b->h_small) cudaFreeHost(b->h_small);
-    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
     if (b->pool) cudaMemPoolDestroy(b->pool);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
@@ -277,13 +320,17 @@ oct::ReplicaDev replica_dev(const oct_batch *b, int64_t slot) {
 }
 
 template <typename T>
-cudaError_t ensure(T **p, size_t *cap, size_t need) {
+cudaError_t ensure(T **p, size_t *cap, size_t need, cudaStream_t st) {
     if (need <= *cap) return cudaSuccess;
     size_t n = std::max<size_t>(need, 2 * *cap);
-    cudaFree(*p);
+    // stream-ordered: work already enqueued may still read the old buffer
+    if (*p) {
+        cudaError_t e = cudaFreeAsync(*p, st);
+        if (e != cudaSuccess) return e;
+    }
     *p = nullptr;
     *cap = 0;
-    cudaError_t e = cudaMalloc(p, sizeof(T) * n);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(p), sizeof(T) * n, st);
     if (e == cudaSuccess) *cap = n;
     return e;
 }
@@ -292,11 +339,9 @@ cudaError_t ensure(T **p, size_t *cap, size_t need) {
 cudaError_t grow_slots(oct_batch *b, size_t need) {
     if (need <= b->capacity) return cudaSuccess;
     const size_t n = std::max<size_t>(need, std::max<size_t>(64, 2 * b->capacity));
-    oct::ReplicaDev *r = nullptr;
     uint32_t *t = nullptr;
     unsigned long long *c = nullptr;
     cudaError_t e = cudaStreamSynchronize(b->stream);
-    if (e == cudaSuccess) e = cudaMalloc(&r, sizeof(oct::ReplicaDev) * n);
     if (e == cudaSuccess) e = cudaMalloc(&t, sizeof(uint32_t) * n);
     if (e == cudaSuccess) e = cudaMalloc(&c, sizeof(unsigned long long) * 2 * n);
     if (e == cudaSuccess && b->capacity) {
@@ -305,15 +350,12 @@ cudaError_t grow_slots(oct_batch *b, size_t need) {
             e = cudaMemcpy(c, b->counters, sizeof(unsigned long long) * 2 * b->capacity, cudaMemcpyDeviceToDevice);
     }
     if (e != cudaSuccess) {
-        cudaFree(r);
         cudaFree(t);
         cudaFree(c);
         return e;
     }
-    cudaFree(b->d_reps);
     cudaFree(b->d_t);
     cudaFree(b->counters);
-    b->d_reps = r;
     b->d_t = t;
     b->counters = c;
     b->capacity = n;
@@ -321,11 +363,13 @@ cudaError_t grow_slots(oct_batch *b, size_t need) {
     return cudaSuccess;
 }
 
-// Rebuilds the replica table and the warp work list of the active replicas.
+// Rebuilds the replica table and the warp work list of the active replicas
+// into the work-list copy the enqueued work does not read, by asynchronous
+// copies on the batch's stream (the host waits only for the staging memory of
+// the copy before last, long finished).
 cudaError_t rebuild(oct_batch *b) {
-    cudaError_t e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return e;
-    drop_graph(b);
+    cudaError_t e = cudaSuccess;
+    drop_graph(b);  // an executable graph still running is freed when it completes
     std::vector<oct::ReplicaDev> rd(b->capacity);
     std::vector<uint32_t> active;
     std::vector<oct::BatchItem> bucket[kModes][6][6];
@@ -367,20 +411,50 @@ cudaError_t rebuild(oct_batch *b) {
             }
         b->n_desc[kind] = static_cast<uint32_t>(descs.size()) - b->desc_first[kind];
     }
-    b->n_active = static_cast<uint32_t>(active.size());
-    e = ensure(&b->d_items, &b->items_cap, std::max<size_t>(1, items.size()));
-    if (e == cudaSuccess) e = ensure(&b->d_descs, &b->descs_cap, std::max<size_t>(1, descs.size()));
-    if (e == cudaSuccess) e = ensure(&b->d_active, &b->active_cap, std::max<size_t>(1, active.size()));
-    if (e == cudaSuccess && b->capacity)
-        e = cudaMemcpy(b->d_reps, rd.data(), sizeof(oct::ReplicaDev) * b->capacity, cudaMemcpyHostToDevice);
+    const int nxt = 1 - b->cur;
+    oct::WorkBuf &w = b->wb[nxt];
+    const size_t n_reps = std::max<size_t>(1, b->capacity);
+    e = ensure(&w.reps, &w.reps_cap, n_reps, b->stream);
+    if (e == cudaSuccess) e = ensure(&w.items, &w.items_cap, std::max<size_t>(1, items.size()), b->stream);
+    if (e == cudaSuccess) e = ensure(&w.descs, &w.descs_cap, std::max<size_t>(1, descs.size()), b->stream);
+    if (e == cudaSuccess) e = ensure(&w.active, &w.active_cap, std::max<size_t>(1, active.size()), b->stream);
+    // pinned staging: reps, items, descs, active back to back (16-byte aligned parts)
+    auto up16 = [](size_t v) { return (v + 15) & ~static_cast<size_t>(15); };
+    const size_t o_items = up16(sizeof(oct::ReplicaDev) * b->capacity);
+    const size_t o_descs = o_items + up16(sizeof(oct::BatchItem) * items.size());
+    const size_t o_active = o_descs + up16(sizeof(oct::WarpDesc) * descs.size());
+    const size_t bytes = std::max<size_t>(16, o_active + sizeof(uint32_t) * active.size());
+    if (e == cudaSuccess && w.copied) e = cudaEventSynchronize(w.copied);  // its last copy has left the staging
+    if (e == cudaSuccess && bytes > w.host_cap) {
+        if (w.host) cudaFreeHost(w.host);
+        w.host = nullptr;
+        w.host_cap = 0;
+        e = cudaMallocHost(reinterpret_cast<void **>(&w.host), 2 * bytes);
+        if (e == cudaSuccess) w.host_cap = 2 * bytes;
+    }
+    if (e == cudaSuccess && !w.copied) e = cudaEventCreateWithFlags(&w.copied, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    if (b->capacity) std::memcpy(w.host, rd.data(), sizeof(oct::ReplicaDev) * b->capacity);
+    if (!items.empty()) std::memcpy(w.host + o_items, items.data(), sizeof(oct::BatchItem) * items.size());
+    if (!descs.empty()) std::memcpy(w.host + o_descs, descs.data(), sizeof(oct::WarpDesc) * descs.size());
+    if (!active.empty()) std::memcpy(w.host + o_active, active.data(), sizeof(uint32_t) * active.size());
+    if (b->capacity)
+        e = cudaMemcpyAsync(w.reps, w.host, sizeof(oct::ReplicaDev) * b->capacity, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && !items.empty())
-        e = cudaMemcpy(b->d_items, items.data(), sizeof(oct::BatchItem) * items.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(w.items, w.host + o_items, sizeof(oct::BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                            b->stream);
     if (e == cudaSuccess && !descs.empty())
-        e = cudaMemcpy(b->d_descs, descs.data(), sizeof(oct::WarpDesc) * descs.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(w.descs, w.host + o_descs, sizeof(oct::WarpDesc) * descs.size(), cudaMemcpyHostToDevice,
+                            b->stream);
     if (e == cudaSuccess && !active.empty())
-        e = cudaMemcpy(b->d_active, active.data(), sizeof(uint32_t) * active.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) b->dirty = false;
-    return e;
+        e = cudaMemcpyAsync(w.active, w.host + o_active, sizeof(uint32_t) * active.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(w.copied, b->stream);
+    if (e != cudaSuccess) return e;
+    b->cur = nxt;
+    b->n_active = static_cast<uint32_t>(active.size());
+    b->dirty = false;
+    return cudaSuccess;
 }
 
 // Enqueues device step k of the current MCS of every active replica.
@@ -390,12 +464,13 @@ cudaError_t enqueue_step(oct_batch *b, uint32_t k, cudaStream_t st) {
         uint32_t *q = b->d_queue + kKinds * k + kind;
         cudaError_t e = cudaMemsetAsync(q, 0, sizeof(uint32_t), st);
         if (e != cudaSuccess) return e;
-        const oct::WarpDesc *descs = b->d_descs + b->desc_first[kind];
+        const oct::WorkBuf &w = b->wb[b->cur];
+        const oct::WarpDesc *descs = w.descs + b->desc_first[kind];
         const uint32_t nd = b->n_desc[kind];
         const int blocks = std::min<int>(b->grid, static_cast<int>((nd + oct::kBatchWarps - 1) / oct::kBatchWarps));
         const dim3 grid(blocks), block(oct::kBatchWarps * 32);
 #define OCT_BATCH(R, LS, SC) \
-    oct::batch_step_kernel<R, LS, SC><<<grid, block, 0, st>>>(b->d_reps, b->d_items, descs, nd, b->d_t, k, q)
+    oct::batch_step_kernel<R, LS, SC><<<grid, block, 0, st>>>(w.reps, w.items, descs, nd, b->d_t, k, q)
         switch (kind) {
             case 0: OCT_BATCH(false, true, 0); break;
             case 1: OCT_BATCH(false, false, 0); break;
@@ -416,7 +491,7 @@ cudaError_t enqueue_step(oct_batch *b, uint32_t k, cudaStream_t st) {
 cudaError_t enqueue_advance(oct_batch *b, cudaStream_t st) {
     if (b->n_active == 0) return cudaSuccess;
     const int blocks = static_cast<int>(std::min<uint32_t>(1024u, (b->n_active + 255u) / 256u));
-    oct::batch_advance_kernel<<<blocks, 256, 0, st>>>(b->d_t, b->d_active, b->n_active);
+    oct::batch_advance_kernel<<<blocks, 256, 0, st>>>(b->d_t, b->wb[b->cur].active, b->n_active);
     return cudaGetLastError();
 }
 
@@ -511,9 +586,95 @@ int measure_slot(oct_batch *b, int64_t slot, oct_w2 *out) {
     return OCT_OK;
 }
 
+// W^2 from an asynchronous measurement record (numerator in 128-bit integers).
+void record_to_w2(const oct::MeasureRecord &r, int64_t L, oct_w2 *out) {
+    const __int128 N = static_cast<__int128>(L) * L;
+    const __int128 S2 = static_cast<__int128>((static_cast<unsigned __int128>(r.res.s2_hi) << 64) | r.res.s2_lo);
+    const __int128 num = N * S2 - static_cast<__int128>(r.res.s1) * r.res.s1;
+    out->t = static_cast<int64_t>(r.t);
+    out->n_sites = static_cast<int64_t>(N);
+    out->s1 = r.res.s1;
+    out->s2_lo = r.res.s2_lo;
+    out->s2_hi = r.res.s2_hi;
+    out->net_flips = static_cast<int64_t>(r.cnt[0]);
+    out->hmax = r.res.hmax;
+    out->w2 = static_cast<double>(num) / (static_cast<double>(N) * static_cast<double>(N));
+}
+
+int ticket_index(oct_batch *b, int64_t ticket, int *idx) {
+    if (ticket < 0 || ticket >= b->req_next || ticket < b->req_next - oct::kMeasureRing)
+        return bfail(OCT_EINVAL, "unknown or expired measurement ticket");
+    *idx = static_cast<int>(ticket % oct::kMeasureRing);
+    return OCT_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int oct_batch_measure_async(oct_batch *b, int64_t slot, int64_t *ticket) {
+    if (!b || !ticket || !valid_slot(b, slot)) return bfail(OCT_EINVAL, "no replica in that slot");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    const int64_t L = b->reps[slot].L;
+    if (!b->d_req) {
+        BATCH_CUDA(cudaMalloc(&b->d_req, sizeof(oct::MeasureRecord) * oct::kMeasureRing));
+        BATCH_CUDA(cudaMallocHost(&b->h_req, sizeof(oct::MeasureRecord) * oct::kMeasureRing));
+        b->req_ev.assign(oct::kMeasureRing, nullptr);
+        b->req_L.assign(oct::kMeasureRing, 0);
+    }
+    const int i = static_cast<int>(b->req_next % oct::kMeasureRing);
+    if (b->req_ev[i]) {
+        BATCH_CUDA(cudaEventSynchronize(b->req_ev[i]));  // the ring wrapped: the oldest record is done
+    } else {
+        BATCH_CUDA(cudaEventCreateWithFlags(&b->req_ev[i], cudaEventDisableTiming));
+    }
+    if (L > b->rows_cap) {  // stream-ordered: an earlier measurement may still use the old rows
+        if (b->d_rows) BATCH_CUDA(cudaFreeAsync(b->d_rows, b->stream));
+        b->d_rows = nullptr;
+        b->rows_cap = 0;
+        BATCH_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&b->d_rows), sizeof(oct::W2RowSums) * L, b->stream));
+        b->rows_cap = L;
+    }
+    oct::MeasureRecord *d = b->d_req + i;
+    BATCH_CUDA(oct::launch_w2(b->lat[slot], static_cast<uint32_t>(L), b->d_rows, &d->res, b->stream));
+    BATCH_CUDA(cudaMemcpyAsync(d->cnt, b->counters + 2 * slot, 2 * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToDevice, b->stream));
+    BATCH_CUDA(cudaMemcpyAsync(&d->t, b->d_t + slot, sizeof(uint32_t), cudaMemcpyDeviceToDevice, b->stream));
+    BATCH_CUDA(cudaMemcpyAsync(b->h_req + i, d, sizeof(oct::MeasureRecord), cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(cudaEventRecord(b->req_ev[i], b->stream));
+    b->req_L[i] = L;
+    *ticket = b->req_next++;
+    return OCT_OK;
+}
+
+int oct_batch_poll(oct_batch *b, int64_t ticket, oct_w2 *out, int *ready) {
+    if (!b || !out || !ready) return bfail(OCT_EINVAL, "NULL argument");
+    int i = 0;
+    int rc = ticket_index(b, ticket, &i);
+    if (rc) return rc;
+    BATCH_CUDA(cudaSetDevice(b->device));
+    const cudaError_t e = cudaEventQuery(b->req_ev[i]);
+    if (e == cudaErrorNotReady) {
+        (void)cudaGetLastError();  // "not ready" is an answer, not an error: do not leave it behind
+        *ready = 0;
+        return OCT_OK;
+    }
+    if (e != cudaSuccess) return bfail(OCT_ECUDA, std::string("oct_batch_poll: ") + cudaGetErrorString(e));
+    record_to_w2(b->h_req[i], b->req_L[i], out);
+    *ready = 1;
+    return OCT_OK;
+}
+
+int oct_batch_wait(oct_batch *b, int64_t ticket, oct_w2 *out) {
+    if (!b || !out) return bfail(OCT_EINVAL, "NULL argument");
+    int i = 0;
+    int rc = ticket_index(b, ticket, &i);
+    if (rc) return rc;
+    BATCH_CUDA(cudaSetDevice(b->device));
+    BATCH_CUDA(cudaEventSynchronize(b->req_ev[i]));
+    record_to_w2(b->h_req[i], b->req_L[i], out);
+    return OCT_OK;
+}
 
 int oct_replica_seed(uint64_t master_seed, uint32_t r, uint64_t *seed) {
     if (!seed) return bfail(OCT_EINVAL, "seed must not be NULL");

@@ -13,8 +13,12 @@ the job's dynamics):
   (up to the next measurement or finish among them, at most ``max_chunk``),
   so work of jobs that arrived at different times overlaps on the device;
 * at a job's measurement times its exact W^2 is computed on the device and
-  handed to the ``on_result`` callback (streamed back);
-* a job that reaches t_max leaves the batch and returns its memory.
+  handed to the ``on_result`` callback (streamed back).  With a batch that
+  measures asynchronously (``measure_async`` / ``poll``), the reduction is
+  enqueued behind the job's MCS and the result delivered when it is done, so
+  the host never waits for the device between ticks;
+* a job that reaches t_max leaves the batch and returns its memory; its
+  latency ends when its last result has been delivered.
 
 Each job's trajectory is the same as running it alone: its random numbers
 depend only on its own key and its own time, not on the mix.
@@ -124,6 +128,8 @@ class ServingEngine:
         self.waiting: deque[Job] = deque()
         self.running: dict[int, Job] = {}
         self.finished: list[Job] = []
+        self.pending: deque = deque()  # (job, ticket) of asynchronous measurements, in stream order
+        self.async_measure = hasattr(self.batch, "measure_async")
         self.ticks = 0
         self.mcs_attempts = 0
 
@@ -166,19 +172,45 @@ class ServingEngine:
         for slot, job in list(self.running.items()):
             job.t += n
             self.mcs_attempts += n * job.L * job.L
+            last = job.t >= job.t_max
             if job.t in job.measure_at:
-                res = self.batch.measure(slot)
-                assert res[0] == job.t, (res[0], job.t)
-                job.results.append(res)
-                if self.on_result:
-                    self.on_result(job, res)
-            if job.t >= job.t_max:
+                if self.async_measure:
+                    self.pending.append((job, self.batch.measure_async(slot)))
+                else:
+                    self._deliver_one(job, self.batch.measure(slot), now)
+            if last:
                 self.batch.remove(slot)
                 del self.running[slot]
                 self.used -= footprint(job.L)
-                job.done = self.clock() if now is None else now
-                self.finished.append(job)
+                if not self.async_measure or job.t_max not in job.measure_at:
+                    job.done = self.clock() if now is None else now
+                    self.finished.append(job)
+        self.deliver()
         return True
+
+    def _deliver_one(self, job: Job, res, now=None) -> None:
+        assert res[0] in job.measure_at, (res[0], job.measure_at)
+        job.results.append(res)
+        if self.on_result:
+            self.on_result(job, res)
+        if self.async_measure and res[0] == job.t_max:
+            job.done = self.clock() if now is None else now
+            self.finished.append(job)
+
+    def deliver(self, block: bool = False) -> int:
+        """Hands the finished asynchronous measurements to their jobs, oldest
+        first (they finish in stream order); with block, waits for all.
+        Returns the number delivered."""
+        n = 0
+        while self.pending:
+            job, ticket = self.pending[0]
+            res = self.batch.wait(ticket) if block else self.batch.poll(ticket)
+            if res is None:
+                break
+            self.pending.popleft()
+            self._deliver_one(job, res)
+            n += 1
+        return n
 
     def run(self, jobs, realtime: bool = True, sleep=time.sleep) -> list[Job]:
         """Serves jobs (sorted by arrival, times relative to the start).  In
@@ -187,14 +219,18 @@ class ServingEngine:
         for job in sorted(jobs, key=lambda j: j.arrival):
             job.arrival += t0
             self.submit(job)
-        while self.waiting or self.running:
+        while self.waiting or self.running or self.pending:
             now = self.clock()
-            if not self.tick(now) and self.waiting:
-                wait = self.waiting[0].arrival - self.clock()
-                if wait > 0 and realtime:
-                    sleep(min(wait, 0.05))
-                elif not realtime:
-                    self.clock_skip(self.waiting[0].arrival)
+            if not self.tick(now):
+                if self.pending and not self.waiting:
+                    self.deliver(block=True)
+                elif self.waiting:
+                    self.deliver()
+                    wait = self.waiting[0].arrival - self.clock()
+                    if wait > 0 and realtime:
+                        sleep(min(wait, 0.05 if not self.pending else 0.001))
+                    elif not realtime:
+                        self.clock_skip(self.waiting[0].arrival)
         return self.finished
 
     def cancel(self, jid: int) -> bool:
@@ -273,6 +309,20 @@ class GpuBatch:
     def measure(self, slot: int):
         m = self._lib.oct_batch_measure_slot(self.h, slot)
         return (m.t, m.s1, m.s2, m.w2, m.net_flips)
+
+    @staticmethod
+    def _tuple(m):
+        return (m.t, m.s1, m.s2, m.w2, m.net_flips)
+
+    def measure_async(self, slot: int) -> int:
+        return self._lib.oct_batch_measure_async(self.h, slot)
+
+    def poll(self, ticket: int):
+        m = self._lib.oct_batch_poll(self.h, ticket)
+        return None if m is None else self._tuple(m)
+
+    def wait(self, ticket: int):
+        return self._tuple(self._lib.oct_batch_wait(self.h, ticket))
 
     def close(self) -> None:
         if self.h:

@@ -93,3 +93,41 @@ def test_invalid_replicas_rejected(g):
         g.Batch([(100, 1.0, 0.0, 1)])
     with pytest.raises(_lib.OctError):
         g.Batch([(256, 1.0, 0.0, 1, 96, 32)])
+
+
+def test_async_measurements_equal_sync_ones(g):
+    """oct_batch_measure_async behind the batch's MCS equals the synchronous
+    measurement of the same state, also when the replica is removed (and its
+    slot reused) right after the call and when membership changes between
+    runs (the work list is rebuilt without waiting for the device)."""
+    from paper_1705_01022_gb300 import _lib
+    reps = _replicas(g, master=13)[:10]
+    with g.Batch(reps) as b, g.Batch(reps) as ref:
+        tickets = []
+        for rnd in range(3):
+            b.run(2)
+            ref.run(2)
+            for slot in range(len(reps)):
+                if rnd < 2 or slot % 2 == 0:
+                    tickets.append((rnd, slot, _lib.oct_batch_measure_async(b.h, slot)))
+            want = {slot: _lib.oct_batch_measure_slot(ref.h, slot) for slot in range(len(reps))
+                    if rnd < 2 or slot % 2 == 0}
+            for r_, slot, tk in tickets:
+                if r_ != rnd:
+                    continue
+                got = _lib.oct_batch_wait(b.h, tk)
+                w = want[slot]
+                assert (got.t, got.s1, got.s2, got.hmax, got.net_flips, got.w2) == \
+                    (w.t, w.s1, w.s2, w.hmax, w.net_flips, w.w2), (rnd, slot)
+            if rnd == 1:
+                # odd slots leave right after their measurement; one new replica joins each batch
+                for slot in range(1, len(reps), 2):
+                    _lib.oct_batch_remove(b.h, slot)
+                    _lib.oct_batch_remove(ref.h, slot)
+                extra = _lib.oct_replica()
+                extra.L, extra.p, extra.q, extra.seed = 256, 0.95, 0.05, 4242
+                assert _lib.oct_batch_add(b.h, extra) == _lib.oct_batch_add(ref.h, extra)
+        got = _lib.oct_batch_poll(b.h, tickets[-1][2])
+        assert got is not None  # long done: poll reports it ready
+        with pytest.raises(_lib.OctError):
+            _lib.oct_batch_poll(b.h, 10**6)

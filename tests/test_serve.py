@@ -152,3 +152,41 @@ def test_jsonl_metrics_lines():
         assert set(rec) == {"job", "L", "p", "q", "t", "s1", "s2", "n_sites", "w2", "net_flips", "since_arrival_s"}
         assert rec["n_sites"] == 128 * 128 and rec["since_arrival_s"] >= 0
     assert [r["t"] for r in lines if r["job"] == 0] == jobs[0].measure_at
+
+
+class FakeAsyncBatch(FakeBatch):
+    """Measures asynchronously: a measurement enqueued before a run completes
+    only once that later run has been issued (like a reduction queued behind
+    the MCS on one stream); a slot may be removed while its measurement is in
+    flight."""
+
+    def __init__(self, clock, rate=1e6):
+        super().__init__(clock, rate)
+        self.queue = []  # [result, runs issued when enqueued]
+
+    def measure_async(self, slot):
+        self.queue.append([self.measure(slot), len(self.runs)])
+        return len(self.queue) - 1
+
+    def poll(self, ticket):
+        res, at = self.queue[ticket]
+        return res if len(self.runs) > at else None
+
+    def wait(self, ticket):
+        return self.queue[ticket][0]
+
+
+def test_asynchronous_measurements_are_all_delivered_in_order():
+    clock = VirtualClock()
+    fb = FakeAsyncBatch(clock)
+    eng = serve.ServingEngine(3 * serve.footprint(1024), batch=fb, max_chunk=16, clock=clock)
+    assert eng.async_measure
+    jobs = [serve.Job(i, 1024 if i % 2 else 512, 1.0, 0.0, i, t_max=20 + 7 * i,
+                      arrival=0.5 * i, measure_at=serve.log_times(20 + 7 * i)) for i in range(8)]
+    done = eng.run(jobs, realtime=False)
+    assert len(done) == 8 and not eng.pending and eng.used == 0
+    for j in done:
+        assert [r[0] for r in j.results] == j.measure_at
+        assert j.done >= j.admitted >= j.arrival
+    # the host never waited on a measurement while jobs were still running
+    assert len(fb.queue) == sum(len(j.measure_at) for j in jobs)

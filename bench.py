@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--cell-steps", type=int, default=2, help="timed MCS per coarse thread-cell shape")
     ap.add_argument("--ac-reps", type=int, default=5)
     ap.add_argument("--tune-mcs", type=int, default=1)
+    ap.add_argument("--strips", action="store_true",
+                    help="with N > 1 ranks: one lattice split into N row strips (strong scaling) "
+                         "instead of N independent replicas")
     return ap.parse_args()
 
 
@@ -496,6 +499,51 @@ def combine_ranks(ms_local: float, attempts_local: int, dist=None, device="cpu")
     return float(t.item()), int(n.item())
 
 
+def strips_main(a, rank, world, local, dist, torch, g, _lib):
+    """Strong scaling: one L x L lattice split into `world` row strips, one per
+    GPU, halo rows exchanged by NCCL between device steps (strips.py).  Prints
+    one JSON line on rank 0."""
+    from paper_1705_01022_gb300 import strips
+    lay = strips.StripLayout(a.L, a.By, world, rank)
+    eng = strips.GpuStripEngine(lay, a.p, a.q, a.seed, a.Bx)
+    run = strips.StripRunner(lay, eng, a.seed, dist)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        dist.barrier()
+        torch.cuda.synchronize()
+
+    run.run(a.warmup)
+    barrier()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        start.record(stream)
+        run.run(a.steps)
+        end.record(stream)
+        barrier()
+    ms = start.elapsed_time(end)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    w = run.measure()
+    if rank == 0:
+        cfg = workload(a)
+        cfg.update({"form": "strips", "parallelism": f"strips{world}", "strip_rows": lay.H, "held_rows": lay.held})
+        print(json.dumps({
+            "metric": METRIC, "value": a.L * a.L * a.steps / (ms_max * 1e6), "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": cfg,
+            "clocks": clk.summary(), "roofline": None, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": 4 * a.steps * world,
+            "w2": {"t": w.t, "w2": w.w2, "s1": w.s1, "hmax": w.hmax, "how": "exact, combined from the strips"},
+            "note": "one lattice over all ranks; halo rows by NCCL point-to-point between device steps"}),
+              flush=True)
+    eng.close()
+    dist.destroy_process_group()
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -518,6 +566,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     g.build()
+    if a.strips and world > 1:
+        return strips_main(a, rank, world, local, dist, torch, g, _lib)
     # a dedicated stream: torch events and the library's kernels share it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)

@@ -90,7 +90,15 @@ typedef struct {
     void *lattice;
     int32_t no_init;
     int32_t scheme;
-    int32_t reserved[6];
+    /* Row strip of a lattice split over several devices (strip_rows = 0: the
+     * handle holds the whole lattice).  The handle's buffer then holds
+     * held_rows full rows from global row strip_row0 on (planar: held_rows
+     * rows of X, then held_rows rows of Y; held_rows * L / 4 bytes), and its
+     * device steps update the device-tile rows whose first row lies in
+     * [strip_row0, strip_row0 + strip_rows).  strip_row0 and strip_rows must be
+     * multiples of 2*By, held_rows >= strip_rows + 2*By and <= L. */
+    int32_t strip_row0, strip_rows, held_rows;
+    int32_t reserved[3];
 } oct_params;
 
 /* Exact roughness, Eq. (3), read as the mean over all L^2 sites:
@@ -136,6 +144,47 @@ int oct_create_ex(const oct_params *prm, oct_sim **out);
  * of single-hit DT on every sub-tile of one set (Sec. 3.1).  Asynchronous on
  * the handle's stream.  Errors: OCT_EINVAL (n < 0 or t would pass 2^32-1). */
 int oct_run_mcs(oct_sim *s, int64_t n);
+
+/* One device step at a time (for a lattice split into row strips over several
+ * devices, whose halo rows are exchanged between device steps).
+ * oct_device_step enqueues device step k (0..3, in this order) of the current
+ * MCS: the sub-tiles of set perm[k] (Sec. 3, DTr); oct_end_mcs then advances
+ * t by one.  Four device steps and oct_end_mcs equal oct_run_mcs(s, 1).
+ * Errors: OCT_EINVAL (k outside 0..3, t would pass 2^32-1). */
+int oct_device_step(oct_sim *s, int k);
+int oct_end_mcs(oct_sim *s);
+
+/* The device layer's draw of MCS t for a lattice of side L under `seed`
+ * (Sec. 3, DTr), computed on the host exactly as the kernels do: the origin
+ * (ox, oy) and the order perm[0..3] of the four sub-tile sets (set sigma is
+ * quadrant (sigma & 1, sigma >> 1) of every device tile).  Strip exchanges
+ * need it: after device step k of a strip, the rows of the next strip it has
+ * changed are its first ((oy - strip_row0) mod 2By) + By*(perm[k] >> 1) -
+ * By + 1 (none if that is <= 0). */
+int oct_mcs_draw(uint64_t seed, int64_t L, uint32_t t, int64_t *ox, int64_t *oy, int32_t perm[4]);
+
+/* Exact roughness of a lattice split into row strips (Eq. (3)).  For its own
+ * rows (buffer rows 0 .. strip_rows-1) a strip handle reports, with heights
+ * e_j + r(x) relative to its first row's h(0, .) (e_j = sum over its rows
+ * 1..j of 2 Y(0,.) - 1, r as for W^2):
+ *   rows, L, f = 2 Y(0, first row) - 1, e_last = e of its last row,
+ *   p1 = sum (e_j + r), p2 = sum (e_j + r)^2 (128-bit, non-negative),
+ *   lo = min (e_j + r), hi = max (e_j + r), net_flips.
+ * oct_strip_combine takes the strips of one lattice in row order (their rows
+ * must add up to L) and forms S1, S2, hmax and W^2 exactly: the first row of
+ * strip r stands at B_r = B_{r-1} + e_last_{r-1} + f_r (B_0 = 0), so its rows
+ * add L rows B_r + p1 to S1 and L rows B_r^2 + 2 B_r p1 + p2 to S2.
+ * oct_strip_measure synchronises the handle's stream. */
+typedef struct {
+    int64_t rows, L;
+    int64_t f, e_last;
+    int64_t p1;
+    uint64_t p2_lo, p2_hi;
+    int64_t lo, hi;
+    int64_t t, net_flips;
+} oct_strip_sums;
+int oct_strip_measure(oct_sim *s, oct_strip_sums *out);
+int oct_strip_combine(const oct_strip_sums *parts, int64_t n, oct_w2 *out);
 
 /* Computes the exact roughness of the current lattice (Eq. (3)); synchronises
  * the handle's stream.  OCT_EINVAL while an asynchronous measurement of the

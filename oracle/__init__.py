@@ -114,6 +114,7 @@ def lib():
         L.oo_subtile_step_sites.argtypes = [ctypes.POINTER(_Params), u32, u32, u32, i64, _P_i64, _P_i64]
         L.oo_subtile_steps_many.argtypes = [ctypes.POINTER(_Params), u64, i64, u32, u32, u32, i64, i64,
                                             i64, _P_u8, _P_u8, _P_u8, _P_u8, _P_i64]
+        L.oo_device_step_strip.argtypes = [ctypes.POINTER(_Params), u32, u32, i64, i64, i64, _P_u8, _P_u8, P_i64]
         L.oo_set_plant.argtypes = [ctypes.c_int]
         L.oo_set_tie_log.argtypes = [ctypes.c_void_p, i64]
         L.oo_tie_log_count.restype = i64
@@ -263,6 +264,17 @@ def subtile_step_sites(prm: "Params", t: int, k: int, T: int, s: int):
     if lib().oo_subtile_step_sites(ctypes.byref(prm.c()), t, k, T, s, lx, ly) != 0:
         raise ValueError("invalid parameters")
     return lx, ly
+
+
+def device_step_strip(Xs, Ys, prm: "Params", t: int, k: int, a: int, Hs: int) -> int:
+    """Device step k of MCS t on the row strip [a, a + Hs) of the multi-GPU
+    partition, in place on the held rows (Xs, Ys) (shape (rows, L), first row
+    = global row a).  Returns the net flips."""
+    net = ctypes.c_int64(0)
+    rc = lib().oo_device_step_strip(ctypes.byref(prm.c()), t, k, a, Hs, Xs.shape[0], Xs, Ys, ctypes.byref(net))
+    if rc != 0:
+        raise ValueError(f"strip step failed ({rc})")
+    return int(net.value)
 
 
 def subtile_steps_many(prm: "Params", seed0: int, n_runs: int, t: int, k: int, T: int, x0: int, y0: int,

@@ -738,6 +738,39 @@ int oo_dtrdt_run(const oo_params *P, uint8_t *X, uint8_t *Y, uint32_t t0, uint32
     return 0;
 }
 
+int oo_device_step_strip(const oo_params *P, uint32_t t, uint32_t k, int64_t a, int64_t Hs, int64_t rows,
+                         uint8_t *Xs, uint8_t *Ys, int64_t *net_flips) {
+    /* Device step k of MCS t restricted to the device-tile rows whose first row
+     * (oy + 2By ty) mod L lies in [a, a + Hs): the strip partition of the
+     * multi-GPU layout.  (Xs, Ys) hold `rows` full rows from global row a on
+     * (the strip and the rows below it that its sub-tiles reach). */
+    if (oo_check_params(P)) return -1;
+    if (Hs < 1 || rows < 1 || rows > P->L) return -1;
+    uint32_t key[2];
+    seed_key(P->seed, key);
+    int64_t ox, oy;
+    int perm[4];
+    oo_mcs_draw(P, t, &ox, &oy, perm);
+    const int64_t tiles_x = P->L / (2 * P->Bx), tiles_y = P->L / (2 * P->By);
+    const int sigma = perm[k];
+    const int64_t sx = sigma & 1, sy = sigma >> 1;
+    view_t v = {P->L, 0, wrap(a, P->L), P->L, rows, Xs, Ys};
+    int64_t net = 0;
+    for (int64_t ty = 0; ty < tiles_y; ++ty) {
+        const int64_t yt = wrap(oy + 2 * P->By * ty, P->L);
+        if (wrap(yt - a, P->L) >= Hs) continue;  /* another strip's tile row */
+        for (int64_t tx = 0; tx < tiles_x; ++tx) {
+            const uint32_t T = (uint32_t)(ty * tiles_x + tx);
+            const int64_t x0 = wrap(ox + 2 * P->Bx * tx + P->Bx * sx, P->L);
+            const int64_t y0 = wrap(yt + P->By * sy, P->L);
+            if (!footprint_inside(&v, x0, y0, P->Bx, P->By)) return -2;  /* strip too short */
+            run_subtile(P, key, t, k, T, x0, y0, &v, &net, NULL, NULL, P->cx * P->cy);
+        }
+    }
+    if (net_flips) *net_flips += net;
+    return 0;
+}
+
 int oo_dtrdt_mcs_window(const oo_params *P, uint32_t t, int64_t wx, int64_t wy, int64_t W,
                         int64_t H, uint8_t *Xw, uint8_t *Yw, int64_t *net_flips) {
     if (oo_check_params(P)) return -1;

@@ -121,6 +121,15 @@ uint32_t oo_dtrdt_tail_word(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, u
 int oo_dtrdt_mcs_window(const oo_params *prm, uint32_t t, int64_t wx, int64_t wy,
                         int64_t W, int64_t H, uint8_t *Xw, uint8_t *Yw, int64_t *net_flips);
 
+/* Device step k of MCS t on one row strip of the multi-GPU partition: the
+ * device-tile rows whose first row (oy + 2By ty) mod L lies in [a, a + Hs)
+ * are updated.  Xs/Ys hold `rows` full rows from global row a on (index
+ * j*L + x for global row (a + j) mod L), which must cover the sub-tiles of
+ * those tile rows and their +y halo row.  Adds the net flips.  Returns 0, -1
+ * for invalid parameters, -2 if a sub-tile reaches past the held rows. */
+int oo_device_step_strip(const oo_params *P, uint32_t t, uint32_t k, int64_t a, int64_t Hs, int64_t rows,
+                         uint8_t *Xs, uint8_t *Ys, int64_t *net_flips);
+
 /* Local sites (lx[i], ly[i]) in the sub-tile of the attempts of every thread
  * cell i = (TC row)*(Bx/cx) + (TC column) in collective step s of sub-tile T,
  * device step k, MCS t (the block layer's site selection alone, for tests of

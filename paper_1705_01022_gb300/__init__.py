@@ -23,12 +23,16 @@ class Simulation:
 
     ``stream``: a ``torch.cuda.Stream`` (or raw cudaStream_t address) to run on;
     ``lattice``: an external device buffer (a torch tensor or raw address) of
-    L*L/4 bytes that the handle uses in place of its own allocation."""
+    L*L/4 bytes (held_rows*L/4 for a strip) that the handle uses in place of
+    its own allocation; ``strip``: (first row, rows owned, rows held) when the
+    handle holds one row strip of a lattice split over devices."""
 
     def __init__(self, L: int, p: float, q: float, seed: int, Bx: int = 0, By: int = 0,
                  cx: int = 0, cy: int = 0, stream=None, lattice=None, no_init: bool = False,
-                 scheme: int = 0):
+                 scheme: int = 0, strip=None):
         prm = oct_params()
+        if strip is not None:  # (first row, rows owned, rows held) of a row strip (see strips.py)
+            prm.strip_row0, prm.strip_rows, prm.held_rows = strip
         prm.L, prm.p, prm.q, prm.seed = L, p, q, seed
         prm.Bx, prm.By, prm.cx, prm.cy = Bx, By, cx, cy
         prm.stream = _address(stream, "cuda_stream")

@@ -28,7 +28,14 @@ class oct_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("Bx", ctypes.c_int32), ("By", ctypes.c_int32),
                 ("cx", ctypes.c_int32), ("cy", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("lattice", ctypes.c_void_p), ("no_init", ctypes.c_int32),
-                ("scheme", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("scheme", ctypes.c_int32), ("strip_row0", ctypes.c_int32), ("strip_rows", ctypes.c_int32),
+                ("held_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class oct_strip_sums(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("L", ctypes.c_int64), ("f", ctypes.c_int64), ("e_last", ctypes.c_int64),
+                ("p1", ctypes.c_int64), ("p2_lo", ctypes.c_uint64), ("p2_hi", ctypes.c_uint64),
+                ("lo", ctypes.c_int64), ("hi", ctypes.c_int64), ("t", ctypes.c_int64), ("net_flips", ctypes.c_int64)]
 
 
 class oct_w2(ctypes.Structure):
@@ -83,6 +90,12 @@ _SIGNATURES = [
                     ctypes.POINTER(_H)], ctypes.c_int),
     ("oct_create_ex", [ctypes.POINTER(oct_params), ctypes.POINTER(_H)], ctypes.c_int),
     ("oct_run_mcs", [_H, ctypes.c_int64], ctypes.c_int),
+    ("oct_device_step", [_H, ctypes.c_int], ctypes.c_int),
+    ("oct_end_mcs", [_H], ctypes.c_int),
+    ("oct_mcs_draw", [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int64),
+                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    ("oct_strip_measure", [_H, ctypes.POINTER(oct_strip_sums)], ctypes.c_int),
+    ("oct_strip_combine", [ctypes.POINTER(oct_strip_sums), ctypes.c_int64, ctypes.POINTER(oct_w2)], ctypes.c_int),
     ("oct_measure_w2", [_H, ctypes.POINTER(oct_w2)], ctypes.c_int),
     ("oct_measure_w2_async", [_H], ctypes.c_int),
     ("oct_w2_wait", [_H, ctypes.POINTER(oct_w2)], ctypes.c_int),
@@ -189,6 +202,34 @@ def oct_create_ex(prm: oct_params) -> int:
 
 def oct_run_mcs(h: int, n: int) -> None:
     _check(load().oct_run_mcs(h, n), "oct_run_mcs")
+
+
+def oct_device_step(h: int, k: int) -> None:
+    _check(load().oct_device_step(h, k), "oct_device_step")
+
+
+def oct_end_mcs(h: int) -> None:
+    _check(load().oct_end_mcs(h), "oct_end_mcs")
+
+
+def oct_mcs_draw(seed: int, L: int, t: int):
+    """(ox, oy, perm) of MCS t, as the kernels draw them."""
+    ox, oy, perm = ctypes.c_int64(), ctypes.c_int64(), (ctypes.c_int32 * 4)()
+    _check(load().oct_mcs_draw(seed, L, t, ctypes.byref(ox), ctypes.byref(oy), perm), "oct_mcs_draw")
+    return ox.value, oy.value, list(perm)
+
+
+def oct_strip_measure(h: int) -> oct_strip_sums:
+    out = oct_strip_sums()
+    _check(load().oct_strip_measure(h, ctypes.byref(out)), "oct_strip_measure")
+    return out
+
+
+def oct_strip_combine(parts) -> oct_w2:
+    arr = (oct_strip_sums * len(parts))(*parts)
+    out = oct_w2()
+    _check(load().oct_strip_combine(arr, len(parts), ctypes.byref(out)), "oct_strip_combine")
+    return out
 
 
 def oct_measure_w2(h: int) -> oct_w2:

@@ -3,6 +3,7 @@
 // method runs in the kernels of dtrdt.cu and lattice.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +13,7 @@
 
 #include "../../include/oct.h"
 #include "oct_internal.h"
+#include "philox.cuh"
 
 namespace {
 
@@ -70,6 +72,8 @@ struct oct_sim {
     uint64_t seed = 0;
     int Bx = 0, By = 0, cx = 4, cy = 4;
     int scheme = 0;
+    int64_t strip_row0 = 0, strip_rows = 0, held_rows = 0;  // strip_rows = 0: the whole lattice
+    int next_k = 0;  // next device step of oct_device_step
     uint32_t *lat = nullptr;
     bool own_lat = false;
     cudaStream_t stream = nullptr;
@@ -145,7 +149,21 @@ int validate(const oct_params *prm, int *Bx, int *By, int *cx, int *cy) {
     if (L % (2 * *Bx) || L % (2 * *By)) return fail(OCT_EINVAL, "L must be a multiple of 2Bx and 2By");
     if (prm->scheme != OCT_SCHEME_DT && prm->scheme != OCT_SCHEME_DB && prm->scheme != OCT_SCHEME_DTR)
         return fail(OCT_EINVAL, "scheme must be OCT_SCHEME_DT, OCT_SCHEME_DB or OCT_SCHEME_DTR");
+    if (prm->strip_rows || prm->strip_row0 || prm->held_rows) {
+        const int64_t t2 = 2 * static_cast<int64_t>(*By);
+        if (prm->strip_rows <= 0 || prm->strip_rows % t2 || prm->strip_row0 < 0 || prm->strip_row0 % t2 ||
+            prm->strip_row0 >= L || prm->strip_rows > L || prm->held_rows < prm->strip_rows + t2 ||
+            prm->held_rows > L)
+            return fail(OCT_EINVAL, "strip: strip_row0, strip_rows multiples of 2*By, strip_rows + 2*By <= "
+                                    "held_rows <= L");
+    }
     return OCT_OK;
+}
+
+bool is_strip(const oct_sim *s) { return s->strip_rows > 0; }
+
+int whole_only(const oct_sim *s, const char *what) {
+    return fail(OCT_EINVAL, std::string(what) + " needs a handle holding the whole lattice (this one holds a strip)");
 }
 
 void destroy_members(oct_sim *s) {
@@ -179,8 +197,12 @@ int sim_create(const oct_params *prm, oct_sim **out) {
     s->cx = cx;
     s->cy = cy;
     s->scheme = prm->scheme;
+    s->strip_row0 = prm->strip_row0;
+    s->strip_rows = prm->strip_rows;
+    s->held_rows = prm->strip_rows ? prm->held_rows : 0;
+    const int64_t plane_rows = is_strip(s) ? s->held_rows : s->L;
     cudaError_t e = cudaGetDevice(&s->device);
-    const size_t lat_bytes = static_cast<size_t>(s->L) * static_cast<size_t>(s->L) / 4;
+    const size_t lat_bytes = static_cast<size_t>(plane_rows) * static_cast<size_t>(s->L) / 4;
     if (e == cudaSuccess) {
         if (prm->stream) {
             s->stream = static_cast<cudaStream_t>(prm->stream);
@@ -211,7 +233,8 @@ int sim_create(const oct_params *prm, oct_sim **out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_t, 0, sizeof(uint32_t), s->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(s->d_net, 0, sizeof(unsigned long long) * 3 * oct::kNetSlots, s->stream);
-    if (e == cudaSuccess && !prm->no_init) e = oct::launch_init_flat(s->lat, static_cast<uint32_t>(s->L), s->stream);
+    if (e == cudaSuccess && !prm->no_init)
+        e = oct::launch_init_flat_rows(s->lat, static_cast<uint32_t>(s->L), static_cast<uint32_t>(plane_rows), s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
         const bool oom = (e == cudaErrorMemoryAllocation);
@@ -251,6 +274,9 @@ int sim_create(const oct_params *prm, oct_sim **out) {
                : (s->scheme == OCT_SCHEME_DTR) ? 3u : 0u;
     a.cx = static_cast<uint32_t>(cx);
     a.cy = static_cast<uint32_t>(cy);
+    a.row0 = static_cast<uint32_t>(s->strip_row0);
+    a.plane_rows = static_cast<uint32_t>(plane_rows);
+    a.strip_tiles_y = is_strip(s) ? static_cast<uint32_t>(s->strip_rows / (2 * By)) : 0u;
     *out = s;
     return OCT_OK;
 }
@@ -262,10 +288,15 @@ int set_time(oct_sim *s, int64_t t) {
     OCT_CUDA(cudaMemsetAsync(s->d_net, 0, sizeof(unsigned long long) * 3 * oct::kNetSlots, s->stream));
     OCT_CUDA(cudaStreamSynchronize(s->stream));
     s->t = static_cast<uint64_t>(t);
+    s->next_k = 0;
     return OCT_OK;
 }
 
-size_t lattice_words(const oct_sim *s) { return static_cast<size_t>(s->L) * static_cast<size_t>(s->L) / 16; }
+// Words of the handle's planar buffer (both planes): the whole lattice, or the held rows of a strip.
+size_t lattice_words(const oct_sim *s) {
+    const int64_t rows = is_strip(s) ? s->held_rows : s->L;
+    return static_cast<size_t>(rows) * static_cast<size_t>(s->L) / 16;
+}
 
 // Canonical rows per conversion chunk: at most 64 MiB of staging.
 uint32_t canon_chunk_rows(const oct_sim *s) {
@@ -298,6 +329,8 @@ int oct_create_ex(const oct_params *prm, oct_sim **out) {
 
 int oct_run_mcs(oct_sim *s, int64_t n) {
     if (!s) return fail(OCT_EINVAL, "NULL handle");
+    if (is_strip(s)) return whole_only(s, "oct_run_mcs (strips run oct_device_step between halo exchanges)");
+    if (s->next_k != 0) return fail(OCT_EINVAL, "an MCS run by oct_device_step is not finished");
     if (n < 0) return fail(OCT_EINVAL, "n must be >= 0");
     if (s->t + static_cast<uint64_t>(n) > 0xFFFFFFFFull) return fail(OCT_EINVAL, "MCS counter would pass 2^32-1");
     OCT_CUDA(cudaSetDevice(s->device));
@@ -321,6 +354,125 @@ int oct_run_mcs(oct_sim *s, int64_t n) {
         OCT_CUDA(oct::launch_advance_t(s->d_t, s->stream));
     }
     s->t += static_cast<uint64_t>(n);
+    return OCT_OK;
+}
+
+int oct_device_step(oct_sim *s, int k) {
+    if (!s) return fail(OCT_EINVAL, "NULL handle");
+    if (k < 0 || k > 3) return fail(OCT_EINVAL, "device step k must lie in 0..3");
+    if (k != s->next_k) return fail(OCT_EINVAL, "device steps must run in the order 0, 1, 2, 3 (then oct_end_mcs)");
+    if (s->t >= 0xFFFFFFFFull) return fail(OCT_EINVAL, "MCS counter would pass 2^32-1");
+    OCT_CUDA(cudaSetDevice(s->device));
+    s->args.k = static_cast<uint32_t>(k);
+    if (s->timing) {
+        if (s->ev_used == kEventPairs) {
+            int rc = flush_timing(s);
+            if (rc) return rc;
+        }
+        OCT_CUDA(cudaEventRecord(s->ev[2 * s->ev_used], s->stream));
+    }
+    OCT_CUDA(oct::launch_dtrdt_step(s->args, s->any_random, s->stream));
+    if (s->timing) {
+        OCT_CUDA(cudaEventRecord(s->ev[2 * s->ev_used + 1], s->stream));
+        ++s->ev_used;
+        ++s->step_launches;
+    }
+    s->next_k = k + 1;
+    return OCT_OK;
+}
+
+int oct_end_mcs(oct_sim *s) {
+    if (!s) return fail(OCT_EINVAL, "NULL handle");
+    if (s->next_k != 4) return fail(OCT_EINVAL, "oct_end_mcs needs device steps 0..3 first");
+    OCT_CUDA(cudaSetDevice(s->device));
+    OCT_CUDA(oct::launch_advance_t(s->d_t, s->stream));
+    s->t += 1;
+    s->next_k = 0;
+    return OCT_OK;
+}
+
+int oct_mcs_draw(uint64_t seed, int64_t L, uint32_t t, int64_t *ox, int64_t *oy, int32_t perm[4]) {
+    if (!ox || !oy || !perm) return fail(OCT_EINVAL, "NULL argument");
+    if (L < 2 || L > (int64_t{1} << 20)) return fail(OCT_EINVAL, "L must lie in [2, 2^20]");
+    const uint4 M = oct::philox4x32_10(t, 0u, 0u, oct::kTagMcs << 28, static_cast<uint32_t>(seed & 0xFFFFFFFFu),
+                                       static_cast<uint32_t>(seed >> 32));
+    *ox = static_cast<int64_t>((static_cast<uint64_t>(M.x) * static_cast<uint64_t>(L)) >> 32);
+    *oy = static_cast<int64_t>((static_cast<uint64_t>(M.y) * static_cast<uint64_t>(L)) >> 32);
+    // the (M.z * 24) >> 32 -th permutation of (0, 1, 2, 3) in lexicographic order
+    uint32_t idx = static_cast<uint32_t>((static_cast<uint64_t>(M.z) * 24u) >> 32);
+    int avail[4] = {0, 1, 2, 3}, n = 4;
+    const uint32_t fact[4] = {6, 2, 1, 1};
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t pick = idx / fact[i];
+        idx %= fact[i];
+        perm[i] = avail[pick];
+        for (int j = static_cast<int>(pick); j < n - 1; ++j) avail[j] = avail[j + 1];
+        --n;
+    }
+    return OCT_OK;
+}
+
+int oct_strip_measure(oct_sim *s, oct_strip_sums *out) {
+    if (!s || !out) return fail(OCT_EINVAL, "NULL argument");
+    if (!is_strip(s)) return fail(OCT_EINVAL, "oct_strip_measure needs a strip handle (use oct_measure_w2)");
+    OCT_CUDA(cudaSetDevice(s->device));
+    OCT_CUDA(oct::launch_net_sum(s->d_net, s->d_net + oct::kNetSlots, s->d_net + 2 * oct::kNetSlots,
+                                 s->d_net_sum, s->stream));
+    OCT_CUDA(oct::launch_w2_rows(s->lat, static_cast<uint32_t>(s->L), static_cast<uint32_t>(s->strip_rows),
+                                 static_cast<uint32_t>(s->held_rows), s->d_rows, s->d_w2, s->stream));
+    auto *res = static_cast<oct::W2Result *>(s->h_small);
+    auto *net = reinterpret_cast<long long *>(static_cast<char *>(s->h_small) + 128);
+    OCT_CUDA(cudaMemcpyAsync(res, s->d_w2, sizeof(oct::W2Result), cudaMemcpyDeviceToHost, s->stream));
+    OCT_CUDA(cudaMemcpyAsync(net, s->d_net_sum, 3 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    OCT_CUDA(cudaStreamSynchronize(s->stream));
+    out->rows = s->strip_rows;
+    out->L = s->L;
+    out->f = res->f0;
+    out->e_last = res->e_last;
+    out->p1 = res->s1;
+    out->p2_lo = res->s2_lo;
+    out->p2_hi = res->s2_hi;
+    out->lo = res->lo;
+    out->hi = res->hi;
+    out->t = static_cast<int64_t>(s->t);
+    out->net_flips = net[0];
+    return OCT_OK;
+}
+
+int oct_strip_combine(const oct_strip_sums *parts, int64_t n, oct_w2 *out) {
+    if (!parts || !out || n < 1) return fail(OCT_EINVAL, "need n >= 1 strips and an output");
+    const int64_t L = parts[0].L;
+    int64_t rows = 0;
+    for (int64_t r = 0; r < n; ++r) {
+        if (parts[r].L != L || parts[r].rows < 1 || parts[r].t != parts[0].t)
+            return fail(OCT_EINVAL, "strips of one lattice at one time, in row order");
+        rows += parts[r].rows;
+    }
+    if (rows != L) return fail(OCT_EINVAL, "the strips' rows must add up to L");
+    __int128 S1 = 0, S2 = 0, B = 0;
+    int64_t hmax = 0, net = 0;
+    for (int64_t r = 0; r < n; ++r) {
+        const oct_strip_sums &p = parts[r];
+        if (r > 0) B += parts[r - 1].e_last + p.f;  // h(0, first row of strip r)
+        const __int128 P2 = static_cast<__int128>((static_cast<unsigned __int128>(p.p2_hi) << 64) | p.p2_lo);
+        const __int128 LH = static_cast<__int128>(L) * p.rows;
+        S1 += LH * B + p.p1;
+        S2 += LH * B * B + 2 * B * p.p1 + P2;
+        const __int128 a = B + p.lo, b = B + p.hi;
+        const __int128 m = std::max(a < 0 ? -a : a, b < 0 ? -b : b);
+        hmax = std::max<int64_t>(hmax, static_cast<int64_t>(m));
+        net += p.net_flips;
+    }
+    const __int128 N = static_cast<__int128>(L) * L;
+    const __int128 num = N * S2 - S1 * S1;
+    out->t = parts[0].t;
+    out->n_sites = static_cast<int64_t>(N);
+    out->s1 = static_cast<int64_t>(S1);
+    out->s2_lo = static_cast<uint64_t>(static_cast<unsigned __int128>(S2));
+    out->s2_hi = static_cast<uint64_t>(static_cast<unsigned __int128>(S2) >> 64);
+    out->net_flips = net;
+    out->hmax = hmax;
+    out->w2 = static_cast<double>(num) / (static_cast<double>(N) * static_cast<double>(N));
     return OCT_OK;
 }
 
@@ -367,6 +519,7 @@ int finish_w2(oct_sim *s, oct_w2 *out) {
 
 int oct_measure_w2(oct_sim *s, oct_w2 *out) {
     if (!s || !out) return fail(OCT_EINVAL, "NULL argument");
+    if (is_strip(s)) return whole_only(s, "oct_measure_w2 (use oct_strip_measure)");
     if (s->w2_pending) return fail(OCT_EINVAL, "a measurement from oct_measure_w2_async is pending: call oct_w2_wait");
     OCT_CUDA(cudaSetDevice(s->device));
     const int rc = enqueue_w2(s);
@@ -376,6 +529,7 @@ int oct_measure_w2(oct_sim *s, oct_w2 *out) {
 
 int oct_measure_w2_async(oct_sim *s) {
     if (!s) return fail(OCT_EINVAL, "NULL argument");
+    if (is_strip(s)) return whole_only(s, "oct_measure_w2_async");
     if (s->w2_pending) return fail(OCT_EINVAL, "a measurement is already pending: call oct_w2_wait");
     OCT_CUDA(cudaSetDevice(s->device));
     return enqueue_w2(s);
@@ -390,7 +544,8 @@ int oct_w2_wait(oct_sim *s, oct_w2 *out) {
 
 int oct_get_lattice(oct_sim *s, uint32_t *host, size_t words) {
     if (!s || !host) return fail(OCT_EINVAL, "NULL argument");
-    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal L*L/16");
+    if (is_strip(s)) return whole_only(s, "oct_get_lattice");
+    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal the buffer's words (L*L/16; held_rows*L/16 for a strip)");
     OCT_CUDA(cudaSetDevice(s->device));
     const uint32_t chunk = canon_chunk_rows(s), ncr = static_cast<uint32_t>(s->L / 4);
     const size_t row_words = static_cast<size_t>(s->L / 4);
@@ -411,7 +566,8 @@ int oct_get_lattice(oct_sim *s, uint32_t *host, size_t words) {
 
 int oct_set_lattice(oct_sim *s, const uint32_t *host, size_t words, int64_t t) {
     if (!s || !host) return fail(OCT_EINVAL, "NULL argument");
-    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal L*L/16");
+    if (is_strip(s)) return whole_only(s, "oct_set_lattice");
+    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal the buffer's words (L*L/16; held_rows*L/16 for a strip)");
     if (t < 0 || t > 0xFFFFFFFFll) return fail(OCT_EINVAL, "t must lie in [0, 2^32-1]");
     OCT_CUDA(cudaSetDevice(s->device));
     const uint32_t chunk = canon_chunk_rows(s), ncr = static_cast<uint32_t>(s->L / 4);
@@ -433,7 +589,7 @@ int oct_set_lattice(oct_sim *s, const uint32_t *host, size_t words, int64_t t) {
 
 int oct_get_planes(oct_sim *s, uint32_t *host, size_t words) {
     if (!s || !host) return fail(OCT_EINVAL, "NULL argument");
-    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal L*L/16");
+    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal the buffer's words (L*L/16; held_rows*L/16 for a strip)");
     OCT_CUDA(cudaSetDevice(s->device));
     OCT_CUDA(cudaMemcpyAsync(host, s->lat, words * 4, cudaMemcpyDeviceToHost, s->stream));
     OCT_CUDA(cudaStreamSynchronize(s->stream));
@@ -442,7 +598,7 @@ int oct_get_planes(oct_sim *s, uint32_t *host, size_t words) {
 
 int oct_get_planes_async(oct_sim *s, uint32_t *host, size_t words) {
     if (!s || !host) return fail(OCT_EINVAL, "NULL argument");
-    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal L*L/16");
+    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal the buffer's words (L*L/16; held_rows*L/16 for a strip)");
     OCT_CUDA(cudaSetDevice(s->device));
     OCT_CUDA(cudaMemcpyAsync(host, s->lat, words * 4, cudaMemcpyDeviceToHost, s->stream));
     return OCT_OK;
@@ -450,7 +606,7 @@ int oct_get_planes_async(oct_sim *s, uint32_t *host, size_t words) {
 
 int oct_set_planes(oct_sim *s, const uint32_t *host, size_t words, int64_t t) {
     if (!s || !host) return fail(OCT_EINVAL, "NULL argument");
-    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal L*L/16");
+    if (words != lattice_words(s)) return fail(OCT_EINVAL, "words must equal the buffer's words (L*L/16; held_rows*L/16 for a strip)");
     if (t < 0 || t > 0xFFFFFFFFll) return fail(OCT_EINVAL, "t must lie in [0, 2^32-1]");
     OCT_CUDA(cudaSetDevice(s->device));
     OCT_CUDA(cudaMemcpyAsync(s->lat, host, words * 4, cudaMemcpyHostToDevice, s->stream));
@@ -459,6 +615,7 @@ int oct_set_planes(oct_sim *s, const uint32_t *host, size_t words, int64_t t) {
 
 int oct_get_window(oct_sim *s, int64_t wx, int64_t wy, int64_t W, int64_t H, uint8_t *X, uint8_t *Y) {
     if (!s || !X || !Y) return fail(OCT_EINVAL, "NULL argument");
+    if (is_strip(s)) return whole_only(s, "oct_get_window");
     const int64_t L = s->L;
     if (W < 1 || H < 1 || W > L || H > L) return fail(OCT_EINVAL, "window must satisfy 1 <= W, H <= L");
     OCT_CUDA(cudaSetDevice(s->device));
@@ -503,7 +660,7 @@ int oct_get_info(oct_sim *s, oct_info *out) {
     out->seed = s->seed;
     out->stream = s->stream;
     out->lattice = s->lat;
-    out->lattice_bytes = s->L * s->L / 4;
+    out->lattice_bytes = static_cast<int64_t>(lattice_words(s) * 4);
     out->scheme = s->scheme;
     out->reserved = 0;
     return OCT_OK;
@@ -554,6 +711,7 @@ int oct_destroy(oct_sim *s) {
 
 int oct_snapshot(oct_sim *s) {
     if (!s) return fail(OCT_EINVAL, "NULL argument");
+    if (is_strip(s)) return whole_only(s, "oct_snapshot");
     OCT_CUDA(cudaSetDevice(s->device));
     const size_t bytes = lattice_words(s) * 4;
     if (!s->snap) {

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, kBatchBlocksPerSM)
         c.p_random = R.p_random;
         c.q_random = R.q_random;
         int net = 0, draws = 0, tails = 0;
-        run_subtile<RANDOM, LANE_SETS, SCHEME>(R.lat, L, R.wpr, R.Bx, R.By, x0, y0, active, c,
+        run_subtile<RANDOM, LANE_SETS, SCHEME>(R.lat, L, L, R.wpr, R.Bx, R.By, x0, y0, active, c,
                                   ring + ((threadIdx.x >> 5) * 32 + (lane & ~(G - 1))) * kRingWordsPerLane,
                                   net, draws, tails);
         // sum over the G lanes of the item (items start at multiples of G)

@@ -18,7 +18,7 @@ bool cells_shape_supported(int cx, int cy) {
 }
 
 cudaError_t launch_cells_step(const StepArgs &a, bool any_random, cudaStream_t st) {
-    const uint32_t n_tiles = a.tiles_x * a.tiles_y;
+    const uint32_t n_tiles = a.tiles_x * (a.strip_tiles_y ? a.strip_tiles_y : a.tiles_y);
     const dim3 grid((n_tiles + kStepWarpsPerBlock - 1) / kStepWarpsPerBlock), block(kStepWarpsPerBlock * 32);
     switch (a.cx * 100 + a.cy) {
         case 804: launch_cells_shape<8, 4>(a, any_random, grid, block, st); break;

@@ -29,6 +29,7 @@
 
 #include "oct_internal.h"
 #include "subtile.cuh"
+#include "tiles.cuh"
 
 namespace oct {
 
@@ -256,7 +257,8 @@ __device__ __forceinline__ void cells_apply(uint32_t (&X)[16], uint32_t (&Y)[16]
 // Device step on one sub-tile with cx x cy-site thread cells: stage, the cx*cy
 // single-hit collective steps, write back.  One sub-tile per warp.
 template <int CX, int CY, bool RANDOM, int SPEC>
-__device__ __forceinline__ void run_subtile_cells(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t Bx, uint32_t By,
+__device__ __forceinline__ void run_subtile_cells(uint32_t *lat, uint32_t L, uint32_t plane_rows, uint32_t wpr,
+                                                  uint32_t Bx, uint32_t By,
                                                   uint32_t x0, uint32_t y0, bool active, const CellCtx &cc,
                                                   uint32_t *ring, int &net, int &draws, int &tails) {
     using S = CellShape<CX, CY>;
@@ -266,7 +268,7 @@ __device__ __forceinline__ void run_subtile_cells(uint32_t *lat, uint32_t L, uin
     tp.head = 0u;
     tp.end = 0u;
     tp.rounds = 0u;
-    const LaneGeom q = lane_geom(lat, L, wpr, By, x0, y0, c);
+    const LaneGeom q = lane_geom(lat, L, plane_rows, wpr, By, x0, y0, c);
     uint32_t X[16], Y[16], E, D;
     stage_lane(q, L, wpr, Bx, x0, active, c, X, Y, E, D);
 
@@ -309,22 +311,13 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSMPacke
     using S = CellShape<CX, CY>;
     __shared__ __align__(16) uint32_t ring[kStepWarpsPerBlock * 32 * kRingWordsPerLane];
     const int lane = threadIdx.x & 31;
-    const uint32_t T = blockIdx.x * kStepWarpsPerBlock + (threadIdx.x >> 5);
-    const uint32_t n_tiles = a.tiles_x * a.tiles_y;
-    if (T >= n_tiles) return;  // the whole warp leaves together
+    const uint32_t w = blockIdx.x * kStepWarpsPerBlock + (threadIdx.x >> 5);
+    if (w >= work_tiles(a)) return;  // the whole warp leaves together
 
     const uint32_t t = *a.t_ptr;
     const uint32_t L = a.L;
-    const uint4 M = philox4x32_10(t, 0u, 0u, kTagMcs << 28, a.k0, a.k1);
-    const uint32_t ox = static_cast<uint32_t>((static_cast<uint64_t>(M.x) * L) >> 32);
-    const uint32_t oy = static_cast<uint32_t>((static_cast<uint64_t>(M.y) * L) >> 32);
-    const uint32_t pidx = static_cast<uint32_t>((static_cast<uint64_t>(M.z) * 24u) >> 32);
-    const int sigma = perm_element(pidx, a.k);
-    const uint32_t tx = T % a.tiles_x, ty = T / a.tiles_x;
-    const uint32_t x0 = static_cast<uint32_t>(
-        (static_cast<uint64_t>(ox) + 2ull * a.Bx * tx + static_cast<uint64_t>(a.Bx) * (sigma & 1)) % L);
-    const uint32_t y0 = static_cast<uint32_t>(
-        (static_cast<uint64_t>(oy) + 2ull * a.By * ty + static_cast<uint64_t>(a.By) * (sigma >> 1)) % L);
+    const TilePlace pl = place_tile(a, w, t);
+    const uint32_t T = pl.T, x0 = pl.x0, y0 = pl.y0;
 
     CellCtx cc;
     LaneCtx &c = cc.c;
@@ -354,7 +347,7 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, kStepBlocksPerSMPacke
     c.g = static_cast<uint32_t>(cc.gr * c.GX + c.gx);  // the lane's group
 
     int net = 0, draws = 0, tails = 0;
-    run_subtile_cells<CX, CY, RANDOM, SPEC>(a.lat, L, a.wpr, a.Bx, a.By, x0, y0, active, cc,
+    run_subtile_cells<CX, CY, RANDOM, SPEC>(a.lat, L, a.plane_rows, a.wpr, a.Bx, a.By, x0, y0, active, cc,
                                             ring + (threadIdx.x >> 5) * 32 * kRingWordsPerLane, net, draws,
                                             tails);
 

@@ -39,6 +39,7 @@
 #include "oct_internal.h"
 
 #include "subtile.cuh"
+#include "tiles.cuh"
 
 namespace oct {
 namespace {
@@ -71,31 +72,23 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, step_min_blocks(SCHEM
     const uint32_t S = PACKED ? segment_lanes(G) : 32u;
     const uint32_t per_warp = 32u / S;
     const uint32_t warp_id = blockIdx.x * kStepWarpsPerBlock + (threadIdx.x >> 5);
-    const uint32_t n_tiles = a.tiles_x * a.tiles_y;
+    const uint32_t n_tiles = work_tiles(a);
     if (warp_id * per_warp >= n_tiles) return;  // the whole warp leaves together
     const uint32_t seg = static_cast<uint32_t>(lane) / S, sub = static_cast<uint32_t>(lane) % S;
-    const uint32_t T = warp_id * per_warp + seg;
+    const uint32_t w = warp_id * per_warp + seg;  // work index of the lane's sub-tile
 
     const uint32_t t = *a.t_ptr;
     const uint32_t L = a.L;
     // Device layer: origin and set order of this MCS (same for every warp).
-    const uint4 M = philox4x32_10(t, 0u, 0u, kTagMcs << 28, a.k0, a.k1);
-    const uint32_t ox = static_cast<uint32_t>((static_cast<uint64_t>(M.x) * L) >> 32);
-    const uint32_t oy = static_cast<uint32_t>((static_cast<uint64_t>(M.y) * L) >> 32);
-    const uint32_t pidx = static_cast<uint32_t>((static_cast<uint64_t>(M.z) * 24u) >> 32);
-    const int sigma = perm_element(pidx, a.k);
-    const uint32_t tx = T % a.tiles_x, ty = T / a.tiles_x;
-    const uint32_t x0 = static_cast<uint32_t>(
-        (static_cast<uint64_t>(ox) + 2ull * a.Bx * tx + static_cast<uint64_t>(a.Bx) * (sigma & 1)) % L);
-    const uint32_t y0 = static_cast<uint32_t>(
-        (static_cast<uint64_t>(oy) + 2ull * a.By * ty + static_cast<uint64_t>(a.By) * (sigma >> 1)) % L);
+    const TilePlace pl = place_tile(a, w < n_tiles ? w : 0u, t);
+    const uint32_t T = pl.T, x0 = pl.x0, y0 = pl.y0;
 
     LaneCtx c;
     c.GX = static_cast<int>(a.GX);
     c.GY = static_cast<int>(a.GY);
     c.gx = static_cast<int>(sub) % c.GX;
     c.gy = static_cast<int>(sub) / c.GX;
-    const bool active = sub < G && T < n_tiles;
+    const bool active = sub < G && w < n_tiles;
     c.active = active;
     c.last = static_cast<int>(seg * S + G - 1u);
     c.t = t;
@@ -113,12 +106,12 @@ __global__ void __launch_bounds__(kStepWarpsPerBlock * 32, step_min_blocks(SCHEM
 
     const uint32_t wpr = a.wpr;
     int net = 0, draws = 0, tails = 0;
-    run_subtile<RANDOM, PACKED, SCHEME>(a.lat, L, wpr, a.Bx, a.By, x0, y0, active, c,
+    run_subtile<RANDOM, PACKED, SCHEME>(a.lat, L, a.plane_rows, wpr, a.Bx, a.By, x0, y0, active, c,
                                         ring + ((threadIdx.x >> 5) * 32 + seg * S) * kRingWordsPerLane,
                                         net, draws, tails);
 
     // Net flips (and acceptance draws): one atomic per warp into a spread of counters.
-    const uint32_t T0 = warp_id * per_warp;
+    const uint32_t T0 = warp_id * per_warp;  // (work index: only spreads the atomics)
     const int total = __reduce_add_sync(kFull, net);
     if (lane == 0 && total != 0)
         atomicAdd(&a.net[T0 % kNetSlots], static_cast<unsigned long long>(static_cast<long long>(total)));
@@ -137,7 +130,7 @@ __global__ void advance_t_kernel(uint32_t *t_ptr) { *t_ptr += 1u; }
 
 cudaError_t launch_dtrdt_step(const StepArgs &a, bool any_random, cudaStream_t st) {
     if (a.cx != 4u || a.cy != 4u) return launch_cells_step(a, any_random, st);
-    const uint32_t n_tiles = a.tiles_x * a.tiles_y;
+    const uint32_t n_tiles = work_tiles(a);
     // DTrDTr routes cells between the lanes of one sub-tile with warp-wide
     // shuffles whose pattern depends on its own draws: one sub-tile per warp.
     const uint32_t S = segment_lanes(a.GX * a.GY);

@@ -18,11 +18,12 @@ namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
-__global__ void init_flat_kernel(uint32_t *lat, uint32_t L, uint64_t n_words, uint32_t wpr) {
-    // X = Y = (x+y) & 1: odd x set on even rows, even x set on odd rows.
+__global__ void init_flat_kernel(uint32_t *lat, uint32_t rows, uint64_t n_words, uint32_t wpr) {
+    // X = Y = (x+y) & 1: odd x set on even rows, even x set on odd rows (the
+    // buffer's first row is an even lattice row).
     for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n_words;
          i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        const uint64_t row = (i / wpr) % L;
+        const uint64_t row = (i / wpr) % rows;
         lat[i] = (row & 1u) ? 0x55555555u : 0xAAAAAAAAu;
     }
 }
@@ -85,7 +86,7 @@ __device__ __forceinline__ uint4 load_chunk(const uint32_t *row, uint32_t w, uin
 constexpr int kW2TableCopies = 16;
 
 __global__ void __launch_bounds__(kW2Warps * 32)
-    w2_rows_kernel(const uint32_t *lat, uint32_t L, W2RowSums *rows) {
+    w2_rows_kernel(const uint32_t *lat, uint32_t L, uint32_t nrows, uint32_t plane_rows, W2RowSums *rows) {
     __shared__ uint2 table[256 * kW2TableCopies];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const uint2 e = byte_entry(static_cast<uint32_t>(i));
@@ -96,10 +97,10 @@ __global__ void __launch_bounds__(kW2Warps * 32)
     const int lane = threadIdx.x & 31;
     const uint2 *const my_table = table + (lane % kW2TableCopies);
     const uint32_t wpr = L >> 5;
-    const uint32_t *Yp = lat + static_cast<size_t>(L) * wpr;
+    const uint32_t *Yp = lat + static_cast<size_t>(plane_rows) * wpr;
     // 16-byte loads need every row to start on a 16-byte boundary
     const bool vec_ok = (wpr % 4u) == 0u && (reinterpret_cast<uintptr_t>(lat) % 16u) == 0u;
-    for (uint32_t y = blockIdx.x * kW2Warps + (threadIdx.x >> 5); y < L; y += gridDim.x * kW2Warps) {
+    for (uint32_t y = blockIdx.x * kW2Warps + (threadIdx.x >> 5); y < nrows; y += gridDim.x * kW2Warps) {
         const uint32_t *row = lat + static_cast<size_t>(y) * wpr;
         long long base = 0;  // q just before the current chunk
         long long q1 = 0, q2 = 0;
@@ -177,14 +178,17 @@ __global__ void __launch_bounds__(kW2Warps * 32)
 
 constexpr int kFinalThreads = 1024;
 
+// Pass 2 over nrows row records of rows of length L: heights h0 = sum of the
+// column steps of rows 1..y (row 0 at 0), S1, S2 (128-bit), the extremes of
+// h0 + r, h0 of the last row and the first row's column step.
 __global__ void __launch_bounds__(kFinalThreads)
-    w2_final_kernel(const W2RowSums *rows, uint32_t L, W2Result *out) {
+    w2_final_kernel(const W2RowSums *rows, uint32_t L, uint32_t nrows, W2Result *out) {
     __shared__ long long part[kFinalThreads];
     __shared__ unsigned long long s2lo[kFinalThreads / 32], s2hi[kFinalThreads / 32];
-    __shared__ long long s1w[kFinalThreads / 32], hmw[kFinalThreads / 32];
+    __shared__ long long s1w[kFinalThreads / 32], low[kFinalThreads / 32], hiw[kFinalThreads / 32];
     const int tid = threadIdx.x;
-    const uint32_t per = (L + kFinalThreads - 1) / kFinalThreads;
-    const uint32_t y_begin = min(L, tid * per), y_end = min(L, (tid + 1) * per);
+    const uint32_t per = (nrows + kFinalThreads - 1) / kFinalThreads;
+    const uint32_t y_begin = min(nrows, tid * per), y_end = min(nrows, (tid + 1) * per);
     // column steps 2c-1 for rows 1..y (row 0 contributes nothing)
     long long local = 0;
     for (uint32_t y = y_begin; y < y_end; ++y)
@@ -199,8 +203,9 @@ __global__ void __launch_bounds__(kFinalThreads)
         __syncthreads();
     }
     long long h0 = part[tid] - local;
+    if (tid == kFinalThreads - 1) out->e_last = part[tid];  // h0 of the last row
     __int128 S1 = 0, S2 = 0;
-    long long hm = 0;
+    long long lo = 1ll << 62, hi = -(1ll << 62);
     const long long Ll = L;
     for (uint32_t y = y_begin; y < y_end; ++y) {
         const W2RowSums r = rows[y];
@@ -208,41 +213,47 @@ __global__ void __launch_bounds__(kFinalThreads)
         S1 += static_cast<__int128>(Ll * h0 + r.r1);
         S2 += static_cast<__int128>(Ll * h0 * h0) + static_cast<__int128>(2 * h0 * r.r1) +
               static_cast<__int128>(r.r2);
-        const long long a = h0 + r.rmin, b = h0 + r.rmax;
-        hm = max(hm, max(a < 0 ? -a : a, b < 0 ? -b : b));
+        lo = min(lo, h0 + r.rmin);
+        hi = max(hi, h0 + r.rmax);
     }
-    // block reduction of S1 (fits 64 bits for L <= 2^20), S2 (128 bits), hmax
+    // block reduction of S1 (fits 64 bits for L <= 2^20), S2 (128 bits), extremes
     long long s1 = static_cast<long long>(S1);
-    unsigned long long lo = static_cast<unsigned long long>(S2);
-    unsigned long long hi = static_cast<unsigned long long>(S2 >> 64);
+    unsigned long long s2l = static_cast<unsigned long long>(S2);
+    unsigned long long s2h = static_cast<unsigned long long>(S2 >> 64);
     for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_down_sync(kFull, s1, o);
-        const unsigned long long lo2 = __shfl_down_sync(kFull, lo, o);
-        const unsigned long long hi2 = __shfl_down_sync(kFull, hi, o);
-        const unsigned long long nlo = lo + lo2;
-        hi = hi + hi2 + (nlo < lo ? 1ull : 0ull);
-        lo = nlo;
-        hm = max(hm, __shfl_down_sync(kFull, hm, o));
+        const unsigned long long lo2 = __shfl_down_sync(kFull, s2l, o);
+        const unsigned long long hi2 = __shfl_down_sync(kFull, s2h, o);
+        const unsigned long long nlo = s2l + lo2;
+        s2h = s2h + hi2 + (nlo < s2l ? 1ull : 0ull);
+        s2l = nlo;
+        lo = min(lo, __shfl_down_sync(kFull, lo, o));
+        hi = max(hi, __shfl_down_sync(kFull, hi, o));
     }
     if ((tid & 31) == 0) {
         s1w[tid >> 5] = s1;
-        s2lo[tid >> 5] = lo;
-        s2hi[tid >> 5] = hi;
-        hmw[tid >> 5] = hm;
+        s2lo[tid >> 5] = s2l;
+        s2hi[tid >> 5] = s2h;
+        low[tid >> 5] = lo;
+        hiw[tid >> 5] = hi;
     }
     __syncthreads();
     if (tid == 0) {
-        long long a1 = 0, am = 0;
+        long long a1 = 0, amn = 1ll << 62, amx = -(1ll << 62);
         unsigned __int128 a2 = 0;
         for (int w = 0; w < kFinalThreads / 32; ++w) {
             a1 += s1w[w];
             a2 += (static_cast<unsigned __int128>(s2hi[w]) << 64) | s2lo[w];
-            am = max(am, hmw[w]);
+            amn = min(amn, low[w]);
+            amx = max(amx, hiw[w]);
         }
         out->s1 = a1;
         out->s2_lo = static_cast<unsigned long long>(a2);
         out->s2_hi = static_cast<unsigned long long>(a2 >> 64);
-        out->hmax = am;
+        out->lo = amn;
+        out->hi = amx;
+        out->hmax = max(amn < 0 ? -amn : amn, amx < 0 ? -amx : amx);
+        out->f0 = rows[0].c ? 1 : -1;
     }
 }
 
@@ -326,14 +337,23 @@ int grid_for(uint64_t n, int threads) {
 }  // namespace
 
 cudaError_t launch_init_flat(uint32_t *lat, uint32_t L, cudaStream_t st) {
+    return launch_init_flat_rows(lat, L, L, st);
+}
+
+cudaError_t launch_init_flat_rows(uint32_t *lat, uint32_t L, uint32_t rows, cudaStream_t st) {
     const uint32_t wpr = L >> 5;
-    const uint64_t n = 2ull * L * wpr;
-    init_flat_kernel<<<grid_for(n, 256), 256, 0, st>>>(lat, L, n, wpr);
+    const uint64_t n = 2ull * rows * wpr;
+    init_flat_kernel<<<grid_for(n, 256), 256, 0, st>>>(lat, rows, n, wpr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_w2(const uint32_t *lat, uint32_t L, W2RowSums *rows, W2Result *out,
                       cudaStream_t st) {
+    return launch_w2_rows(lat, L, L, L, rows, out, st);
+}
+
+cudaError_t launch_w2_rows(const uint32_t *lat, uint32_t L, uint32_t nrows, uint32_t plane_rows, W2RowSums *rows,
+                           W2Result *out, cudaStream_t st) {
     // one wave of resident blocks (32 KB of table each), rows taken grid-stride
     static int sms = 0;
     if (sms == 0) {
@@ -342,13 +362,13 @@ cudaError_t launch_w2(const uint32_t *lat, uint32_t L, W2RowSums *rows, W2Result
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
             sms = 152;
     }
-    const uint64_t want = (static_cast<uint64_t>(L) + kW2Warps - 1) / kW2Warps;
+    const uint64_t want = (static_cast<uint64_t>(nrows) + kW2Warps - 1) / kW2Warps;
     const uint64_t wave = static_cast<uint64_t>(sms) * 6u;
     const int blocks = static_cast<int>(want < wave ? want : wave);
-    w2_rows_kernel<<<blocks, kW2Warps * 32, 0, st>>>(lat, L, rows);
+    w2_rows_kernel<<<blocks, kW2Warps * 32, 0, st>>>(lat, L, nrows, plane_rows, rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    w2_final_kernel<<<1, kFinalThreads, 0, st>>>(rows, L, out);
+    w2_final_kernel<<<1, kFinalThreads, 0, st>>>(rows, L, nrows, out);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,10 @@ struct StepArgs {
     unsigned long long *tails; // kNetSlots counters of tail-stream Philox blocks generated
     uint32_t scheme;           // 0: DT; 1: DB (borders together); 2: DB with delayed borders; 3: DTrDTr
     uint32_t cx, cy;           // thread cell in sites (4 x 4, or a coarser DTrDT cell of cells.cu)
+    // Row strip of the multi-GPU partition (strip_tiles_y = 0: the whole lattice).
+    uint32_t row0;             // global row of buffer row 0
+    uint32_t plane_rows;       // rows per bit plane in the buffer (L for the whole lattice)
+    uint32_t strip_tiles_y;    // device-tile rows the strip owns (0: all)
 };
 
 constexpr int kNetSlots = 1024;
@@ -46,8 +50,10 @@ cudaError_t launch_cells_step(const StepArgs &a, bool any_random, cudaStream_t s
 // Adds one to the device MCS counter.
 cudaError_t launch_advance_t(uint32_t *t_ptr, cudaStream_t st);
 
-// Flat start h = (x+y) mod 2 on the planar lattice.
+// Flat start h = (x+y) mod 2 on the planar lattice (or on `rows` rows from an
+// even lattice row on, bit planes of `rows` rows each).
 cudaError_t launch_init_flat(uint32_t *lat, uint32_t L, cudaStream_t st);
+cudaError_t launch_init_flat_rows(uint32_t *lat, uint32_t L, uint32_t rows, cudaStream_t st);
 
 // Exact roughness sums.
 struct W2RowSums {
@@ -61,9 +67,16 @@ struct W2Result {
     long long s1;
     unsigned long long s2_lo, s2_hi;
     long long hmax;
+    long long lo, hi;  // extremes of the heights (relative to the first row's h(0, .))
+    long long e_last;  // h(0, .) of the last row
+    long long f0;      // 2 Y(0, first row) - 1
 };
 cudaError_t launch_w2(const uint32_t *lat, uint32_t L, W2RowSums *rows, W2Result *out,
                       cudaStream_t st);
+// The same over the first nrows rows of a buffer whose bit planes hold
+// plane_rows rows each (a strip of a lattice split over devices).
+cudaError_t launch_w2_rows(const uint32_t *lat, uint32_t L, uint32_t nrows, uint32_t plane_rows, W2RowSums *rows,
+                           W2Result *out, cudaStream_t st);
 
 // Two-time autocorrelation sums of lattice lat_t against lat_s (both planar, L x L).
 struct AcRowSums {

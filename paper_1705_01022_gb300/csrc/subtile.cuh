@@ -750,11 +750,12 @@ struct LaneGeom {
     uint32_t sh, wA, wB, ybase, yh;
 };
 
-__device__ __forceinline__ LaneGeom lane_geom(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t By, uint32_t x0,
-                                              uint32_t y0, const LaneCtx &c) {
+// (y0 in buffer rows; the Y plane follows plane_rows rows of X.)
+__device__ __forceinline__ LaneGeom lane_geom(uint32_t *lat, uint32_t L, uint32_t plane_rows, uint32_t wpr,
+                                              uint32_t By, uint32_t x0, uint32_t y0, const LaneCtx &c) {
     LaneGeom q;
     q.Xp = lat;
-    q.Yp = lat + static_cast<size_t>(L) * wpr;
+    q.Yp = lat + static_cast<size_t>(plane_rows) * wpr;
     q.sh = x0 & 31u;
     q.wA = ((x0 >> 5) + static_cast<uint32_t>(c.gx)) % wpr;
     q.wB = (q.wA + 1u == wpr) ? 0u : q.wA + 1u;
@@ -931,8 +932,8 @@ __device__ __forceinline__ void write_back(const LaneGeom &q, uint32_t L, uint32
 // 5 DTrDT with both rates strictly inside (0, 1), 6 DTrDB with deposition only,
 // 7 DTrDB with delayed borders and both rates random.
 template <bool RANDOM, bool LANE_SETS, int SCHEME = 0>
-__device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t wpr, uint32_t Bx,
-                                            uint32_t By, uint32_t x0, uint32_t y0, bool active,
+__device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t plane_rows, uint32_t wpr,
+                                            uint32_t Bx, uint32_t By, uint32_t x0, uint32_t y0, bool active,
                                             const LaneCtx &c, uint32_t *ring, int &net, int &draws,
                                             int &tails) {
     TailPool tp;
@@ -940,7 +941,7 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
     tp.head = 0u;
     tp.end = 0u;
     tp.rounds = 0u;
-    const LaneGeom q = lane_geom(lat, L, wpr, By, x0, y0, c);
+    const LaneGeom q = lane_geom(lat, L, plane_rows, wpr, By, x0, y0, c);
     uint32_t X[16], Y[16], E, D;
     stage_lane(q, L, wpr, Bx, x0, active, c, X, Y, E, D);
 

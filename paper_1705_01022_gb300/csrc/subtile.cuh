@@ -992,10 +992,17 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
         constexpr int kSpec = SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0;
         if (LANE_SETS)
             step_candidates_rt<RANDOM, kSpec>(X, Y, E, D, site, s, d & 1u, d >> 1, c, cnd0, cnd1, pmin, pmax);
-        else if (d & 2u)
-            step_candidates<1, RANDOM, kSpec>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
+        // the candidate phase with the set's column offset as a constant as well
+        // (the flip phase stays specialised on the row offset alone: four copies
+        // of it measured slower, from instruction-cache pressure)
+        else if (d == 3u)
+            step_candidates<1, RANDOM, kSpec>(X, Y, E, D, site, s, 1u, c, cnd0, cnd1, pmin, pmax);
+        else if (d == 2u)
+            step_candidates<1, RANDOM, kSpec>(X, Y, E, D, site, s, 0u, c, cnd0, cnd1, pmin, pmax);
+        else if (d == 1u)
+            step_candidates<0, RANDOM, kSpec>(X, Y, E, D, site, s, 1u, c, cnd0, cnd1, pmin, pmax);
         else
-            step_candidates<0, RANDOM, kSpec>(X, Y, E, D, site, s, d & 1u, c, cnd0, cnd1, pmin, pmax);
+            step_candidates<0, RANDOM, kSpec>(X, Y, E, D, site, s, 0u, c, cnd0, cnd1, pmin, pmax);
         uint32_t acc = 0u;
         if (RANDOM) {
             draws += __popc(pmin | pmax);

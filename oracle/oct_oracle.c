@@ -283,7 +283,12 @@ static void touch(conflict_t *cf, int64_t bit, int64_t tile, int64_t tc) {
 /* Acceptance uniforms (a reading: the paper names no generator).  The
  * uniform u of a thread cell's attempt is 32 bits, most significant first:
  *   - bits 31..28: "level" bits, positional per group: bit (31-l) of u is bit
- *     pos = 4j+m of word l (l = 0..3) of Philox(seed, (t, k|(s*8)<<2, T, ACC<<28|g));
+ *     spl_off + pos of word l (l = 0..3) of Philox(seed, (t, k|((s/spl)*8)<<2,
+ *     T, ACC<<28|g)), pos = 4j+m, where a group of tpb cells per 32-site band
+ *     uses 4*tpb positions per step, so one block serves spl = 8/tpb = cx/4
+ *     consecutive steps and step s takes positions from spl_off =
+ *     (s % spl)*4*tpb on (spl = 1 for 4x4-site cells and for bands narrower
+ *     than 32 sites);
  *   - bits 27..0: only needed when bits 31..28 equal those of P32 (otherwise
  *     u < P32 is already decided); they are the top 28 bits of the next word
  *     of the group's own tail stream, word i = word i%4 of
@@ -291,8 +296,8 @@ static void touch(conflict_t *cf, int64_t bit, int64_t tile, int64_t tc) {
  *     start of each device step; within a collective step (a DB phase) the
  *     group's candidates that need one take words in order of position pos. */
 static void acc_level_words(const uint32_t key[2], uint32_t t, uint32_t k, uint32_t T, uint32_t g,
-                            uint32_t s, uint32_t lw[4]) {
-    philox_at(key, t, k | ((s * 8) << 2), T, (OO_TAG_ACC << 28) | g, lw);
+                            uint32_t s, uint32_t spl, uint32_t lw[4]) {
+    philox_at(key, t, k | (((s / spl) * 8) << 2), T, (OO_TAG_ACC << 28) | g, lw);
 }
 
 /* Bits 31..28 of the uniform of the thread cell at position pos. */
@@ -313,7 +318,7 @@ uint32_t oo_dtrdt_acc_prefix(uint64_t seed, uint32_t t, uint32_t k, uint32_t T, 
                              uint32_t s, int pos) {
     uint32_t key[2], w[4];
     seed_key(seed, key);
-    acc_level_words(key, t, k, T, g, s, w);
+    acc_level_words(key, t, k, T, g, s, 1u, w);
     return acc_prefix(w, pos);
 }
 
@@ -517,6 +522,8 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
     const int bpt = bx_bits + by_bits;
     const int64_t fw = 32 / tcs_per_band;
     const int spw = (bpt > 0 && 2 * bpt <= fw) ? 2 : 1;
+    /* steps served by one level block: cx/4 in 32-site bands, else 1 */
+    const uint32_t spl_acc = BW == 32 ? (uint32_t)(8 / tcs_per_band) : 1u;
     const uint32_t site_tag = db ? OO_TAG_SITE_DB : OO_TAG_SITE;
     const int64_t n_steps = cx * cy;
     const uint64_t thr_p = oo_threshold32(P->p), thr_q = oo_threshold32(P->q);
@@ -542,7 +549,7 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
                 if (bpt > 0)
                     philox_at(key, t, k | (uint32_t)((s / spw) << 2), T, (site_tag << 28) | g, site_w);
                 uint32_t lw[4];
-                acc_level_words(key, t, k, T, g, (uint32_t)s, lw);
+                acc_level_words(key, t, k, T, g, (uint32_t)s, spl_acc, lw);
                 for (int64_t m = 0; m < 4; ++m) {
                     const int64_t c = 4 * gr + m; /* TC row */
                     if (c >= tc_rows) break;
@@ -565,7 +572,7 @@ static void run_subtile(const oo_params *P, const uint32_t key[2], uint32_t t, u
                         A->iu = vidx(v, gx, gy + 1);
                         A->g = g;
                         A->pos = (int)(4 * j + m);
-                        A->hi = acc_prefix(lw, A->pos);
+                        A->hi = acc_prefix(lw, (int)((s % spl_acc) * 4 * tcs_per_band) + A->pos);
                         A->thr_min = thr_p;
                         A->thr_max = thr_q;
                         A->random_min = p_random;

@@ -1,4 +1,5 @@
-"""Autotuner for the block tile (the sub-tile of the device layer, Bx x By sites).
+"""Autotuner for the block tile (the sub-tile of the device layer, Bx x By
+sites) and the thread cell (cx x cy sites) of DTrDT.
 
 The sub-tile shape is a parameter of the domain decomposition, not only of the
 launch: it decides which sites are updated together and how the random
@@ -15,12 +16,23 @@ the policies are timed on the actual replica set: what a warp carries and how
 the batched kernel packs it depend on the whole mix, not on one L.
 
 Candidates are the shapes the step kernel accepts for this L: Bx a multiple of
-32 and By a multiple of 16 (4 x 4-site thread cells, the one cell shape the
-GPU path supports), at most 32 groups of 32 x 16 sites, and L a multiple of
-2Bx and 2By.  By default the group counts in x and y are powers of two, which
-is also what a batched replica needs.  Each candidate runs a warm-up MCS and
-then `mcs` timed MCS on the library's own per-launch CUDA-event timing; the
-score is attempts per ns of the device-step kernel.
+32 and By a multiple of 16 (timed with 4 x 4-site thread cells), at most 32
+groups of 32 x 16 sites, and L a multiple of 2Bx and 2By.  By default the
+group counts in x and y are powers of two, which is also what a batched
+replica needs.  Each candidate runs a warm-up MCS and then `mcs` timed MCS on
+the library's own per-launch CUDA-event timing; the score is attempts per ns
+of the device-step kernel.
+
+The thread cell (`tune_cell`) is a choice between speed and fidelity, not
+speed alone: finer cells run faster (more attempts per lane and step) but
+lower the roughness prefactor below that of sequential RS (Sec. 4.2), while
+coarse cells are indistinguishable from sequential runs (Sec. 5).  The tuner
+therefore measures both on the GPU: the device-step rate of every supported
+cell at the job's L and sub-tile, and each cell's W^2 on an ensemble of small
+lattices at the job's p and q, relative to the coarsest cell (the stand-in for
+RS, which has no parallel form).  It returns the fastest cell whose relative
+W^2 lies within `max_shift` of 1 at every measured time, and records the whole
+table like the sub-tile choice.
 """
 from __future__ import annotations
 
@@ -29,7 +41,10 @@ import os
 import time
 from dataclasses import dataclass, field
 
-CELL = (4, 4)   # thread-cell shape (cx, cy) of the GPU path
+CELL = (4, 4)   # thread-cell shape (cx, cy) the sub-tile is timed with
+# thread cells of the GPU's DTrDT block layer, finest first; the last is the
+# coarsest (the fidelity reference of tune_cell)
+CELLS = ((4, 4), (8, 4), (4, 8), (8, 8), (16, 4), (4, 16), (16, 8), (8, 16), (32, 4), (16, 16), (32, 8), (32, 16))
 GROUP = (32, 16)  # sites held by one warp lane
 MAX_GROUPS = 32
 
@@ -109,11 +124,11 @@ class TuneCache:
 
 
 def measure(L: int, p: float, q: float, Bx: int, By: int, seed: int = 1, mcs: int = 2,
-            stream=None, lattice=None) -> float:
+            stream=None, lattice=None, cx: int = 4, cy: int = 4) -> float:
     """Attempts per ns of the device-step kernel for one shape (flat start,
     one warm-up MCS, then `mcs` timed MCS)."""
     from . import Simulation, _lib
-    with Simulation(L, p, q, seed, Bx=Bx, By=By, stream=stream, lattice=lattice) as sim:
+    with Simulation(L, p, q, seed, Bx=Bx, By=By, cx=cx, cy=cy, stream=stream, lattice=lattice) as sim:
         sim.run(1)
         sim.sync()
         _lib.oct_set_timing(sim.h, True)
@@ -152,14 +167,116 @@ def choose(L: int, p: float, q: float, cache: TuneCache | None = None, **kw) -> 
 
 
 def tuned_simulation(L: int, p: float, q: float, seed: int, cache: TuneCache | None = None,
-                     stream=None, lattice=None, **kw):
+                     stream=None, lattice=None, max_shift: float | None = None, **kw):
     """A Simulation on the tuned (recorded) sub-tile shape; the record is
-    attached as `.tuning`."""
+    attached as `.tuning`.  With `max_shift`, the thread cell is tuned too
+    (`choose_cell` on the tuned sub-tile) and its record attached as
+    `.cell_tuning`; else the cell is 4 x 4 sites."""
     from . import Simulation
+    cache = cache if cache is not None else TuneCache()
     rec = choose(L, p, q, cache=cache, stream=stream, **kw)
-    sim = Simulation(L, p, q, seed, Bx=rec["Bx"], By=rec["By"], stream=stream, lattice=lattice)
+    cell, crec = CELL, None
+    if max_shift is not None:
+        crec = choose_cell(L, p, q, rec["Bx"], rec["By"], max_shift=max_shift, cache=cache, stream=stream,
+                           mcs=kw.get("mcs", 1))
+        cell = (crec["cx"], crec["cy"])
+    sim = Simulation(L, p, q, seed, Bx=rec["Bx"], By=rec["By"], cx=cell[0], cy=cell[1], stream=stream,
+                     lattice=lattice)
     sim.tuning = rec
+    sim.cell_tuning = crec
     return sim
+
+
+# ---------------------------------------------------------------------------
+# thread cell: speed against fidelity
+STAT_L = 256          # lattice size of the fidelity ensemble
+STAT_SEEDS = 32       # realizations per cell
+STAT_TIMES = (4, 16)  # MCS at which W^2 is compared
+STAT_SHAPE = (64, 64)  # sub-tile of the fidelity ensemble
+
+
+def ensemble_w2(p: float, q: float, cell, L: int = STAT_L, seeds: int = STAT_SEEDS, times=STAT_TIMES,
+                seed0: int = 1, shape=STAT_SHAPE, stream=None) -> list[list[float]]:
+    """W^2 at `times` for `seeds` realizations (seeds seed0 .. seed0+seeds-1)
+    of DTrDT with thread cell `cell` from the flat start: a seeds x len(times)
+    list."""
+    from . import Simulation
+    out = []
+    for i in range(seeds):
+        row, t = [], 0
+        with Simulation(L, p, q, seed0 + i, Bx=shape[0], By=shape[1], cx=cell[0], cy=cell[1],
+                        stream=stream) as sim:
+            for tt in times:
+                sim.run(tt - t)
+                t = tt
+                row.append(float(sim.measure().w2))
+        out.append(row)
+    return out
+
+
+def relative_w2(cell_w2, ref_w2) -> list[tuple[float, float]]:
+    """(mean W^2 of the cell / mean W^2 of the reference, standard error of
+    the ratio) at each time, the two ensembles independent."""
+    import statistics
+    res = []
+    for j in range(len(cell_w2[0])):
+        a = [r[j] for r in cell_w2]
+        b = [r[j] for r in ref_w2]
+        ma, mb = statistics.fmean(a), statistics.fmean(b)
+        va = statistics.variance(a) / len(a) if len(a) > 1 else 0.0
+        vb = statistics.variance(b) / len(b) if len(b) > 1 else 0.0
+        ratio = ma / mb
+        res.append((ratio, abs(ratio) * (va / ma ** 2 + vb / mb ** 2) ** 0.5))
+    return res
+
+
+def pick_cell(table: list[dict], max_shift: float) -> dict:
+    """The fastest row whose relative W^2 lies within max_shift of 1 at every
+    time; the reference row (shift 0 by definition) always qualifies."""
+    ok = [r for r in table if all(abs(x - 1.0) <= max_shift for x in r["w2_ratio"])]
+    return max(ok, key=lambda r: r["attempts_per_ns"])
+
+
+def tune_cell(L: int, p: float, q: float, Bx: int, By: int, max_shift: float = 0.01, seed: int = 1,
+              mcs: int = 1, cells=CELLS, stream=None, measure_fn=None, w2_fn=None) -> dict:
+    """Measures every cell's device-step rate at (L, Bx, By) and its W^2
+    relative to the coarsest cell on the fidelity ensemble, and returns the
+    record of the choice: {device, L, p, q, Bx, By, cx, cy, attempts_per_ns,
+    max_shift, reference, table, stat, when}."""
+    cells = [tuple(c) for c in cells]
+    ref = max(cells, key=lambda c: (c[0] * c[1], c[0]))
+    fn = measure_fn or (lambda c: measure(L, p, q, Bx, By, seed, mcs, stream, cx=c[0], cy=c[1]))
+    wfn = w2_fn or (lambda c: ensemble_w2(p, q, c, stream=stream))
+    ref_w2 = wfn(ref)
+    table = []
+    for c in cells:
+        rel = [(1.0, 0.0)] * len(ref_w2[0]) if c == ref else relative_w2(wfn(c), ref_w2)
+        table.append({"cx": c[0], "cy": c[1], "attempts_per_ns": float(fn(c)),
+                      "w2_ratio": [r for r, _ in rel], "w2_ratio_err": [e for _, e in rel]})
+    best = pick_cell(table, max_shift)
+    return {"device": device_name() if measure_fn is None else "test", "L": L, "p": p, "q": q,
+            "Bx": Bx, "By": By, "cx": best["cx"], "cy": best["cy"], "attempts_per_ns": best["attempts_per_ns"],
+            "max_shift": max_shift, "reference": list(ref), "table": table,
+            "stat": {"L": STAT_L, "seeds": STAT_SEEDS, "times": list(STAT_TIMES), "shape": list(STAT_SHAPE)},
+            "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+
+
+def cell_key(device: str, L: int, p: float, q: float, Bx: int, By: int, max_shift: float) -> str:
+    return f"{device}|L={L}|p={p!r}|q={q!r}|{Bx}x{By}|cell|max_shift={max_shift!r}"
+
+
+def choose_cell(L: int, p: float, q: float, Bx: int, By: int, max_shift: float = 0.01,
+                cache: TuneCache | None = None, **kw) -> dict:
+    """The recorded cell choice for (GPU, L, p, q, sub-tile, max_shift),
+    measuring once if there is none."""
+    cache = cache if cache is not None else TuneCache()
+    dev = device_name() if kw.get("measure_fn") is None else "test"
+    key = cell_key(dev, L, p, q, Bx, By, max_shift)
+    rec = cache.entries.get(key)
+    if rec is None:
+        rec = tune_cell(L, p, q, Bx, By, max_shift=max_shift, **kw)
+        cache.put_key(key, rec)
+    return rec
 
 
 # ---------------------------------------------------------------------------

@@ -15,10 +15,12 @@
 //              (s%spw)*(cx/spw) .. + bpt-1 for cell j of the band; the low
 //              log2(cx/2) bits are the x offset inside the sub-cell, the next
 //              log2(cy/2) the y offset (bpt = their sum, spw = 2 if 2 bpt <= cx)
-//   acceptance bits 31..28 of the uniform of cell (j, m): bit 4j+m of the
-//              four words of (t, k|(s*8)<<2, T, ACC<<28|g); bits 27..0, only
-//              for ties, from the sub-tile's tail stream in order of group,
-//              then position 4j+m.
+//   acceptance bits 31..28 of the uniform of cell (j, m): bit
+//              (s%SPL)*4*TPB + 4j+m of the four words of
+//              (t, k|((s/SPL)*8)<<2, T, ACC<<28|g), SPL = cx/4 steps per
+//              block (a group uses 4*TPB of the 32 positions per step);
+//              bits 27..0, only for ties, from the group's tail stream in
+//              order of position 4j+m.
 // Because the positions 4j+m of one group interleave the lanes of the group
 // (each holds some of its TC rows m), a tied candidate's place in the tail
 // stream is the number of ties of the earlier groups plus the ties of its
@@ -46,6 +48,7 @@ struct CellShape {
     static constexpr int NTR = 16 / CY;                      // TC rows per lane
     static constexpr int GS = CY / 4;                        // lane rows per group
     static constexpr int SPW = (2 * BPT <= CX) ? 2 : 1;      // steps served by one site field
+    static constexpr int SPL = CX / 4;                       // steps served by one level block
     static constexpr int STEPS = CX * CY;                    // collective steps per device step
     static constexpr uint32_t CMASK = CX == 32 ? 0xFFFFFFFFu : ((1u << CX) - 1u);
 };
@@ -272,7 +275,7 @@ __device__ __forceinline__ void run_subtile_cells(uint32_t *lat, uint32_t L, uin
     uint32_t X[16], Y[16], E, D;
     stage_lane(q, L, wpr, Bx, x0, active, c, X, Y, E, D);
 
-    uint4 setw = make_uint4(0u, 0u, 0u, 0u), site = make_uint4(0u, 0u, 0u, 0u);
+    uint4 setw = make_uint4(0u, 0u, 0u, 0u), site = make_uint4(0u, 0u, 0u, 0u), lvl = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t s = 0; s < static_cast<uint32_t>(S::STEPS); ++s) {
         if ((s & 63u) == 0u) setw = philox4x32_10(c.t, c.k | ((s >> 6) << 2), c.T, kTagSet << 28, c.k0, c.k1);
         const uint32_t d = (word_of(setw, (s >> 4) & 3u) >> (2u * (s & 15u))) & 3u;
@@ -286,7 +289,11 @@ __device__ __forceinline__ void run_subtile_cells(uint32_t *lat, uint32_t L, uin
         uint32_t acc = 0u;
         if (RANDOM) {
             draws += __popc(pmin | pmax);
-            acc = cells_accept<S::GS>(pmin, pmax, level_words(s, c), cc, tp);
+            if (s % S::SPL == 0u)
+                lvl = philox4x32_10(c.t, c.k | (((s / S::SPL) * 8u) << 2), c.T, (kTagAcc << 28) | c.g, c.k0, c.k1);
+            const uint32_t sh = (s % S::SPL) * 4u * S::TPB;  // this step's positions
+            const uint4 W = make_uint4(lvl.x >> sh, lvl.y >> sh, lvl.z >> sh, lvl.w >> sh);
+            acc = cells_accept<S::GS>(pmin, pmax, W, cc, tp);
             net += random_net(acc, pmin, pmax);
         }
         if (d & 2u)

@@ -116,3 +116,82 @@ def test_tune_batch_with_a_fake_timer(tmp_path):
     assert seen == [] and again["policy"] == "square"
     # a different mix is a different decision
     assert at.batch_key(reps) != at.batch_key(reps[:-1])
+
+
+# ------------------------------------------------------------ thread cell ---
+
+def test_cells_are_the_supported_shapes_finest_first():
+    areas = [cx * cy for cx, cy in at.CELLS]
+    assert areas == sorted(areas) and at.CELLS[0] == (4, 4) and at.CELLS[-1] == (32, 16)
+    assert len(set(at.CELLS)) == len(at.CELLS)
+    for cx, cy in at.CELLS:
+        assert cx in (4, 8, 16, 32) and cy in (4, 8, 16)
+
+
+def test_relative_w2_of_independent_ensembles():
+    a = [[2.0, 4.0], [4.0, 8.0]]
+    b = [[3.0, 6.0], [3.0, 6.0]]
+    rel = at.relative_w2(a, b)
+    assert rel[0][0] == pytest.approx(1.0) and rel[1][0] == pytest.approx(1.0)
+    # var(a)/n = 2/2 = 1 at t0, mean 3: error = 1 * sqrt(1/9)
+    assert rel[0][1] == pytest.approx(1.0 / 3.0)
+    assert at.relative_w2([[1.0], [1.0]], [[2.0], [2.0]]) == [(0.5, 0.0)]
+
+
+def _fake_cells(shift_per_area):
+    """Rates fall with the cell's area, the W^2 deficit falls with it too."""
+    def rate(c):
+        return 2000.0 * 16 / (c[0] * c[1])
+
+    def w2(c):
+        d = shift_per_area / (c[0] * c[1])
+        return [[10.0 * (1 - d), 20.0 * (1 - d)], [10.0 * (1 - d), 20.0 * (1 - d)]]
+    return rate, w2
+
+
+@pytest.mark.parametrize("max_shift,want", [(0.0, (32, 16)), (0.003, (16, 16)), (0.005, (16, 8)),
+                                            (0.02, (8, 4)), (0.05, (4, 4))])
+def test_fastest_cell_within_the_allowed_shift(max_shift, want):
+    # deficit 0.64/area against exact W^2: 4x4 4 %, 8x4 2 %, 8x8 1 %, 16x8 0.5 %, 16x16 0.25 %, 32x16
+    # 0.125 %; relative to 32x16 that is a shift of 3.9 %, 1.9 %, 0.88 %, 0.38 % and 0.13 %; equal rates
+    # (16x16 and 32x8) go to the first in CELLS
+    rate, w2 = _fake_cells(0.64)
+    rec = at.tune_cell(4096, 1.0, 0.0, 256, 64, max_shift=max_shift, measure_fn=rate, w2_fn=w2)
+    assert (rec["cx"], rec["cy"]) == want
+    assert rec["reference"] == [32, 16]
+    ref_row = [r for r in rec["table"] if (r["cx"], r["cy"]) == (32, 16)][0]
+    assert ref_row["w2_ratio"] == [1.0, 1.0]
+    assert len(rec["table"]) == len(at.CELLS)
+    chosen = [r for r in rec["table"] if (r["cx"], r["cy"]) == want][0]
+    assert rec["attempts_per_ns"] == chosen["attempts_per_ns"]
+
+
+def test_cell_choice_is_recorded_and_reused(tmp_path):
+    rate, w2 = _fake_cells(0.64)
+    calls = []
+
+    def counting_rate(c):
+        calls.append(c)
+        return rate(c)
+
+    path = str(tmp_path / "tune.json")
+    rec = at.choose_cell(1 << 17, 0.95, 0.05, 256, 64, max_shift=0.02, cache=at.TuneCache.load(path),
+                         measure_fn=counting_rate, w2_fn=w2)
+    assert len(calls) == len(at.CELLS)
+    calls.clear()
+    again = at.choose_cell(1 << 17, 0.95, 0.05, 256, 64, max_shift=0.02, cache=at.TuneCache.load(path),
+                           measure_fn=counting_rate, w2_fn=w2)
+    assert calls == [] and (again["cx"], again["cy"]) == (rec["cx"], rec["cy"]) and again["when"] == rec["when"]
+    # another tolerance or another (p, q) is a separate decision
+    at.choose_cell(1 << 17, 0.95, 0.05, 256, 64, max_shift=0.001, cache=at.TuneCache.load(path),
+                   measure_fn=counting_rate, w2_fn=w2)
+    at.choose_cell(1 << 17, 0.5, 0.5, 256, 64, max_shift=0.02, cache=at.TuneCache.load(path),
+                   measure_fn=counting_rate, w2_fn=w2)
+    assert len(at.TuneCache.load(path).entries) == 3
+
+
+def test_reference_cell_is_chosen_when_every_finer_cell_shifts_too_much():
+    rate, w2 = _fake_cells(50.0)
+    rec = at.tune_cell(1024, 0.5, 0.5, 64, 64, max_shift=0.01, measure_fn=rate, w2_fn=w2,
+                       cells=[(4, 4), (8, 8), (16, 16)])
+    assert (rec["cx"], rec["cy"]) == (16, 16) and rec["reference"] == [16, 16]

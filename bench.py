@@ -3,7 +3,8 @@
 One step = one MCS (L^2 update attempts: four device steps of DTr plus
 single-hit DT) over the whole lattice, resident in HBM.  Default workload:
 L = 2^17 (1.7e10 sites, 4 GiB packed), KPZ with p = 0.95, q = 0.05, flat
-start, seed 1 (+ rank), 256 x 64-site sub-tiles, 4 x 4-site thread cells.
+start, seed 1 (+ rank), 1024 x 16-site sub-tiles, 4 x 4-site thread cells
+(the DTrDB, DTrDTr and coarse-cell legs: 256 x 64-site sub-tiles).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -40,8 +41,10 @@ def parse():
     ap.add_argument("--p", type=float, default=0.95)
     ap.add_argument("--q", type=float, default=0.05)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--Bx", type=int, default=256)
-    ap.add_argument("--By", type=int, default=64)
+    ap.add_argument("--Bx", type=int, default=1024)
+    ap.add_argument("--By", type=int, default=16)
+    ap.add_argument("--side-Bx", type=int, default=256, help="sub-tile of the DTrDB, DTrDTr and coarse-cell legs")
+    ap.add_argument("--side-By", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=48)
     ap.add_argument("--e2e-lattices", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -138,7 +141,9 @@ def philox_blocks_per_lane(scheme: str, cx: int, cy: int, random: bool) -> float
     (one block per 64 collective steps), the DTrDTr block origins (one block
     per 16 steps), the site words (DT: one block per 2 steps when two steps
     share a site field, else per step; DB: per step) and, with acceptance
-    draws, the four level words (one block per step)."""
+    draws, the four level words (DT: one block per cx/4 steps, since a
+    group of 32/cx cells per band uses 4*32/cx of a word's 32 bits per step;
+    DB and DTrDTr: one block per step)."""
     steps = cx * cy
     bpt = (cx // 2).bit_length() - 1 + (cy // 2).bit_length() - 1
     spw = 2 if 2 * bpt <= cx else 1
@@ -150,7 +155,7 @@ def philox_blocks_per_lane(scheme: str, cx: int, cy: int, random: bool) -> float
         if scheme == "DTR":
             blocks += -(-steps // 16)
     if random:
-        blocks += steps
+        blocks += steps / (cx // 4 if scheme == "DT" else 1)
     return blocks
 
 
@@ -171,9 +176,10 @@ def alu_accounting(scheme, cx, cy, random, attempts, tail_blocks, draws, tcs_per
             "survey": {"bits_per_attempt": survey_bits, "ops_per_attempt": 0.5 * survey_bits + 4.0}}
 
 
-def step_traffic(src_hash: str):
-    """DRAM bytes per device-step launch from a committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+def step_traffic(src_hash: str, Bx: int, By: int, L: int):
+    """DRAM bytes per device-step launch at this sub-tile shape and L from a
+    committed ncu summary, if it was taken on the current kernel sources (else
+    None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "dtrdt_step_traffic.json")) as f:
             d = json.load(f)
@@ -181,16 +187,23 @@ def step_traffic(src_hash: str):
         return None
     if d.get("kernel_sources_sha256") != src_hash:
         return None
-    return d.get("dram_bytes_per_launch")
+    cap = d.get("captures", {}).get(f"{Bx}x{By}")
+    if not cap:
+        return None
+    # traffic grows with the sites a launch updates
+    return cap["dram_bytes_per_launch"] * (L / cap["captured_L"]) ** 2
+
+
+STEP_SOURCES = ("dtrdt.cu", "subtile.cuh", "tiles.cuh", "philox.cuh")
 
 
 def src_hash():
-    """sha256 of the step kernel's two source files with comments and blank
-    lines removed (a comment edit does not invalidate a capture)."""
+    """sha256 of the step kernel's source files with comments and blank lines
+    removed (a comment edit does not invalidate a capture)."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for name in ("dtrdt.cu", "subtile.cuh"):
+    for name in STEP_SOURCES:
         with open(os.path.join(ROOT, "paper_1705_01022_gb300", "csrc", name)) as f:
             text = f.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
@@ -200,12 +213,14 @@ def src_hash():
     return h.hexdigest()
 
 
-def cpu_baseline_window(oracle, a, state_getter, t, target_s, scheme=0, seed=None, name="DTrDT"):
+def cpu_baseline_window(oracle, a, state_getter, t, target_s, scheme=0, seed=None, name="DTrDT", shape=None):
     """Times the oracle replaying MCS t on windows of the lattice (read from the
-    running simulation), growing the window until about target_s of CPU work."""
-    prm = oracle.Params(L=a.L, p=a.p, q=a.q, seed=a.seed if seed is None else seed, Bx=a.Bx, By=a.By,
+    running simulation), growing the window until about target_s of CPU work.
+    shape: the sub-tile (Bx, By) of the run (default: the bench's)."""
+    Bx, By = shape or (a.Bx, a.By)
+    prm = oracle.Params(L=a.L, p=a.p, q=a.q, seed=a.seed if seed is None else seed, Bx=Bx, By=By,
                         scheme=scheme)
-    tw, th = 2 * a.Bx, 2 * a.By
+    tw, th = 2 * Bx, 2 * By
     ox, oy, _ = oracle.mcs_draw(prm, t)
     nx, ny, spent, attempts = 2, 2, 0.0, 0
     while True:
@@ -630,7 +645,9 @@ def main():
     hbm_gbs = 2 * (L * L / 16) / (launch_ms * 1e-3) / 1e9  # quarter lattice read + written
     roofline = {
         "bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
-        "frac": achieved_tops / peak_tops, "traffic": step_traffic(src_hash()),
+        "frac": achieved_tops / peak_tops, "traffic": step_traffic(src_hash(), a.Bx, a.By, L),
+        "traffic_vs_algorithmic": (lambda tr: tr / (2 * L * L / 16) if tr else None)(
+            step_traffic(src_hash(), a.Bx, a.By, L)),
         "kernel": "dtrdt_step_kernel", "launch_ms": launch_ms, "launches": launches,
         "ops_per_attempt": ops_per_attempt, "draw_fraction": f_draw,
         "accounting": "generated: 0.5 op per random bit the kernel generates + 4 ops per attempt",
@@ -739,7 +756,7 @@ def main():
 
         def timed(p, q, scheme, n, oracle_scheme=None):
             # continues from the lattice as it stands (no_init), new time origin
-            with g.Simulation(L, p, q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice,
+            with g.Simulation(L, p, q, seed, Bx=a.side_Bx, By=a.side_By, stream=stream, lattice=lattice,
                               no_init=True, scheme=scheme) as h:
                 h.run(2)
                 torch.cuda.synchronize()
@@ -761,7 +778,8 @@ def main():
                     oracle.build()
                     cpu_ = cpu_baseline_window(oracle, a, lambda x, y, W, H: h.window(x, y, W, H), h.t,
                                                a.cpu_seconds / 4, scheme=oracle_scheme, seed=seed,
-                                               name={1: "DTrDB", 3: "DTrDTr"}[oracle_scheme])
+                                               name={1: "DTrDB", 3: "DTrDTr"}[oracle_scheme],
+                                               shape=(a.side_Bx, a.side_By))
                     cpu_.pop("_window")
             return L * L * n / (st_.elapsed_time(en_) * 1e6), step_ms, f_draw, cpu_
 
@@ -778,12 +796,13 @@ def main():
                     "survey_accounting": {"ops_per_attempt": acc["survey"]["ops_per_attempt"],
                                           "achieved": sv, "frac": sv / peak_tops}}
 
-        tcs = (a.Bx // 4) * (a.By // 4)
+        tcs = (a.side_Bx // 4) * (a.side_By // 4)
         db_v, db_step, db_f, db_cpu = timed(a.p, a.q, _lib.OCT_SCHEME_DB, a.db_steps, oracle_scheme=1)
         db_tail = tails_[0]
         kdt_v, kdt_step, _, _ = timed(1.0, 0.0, _lib.OCT_SCHEME_DT, a.db_steps)
         kdb_v, kdb_step, _, _ = timed(1.0, 0.0, _lib.OCT_SCHEME_DB, a.db_steps)
         dtrdb = {"value": db_v, "unit": UNIT, "mcs": a.db_steps, "device_step_ms": db_step,
+                 "sub_tile": [a.side_Bx, a.side_By],
                  "scheme": "DTrDB: single-hit dead border at block level, borders delayed (p, q > 0)",
                  "start": "the DTrDT state after the timed region and the end-to-end steps",
                  "relative_to_dtrdt": db_v / (value / world),
@@ -796,6 +815,7 @@ def main():
         dtr_v, dtr_step, dtr_f, dtr_cpu = timed(a.p, a.q, _lib.OCT_SCHEME_DTR, a.db_steps, oracle_scheme=3)
         dtr_tail = tails_[0]
         dtrdtr = {"value": dtr_v, "unit": UNIT, "mcs": a.db_steps, "device_step_ms": dtr_step,
+                  "sub_tile": [a.side_Bx, a.side_By],
                   "scheme": "DTrDTr: double tiling with a block-layer origin moved after every collective step",
                   "start": "the DTrDB state after its run", "relative_to_dtrdt": dtr_v / (value / world),
                   "roofline": dict(alu_roofline(dtr_step, "DTR", dtr_f, dtr_tail), draw_fraction=dtr_f,
@@ -803,8 +823,9 @@ def main():
                   "cpu_baseline": dtr_cpu}
         # ---- DTrDT with the paper's coarser thread cells (TC=1,1 .. 3,2) on the same workload ----
         cells = {}
-        for cx, cy in (((8, 8), (16, 8), (16, 16), (32, 16)) if a.cell_steps > 0 else ()):
-            with g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, cx=cx, cy=cy, stream=stream, lattice=lattice,
+        for cx, cy in (((4, 4), (8, 8), (16, 8), (16, 16), (32, 16)) if a.cell_steps > 0 else ()):
+            with g.Simulation(L, a.p, a.q, seed, Bx=a.side_Bx, By=a.side_By, cx=cx, cy=cy, stream=stream,
+                              lattice=lattice,
                               no_init=True) as h:
                 h.run(1)
                 torch.cuda.synchronize()
@@ -819,7 +840,7 @@ def main():
                 st1 = _lib.oct_get_stats(h.h)
                 n_att = L * L * a.cell_steps
                 acc_ = alu_accounting("DT", cx, cy, any_random, n_att, st1.tail_blocks - st0.tail_blocks,
-                                      st1.draws - st0.draws, (a.Bx // cx) * (a.By // cy))
+                                      st1.draws - st0.draws, (a.side_Bx // cx) * (a.side_By // cy))
                 step_ = kms / max(1, kl)
                 ach = acc_["generated"]["ops_per_attempt"] * (L * L / 4) / (step_ * 1e-3) / 1e12
                 cells[f"{cx}x{cy}"] = {
@@ -828,6 +849,18 @@ def main():
                     "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tops, "frac": ach / peak_tops,
                                  "ops_per_attempt": acc_["generated"]["ops_per_attempt"],
                                  "bits_per_attempt": acc_["generated"]["bits_per_attempt"]}}
+        if cells:
+            # the cell tuner's choice on these rates: the fastest cell whose W^2 (ensemble of small
+            # lattices at this p, q) lies within 1 % of the coarsest cell's
+            from paper_1705_01022_gb300 import autotune
+            rates = {tuple(int(v) for v in k.split("x")): c["value"] for k, c in cells.items()}
+            rec = autotune.tune_cell(L, a.p, a.q, a.side_Bx, a.side_By, max_shift=0.01, cells=list(rates),
+                                     measure_fn=lambda c: rates[c], stream=stream)
+            cells["sub_tile"] = [a.side_Bx, a.side_By]
+            cells["tuner"] = {"max_shift": rec["max_shift"], "choice": [rec["cx"], rec["cy"]],
+                              "reference": rec["reference"], "fidelity_ensemble": rec["stat"],
+                              "table": [[r["cx"], r["cy"], round(r["attempts_per_ns"], 1),
+                                         [round(x, 4) for x in r["w2_ratio"]]] for r in rec["table"]]}
         sim = g.Simulation(L, a.p, a.q, seed, Bx=a.Bx, By=a.By, stream=stream, lattice=lattice)
         sim.run(a.warmup + a.steps)
 

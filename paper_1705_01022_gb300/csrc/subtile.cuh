@@ -155,15 +155,15 @@ __device__ __forceinline__ void step_candidates(const uint32_t (&X)[16], const u
                                                 uint32_t dx, const LaneCtx &c, uint32_t (&cnd0)[4],
                                                 uint32_t (&cnd1)[4], uint32_t &pmin, uint32_t &pmax) {
     const uint32_t sw[4] = {site.x, site.y, site.z, site.w};
-    const uint32_t par = 2u * (s & 1u);
     const uint32_t sh2 = 2u * dx;
     pmin = 0u;
     pmax = 0u;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        // Site draw: bit 4j = x offset, bit 4j+1 = y offset of TC column j.
-        const uint32_t u = sw[m] >> par;
-        const uint32_t col = (((u & kNib) << 1) | (~u & kNib)) << sh2;
+        // Site draw: bit 4j = x offset, bit 4j+1 = y offset of TC column j (for odd
+        // steps run_subtile has shifted the words down to the step's field).
+        const uint32_t u = sw[m];
+        const uint32_t col = ((u & kNib) + kNib) << sh2;  // 1 + xoff: one-hot, no carries
         const uint32_t yoff = ((u >> 1) & kNib) * 0xFu;
         const int r0 = 4 * m + 2 * DY, r1 = r0 + 1;
         const uint32_t xa = X[r0], xb = X[r1];
@@ -183,8 +183,10 @@ __device__ __forceinline__ void step_candidates(const uint32_t (&X)[16], const u
             const uint32_t mn = (cnd0[m] & ~xa) | (cnd1[m] & ~xb);
             const uint32_t mx = (cnd0[m] & xa) | (cnd1[m] & xb);
             const uint32_t cmn = SPEC == 2 ? mn : mn & c.p_random, cmx = SPEC == 2 ? mx : mx & c.q_random;
-            pmin |= (((cmn >> sh2) | (cmn >> (sh2 + 1u))) & kNib) << m;
-            pmax |= (((cmx >> sh2) | (cmx >> (sh2 + 1u))) & kNib) << m;
+            // a cell has at most one candidate, at bit 4j + sh2 + xoff: 3 cmn sets bit
+            // 4j + sh2 + 1 for either xoff (no carries: candidates are >= 3 bits apart)
+            pmin |= (((cmn * 3u) >> (sh2 + 1u)) & kNib) << m;
+            pmax |= (((cmx * 3u) >> (sh2 + 1u)) & kNib) << m;
         }
     }
 }
@@ -286,15 +288,14 @@ __device__ __forceinline__ void step_candidates_rt(const uint32_t (&X)[16], cons
                                                    uint32_t (&cnd0)[4], uint32_t (&cnd1)[4],
                                                    uint32_t &pmin, uint32_t &pmax) {
     const uint32_t sw[4] = {site.x, site.y, site.z, site.w};
-    const uint32_t par = 2u * (s & 1u);
-    const uint32_t sh2 = 2u * dx;
+    const uint32_t sh2 = 2u * dx;  // site words: shifted to the step's field by run_subtile
     const uint32_t ro = 2u * dy;
     pmin = 0u;
     pmax = 0u;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const uint32_t u = sw[m] >> par;
-        const uint32_t col = (((u & kNib) << 1) | (~u & kNib)) << sh2;
+        const uint32_t u = sw[m];
+        const uint32_t col = ((u & kNib) + kNib) << sh2;  // 1 + xoff: one-hot, no carries
         const uint32_t yoff = ((u >> 1) & kNib) * 0xFu;
         const uint32_t xa = dy ? X[4 * m + 2] : X[4 * m];
         const uint32_t xb = dy ? X[4 * m + 3] : X[4 * m + 1];
@@ -315,8 +316,8 @@ __device__ __forceinline__ void step_candidates_rt(const uint32_t (&X)[16], cons
             const uint32_t mn = (cnd0[m] & ~xa) | (cnd1[m] & ~xb);
             const uint32_t mx = (cnd0[m] & xa) | (cnd1[m] & xb);
             const uint32_t cmn = SPEC == 2 ? mn : mn & c.p_random, cmx = SPEC == 2 ? mx : mx & c.q_random;
-            pmin |= (((cmn >> sh2) | (cmn >> (sh2 + 1u))) & kNib) << m;
-            pmax |= (((cmx >> sh2) | (cmx >> (sh2 + 1u))) & kNib) << m;
+            pmin |= (((cmn * 3u) >> (sh2 + 1u)) & kNib) << m;  // see step_candidates
+            pmax |= (((cmx * 3u) >> (sh2 + 1u)) & kNib) << m;
         }
     }
 }
@@ -328,6 +329,7 @@ __device__ __forceinline__ void step_apply_rt(uint32_t (&X)[16], uint32_t (&Y)[1
     const uint32_t ro = 2u * dy;
     const uint32_t dym = dy ? 0xFFFFFFFFu : 0u;
     uint32_t dE = 0, dB0 = 0, dD = 0, dY0 = 0;
+    uint32_t g0[4], g1[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         uint32_t amin = c.p_always, amax = c.q_always, spread = 0u;
@@ -336,8 +338,6 @@ __device__ __forceinline__ void step_apply_rt(uint32_t (&X)[16], uint32_t (&Y)[1
             amin |= spread & c.p_random;
             amax |= spread & c.q_random;
         }
-        const uint32_t xa = dy ? X[4 * m + 2] : X[4 * m];
-        const uint32_t xb = dy ? X[4 * m + 3] : X[4 * m + 1];
         uint32_t f0, f1;
         if (SPEC == 1) {
             f0 = cnd0[m];
@@ -347,15 +347,14 @@ __device__ __forceinline__ void step_apply_rt(uint32_t (&X)[16], uint32_t (&Y)[1
             f0 = cnd0[m] & spread;
             f1 = cnd1[m] & spread;
         } else {
+            const uint32_t xa = dy ? X[4 * m + 2] : X[4 * m];
+            const uint32_t xb = dy ? X[4 * m + 3] : X[4 * m + 1];
             f0 = cnd0[m] & ((~xa & amin) | (xa & amax));
             f1 = cnd1[m] & ((~xb & amin) | (xb & amax));
             net += always_net<RANDOM>(f0, xa, c) + always_net<RANDOM>(f1, xb, c);
         }
-        const uint32_t nxa = xa ^ (f0 * 3u), nxb = xb ^ (f1 * 3u);  // 3f = f ^ (f << 1), see step_apply
-        X[4 * m] = dy ? X[4 * m] : nxa;
-        X[4 * m + 1] = dy ? X[4 * m + 1] : nxb;
-        X[4 * m + 2] = dy ? nxa : X[4 * m + 2];
-        X[4 * m + 3] = dy ? nxb : X[4 * m + 3];
+        g0[m] = f0 * 3u;  // 3f = f ^ (f << 1), see step_apply; applied after the exchange
+        g1[m] = f1 * 3u;
         const uint32_t f01 = f0 ^ f1;
         Y[4 * m] ^= f0 & ~dym;
         Y[4 * m + 1] ^= f01 & ~dym;
@@ -365,22 +364,34 @@ __device__ __forceinline__ void step_apply_rt(uint32_t (&X)[16], uint32_t (&Y)[1
             Y[(4 * m + 4) & 15] ^= f1 & dym;
         else
             D ^= f1 & dym;
-        const uint32_t r0 = 4u * m + ro;
-        dE |= ((f0 >> 31) << r0) | ((f1 >> 31) << (r0 + 1u));
-        dB0 |= ((f0 & 1u) << r0) | ((f1 & 1u) << (r0 + 1u));
+        dE |= ((f0 >> 31) << (4 * m)) | ((f1 >> 31) << (4 * m + 1));
+        dB0 |= ((f0 & 1u) << (4 * m)) | ((f1 & 1u) << (4 * m + 1));
         if (m == 3) dD = f1 & dym;
         if (m == 0) dY0 = f0 & ~dym;
     }
-    // dE is zero unless dx = 1, dB0 zero unless dx = 0; dD zero unless dy = 1,
-    // dY0 zero unless dy = 0, so both directions can always be exchanged.
-    E ^= dE;
-    const uint32_t vr = __shfl_up_sync(kFull, dE, 1);
-    const uint32_t vl = __shfl_down_sync(kFull, dB0, 1);
-    if (c.gx > 0) {
+    if (c.GX > 1) {  // warp-uniform: every sub-tile of a warp has the same shape
+        dE <<= ro;
+        dB0 <<= ro;
+        E ^= dE;
+        uint32_t vr = __shfl_up_sync(kFull, dE, 1);
+        const uint32_t vl = __shfl_down_sync(kFull, dB0, 1);
+        vr = c.gx > 0 ? (vr >> ro) : 0u;  // the left lane is in the same sub-tile: same row offset
 #pragma unroll
-        for (int r = 0; r < 16; ++r) X[r] ^= (vr >> r) & 1u;
+        for (int m = 0; m < 4; ++m) {
+            g0[m] ^= (vr >> (4 * m)) & 1u;
+            g1[m] ^= (vr >> (4 * m + 1)) & 1u;
+        }
+        if (c.gx < c.GX - 1) E ^= vl;
+    } else {
+        E ^= dE << ro;
     }
-    if (c.gx < c.GX - 1) E ^= vl;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        X[4 * m] ^= g0[m] & ~dym;
+        X[4 * m + 1] ^= g1[m] & ~dym;
+        X[4 * m + 2] ^= g0[m] & dym;
+        X[4 * m + 3] ^= g1[m] & dym;
+    }
     const uint32_t vd = __shfl_up_sync(kFull, dD, c.GX);
     const uint32_t vu = __shfl_down_sync(kFull, dY0, c.GX);
     if (c.gy > 0) Y[0] ^= vd;
@@ -987,6 +998,8 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
         }
         if ((s & 1u) == 0u)
             site = philox4x32_10(c.t, c.k | ((s >> 1) << 2), c.T, (kTagSite << 28) | c.g, c.k0, c.k1);
+        else
+            site = make_uint4(site.x >> 2, site.y >> 2, site.z >> 2, site.w >> 2);
         const uint32_t d = (setw.x >> (2u * s)) & 3u;
         uint32_t cnd0[4], cnd1[4], pmin, pmax;
         constexpr int kSpec = SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0;

@@ -164,7 +164,8 @@ __device__ __forceinline__ void step_candidates(const uint32_t (&X)[16], const u
         // steps run_subtile has shifted the words down to the step's field).
         const uint32_t u = sw[m];
         const uint32_t col = ((u & kNib) + kNib) << sh2;  // 1 + xoff: one-hot, no carries
-        const uint32_t yoff = ((u >> 1) & kNib) * 0xFu;
+        // the y offset, spread over the two columns col can take (bits 2dx, 2dx+1)
+        const uint32_t yoff = dx ? (u & (kNib << 1)) * 6u : ((u >> 1) & kNib) * 3u;
         const int r0 = 4 * m + 2 * DY, r1 = r0 + 1;
         const uint32_t xa = X[r0], xb = X[r1];
         const uint32_t xra = __funnelshift_r(xa, E >> r0, 1);
@@ -179,7 +180,12 @@ __device__ __forceinline__ void step_candidates(const uint32_t (&X)[16], const u
         }
         cnd0[m] = col & ~yoff & (xa ^ xra) & (ya ^ yb) & ~(xa ^ ya);
         cnd1[m] = col & yoff & (xb ^ xrb) & (yb ^ yc) & ~(xb ^ yb);
-        if (RANDOM) {
+        if (RANDOM && SPEC == 2) {
+            const uint32_t cc = cnd0[m] | cnd1[m];
+            const uint32_t mx = (cnd0[m] & xa) | (cnd1[m] & xb);
+            pmin |= (((cc * 3u) >> (sh2 + 1u)) & kNib) << m;
+            pmax |= (((mx * 3u) >> (sh2 + 1u)) & kNib) << m;
+        } else if (RANDOM) {
             const uint32_t mn = (cnd0[m] & ~xa) | (cnd1[m] & ~xb);
             const uint32_t mx = (cnd0[m] & xa) | (cnd1[m] & xb);
             const uint32_t cmn = SPEC == 2 ? mn : mn & c.p_random, cmx = SPEC == 2 ? mx : mx & c.q_random;
@@ -189,6 +195,7 @@ __device__ __forceinline__ void step_candidates(const uint32_t (&X)[16], const u
             pmax |= (((cmx * 3u) >> (sh2 + 1u)) & kNib) << m;
         }
     }
+    if (RANDOM && SPEC == 2) pmin &= ~pmax;  // pmin held every candidate: keep the minima
 }
 
 // Phase 3 with sub-cell set (dx, DY): flips of the accepted candidates (acc:

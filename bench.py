@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--loop-steps", type=int, default=3)
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--serve-jobs", type=int, default=96)
+    ap.add_argument("--serve-jobs", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-policy", default="large", help="autotune.batch_shape policy of the serving leg")
     ap.add_argument("--db-steps", type=int, default=30)

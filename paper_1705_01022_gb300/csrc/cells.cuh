@@ -278,7 +278,9 @@ __device__ __forceinline__ void run_subtile_cells(uint32_t *lat, uint32_t L, uin
     uint4 setw = make_uint4(0u, 0u, 0u, 0u), site = make_uint4(0u, 0u, 0u, 0u), lvl = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t s = 0; s < static_cast<uint32_t>(S::STEPS); ++s) {
         if ((s & 63u) == 0u) setw = philox4x32_10(c.t, c.k | ((s >> 6) << 2), c.T, kTagSet << 28, c.k0, c.k1);
-        const uint32_t d = (word_of(setw, (s >> 4) & 3u) >> (2u * (s & 15u))) & 3u;
+        // the set, broadcast from lane 0 (all lanes drew the same one) so that the
+        // branches on it are warp-uniform for the compiler
+        const uint32_t d = __shfl_sync(kFull, (word_of(setw, (s >> 4) & 3u) >> (2u * (s & 15u))) & 3u, 0);
         if (s % S::SPW == 0u)
             site = philox4x32_10(c.t, c.k | ((s / S::SPW) << 2), c.T, (kTagSite << 28) | c.g, c.k0, c.k1);
         uint32_t cand[8], pmin, pmax;

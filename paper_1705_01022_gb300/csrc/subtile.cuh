@@ -1007,7 +1007,10 @@ __device__ __forceinline__ void run_subtile(uint32_t *lat, uint32_t L, uint32_t 
             site = philox4x32_10(c.t, c.k | ((s >> 1) << 2), c.T, (kTagSite << 28) | c.g, c.k0, c.k1);
         else
             site = make_uint4(site.x >> 2, site.y >> 2, site.z >> 2, site.w >> 2);
-        const uint32_t d = (setw.x >> (2u * s)) & 3u;
+        // the set (every lane of a one-sub-tile warp drew the same one; the broadcast
+        // from lane 0 lets the compiler treat the branches on it as warp-uniform)
+        const uint32_t d_own = (setw.x >> (2u * s)) & 3u;
+        const uint32_t d = LANE_SETS ? d_own : __shfl_sync(kFull, d_own, 0);
         uint32_t cnd0[4], cnd1[4], pmin, pmax;
         constexpr int kSpec = SCHEME == 4 ? 1 : SCHEME == 5 ? 2 : 0;
         if (LANE_SETS)

@@ -5,11 +5,14 @@
 //   h(x,y) = h(0,y) + r(x,y),  r(x,y) = sum_{x'=1..x} (2 X(x',y) - 1).
 // Pass 1 (one warp per row): with q(x) = sum_{x'=0..x} (2X(x',y)-1) and
 // s0 = 2X(0,y)-1, r = q - s0, so the row sums of r and r^2 follow from those
-// of q, which a warp computes with 128-bit coalesced loads, a warp scan of
-// per-lane step counts and a 256-entry byte table (sum of the running step
-// inside a byte, its square, its extremes).  Pass 2 (one block): a scan of the
-// column bits gives h(0,y), and S1 = sum_y (L h0 + R1), S2 = sum_y (L h0^2 +
-// 2 h0 R1 + R2) accumulate in 128-bit integers.  Per-row terms are bounded by
+// of q.  A warp takes the row in chunks of 512 words, 16 consecutive words per
+// lane (16-byte coalesced loads); each lane reduces its words with a 256-entry
+// byte table (per byte: the sum of the running step inside it, of its square,
+// the net step and the extremes) and integer multiply-adds, and a warp scan of
+// the lanes' net steps lifts the lane sums to the row.  Pass 2: a scan of the
+// column bits gives h0 = h(0,y), and S1 = sum_y (L h0 + R1), S2 = sum_y (L h0^2 +
+// 2 h0 R1 + R2) accumulate in 128-bit integers, per block of rows and then
+// over the blocks.  Per-row terms are bounded by
 // 4 L^3 < 2^63 for L <= 2^20, so only the cross-row sums need 128 bits.
 #include "oct_internal.h"
 
@@ -28,11 +31,13 @@ __global__ void init_flat_kernel(uint32_t *lat, uint32_t rows, uint64_t n_words,
     }
 }
 
-// Byte table: for byte value v, with running step e_i = sum_{j<=i} (2 b_j - 1),
-// i = 0..7:
-//   .x = sum e_i (signed byte) | net e_7 << 8 (signed byte) | sum e_i^2 << 16
-//   .y = the extremes as two biased 16-bit halves for one packed minimum:
-//        (min e_i + kW2Bias) | (kW2Bias - max e_i) << 16
+// Byte table of the row pass.  For byte value v, with the running step
+// e_i = sum_{j<=i} (2 b_j - 1), i = 0..7, t1 = sum e_i, t2 = sum e_i^2, n = e_7:
+//   .x = 2 t1 + t2 2^17 + n 2^27   (mod 2^32; |2 t1| <= 72 < 2^17 <= t2 2^17)
+//   .y = (min e_i + kW2Bias) | (kW2Bias - max e_i) << 16
+// The four .x of a word plus 512 hold sum 2 t1 + 512 in bits 0..16 and
+// sum t2 <= 816 in bits 17..26; read as a signed word, floor(.x / 2^27) = n
+// (t2 >= 4, so the part below bit 27 is positive).
 constexpr uint32_t kW2Bias = 0x8000u;
 
 __device__ __forceinline__ uint2 byte_entry(uint32_t v) {
@@ -45,14 +50,9 @@ __device__ __forceinline__ uint2 byte_entry(uint32_t v) {
         mx = max(mx, e);
     }
     uint2 r;
-    r.x = (static_cast<uint32_t>(s1) & 0xFFu) | ((static_cast<uint32_t>(e) & 0xFFu) << 8) |
-          (static_cast<uint32_t>(s2) << 16);
+    r.x = static_cast<uint32_t>(2 * s1) + (static_cast<uint32_t>(s2) << 17) + (static_cast<uint32_t>(e) << 27);
     r.y = (kW2Bias + static_cast<uint32_t>(mn)) | ((kW2Bias - static_cast<uint32_t>(mx)) << 16);
     return r;
-}
-
-__device__ __forceinline__ int sbyte(uint32_t x, int k) {
-    return static_cast<int>(static_cast<signed char>(static_cast<unsigned char>(x >> (8 * k))));
 }
 
 // Halfword-wise unsigned minimum of two packed pairs.
@@ -62,174 +62,362 @@ __device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b) {
     return r;
 }
 
-constexpr int kW2Warps = 8;
-
-// The 4 words w..w+3 of a row (one 16-byte load where the row allows it);
-// words past the row's end read as 0 and are not counted.
-__device__ __forceinline__ uint4 load_chunk(const uint32_t *row, uint32_t w, uint32_t wpr, bool vec_ok) {
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (vec_ok && w + 3u < wpr) {
-        v = *reinterpret_cast<const uint4 *>(row + w);
-    } else if (w < wpr) {
-        v.x = row[w];
-        if (w + 1u < wpr) v.y = row[w + 1];
-        if (w + 2u < wpr) v.z = row[w + 2];
-        if (w + 3u < wpr) v.w = row[w + 3];
-    }
-    return v;
+// hi32(a * b) + c, signed
+__device__ __forceinline__ int mad_hi_s32(uint32_t a, int b, int c) {
+    int d;
+    asm("mad.hi.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
 }
 
-// Copies of the byte table: lane l reads copy l % 16, entry e of copy c at
-// uint2 index 16 e + c, i.e. banks 2c and 2c + 1.  The 16 lanes of a
-// half-warp (one 8-byte shared-memory transaction) then never share a bank,
-// whatever bytes they look up.
-constexpr int kW2TableCopies = 16;
+constexpr int kW2Warps = 8;
+constexpr int kW2BlocksPerSM = 3;
+constexpr int kW2LaneWords = 16;                      // words per lane and chunk
+constexpr uint32_t kW2ChunkWords = 32u * kW2LaneWords;  // words per warp and chunk
+// Table entry v of copy c at byte offset 256 v + 8 c, c = lane % 16: the shared
+// address of byte k of a word w is one byte permute (byte k of w above the
+// copy offset).  The 16 lanes of a half-warp (one 8-byte shared-memory
+// transaction) read banks 2c, 2c + 1, whatever bytes they look up.
+constexpr int kW2TableBytes = 256 * 256;
 
-__global__ void __launch_bounds__(kW2Warps * 32)
+// Running sums of one lane over the words of its chunk: P = running step
+// before the current word (relative to the lane's first bit); M2, Mz and SPw
+// accumulate the square sums, the linear sums and the word-start prefixes
+// (with constant offsets removed once per chunk); ext is the packed pair of
+// extremes of the lane's running step, biased by kW2Bias.
+struct W2Lane {
+    int P;
+    uint32_t M2, Mz;
+    int SPw;
+    uint32_t ext;
+};
+
+// One 32-site word w.  With a_j the running step inside the word (j = 0..31)
+// and P the lane's running step before it, the word adds
+//   sum (P + a_j) = 32 P + A1,  sum (P + a_j)^2 = P (32 P + 2 A1) + A2.
+// Byte k (P_k = running step before it inside the word, P_0 = 0) contributes
+// 8 P_k + t1 to A1 and 8 P_k^2 + 2 P_k t1 + t2 to A2.  u = 8 P_k + .x is
+// 8 P_k + 2 t1 in its low 17 bits (the t2 and n fields only add multiples of
+// 2^17), so
+//   acc2 = 2^16 + sum_{k>=1} u P_k = 2^16 + V (mod 2^17), |V| <= 3 * 264 * 24 < 2^16,
+// with V = sum (8 P_k^2 + 2 P_k t1), A2 = V + sum t2 and 2 A1 = 16 sum P_k + sum 2 t1.
+// P_{k+1} = P_k + n is one multiply-high of .x.
+__device__ __forceinline__ void w2_word(const unsigned char *tab, uint32_t slot, uint32_t w, W2Lane &a) {
+    const uint2 e0 = *reinterpret_cast<const uint2 *>(tab + __byte_perm(w, slot, 0x6504));
+    const uint2 e1 = *reinterpret_cast<const uint2 *>(tab + __byte_perm(w, slot, 0x6514));
+    const uint2 e2 = *reinterpret_cast<const uint2 *>(tab + __byte_perm(w, slot, 0x6524));
+    const uint2 e3 = *reinterpret_cast<const uint2 *>(tab + __byte_perm(w, slot, 0x6534));
+    // extremes: .y + P_k (1 - 2^16) = (min + bias + P_k) | (bias - max - P_k) << 16
+    const int p1 = mad_hi_s32(e0.x, 32, 0);
+    uint32_t u = static_cast<uint32_t>(p1) * 8u + e1.x;
+    uint32_t acc2 = u * static_cast<uint32_t>(p1) + 0x10000u;
+    const uint32_t c1 = e1.y + static_cast<uint32_t>(p1) * 0xFFFF0001u;
+    const int p2 = mad_hi_s32(e1.x, 32, p1);
+    u = static_cast<uint32_t>(p2) * 8u + e2.x;
+    acc2 += u * static_cast<uint32_t>(p2);
+    const uint32_t c2 = e2.y + static_cast<uint32_t>(p2) * 0xFFFF0001u;
+    const int p3 = mad_hi_s32(e2.x, 32, p2);
+    u = static_cast<uint32_t>(p3) * 8u + e3.x;
+    acc2 += u * static_cast<uint32_t>(p3);
+    const uint32_t c3 = e3.y + static_cast<uint32_t>(p3) * 0xFFFF0001u;
+    const int p4 = mad_hi_s32(e3.x, 32, p3);
+    const uint32_t ext = min_u16x2(min_u16x2(e0.y, c1), min_u16x2(c2, c3));
+    // S = sum .x + 512: Sl = sum 2 t1 + 512, bits 17..26 sum t2
+    const uint32_t S = e0.x + e1.x + e2.x + e3.x + 512u;
+    const uint32_t Sl = S & 0x1FFFFu, T2 = (S >> 17) & 0x3FFu;
+    const uint32_t SP = static_cast<uint32_t>(p1 + p2 + p3);
+    const uint32_t tw = SP * 16u + Sl;  // 2 A1 + 512
+    // lane sums: zp = 32 P + 2 A1 + 512, P zp + Vb + t2 = (word's square sum)
+    // + 512 P + 2^16; the offsets are removed at the end of the chunk
+    const uint32_t P = static_cast<uint32_t>(a.P);
+    const uint32_t zp = P * 32u + tw;
+    a.M2 = zp * P + a.M2 + (acc2 & 0x1FFFFu) + T2;
+    a.Mz += zp;
+    a.SPw += a.P;
+    a.ext = min_u16x2(a.ext, ext + P * 0xFFFF0001u);
+    a.P += p4;
+}
+
+// The lane's kW2LaneWords words of the chunk at word w0 of a row (16-byte
+// loads where the row allows them); words past the row's end read as 0 and
+// are not counted.
+__device__ __forceinline__ void load_lane(const uint32_t *row, uint32_t w, uint32_t wpr, bool vec_ok,
+                                          uint32_t (&v)[kW2LaneWords]) {
+    if (vec_ok && w + kW2LaneWords <= wpr) {
+#pragma unroll
+        for (int i = 0; i < kW2LaneWords / 4; ++i) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(row + w + 4 * i);
+            v[4 * i] = q.x;
+            v[4 * i + 1] = q.y;
+            v[4 * i + 2] = q.z;
+            v[4 * i + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kW2LaneWords; ++i) v[i] = (w + i < wpr) ? row[w + i] : 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kW2Warps * 32, kW2BlocksPerSM)
     w2_rows_kernel(const uint32_t *lat, uint32_t L, uint32_t nrows, uint32_t plane_rows, W2RowSums *rows) {
-    __shared__ uint2 table[256 * kW2TableCopies];
+    extern __shared__ __align__(16) unsigned char w2_table[];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         const uint2 e = byte_entry(static_cast<uint32_t>(i));
 #pragma unroll
-        for (int c = 0; c < kW2TableCopies; ++c) table[i * kW2TableCopies + c] = e;
+        for (int c = 0; c < 16; ++c) *reinterpret_cast<uint2 *>(w2_table + 256 * i + 8 * c) = e;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const uint2 *const my_table = table + (lane % kW2TableCopies);
+    const uint32_t slot = 8u * static_cast<uint32_t>(lane & 15);
     const uint32_t wpr = L >> 5;
     const uint32_t *Yp = lat + static_cast<size_t>(plane_rows) * wpr;
     // 16-byte loads need every row to start on a 16-byte boundary
     const bool vec_ok = (wpr % 4u) == 0u && (reinterpret_cast<uintptr_t>(lat) % 16u) == 0u;
-    for (uint32_t y = blockIdx.x * kW2Warps + (threadIdx.x >> 5); y < nrows; y += gridDim.x * kW2Warps) {
-        const uint32_t *row = lat + static_cast<size_t>(y) * wpr;
-        long long base = 0;  // q just before the current chunk
-        long long q1 = 0, q2 = 0;
-        int qmin = 1 << 30, qmax = -(1 << 30);
-        // Chunks of 128 words: lane i takes words 4i..4i+3; the next chunk's
-        // load is issued before the current one is reduced.
-        uint4 v = load_chunk(row, 4u * lane, wpr, vec_ok);
-        for (uint32_t w0 = 0; w0 < wpr; w0 += 128u) {
-            const uint32_t w = w0 + 4u * lane;
-            const uint4 vn = load_chunk(row, w + 128u, wpr, vec_ok);
-            const int nw = (w < wpr) ? static_cast<int>(min(4u, wpr - w)) : 0;
-            const int nbits = 32 * nw;
-            const int step = 2 * (__popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w)) - nbits;
-            int incl = step;
+    // The warp's rows y0, y0 + stride, ... are taken chunk by chunk (chunks of
+    // kW2ChunkWords words, lane i on words 16i..16i+15 of the chunk); the next
+    // chunk's loads, across row ends too, are issued before the current chunk
+    // is reduced.
+    const uint32_t stride = gridDim.x * kW2Warps;
+    const uint32_t nchunks = (wpr + kW2ChunkWords - 1) / kW2ChunkWords;
+    uint32_t y = blockIdx.x * kW2Warps + (threadIdx.x >> 5), c = 0;
+    uint32_t v[kW2LaneWords], vn[kW2LaneWords];
+    if (y < nrows) load_lane(lat + static_cast<size_t>(y) * wpr, kW2LaneWords * lane, wpr, vec_ok, v);
+    long long base = 0;  // q just before the current chunk
+    long long q1 = 0, q2 = 0;
+    int qmin = 1 << 30, qmax = -(1 << 30);
+    while (y < nrows) {
+        const uint32_t w0 = c * kW2ChunkWords;
+        const uint32_t w = w0 + kW2LaneWords * lane;
+        const bool last = c + 1 == nchunks;
+        const uint32_t ny = last ? y + stride : y, nc = last ? 0u : c + 1;
+        if (ny < nrows)
+            load_lane(lat + static_cast<size_t>(ny) * wpr, nc * kW2ChunkWords + kW2LaneWords * lane, wpr, vec_ok, vn);
+        W2Lane a{0, 0u, 0u, 0, 0xFFFFFFFFu};
+        uint32_t nw = 0;
+        if (w0 + kW2ChunkWords <= wpr) {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int n = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += n;
-            }
-            // Lane-local running sum a (0 at the lane's first bit) in 32 bits:
-            // |a| <= 128, sum a <= 2^14, sum a^2 <= 2^21.
-            // ext: running packed minimum of (a + min e + bias | bias - a - max e),
-            // both halves within [bias - 136, bias + 136]
-            int a = 0, l1 = 0, l2 = 0;
-            uint32_t ext = 0xFFFFFFFFu;
-            const uint32_t words[4] = {v.x, v.y, v.z, v.w};
+            for (int j = 0; j < kW2LaneWords; ++j) w2_word(w2_table, slot, v[j], a);
+            nw = kW2LaneWords;
+        } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (j >= nw) break;
-#pragma unroll
-                for (int byte = 0; byte < 4; ++byte) {
-                    const uint2 te = my_table[((words[j] >> (8 * byte)) & 0xFFu) * kW2TableCopies];
-                    const int t1 = sbyte(te.x, 0), net = sbyte(te.x, 1);
-                    l1 += 8 * a + t1;
-                    l2 += a * (8 * a + 2 * t1) + static_cast<int>(te.x >> 16);
-                    // + a in the low half, - a in the high half (a * (1 - 2^16))
-                    ext = min_u16x2(ext, te.y + static_cast<uint32_t>(a) * 0xFFFF0001u);
-                    a += net;
+            for (int j = 0; j < kW2LaneWords; ++j)
+                if (w + j < wpr) {
+                    w2_word(w2_table, slot, v[j], a);
+                    ++nw;
                 }
-            }
-            // lift to the row: q = B + a with B = q before this lane's first bit
-            const long long B = base + (incl - step);
-            q1 += static_cast<long long>(nbits) * B + l1;
-            q2 += static_cast<long long>(nbits) * B * B + 2 * B * l1 + l2;
-            if (nw > 0) {
-                const int lmn = static_cast<int>(ext & 0xFFFFu) - static_cast<int>(kW2Bias);
-                const int lmx = static_cast<int>(kW2Bias) - static_cast<int>(ext >> 16);
-                qmin = min(qmin, static_cast<int>(B) + lmn);
-                qmax = max(qmax, static_cast<int>(B) + lmx);
-            }
-            base += __shfl_sync(kFull, incl, 31);
-            v = vn;
         }
+        // lane-relative sums: sum q' and sum q'^2 over the lane's 32 nw sites
+        // (|q'| <= 512, so both fit 32 bits), extremes and net step
+        const int M2 = static_cast<int>(a.M2 - 512u * static_cast<uint32_t>(a.SPw) - 65536u * nw);
+        const int M1 = static_cast<int>(a.Mz + 32u * static_cast<uint32_t>(a.SPw) - 512u * nw) / 2;
+        const int step = a.P;
+        int incl = step;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            q1 += __shfl_xor_sync(kFull, q1, o);
-            q2 += __shfl_xor_sync(kFull, q2, o);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += n;
         }
-        qmin = __reduce_min_sync(kFull, qmin);
-        qmax = __reduce_max_sync(kFull, qmax);
-        if (lane == 0) {
-            const long long s0 = (row[0] & 1u) ? 1 : -1;
-            const long long Ll = L;
-            W2RowSums o;
-            o.r1 = q1 - Ll * s0;
-            o.r2 = q2 - 2 * s0 * q1 + Ll * s0 * s0;
-            o.rmin = qmin - static_cast<int>(s0);
-            o.rmax = qmax - static_cast<int>(s0);
-            o.c = static_cast<int>(Yp[static_cast<size_t>(y) * wpr] & 1u);
-            o.pad = 0;
-            rows[y] = o;
+        // lift to the row: q = B + q' with B = q before this lane's first bit
+        const long long B = base + (incl - step);
+        const long long nbits = 32ll * nw;
+        q1 += nbits * B + M1;
+        q2 += nbits * B * B + 2 * B * M1 + M2;
+        if (nw > 0) {
+            const int lmn = static_cast<int>(a.ext & 0xFFFFu) - static_cast<int>(kW2Bias);
+            const int lmx = static_cast<int>(kW2Bias) - static_cast<int>(a.ext >> 16);
+            qmin = min(qmin, static_cast<int>(B) + lmn);
+            qmax = max(qmax, static_cast<int>(B) + lmx);
         }
+        base += __shfl_sync(kFull, incl, 31);
+        if (last) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                q1 += __shfl_xor_sync(kFull, q1, o);
+                q2 += __shfl_xor_sync(kFull, q2, o);
+            }
+            qmin = __reduce_min_sync(kFull, qmin);
+            qmax = __reduce_max_sync(kFull, qmax);
+            if (lane == 0) {
+                const uint32_t *row = lat + static_cast<size_t>(y) * wpr;
+                const long long s0 = (row[0] & 1u) ? 1 : -1;
+                const long long Ll = L;
+                W2RowSums o;
+                o.r1 = q1 - Ll * s0;
+                o.r2 = q2 - 2 * s0 * q1 + Ll * s0 * s0;
+                o.rmin = qmin - static_cast<int>(s0);
+                o.rmax = qmax - static_cast<int>(s0);
+                o.c = static_cast<int>(Yp[static_cast<size_t>(y) * wpr] & 1u);
+                o.pad = 0;
+                rows[y] = o;
+            }
+            base = 0;
+            q1 = q2 = 0;
+            qmin = 1 << 30;
+            qmax = -(1 << 30);
+        }
+        y = ny;
+        c = nc;
+#pragma unroll
+        for (int j = 0; j < kW2LaneWords; ++j) v[j] = vn[j];
     }
 }
 
-constexpr int kFinalThreads = 1024;
+// Pass 2 runs in two kernels.  Pass 2a: one block per kW2BlockRows rows
+// computes, relative to the height h0 of its first row, the sums
+//   A = sum_y (L h0l + R1),  Q = sum_y (L h0l^2 + 2 h0l R1 + R2)
+// (h0l = h0(y) - h0(first row)), the extremes of h0l + r and the rise of h0l
+// to its last row, and stores them in place of its first row record.  Pass 2b
+// (one block) scans the rises for each block's first-row height H and adds
+// S1 = sum (A + L n H), S2 = sum (Q + 2 H A + L n H^2) over the blocks
+// (n rows each) in 128-bit integers.
+constexpr int kW2BlockRows = 256;
+constexpr int kW2CombineThreads = 1024;
 
-// Pass 2 over nrows row records of rows of length L: heights h0 = sum of the
-// column steps of rows 1..y (row 0 at 0), S1, S2 (128-bit), the extremes of
-// h0 + r, h0 of the last row and the first row's column step.
-__global__ void __launch_bounds__(kFinalThreads)
-    w2_final_kernel(const W2RowSums *rows, uint32_t L, uint32_t nrows, W2Result *out) {
-    __shared__ long long part[kFinalThreads];
-    __shared__ unsigned long long s2lo[kFinalThreads / 32], s2hi[kFinalThreads / 32];
-    __shared__ long long s1w[kFinalThreads / 32], low[kFinalThreads / 32], hiw[kFinalThreads / 32];
+// The record of one pass-2a block, stored over its first row record.
+struct W2BlockSums {
+    long long a;                 // A
+    unsigned long long q_lo;     // Q (>= 0: a sum of squared heights), bits 0..63
+    unsigned int q_hi;           // bits 64..95 (Q < 2^70 for L <= 2^20)
+    int lo, hi;                  // extremes of h0l + r over the block's rows
+    int ec;                      // 2 h0l(last row) + Y(0, first row)
+};
+static_assert(sizeof(W2BlockSums) == sizeof(W2RowSums), "a block record replaces one row record");
+
+// 128-bit unsigned sum of (lo, hi) pairs over a warp, in lane 0.
+__device__ __forceinline__ void warp_sum_u128(unsigned long long &lo, unsigned long long &hi) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long l2 = __shfl_down_sync(kFull, lo, o);
+        const unsigned long long h2 = __shfl_down_sync(kFull, hi, o);
+        const unsigned long long nl = lo + l2;
+        hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+        lo = nl;
+    }
+}
+
+__global__ void __launch_bounds__(kW2BlockRows)
+    w2_block_kernel(W2RowSums *rows, uint32_t L, uint32_t nrows) {
+    __shared__ int wsum[kW2BlockRows / 32];
+    __shared__ long long sa[kW2BlockRows / 32];
+    __shared__ unsigned long long sqlo[kW2BlockRows / 32], sqhi[kW2BlockRows / 32];
+    __shared__ int slo[kW2BlockRows / 32], shi[kW2BlockRows / 32];
+    __shared__ int last_h0l;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t y0 = blockIdx.x * kW2BlockRows, y = y0 + tid;
+    const uint32_t n = min(static_cast<uint32_t>(kW2BlockRows), nrows - y0);
+    const bool valid = static_cast<uint32_t>(tid) < n;
+    W2RowSums r{};
+    if (valid) r = rows[y];
+    // column step into row y from row y - 1 (none into the block's first row)
+    int incl = (valid && tid > 0) ? (r.c ? 1 : -1) : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    const long long h = before + incl;  // h0l(y)
+    if (static_cast<uint32_t>(tid) == n - 1) last_h0l = static_cast<int>(h);
+    const long long Ll = L;
+    long long a = 0;
+    unsigned long long qlo = 0, qhi = 0;
+    int lo = 1 << 30, hi = -(1 << 30);
+    if (valid) {
+        a = Ll * h + r.r1;
+        // sum_x (h0l + r(x))^2 >= 0; |terms| < 2^63 for L <= 2^20
+        const __int128 q = static_cast<__int128>(Ll * h * h) + static_cast<__int128>(2 * h * r.r1) +
+                           static_cast<__int128>(r.r2);
+        qlo = static_cast<unsigned long long>(q);
+        qhi = static_cast<unsigned long long>(q >> 64);
+        lo = static_cast<int>(h) + r.rmin;
+        hi = static_cast<int>(h) + r.rmax;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(kFull, a, o);
+    warp_sum_u128(qlo, qhi);
+    lo = __reduce_min_sync(kFull, lo);
+    hi = __reduce_max_sync(kFull, hi);
+    if (lane == 0) {
+        sa[warp] = a;
+        sqlo[warp] = qlo;
+        sqhi[warp] = qhi;
+        slo[warp] = lo;
+        shi[warp] = hi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        W2BlockSums b;
+        b.a = 0;
+        unsigned __int128 q = 0;
+        b.lo = 1 << 30;
+        b.hi = -(1 << 30);
+        for (int w = 0; w < kW2BlockRows / 32; ++w) {
+            b.a += sa[w];
+            q += (static_cast<unsigned __int128>(sqhi[w]) << 64) | sqlo[w];
+            b.lo = min(b.lo, slo[w]);
+            b.hi = max(b.hi, shi[w]);
+        }
+        b.q_lo = static_cast<unsigned long long>(q);
+        b.q_hi = static_cast<unsigned int>(q >> 64);
+        b.ec = 2 * last_h0l + r.c;  // thread 0 holds the block's first row
+        *reinterpret_cast<W2BlockSums *>(rows + y0) = b;
+    }
+}
+
+__global__ void __launch_bounds__(kW2CombineThreads)
+    w2_combine_kernel(const W2RowSums *rows, uint32_t L, uint32_t nrows, W2Result *out) {
+    __shared__ long long part[kW2CombineThreads];
+    __shared__ unsigned long long s2lo[kW2CombineThreads / 32], s2hi[kW2CombineThreads / 32];
+    __shared__ long long s1w[kW2CombineThreads / 32], low[kW2CombineThreads / 32], hiw[kW2CombineThreads / 32];
     const int tid = threadIdx.x;
-    const uint32_t per = (nrows + kFinalThreads - 1) / kFinalThreads;
-    const uint32_t y_begin = min(nrows, tid * per), y_end = min(nrows, (tid + 1) * per);
-    // column steps 2c-1 for rows 1..y (row 0 contributes nothing)
+    const uint32_t nb = (nrows + kW2BlockRows - 1) / kW2BlockRows;
+    const uint32_t per = (nb + kW2CombineThreads - 1) / kW2CombineThreads;
+    const uint32_t b_begin = min(nb, tid * per), b_end = min(nb, (tid + 1) * per);
+    auto rec = [&](uint32_t b) {
+        return *reinterpret_cast<const W2BlockSums *>(rows + static_cast<size_t>(b) * kW2BlockRows);
+    };
+    // rise of h0 from the last row of block b - 1 to the last row of block b
+    auto rise = [](const W2BlockSums &r, uint32_t b) {
+        return static_cast<long long>(r.ec >> 1) + (b > 0 ? ((r.ec & 1) ? 1 : -1) : 0);
+    };
     long long local = 0;
-    for (uint32_t y = y_begin; y < y_end; ++y)
-        if (y > 0) local += rows[y].c ? 1 : -1;
+    for (uint32_t b = b_begin; b < b_end; ++b) local += rise(rec(b), b);
     part[tid] = local;
     __syncthreads();
-    // exclusive scan of the per-thread column sums (Hillis-Steele on shared memory)
-    for (int o = 1; o < kFinalThreads; o <<= 1) {
+    for (int o = 1; o < kW2CombineThreads; o <<= 1) {
         const long long v = (tid >= o) ? part[tid - o] : 0;
         __syncthreads();
         part[tid] += v;
         __syncthreads();
     }
-    long long h0 = part[tid] - local;
-    if (tid == kFinalThreads - 1) out->e_last = part[tid];  // h0 of the last row
+    long long last = part[tid] - local;  // h0 of the last row before b_begin
     __int128 S1 = 0, S2 = 0;
     long long lo = 1ll << 62, hi = -(1ll << 62);
     const long long Ll = L;
-    for (uint32_t y = y_begin; y < y_end; ++y) {
-        const W2RowSums r = rows[y];
-        if (y > 0) h0 += r.c ? 1 : -1;
-        S1 += static_cast<__int128>(Ll * h0 + r.r1);
-        S2 += static_cast<__int128>(Ll * h0 * h0) + static_cast<__int128>(2 * h0 * r.r1) +
-              static_cast<__int128>(r.r2);
-        lo = min(lo, h0 + r.rmin);
-        hi = max(hi, h0 + r.rmax);
+    for (uint32_t b = b_begin; b < b_end; ++b) {
+        const W2BlockSums r = rec(b);
+        const long long H = last + (b > 0 ? ((r.ec & 1) ? 1 : -1) : 0);  // h0 of the block's first row
+        const long long n = min(static_cast<uint32_t>(kW2BlockRows), nrows - b * kW2BlockRows);
+        const __int128 Q = static_cast<__int128>((static_cast<unsigned __int128>(r.q_hi) << 64) | r.q_lo);
+        S1 += static_cast<__int128>(r.a) + static_cast<__int128>(Ll * n) * H;
+        S2 += Q + static_cast<__int128>(2 * H) * r.a + static_cast<__int128>(Ll * n) * H * H;
+        lo = min(lo, H + r.lo);
+        hi = max(hi, H + r.hi);
+        last = H + (r.ec >> 1);
     }
+    if (b_end == nb && b_begin < b_end) out->e_last = last;  // h0 of the last row
     // block reduction of S1 (fits 64 bits for L <= 2^20), S2 (128 bits), extremes
     long long s1 = static_cast<long long>(S1);
     unsigned long long s2l = static_cast<unsigned long long>(S2);
     unsigned long long s2h = static_cast<unsigned long long>(S2 >> 64);
     for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_down_sync(kFull, s1, o);
-        const unsigned long long lo2 = __shfl_down_sync(kFull, s2l, o);
-        const unsigned long long hi2 = __shfl_down_sync(kFull, s2h, o);
-        const unsigned long long nlo = s2l + lo2;
-        s2h = s2h + hi2 + (nlo < s2l ? 1ull : 0ull);
-        s2l = nlo;
         lo = min(lo, __shfl_down_sync(kFull, lo, o));
         hi = max(hi, __shfl_down_sync(kFull, hi, o));
     }
+    warp_sum_u128(s2l, s2h);
     if ((tid & 31) == 0) {
         s1w[tid >> 5] = s1;
         s2lo[tid >> 5] = s2l;
@@ -241,7 +429,7 @@ __global__ void __launch_bounds__(kFinalThreads)
     if (tid == 0) {
         long long a1 = 0, amn = 1ll << 62, amx = -(1ll << 62);
         unsigned __int128 a2 = 0;
-        for (int w = 0; w < kFinalThreads / 32; ++w) {
+        for (int w = 0; w < kW2CombineThreads / 32; ++w) {
             a1 += s1w[w];
             a2 += (static_cast<unsigned __int128>(s2hi[w]) << 64) | s2lo[w];
             amn = min(amn, low[w]);
@@ -253,7 +441,7 @@ __global__ void __launch_bounds__(kFinalThreads)
         out->lo = amn;
         out->hi = amx;
         out->hmax = max(amn < 0 ? -amn : amn, amx < 0 ? -amx : amx);
-        out->f0 = rows[0].c ? 1 : -1;
+        out->f0 = (rec(0).ec & 1) ? 1 : -1;
     }
 }
 
@@ -309,23 +497,29 @@ __global__ void unpack_canonical_kernel(const uint32_t *in, uint32_t L, uint32_t
     }
 }
 
-__global__ void net_sum_kernel(const unsigned long long *net, const unsigned long long *draws,
-                               const unsigned long long *tails, long long *out) {
-    long long s = 0, d = 0, b = 0;
-    for (int i = threadIdx.x; i < kNetSlots; i += 32) {
-        s += static_cast<long long>(net[i]);
-        d += static_cast<long long>(draws[i]);
-        b += static_cast<long long>(tails[i]);
-    }
+// One thread per counter slot (kNetSlots threads), then a block reduction.
+__global__ void __launch_bounds__(kNetSlots)
+    net_sum_kernel(const unsigned long long *net, const unsigned long long *draws, const unsigned long long *tails,
+                   long long *out) {
+    __shared__ long long part[3][kNetSlots / 32];
+    const int i = threadIdx.x;
+    long long s = static_cast<long long>(net[i]), d = static_cast<long long>(draws[i]),
+              b = static_cast<long long>(tails[i]);
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_down_sync(kFull, s, o);
         d += __shfl_down_sync(kFull, d, o);
         b += __shfl_down_sync(kFull, b, o);
     }
-    if (threadIdx.x == 0) {
-        out[0] = s;
-        out[1] = d;
-        out[2] = b;
+    if ((i & 31) == 0) {
+        part[0][i >> 5] = s;
+        part[1][i >> 5] = d;
+        part[2][i >> 5] = b;
+    }
+    __syncthreads();
+    if (i < 3) {
+        long long t = 0;
+        for (int w = 0; w < kNetSlots / 32; ++w) t += part[i][w];
+        out[i] = t;
     }
 }
 
@@ -354,21 +548,34 @@ cudaError_t launch_w2(const uint32_t *lat, uint32_t L, W2RowSums *rows, W2Result
 
 cudaError_t launch_w2_rows(const uint32_t *lat, uint32_t L, uint32_t nrows, uint32_t plane_rows, W2RowSums *rows,
                            W2Result *out, cudaStream_t st) {
-    // one wave of resident blocks (32 KB of table each), rows taken grid-stride
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 152;
+    // one wave of resident blocks (64 KB of table each), rows taken grid-stride;
+    // the table needs the dynamic shared-memory limit raised once per device
+    constexpr int kMaxDevices = 64;
+    static int sms[kMaxDevices] = {};
+    static bool smem_set[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (sms[dev] <= 0) {
+        e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    if (!smem_set[dev]) {
+        e = cudaFuncSetAttribute(w2_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kW2TableBytes);
+        if (e != cudaSuccess) return e;
+        smem_set[dev] = true;
     }
     const uint64_t want = (static_cast<uint64_t>(nrows) + kW2Warps - 1) / kW2Warps;
-    const uint64_t wave = static_cast<uint64_t>(sms) * 6u;
+    const uint64_t wave = static_cast<uint64_t>(sms[dev]) * kW2BlocksPerSM;
     const int blocks = static_cast<int>(want < wave ? want : wave);
-    w2_rows_kernel<<<blocks, kW2Warps * 32, 0, st>>>(lat, L, nrows, plane_rows, rows);
-    cudaError_t e = cudaGetLastError();
+    w2_rows_kernel<<<blocks, kW2Warps * 32, kW2TableBytes, st>>>(lat, L, nrows, plane_rows, rows);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    w2_final_kernel<<<1, kFinalThreads, 0, st>>>(rows, L, nrows, out);
+    w2_block_kernel<<<(nrows + kW2BlockRows - 1) / kW2BlockRows, kW2BlockRows, 0, st>>>(rows, L, nrows);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    w2_combine_kernel<<<1, kW2CombineThreads, 0, st>>>(rows, L, nrows, out);
     return cudaGetLastError();
 }
 
@@ -388,7 +595,7 @@ cudaError_t launch_unpack_canonical(const uint32_t *in, uint32_t L, uint32_t cy0
 
 cudaError_t launch_net_sum(const unsigned long long *net, const unsigned long long *draws,
                            const unsigned long long *tails, long long *out, cudaStream_t st) {
-    net_sum_kernel<<<1, 32, 0, st>>>(net, draws, tails, out);
+    net_sum_kernel<<<1, kNetSlots, 0, st>>>(net, draws, tails, out);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,7 @@
 // roughness value: a host framework or plugin that owns all device memory and
 // hands this library only a buffer and a stream, or a latency-critical loop in
 // which cudaMalloc/cudaFree are not allowed because they can synchronise the
-// device and stall other work.  For them this entry point runs the same two
+// device and stall other work.  For them this entry point runs the same
 // roughness kernels as oct_measure_w2, but keeps their scratch (per-row partial
 // sums and the 32-byte result block) in a fixed array compiled into the
 // library instead of in handle-owned allocations.
@@ -77,8 +77,8 @@ extern "C" int oct_w2_noalloc(const void *lattice, int64_t L, void *stream, oct_
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto *rows = static_cast<oct::W2RowSums *>(scratch);
     auto *res = reinterpret_cast<oct::W2Result *>(static_cast<unsigned char *>(scratch) + kRowBytes);
-    // Both kernels overwrite every row record and the whole result block they
-    // read, so nothing left over from an earlier call needs clearing.
+    // The kernels overwrite every row record and the whole result block before
+    // they read them, so nothing left over from an earlier call needs clearing.
     e = oct::launch_w2(static_cast<const uint32_t *>(lattice), static_cast<uint32_t>(L), rows, res, st);
     oct::W2Result h;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, res, sizeof(h), cudaMemcpyDeviceToHost, st);

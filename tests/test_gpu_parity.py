@@ -265,12 +265,15 @@ def test_every_tunable_shape_bit_exact(g, oracle, shape):
             _assert_same(oracle, sim, X, Y, net, f"{Bx}x{By} p={p}")
 
 
-@pytest.mark.parametrize("L,Bx,By", [(192, 32, 32), (4160, 32, 32), (4224, 64, 64)])
+@pytest.mark.parametrize("L,Bx,By", [(192, 32, 32), (4160, 32, 32), (4224, 64, 64),
+                                      (16448, 32, 32), (16512, 64, 64)])
 def test_roughness_on_ragged_rows(g, oracle, L, Bx, By):
-    """The W^2 row pass on rows of 6 words (scalar loads), 130 words (a ragged
-    second chunk of 2 words) and 132 words (16-byte loads, ragged second chunk):
-    S1, S2 and hmax of the GPU lattice equal the oracle's O3 on the same
-    lattice, after a few MCS of rough dynamics (EW, then KPZ-like)."""
+    """The W^2 row pass (chunks of 512 words, 16 per lane) on rows of 6 words
+    (scalar loads), 130 and 132 words (one partial chunk, scalar and 16-byte
+    loads), 514 words (a full chunk, then 2 words on scalar loads) and 516
+    words (a full chunk, then 4 words on 16-byte loads): S1, S2 and hmax of the
+    GPU lattice equal the oracle's O3 on the same lattice, after a few MCS of
+    rough dynamics (EW, then KPZ-like)."""
     for p, q, n in ((0.5, 0.5, 3), (0.95, 0.05, 5)):
         with g.Simulation(L, p, q, 77, Bx=Bx, By=By) as sim:
             sim.run(n)

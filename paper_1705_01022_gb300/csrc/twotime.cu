@@ -19,8 +19,9 @@
 // running steps and its net step; for a pair of nibbles, the sum of the
 // products of their running steps.  The lane's local sums are lifted to the
 // row's with one 64-bit multiply-add per lattice.
-// Pass 2 (one block): a scan of the column-0 Y bits gives h(0,y) of both
-// lattices, and S_t, S_s and C accumulate in 64/128-bit integers:
+// Pass 2: a scan of the column-0 Y bits gives h(0,y) of both lattices, and
+// S_t, S_s and C accumulate in 64/128-bit integers, per block of rows and then
+// over the blocks:
 //   C = sum_y [L h0_t h0_s + h0_t R_s + h0_s R_t + R_ts].
 // Row terms are at most L^3 in magnitude (2^60 at the largest L, 2^20).
 #include "oct_internal.h"
@@ -174,27 +175,140 @@ __global__ void __launch_bounds__(kAcWarps * 32)
     }
 }
 
-constexpr int kAcFinalThreads = 1024;
+// Pass 2 in two kernels, as for the roughness: pass 2a, one block per
+// kAcBlockRows rows, sums relative to the heights of its first row
+// (h0l = h0 - h0(first row), both lattices)
+//   At = sum (L h0l_t + R_t),  As = sum (L h0l_s + R_s),
+//   Cb = sum (L h0l_t h0l_s + h0l_t R_s + h0l_s R_t + R_ts),
+// the occupation counts and the rises of h0l; it stores them over its first
+// two row records (a block has at least 32 rows: L is a multiple of 32).
+// Pass 2b scans the rises for the block heights H_t, H_s and adds
+//   C = sum (Cb + H_t As + H_s At + L n H_t H_s),  S = sum (A + L n H).
+constexpr int kAcBlockRows = 256;
+constexpr int kAcCombineThreads = 1024;
 
-__global__ void __launch_bounds__(kAcFinalThreads)
-    ac_final_kernel(const AcRowSums *rows, uint32_t L, AcResult *out) {
-    __shared__ long long part_t[kAcFinalThreads], part_s[kAcFinalThreads];
-    __shared__ long long red[8][kAcFinalThreads / 32];
-    __shared__ unsigned long long clo[kAcFinalThreads / 32], chi[kAcFinalThreads / 32];
-    const int tid = threadIdx.x;
-    const uint32_t per = (L + kAcFinalThreads - 1) / kAcFinalThreads;
-    const uint32_t y_begin = min(L, tid * per), y_end = min(L, (tid + 1) * per);
-    // column steps 2c-1 of rows 1..y (row 0 contributes nothing), both lattices
-    long long lt = 0, ls = 0;
-    for (uint32_t y = y_begin; y < y_end; ++y)
-        if (y > 0) {
-            lt += rows[y].ct ? 1 : -1;
-            ls += rows[y].cs ? 1 : -1;
+struct AcBlockSums {
+    long long at, as;
+    unsigned long long c_lo;
+    long long c_hi;      // Cb as a two's-complement 128-bit value
+    long long nx, ny, mt, ms;
+    int et, es;          // 2 h0l(last row) + Y(0, first row), per lattice
+};
+static_assert(sizeof(AcBlockSums) <= 2 * sizeof(AcRowSums), "a block record replaces two row records");
+
+// 128-bit two's-complement sum of (lo, hi) pairs over a warp, in lane 0.
+__device__ __forceinline__ void warp_sum_128(unsigned long long &lo, unsigned long long &hi) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long l2 = __shfl_down_sync(kFull, lo, o);
+        const unsigned long long h2 = __shfl_down_sync(kFull, hi, o);
+        const unsigned long long nl = lo + l2;
+        hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+        lo = nl;
+    }
+}
+
+__global__ void __launch_bounds__(kAcBlockRows) ac_block_kernel(AcRowSums *rows, uint32_t L) {
+    __shared__ int wsum[kAcBlockRows / 32];
+    __shared__ long long red[6][kAcBlockRows / 32];
+    __shared__ unsigned long long clo[kAcBlockRows / 32], chi[kAcBlockRows / 32];
+    __shared__ int last_t, last_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t y0 = blockIdx.x * kAcBlockRows;
+    const uint32_t n = min(static_cast<uint32_t>(kAcBlockRows), L - y0);
+    const bool valid = static_cast<uint32_t>(tid) < n;
+    AcRowSums r{};
+    if (valid) r = rows[y0 + tid];
+    // column steps into row y of both lattices (none into the block's first
+    // row), scanned together: |prefix| <= 256 fits the low 16 bits
+    const int st = (valid && tid > 0) ? (r.ct ? 1 : -1) : 0, ss = (valid && tid > 0) ? (r.cs ? 1 : -1) : 0;
+    int incl = st + ss * 65536;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    for (int w = 0; w < warp; ++w) incl += wsum[w];
+    const long long ht = static_cast<short>(incl & 0xFFFF);
+    const long long hs = (incl - static_cast<int>(ht)) / 65536;
+    if (static_cast<uint32_t>(tid) == n - 1) {
+        last_t = static_cast<int>(ht);
+        last_s = static_cast<int>(hs);
+    }
+    const long long Ll = L;
+    long long v[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long lo = 0, hi = 0;
+    if (valid) {
+        v[0] = Ll * ht + r.rt;
+        v[1] = Ll * hs + r.rs;
+        v[2] = r.nx;
+        v[3] = r.ny;
+        v[4] = r.mt;
+        v[5] = r.ms;
+        const __int128 c = static_cast<__int128>(Ll * ht * hs) + static_cast<__int128>(ht * r.rs) +
+                           static_cast<__int128>(hs * r.rt) + static_cast<__int128>(r.rts);
+        lo = static_cast<unsigned long long>(c);
+        hi = static_cast<unsigned long long>(static_cast<unsigned __int128>(c) >> 64);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) v[i] += __shfl_down_sync(kFull, v[i], o);
+    warp_sum_128(lo, hi);
+    if (lane == 0) {
+        for (int i = 0; i < 6; ++i) red[i][warp] = v[i];
+        clo[warp] = lo;
+        chi[warp] = hi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        AcBlockSums b{};
+        long long a[6] = {0, 0, 0, 0, 0, 0};
+        unsigned __int128 c = 0;
+        for (int w = 0; w < kAcBlockRows / 32; ++w) {
+            for (int i = 0; i < 6; ++i) a[i] += red[i][w];
+            c += (static_cast<unsigned __int128>(chi[w]) << 64) | clo[w];
         }
+        b.at = a[0];
+        b.as = a[1];
+        b.nx = a[2];
+        b.ny = a[3];
+        b.mt = a[4];
+        b.ms = a[5];
+        b.c_lo = static_cast<unsigned long long>(c);
+        b.c_hi = static_cast<long long>(static_cast<unsigned long long>(c >> 64));
+        b.et = 2 * last_t + r.ct;  // thread 0 holds the block's first row
+        b.es = 2 * last_s + r.cs;
+        *reinterpret_cast<AcBlockSums *>(rows + y0) = b;
+    }
+}
+
+__global__ void __launch_bounds__(kAcCombineThreads)
+    ac_combine_kernel(const AcRowSums *rows, uint32_t L, AcResult *out) {
+    __shared__ long long part_t[kAcCombineThreads], part_s[kAcCombineThreads];
+    __shared__ long long red[6][kAcCombineThreads / 32];
+    __shared__ unsigned long long clo[kAcCombineThreads / 32], chi[kAcCombineThreads / 32];
+    const int tid = threadIdx.x;
+    const uint32_t nb = (L + kAcBlockRows - 1) / kAcBlockRows;
+    const uint32_t per = (nb + kAcCombineThreads - 1) / kAcCombineThreads;
+    const uint32_t b_begin = min(nb, tid * per), b_end = min(nb, (tid + 1) * per);
+    auto rec = [&](uint32_t b) {
+        return *reinterpret_cast<const AcBlockSums *>(rows + static_cast<size_t>(b) * kAcBlockRows);
+    };
+    // step into a block's first row (none into row 0) and rise to its last row
+    auto step_in = [](int e, uint32_t b) { return b > 0 ? ((e & 1) ? 1ll : -1ll) : 0ll; };
+    long long lt = 0, ls = 0;
+    for (uint32_t b = b_begin; b < b_end; ++b) {
+        const AcBlockSums r = rec(b);
+        lt += step_in(r.et, b) + (r.et >> 1);
+        ls += step_in(r.es, b) + (r.es >> 1);
+    }
     part_t[tid] = lt;
     part_s[tid] = ls;
     __syncthreads();
-    for (int o = 1; o < kAcFinalThreads; o <<= 1) {
+    for (int o = 1; o < kAcCombineThreads; o <<= 1) {
         const long long vt = (tid >= o) ? part_t[tid - o] : 0;
         const long long vs = (tid >= o) ? part_s[tid - o] : 0;
         __syncthreads();
@@ -202,38 +316,33 @@ __global__ void __launch_bounds__(kAcFinalThreads)
         part_s[tid] += vs;
         __syncthreads();
     }
-    long long h0t = part_t[tid] - lt, h0s = part_s[tid] - ls;
+    long long last_t = part_t[tid] - lt, last_s = part_s[tid] - ls;  // h0 of the last row before b_begin
     const long long Ll = L;
-    long long St = 0, Ss = 0, nx = 0, ny = 0, mt = 0, ms = 0;
+    long long v[6] = {0, 0, 0, 0, 0, 0};
     __int128 C = 0;
-    for (uint32_t y = y_begin; y < y_end; ++y) {
-        const AcRowSums r = rows[y];
-        if (y > 0) {
-            h0t += r.ct ? 1 : -1;
-            h0s += r.cs ? 1 : -1;
-        }
-        St += Ll * h0t + r.rt;
-        Ss += Ll * h0s + r.rs;
-        C += static_cast<__int128>(Ll * h0t * h0s) + static_cast<__int128>(h0t * r.rs) +
-             static_cast<__int128>(h0s * r.rt) + static_cast<__int128>(r.rts);
-        nx += r.nx;
-        ny += r.ny;
-        mt += r.mt;
-        ms += r.ms;
+    for (uint32_t b = b_begin; b < b_end; ++b) {
+        const AcBlockSums r = rec(b);
+        const long long Ht = last_t + step_in(r.et, b), Hs = last_s + step_in(r.es, b);
+        const long long nr = min(static_cast<uint32_t>(kAcBlockRows), L - b * kAcBlockRows);
+        const __int128 Cb = static_cast<__int128>((static_cast<unsigned __int128>(r.c_hi) << 64) | r.c_lo);
+        C += Cb + static_cast<__int128>(Ht) * r.as + static_cast<__int128>(Hs) * r.at +
+             static_cast<__int128>(Ll * nr) * Ht * Hs;
+        v[0] += r.at + Ll * nr * Ht;
+        v[1] += r.as + Ll * nr * Hs;
+        v[2] += r.nx;
+        v[3] += r.ny;
+        v[4] += r.mt;
+        v[5] += r.ms;
+        last_t = Ht + (r.et >> 1);
+        last_s = Hs + (r.es >> 1);
     }
     // block reduction; C as a two's-complement 128-bit value in (lo, hi)
-    long long v[6] = {St, Ss, nx, ny, mt, ms};
     unsigned long long lo = static_cast<unsigned long long>(C);
     unsigned long long hi = static_cast<unsigned long long>(static_cast<unsigned __int128>(C) >> 64);
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
         for (int i = 0; i < 6; ++i) v[i] += __shfl_down_sync(kFull, v[i], o);
-        const unsigned long long lo2 = __shfl_down_sync(kFull, lo, o);
-        const unsigned long long hi2 = __shfl_down_sync(kFull, hi, o);
-        const unsigned long long nlo = lo + lo2;
-        hi = hi + hi2 + (nlo < lo ? 1ull : 0ull);
-        lo = nlo;
-    }
+    warp_sum_128(lo, hi);
     if ((tid & 31) == 0) {
         for (int i = 0; i < 6; ++i) red[i][tid >> 5] = v[i];
         clo[tid >> 5] = lo;
@@ -243,7 +352,7 @@ __global__ void __launch_bounds__(kAcFinalThreads)
     if (tid == 0) {
         long long a[6] = {0, 0, 0, 0, 0, 0};
         unsigned __int128 c = 0;
-        for (int w = 0; w < kAcFinalThreads / 32; ++w) {
+        for (int w = 0; w < kAcCombineThreads / 32; ++w) {
             for (int i = 0; i < 6; ++i) a[i] += red[i][w];
             c += (static_cast<unsigned __int128>(chi[w]) << 64) | clo[w];
         }
@@ -267,7 +376,10 @@ cudaError_t launch_two_time(const uint32_t *lat_t, const uint32_t *lat_s, uint32
     ac_rows_kernel<<<blocks, kAcWarps * 32, 0, st>>>(lat_t, lat_s, L, rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    ac_final_kernel<<<1, kAcFinalThreads, 0, st>>>(rows, L, out);
+    ac_block_kernel<<<(L + kAcBlockRows - 1) / kAcBlockRows, kAcBlockRows, 0, st>>>(rows, L);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ac_combine_kernel<<<1, kAcCombineThreads, 0, st>>>(rows, L, out);
     return cudaGetLastError();
 }
 

@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--serve-jobs", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-policy", default="large", help="autotune.batch_shape policy of the serving leg")
+    ap.add_argument("--serve-inflight", type=int, default=4,
+                    help="ticks the serving loop keeps enqueued ahead of the device per batch (0: no limit)")
+    ap.add_argument("--serve-batches", type=int, default=2,
+                    help="batches (streams) the serving loop spreads its jobs over")
     ap.add_argument("--db-steps", type=int, default=30)
     ap.add_argument("--cell-steps", type=int, default=2, help="timed MCS per coarse thread-cell shape")
     ap.add_argument("--ac-reps", type=int, default=5)
@@ -424,7 +428,7 @@ def serving_leg(a, g, _lib, torch, stream, capacity):
     out = {"workload": ("Poisson job stream: L log-uniform in [128, 16384] (multiples of 128), t_max "
                         "log-uniform in [10, 10^4] MCS, (p,q) uniform over (1,0), (0.8,0.2), (0.5,0.5), "
                         "W^2 streamed at 8 log-spaced times per job, HBM budget 64 GiB"),
-           "shape_policy": a.serve_policy,
+           "shape_policy": a.serve_policy, "max_inflight_ticks": a.serve_inflight, "batches": a.serve_batches,
            "capacity_attempts_per_ns": capacity, "expected_attempts_per_job": work, "loads": []}
     # One job list (Poisson gaps of mean 1, keys from master seed 1).  The offered
     # load rho is the work the list actually holds per second of its arrival
@@ -441,7 +445,8 @@ def serving_leg(a, g, _lib, torch, stream, capacity):
         scale = realized / (rho * capacity * 1e9) / span
         jobs = [serve.Job(j.jid, j.L, j.p, j.q, j.seed, j.t_max, arrival=j.arrival * scale,
                           measure_at=list(j.measure_at)) for j in base]
-        eng = serve.ServingEngine(64 << 30, stream=stream, max_chunk=64, shape_policy=a.serve_policy)
+        eng = serve.ServingEngine(64 << 30, stream=stream, max_chunk=64, shape_policy=a.serve_policy,
+                                  max_inflight=a.serve_inflight, n_batches=a.serve_batches)
         t0 = time.perf_counter()
         done = eng.run(jobs)
         torch.cuda.synchronize()
@@ -450,7 +455,7 @@ def serving_leg(a, g, _lib, torch, stream, capacity):
         res.update({"offered_load": rho, "rate_jobs_per_s": (len(base) - 1) / (span * scale), "ticks": eng.ticks,
                     "arrival_span_s": span * scale, "fraction_of_capacity": res["attempts_per_ns"] / capacity})
         out["loads"].append(res)
-        eng.batch.close()
+        eng.close()
     return out
 
 

@@ -435,6 +435,21 @@ int oct_batch_get_stats(oct_batch *b, int64_t *ticks, int64_t *n_active, int64_t
 /* Waits for the batch's stream. */
 int oct_batch_sync(oct_batch *b);
 
+/* Stream marks, so that a caller can bound how much work it keeps enqueued
+ * ahead of the device (a serving loop that lets newly admitted replicas join
+ * the next launches instead of queueing behind work already enqueued).
+ * oct_batch_mark records the point the batch's stream has reached (after all
+ * work enqueued so far) and returns its number in *mark; oct_batch_mark_done
+ * sets *done = 1 once the device has passed it, else 0; oct_batch_mark_wait
+ * blocks until it has.  The last 64 marks are kept: recording a new mark first
+ * waits for the one 64 marks older, so an older mark always reads as passed.
+ * Marks are this library's scheduling aid; the paper has no counterpart.
+ * Errors: OCT_EINVAL for a NULL argument or a mark not handed out,
+ * OCT_ECUDA. */
+int oct_batch_mark(oct_batch *b, int64_t *mark);
+int oct_batch_mark_done(oct_batch *b, int64_t mark, int *done);
+int oct_batch_mark_wait(oct_batch *b, int64_t mark);
+
 /* With timing on, oct_batch_run launches device step by device step (no
  * graph) and brackets each with CUDA events; step_ms sums them. */
 int oct_batch_set_timing(oct_batch *b, int enable);

@@ -140,6 +140,9 @@ _SIGNATURES = [
                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
      ctypes.c_int),
     ("oct_batch_sync", [_H], ctypes.c_int),
+    ("oct_batch_mark", [_H, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    ("oct_batch_mark_done", [_H, ctypes.c_int64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    ("oct_batch_mark_wait", [_H, ctypes.c_int64], ctypes.c_int),
     ("oct_batch_set_timing", [_H, ctypes.c_int], ctypes.c_int),
     ("oct_batch_get_timing", [_H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
      ctypes.c_int),
@@ -410,6 +413,23 @@ def oct_batch_get_stats(h: int):
 
 def oct_batch_sync(h: int) -> None:
     _check(load().oct_batch_sync(h), "oct_batch_sync")
+
+
+def oct_batch_mark(h: int) -> int:
+    """Number of a mark at the point the batch's stream has reached."""
+    m = ctypes.c_int64()
+    _check(load().oct_batch_mark(h, ctypes.byref(m)), "oct_batch_mark")
+    return m.value
+
+
+def oct_batch_mark_done(h: int, mark: int) -> bool:
+    done = ctypes.c_int()
+    _check(load().oct_batch_mark_done(h, mark, ctypes.byref(done)), "oct_batch_mark_done")
+    return bool(done.value)
+
+
+def oct_batch_mark_wait(h: int, mark: int) -> None:
+    _check(load().oct_batch_mark_wait(h, mark), "oct_batch_mark_wait")
 
 
 def oct_batch_set_timing(h: int, enable: bool) -> None:

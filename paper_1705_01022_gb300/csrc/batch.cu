@@ -182,6 +182,7 @@ struct MeasureRecord {
     uint32_t pad[3];
 };
 constexpr int kMeasureRing = 1024;
+constexpr int kMarkRing = 64;
 
 }  // namespace
 }  // namespace oct
@@ -223,12 +224,19 @@ struct oct_batch {
     int grid = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // side streams and events of the captured MCS: one branch per kind
+    cudaStream_t side[kKinds] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kKinds] = {};
     // asynchronous measurements: a ring of records (device and pinned host)
     oct::MeasureRecord *d_req = nullptr;
     oct::MeasureRecord *h_req = nullptr;
     std::vector<cudaEvent_t> req_ev;
     std::vector<int64_t> req_L;
     int64_t req_next = 0;  // tickets handed out so far
+    // stream marks (oct_batch_mark): a ring of events
+    std::vector<cudaEvent_t> mark_ev;
+    int64_t mark_next = 0;  // marks handed out so far
     bool timing = false;
     std::vector<cudaEvent_t> ev;
     int ev_used = 0;
@@ -268,7 +276,14 @@ void batch_free(oct_batch *b) {
     if (b->h_req) cudaFreeHost(b->h_req);
     for (cudaEvent_t e : b->req_ev)
         if (e) cudaEventDestroy(e);  // ring events are created on first use
+    for (cudaEvent_t e : b->mark_ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(b->d_queue);
+    for (int kind = 0; kind < kKinds; ++kind) {
+        if (b->side[kind]) cudaStreamDestroy(b->side[kind]);
+        if (b->join_ev[kind]) cudaEventDestroy(b->join_ev[kind]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     cudaFree(b->d_rows);
     cudaFree(b->d_w2);
     if (b->h_small) cudaFreeHost(b->h_small);
@@ -457,32 +472,37 @@ cudaError_t rebuild(oct_batch *b) {
     return cudaSuccess;
 }
 
-// Enqueues device step k of the current MCS of every active replica.
+// Enqueues device step k of the current MCS of the replicas of one kind.
+cudaError_t enqueue_kind_step(oct_batch *b, uint32_t k, int kind, cudaStream_t st) {
+    uint32_t *q = b->d_queue + kKinds * k + kind;
+    cudaError_t e = cudaMemsetAsync(q, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const oct::WorkBuf &w = b->wb[b->cur];
+    const oct::WarpDesc *descs = w.descs + b->desc_first[kind];
+    const uint32_t nd = b->n_desc[kind];
+    const int blocks = std::min<int>(b->grid, static_cast<int>((nd + oct::kBatchWarps - 1) / oct::kBatchWarps));
+    const dim3 grid(blocks), block(oct::kBatchWarps * 32);
+#define OCT_BATCH(R, LS, SC) \
+    oct::batch_step_kernel<R, LS, SC><<<grid, block, 0, st>>>(w.reps, w.items, descs, nd, b->d_t, k, q)
+    switch (kind) {
+        case 0: OCT_BATCH(false, true, 0); break;
+        case 1: OCT_BATCH(false, false, 0); break;
+        case 2: OCT_BATCH(true, true, 0); break;
+        case 3: OCT_BATCH(true, false, 0); break;
+        case 4: OCT_BATCH(true, true, 5); break;
+        case 5: OCT_BATCH(true, false, 5); break;
+        case 6: OCT_BATCH(false, true, 4); break;
+        default: OCT_BATCH(false, false, 4); break;
+    }
+#undef OCT_BATCH
+    return cudaGetLastError();
+}
+
+// Enqueues device step k of the current MCS of every active replica, kind by kind.
 cudaError_t enqueue_step(oct_batch *b, uint32_t k, cudaStream_t st) {
     for (int kind = 0; kind < kKinds; ++kind) {
         if (b->n_desc[kind] == 0) continue;
-        uint32_t *q = b->d_queue + kKinds * k + kind;
-        cudaError_t e = cudaMemsetAsync(q, 0, sizeof(uint32_t), st);
-        if (e != cudaSuccess) return e;
-        const oct::WorkBuf &w = b->wb[b->cur];
-        const oct::WarpDesc *descs = w.descs + b->desc_first[kind];
-        const uint32_t nd = b->n_desc[kind];
-        const int blocks = std::min<int>(b->grid, static_cast<int>((nd + oct::kBatchWarps - 1) / oct::kBatchWarps));
-        const dim3 grid(blocks), block(oct::kBatchWarps * 32);
-#define OCT_BATCH(R, LS, SC) \
-    oct::batch_step_kernel<R, LS, SC><<<grid, block, 0, st>>>(w.reps, w.items, descs, nd, b->d_t, k, q)
-        switch (kind) {
-            case 0: OCT_BATCH(false, true, 0); break;
-            case 1: OCT_BATCH(false, false, 0); break;
-            case 2: OCT_BATCH(true, true, 0); break;
-            case 3: OCT_BATCH(true, false, 0); break;
-            case 4: OCT_BATCH(true, true, 5); break;
-            case 5: OCT_BATCH(true, false, 5); break;
-            case 6: OCT_BATCH(false, true, 4); break;
-            default: OCT_BATCH(false, false, 4); break;
-        }
-#undef OCT_BATCH
-        e = cudaGetLastError();
+        cudaError_t e = enqueue_kind_step(b, k, kind, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -495,11 +515,26 @@ cudaError_t enqueue_advance(oct_batch *b, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// One MCS for capture on st: the replicas of different kinds share no memory
+// and no counter, so each kind's four device steps are a branch of their own
+// (forked from st on a side stream and joined back before the MCS counters
+// advance); the branches run concurrently, so one kind's launches fill the
+// device while another's drain.
 cudaError_t enqueue_mcs(oct_batch *b, cudaStream_t st) {
-    for (uint32_t k = 0; k < 4; ++k) {
-        cudaError_t e = enqueue_step(b, k, st);
-        if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!b->fork_ev) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork_ev, st);
+    for (int kind = 0; kind < kKinds && e == cudaSuccess; ++kind) {
+        if (b->n_desc[kind] == 0) continue;
+        if (!b->side[kind]) e = cudaStreamCreateWithFlags(&b->side[kind], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !b->join_ev[kind])
+            e = cudaEventCreateWithFlags(&b->join_ev[kind], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side[kind], b->fork_ev, 0);
+        for (uint32_t k = 0; k < 4 && e == cudaSuccess; ++k) e = enqueue_kind_step(b, k, kind, b->side[kind]);
+        if (e == cudaSuccess) e = cudaEventRecord(b->join_ev[kind], b->side[kind]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join_ev[kind], 0);
     }
+    if (e != cudaSuccess) return e;
     return enqueue_advance(b, st);
 }
 
@@ -926,6 +961,50 @@ int oct_batch_sync(oct_batch *b) {
     if (!b) return bfail(OCT_EINVAL, "NULL batch");
     BATCH_CUDA(cudaSetDevice(b->device));
     BATCH_CUDA(cudaStreamSynchronize(b->stream));
+    return OCT_OK;
+}
+
+int oct_batch_mark(oct_batch *b, int64_t *mark) {
+    if (!b || !mark) return bfail(OCT_EINVAL, "NULL argument");
+    BATCH_CUDA(cudaSetDevice(b->device));
+    if (b->mark_ev.empty()) b->mark_ev.assign(oct::kMarkRing, nullptr);
+    const int i = static_cast<int>(b->mark_next % oct::kMarkRing);
+    if (b->mark_ev[i]) {
+        // the ring wrapped: the mark recorded here kMarkRing marks ago is passed first
+        BATCH_CUDA(cudaEventSynchronize(b->mark_ev[i]));
+    } else {
+        BATCH_CUDA(cudaEventCreateWithFlags(&b->mark_ev[i], cudaEventDisableTiming));
+    }
+    BATCH_CUDA(cudaEventRecord(b->mark_ev[i], b->stream));
+    *mark = b->mark_next++;
+    return OCT_OK;
+}
+
+int oct_batch_mark_done(oct_batch *b, int64_t mark, int *done) {
+    if (!b || !done) return bfail(OCT_EINVAL, "NULL argument");
+    if (mark < 0 || mark >= b->mark_next) return bfail(OCT_EINVAL, "unknown stream mark");
+    if (mark < b->mark_next - oct::kMarkRing) {  // its event was reused after the device passed it
+        *done = 1;
+        return OCT_OK;
+    }
+    BATCH_CUDA(cudaSetDevice(b->device));
+    const cudaError_t e = cudaEventQuery(b->mark_ev[mark % oct::kMarkRing]);
+    if (e == cudaErrorNotReady) {
+        (void)cudaGetLastError();
+        *done = 0;
+        return OCT_OK;
+    }
+    if (e != cudaSuccess) return bfail(OCT_ECUDA, std::string("oct_batch_mark_done: ") + cudaGetErrorString(e));
+    *done = 1;
+    return OCT_OK;
+}
+
+int oct_batch_mark_wait(oct_batch *b, int64_t mark) {
+    if (!b) return bfail(OCT_EINVAL, "NULL batch");
+    if (mark < 0 || mark >= b->mark_next) return bfail(OCT_EINVAL, "unknown stream mark");
+    if (mark < b->mark_next - oct::kMarkRing) return OCT_OK;
+    BATCH_CUDA(cudaSetDevice(b->device));
+    BATCH_CUDA(cudaEventSynchronize(b->mark_ev[mark % oct::kMarkRing]));
     return OCT_OK;
 }
 

@@ -2,16 +2,18 @@
 
 A job is one realization (L, p, q, seed) to run for t_max MCS, with W^2 sent
 back at log-spaced times.  Jobs arrive over time (e.g. as a Poisson stream).
-The engine keeps one batch (``oct_batch_*`` in include/oct.h) whose replicas
-are the running jobs, each on the sub-tile its shape policy gives (see
-autotune.batch_shape; the shape is recorded in the job, since it is part of
-the job's dynamics):
+The engine keeps one or more batches (``oct_batch_*`` in include/oct.h), each
+on its own stream, whose replicas are the running jobs, each on the sub-tile
+its shape policy gives (see autotune.batch_shape; the shape is recorded in the
+job, since it is part of the job's dynamics):
 
 * admission: a waiting job that has arrived joins the batch as soon as its
   lattice fits the HBM budget (first come, first served);
-* every tick advances all running jobs together by the same number of MCS
-  (up to the next measurement or finish among them, at most ``max_chunk``),
-  so work of jobs that arrived at different times overlaps on the device;
+* a tick of a batch advances all its running jobs together by the same
+  number of MCS (up to the next measurement or finish among them, at most
+  ``max_chunk``), so work of jobs that arrived at different times overlaps on
+  the device; batches tick independently (a new job joins the batch with the
+  fewest running sites), so their launches overlap too;
 * at a job's measurement times its exact W^2 is computed on the device and
   handed to the ``on_result`` callback (streamed back).  With a batch that
   measures asynchronously (``measure_async`` / ``poll``), the reduction is
@@ -52,6 +54,7 @@ class Job:
     results: list = field(default_factory=list)  # (t, s1, s2, w2, net_flips)
     cancelled: bool = False
     shape: tuple = (0, 0)  # sub-tile (Bx, By) the engine chose; part of the job's dynamics
+    batch: int = -1        # index of the engine's batch the job runs in
 
     @property
     def attempts(self) -> int:
@@ -112,31 +115,52 @@ def expected_work(L_range=(128, 16384), t_range=(10, 10_000)) -> float:
 
 
 class ServingEngine:
-    """Runs jobs through one dynamic batch.  ``batch`` must offer add(job),
-    remove(slot), run(n) and measure(slot) -> (t, s1, s2, w2, net_flips);
-    by default it is the GPU batch of this package."""
+    """Runs jobs through one or more dynamic batches.  A batch must offer
+    add(job), remove(slot), run(n) and measure(slot) -> (t, s1, s2, w2,
+    net_flips); ``batch`` is one such object or a list of them, by default
+    ``n_batches`` GPU batches of this package, each on its own stream.
+
+    With several batches a new job joins the one whose running jobs hold the
+    fewest sites, and each batch advances on its own: one batch's MCS does not
+    wait for another's, so a batch of small or few jobs, whose device steps
+    are bound by latency rather than by work, overlaps with the others on the
+    device instead of setting the pace of every job."""
 
     def __init__(self, hbm_budget: int, batch=None, stream=None, max_chunk: int = 64,
-                 on_result=None, clock=time.perf_counter, shape_policy: str = "large"):
+                 on_result=None, clock=time.perf_counter, shape_policy: str = "large",
+                 max_inflight: int = 4, n_batches: int = 1):
         self.budget = int(hbm_budget)
         self.shape_policy = shape_policy  # autotune.batch_shape policy for each job's sub-tile
         self.used = 0
-        self.batch = batch if batch is not None else GpuBatch(stream)
+        if batch is None:
+            batch = [GpuBatch(stream if i == 0 else None) for i in range(max(1, n_batches))]
+        self.batches = list(batch) if isinstance(batch, (list, tuple)) else [batch]
+        self.batch = self.batches[0]
         self.max_chunk = max_chunk
         self.on_result = on_result
         self.clock = clock
         self.waiting: deque[Job] = deque()
-        self.running: dict[int, Job] = {}
+        self.running: dict[tuple, Job] = {}  # (batch index, slot) -> job
         self.finished: list[Job] = []
-        self.pending: deque = deque()  # (job, ticket) of asynchronous measurements, in stream order
-        self.async_measure = hasattr(self.batch, "measure_async")
+        self.pending: deque = deque()  # (job, batch index, ticket) of asynchronous measurements
+        self.async_measure = all(hasattr(b, "measure_async") for b in self.batches)
         self.ticks = 0
         self.mcs_attempts = 0
+        # At most max_inflight ticks of a batch stay enqueued ahead of the
+        # device (stream marks): a job admitted now joins the launches right
+        # behind them instead of queueing behind everything the host could
+        # enqueue.  A batch at its limit is skipped until its oldest tick is done.
+        self.max_inflight = max_inflight
+        self.inflight = [deque() for _ in self.batches]
+        self.throttled = max_inflight > 0 and all(hasattr(b, "mark") for b in self.batches)
 
     def submit(self, job: Job) -> None:
         if footprint(job.L) > self.budget:
             raise ValueError(f"job {job.jid} needs {footprint(job.L)} B, more than the budget")
         self.waiting.append(job)
+
+    def _sites(self, bi: int) -> int:
+        return sum(j.L * j.L for (b, _), j in self.running.items() if b == bi)
 
     def _admit(self, now: float) -> None:
         while self.waiting and self.waiting[0].arrival <= now:
@@ -146,47 +170,77 @@ class ServingEngine:
             self.waiting.popleft()
             from .autotune import batch_shape
             job.shape = batch_shape(job.L, self.shape_policy)
-            job.slot = self.batch.add(job)
+            bi = min(range(len(self.batches)), key=self._sites)
+            job.batch = bi
+            job.slot = self.batches[bi].add(job)
             job.admitted = now
             job.t = 0
             self.used += footprint(job.L)
-            self.running[job.slot] = job
+            self.running[(bi, job.slot)] = job
 
-    def _chunk(self) -> int:
+    def _chunk(self, bi: int) -> int:
         n = self.max_chunk
-        for job in self.running.values():
+        for (b, _), job in self.running.items():
+            if b != bi:
+                continue
             i = bisect.bisect_right(job.measure_at, job.t)
             nxt = job.measure_at[i] if i < len(job.measure_at) else job.t_max
             n = min(n, nxt - job.t)
         return max(1, n)
 
+    def _ready(self, bi: int) -> bool:
+        """Whether batch bi may take another tick (its in-flight limit)."""
+        q = self.inflight[bi]
+        while q and len(q) >= self.max_inflight and self.batches[bi].mark_done(q[0]):
+            q.popleft()
+        return len(q) < self.max_inflight
+
     def tick(self, now: float | None = None) -> bool:
-        """Admits arrived jobs and advances the running ones to their next
-        event.  Returns False if nothing was running."""
+        """Admits arrived jobs and advances the running ones of every batch
+        that may take a tick to their next event.  Returns False if nothing
+        was running."""
         self._admit(self.clock() if now is None else now)
         if not self.running:
             return False
-        n = self._chunk()
-        self.batch.run(n)
+        busy = {b for b, _ in self.running}
+        ran = False
+        for bi in sorted(busy):
+            if self.throttled and not self._ready(bi):
+                continue
+            self._tick_batch(bi, now)
+            ran = True
+        if self.throttled and not ran:
+            # every batch is at its limit: wait for the oldest tick of one of them
+            bi = min(busy, key=lambda b: self.inflight[b][0])
+            self.batches[bi].wait_mark(self.inflight[bi].popleft())
+        self.deliver()
+        return True
+
+    def _tick_batch(self, bi: int, now) -> None:
+        batch = self.batches[bi]
+        n = self._chunk(bi)
+        batch.run(n)
         self.ticks += 1
-        for slot, job in list(self.running.items()):
+        for (b, slot), job in list(self.running.items()):
+            if b != bi:
+                continue
             job.t += n
             self.mcs_attempts += n * job.L * job.L
             last = job.t >= job.t_max
             if job.t in job.measure_at:
                 if self.async_measure:
-                    self.pending.append((job, self.batch.measure_async(slot)))
+                    self.pending.append((job, bi, batch.measure_async(slot)))
                 else:
-                    self._deliver_one(job, self.batch.measure(slot), now)
+                    self._deliver_one(job, batch.measure(slot), now)
             if last:
-                self.batch.remove(slot)
-                del self.running[slot]
+                batch.remove(slot)
+                del self.running[(bi, slot)]
                 self.used -= footprint(job.L)
                 if not self.async_measure or job.t_max not in job.measure_at:
                     job.done = self.clock() if now is None else now
                     self.finished.append(job)
-        self.deliver()
-        return True
+        if self.throttled:
+            self.inflight[bi].append(batch.mark())
 
     def _deliver_one(self, job: Job, res, now=None) -> None:
         assert res[0] in job.measure_at, (res[0], job.measure_at)
@@ -198,13 +252,13 @@ class ServingEngine:
             self.finished.append(job)
 
     def deliver(self, block: bool = False) -> int:
-        """Hands the finished asynchronous measurements to their jobs, oldest
-        first (they finish in stream order); with block, waits for all.
-        Returns the number delivered."""
+        """Hands the finished asynchronous measurements to their jobs, in the
+        order they were enqueued; with block, waits for all.  Returns the
+        number delivered."""
         n = 0
         while self.pending:
-            job, ticket = self.pending[0]
-            res = self.batch.wait(ticket) if block else self.batch.poll(ticket)
+            job, bi, ticket = self.pending[0]
+            res = self.batches[bi].wait(ticket) if block else self.batches[bi].poll(ticket)
             if res is None:
                 break
             self.pending.popleft()
@@ -235,17 +289,17 @@ class ServingEngine:
 
     def cancel(self, jid: int) -> bool:
         """Withdraws a job: a waiting one leaves the queue, a running one leaves
-        the batch at once and returns its memory (its streamed results stay).
+        its batch at once and returns its memory (its streamed results stay).
         Returns False if the job is unknown or already finished."""
         for job in list(self.waiting):
             if job.jid == jid:
                 self.waiting.remove(job)
                 job.cancelled = True
                 return True
-        for slot, job in list(self.running.items()):
+        for (bi, slot), job in list(self.running.items()):
             if job.jid == jid:
-                self.batch.remove(slot)
-                del self.running[slot]
+                self.batches[bi].remove(slot)
+                del self.running[(bi, slot)]
                 self.used -= footprint(job.L)
                 job.cancelled = True
                 return True
@@ -255,6 +309,12 @@ class ServingEngine:
         """Advances a virtual clock (only meaningful with an injected clock)."""
         if hasattr(self.clock, "advance_to"):
             self.clock.advance_to(t)
+
+    def close(self) -> None:
+        """Releases every batch that has a close method."""
+        for b in self.batches:
+            if hasattr(b, "close"):
+                b.close()
 
 
 def jsonl_logger(fp, clock=time.perf_counter):
@@ -316,6 +376,15 @@ class GpuBatch:
 
     def measure_async(self, slot: int) -> int:
         return self._lib.oct_batch_measure_async(self.h, slot)
+
+    def mark(self) -> int:
+        return self._lib.oct_batch_mark(self.h)
+
+    def mark_done(self, mark: int) -> bool:
+        return self._lib.oct_batch_mark_done(self.h, mark)
+
+    def wait_mark(self, mark: int) -> None:
+        self._lib.oct_batch_mark_wait(self.h, mark)
 
     def poll(self, ticket: int):
         m = self._lib.oct_batch_poll(self.h, ticket)

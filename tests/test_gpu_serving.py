@@ -64,3 +64,32 @@ def test_full_warp_jobs_in_the_mix(g):
                 t = tt
                 m = sim.measure()
                 assert (tt, s1, s2, w2, net) == (m.t, m.s1, m.s2, m.w2, m.net_flips), job.jid
+
+
+def test_stream_marks(g):
+    """oct_batch_mark / _done / _wait: a mark is passed once the device has run
+    the MCS enqueued before it; marks not handed out are refused; a mark more
+    than 64 marks old reads as passed."""
+    from paper_1705_01022_gb300 import _lib
+    r = _lib.oct_replica()
+    r.L, r.p, r.q, r.seed = 1024, 0.95, 0.05, 3
+    h = _lib.oct_batch_create([r], None)
+    try:
+        _lib.oct_batch_run(h, 3)
+        m = _lib.oct_batch_mark(h)
+        _lib.oct_batch_mark_wait(h, m)
+        assert _lib.oct_batch_mark_done(h, m)
+        for bad in (-1, m + 1):
+            with pytest.raises(_lib.OctError):
+                _lib.oct_batch_mark_done(h, bad)
+            with pytest.raises(_lib.OctError):
+                _lib.oct_batch_mark_wait(h, bad)
+        marks = []
+        for _ in range(70):
+            _lib.oct_batch_run(h, 1)
+            marks.append(_lib.oct_batch_mark(h))
+        assert _lib.oct_batch_mark_done(h, marks[0])  # recycled: passed before its event was reused
+        _lib.oct_batch_mark_wait(h, marks[-1])
+        assert all(_lib.oct_batch_mark_done(h, x) for x in marks)
+    finally:
+        _lib.oct_batch_destroy(h)

@@ -190,3 +190,72 @@ def test_asynchronous_measurements_are_all_delivered_in_order():
         assert j.done >= j.admitted >= j.arrival
     # the host never waited on a measurement while jobs were still running
     assert len(fb.queue) == sum(len(j.measure_at) for j in jobs)
+
+
+class FakeMarkedBatch(FakeAsyncBatch):
+    """Runs are only issued, not done: the device is a queue of issued runs
+    that finishes one run per wait; marks record the issued count."""
+
+    def __init__(self, clock, rate=1e6):
+        super().__init__(clock, rate)
+        self.marks, self.done_runs, self.max_ahead, self.last_waited = [], 0, 0, -1
+
+    def run(self, n):
+        super().run(n)
+        self.max_ahead = max(self.max_ahead, len(self.runs) - self.done_runs)
+
+    def mark(self):
+        self.marks.append(len(self.runs))
+        return len(self.marks) - 1
+
+    def mark_done(self, m):
+        return self.marks[m] <= self.done_runs
+
+    def wait_mark(self, m):
+        assert m > self.last_waited  # oldest first
+        self.last_waited = m
+        self.done_runs = max(self.done_runs, self.marks[m])
+
+
+@pytest.mark.parametrize("max_inflight", [1, 2, 4])
+def test_engine_keeps_at_most_max_inflight_ticks_ahead(max_inflight):
+    """With stream marks, the host waits for the tick max_inflight ticks back
+    before it goes on, so a newly admitted job joins launches that follow at
+    most max_inflight enqueued ticks; every job still gets all its results."""
+    clock = VirtualClock()
+    fb = FakeMarkedBatch(clock)
+    eng = serve.ServingEngine(4 * serve.footprint(1024), batch=fb, max_chunk=8, clock=clock,
+                              max_inflight=max_inflight)
+    assert eng.throttled
+    jobs = [serve.Job(i, 512 + 128 * (i % 4), 1.0, 0.0, i, t_max=30 + 11 * i,
+                      arrival=0.3 * i, measure_at=serve.log_times(30 + 11 * i)) for i in range(10)]
+    done = eng.run(jobs, realtime=False)
+    assert len(done) == 10 and not eng.pending and eng.used == 0
+    for j in done:
+        assert [r[0] for r in j.results] == j.measure_at
+    assert len(fb.marks) == eng.ticks
+    # after each tick at most max_inflight ticks were issued and not yet passed
+    assert fb.max_ahead <= max_inflight
+    assert len(eng.inflight[0]) <= max_inflight
+
+
+def test_jobs_spread_over_several_batches_that_tick_independently():
+    """With two batches a new job joins the one with fewer running sites;
+    each batch advances by its own chunks, and every job still gets all its
+    measurements, in order, with the memory returned at the end."""
+    clock = VirtualClock()
+    fbs = [FakeMarkedBatch(clock), FakeMarkedBatch(clock)]
+    eng = serve.ServingEngine(6 * serve.footprint(1024), batch=fbs, max_chunk=8, clock=clock, max_inflight=2)
+    jobs = [serve.Job(i, [1024, 256, 512, 768][i % 4], 1.0, 0.0, i, t_max=25 + 13 * i,
+                      arrival=0.2 * i, measure_at=serve.log_times(25 + 13 * i)) for i in range(12)]
+    done = eng.run(jobs, realtime=False)
+    assert len(done) == 12 and not eng.pending and not eng.running and eng.used == 0
+    for j in done:
+        assert j.batch in (0, 1)
+        assert [r[0] for r in j.results] == j.measure_at
+    used = {j.batch for j in done}
+    assert used == {0, 1}
+    # the batches ran different chunk sequences (they do not move in lock step)
+    assert [n for n, _ in fbs[0].runs] != [n for n, _ in fbs[1].runs]
+    # the first two jobs (both arriving while nothing runs) went to different batches
+    assert jobs[0].batch != jobs[1].batch

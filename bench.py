@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--serve-policy", default="large", help="autotune.batch_shape policy of the serving leg")
     ap.add_argument("--serve-inflight", type=int, default=4,
                     help="ticks the serving loop keeps enqueued ahead of the device per batch (0: no limit)")
-    ap.add_argument("--serve-batches", type=int, default=2,
+    ap.add_argument("--serve-batches", type=int, default=1,
                     help="batches (streams) the serving loop spreads its jobs over")
     ap.add_argument("--db-steps", type=int, default=30)
     ap.add_argument("--cell-steps", type=int, default=2, help="timed MCS per coarse thread-cell shape")

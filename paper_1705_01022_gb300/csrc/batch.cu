@@ -183,6 +183,7 @@ struct MeasureRecord {
 };
 constexpr int kMeasureRing = 1024;
 constexpr int kMarkRing = 64;
+constexpr int kGraphMcs = 4;  // MCS in the batch's longer captured graph
 
 }  // namespace
 }  // namespace oct
@@ -209,6 +210,9 @@ struct oct_batch {
     // acceptance draws, 1 draws, 2 draws for both rates, 3 deposition only
     uint32_t n_desc[kKinds] = {};
     uint32_t desc_first[kKinds] = {};
+    // the active replicas ordered by kind: act_n[kind] of them from act_first[kind]
+    uint32_t act_first[kKinds] = {};
+    uint32_t act_n[kKinds] = {};
     uint32_t *d_queue = nullptr;  // 4 * kKinds counters: (device step, kind)
     oct::W2RowSums *d_rows = nullptr;
     int64_t rows_cap = 0;
@@ -223,7 +227,9 @@ struct oct_batch {
     uint64_t ticks = 0;  // MCS run by oct_batch_run
     int grid = 0;
     cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec = nullptr;        // one MCS
+    cudaGraph_t graph_n = nullptr;
+    cudaGraphExec_t exec_n = nullptr;      // kGraphMcs MCS
     // side streams and events of the captured MCS: one branch per kind
     cudaStream_t side[kKinds] = {};
     cudaEvent_t fork_ev = nullptr;
@@ -249,8 +255,12 @@ namespace {
 void drop_graph(oct_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->exec_n) cudaGraphExecDestroy(b->exec_n);
+    if (b->graph_n) cudaGraphDestroy(b->graph_n);
     b->exec = nullptr;
     b->graph = nullptr;
+    b->exec_n = nullptr;
+    b->graph_n = nullptr;
 }
 
 void batch_free(oct_batch *b) {
@@ -386,21 +396,27 @@ cudaError_t rebuild(oct_batch *b) {
     cudaError_t e = cudaSuccess;
     drop_graph(b);  // an executable graph still running is freed when it completes
     std::vector<oct::ReplicaDev> rd(b->capacity);
-    std::vector<uint32_t> active;
+    std::vector<uint32_t> by_kind[kKinds];
     std::vector<oct::BatchItem> bucket[kModes][6][6];
     for (size_t slot = 0; slot < b->reps.size(); ++slot) {
         if (!b->used[slot]) continue;
         rd[slot] = replica_dev(b, static_cast<int64_t>(slot));
         const oct::ReplicaDev &D = rd[slot];
-        active.push_back(static_cast<uint32_t>(slot));
         const int mode = (D.p_random && D.q_random) ? 2
                          : (D.p_random || D.q_random) ? 1
                          : (D.p_always && !D.q_always) ? 3 : 0;
         int gxi = 0, gyi = 0;
         while ((1u << gxi) < D.GX) ++gxi;
         while ((1u << gyi) < D.GY) ++gyi;
+        by_kind[2 * mode + ((D.GX << gyi) == 32u ? 1 : 0)].push_back(static_cast<uint32_t>(slot));
         for (uint32_t T = 0; T < D.tiles_x * D.tiles_y; ++T)
             bucket[mode][gxi][gyi].push_back({static_cast<uint32_t>(slot), T});
+    }
+    std::vector<uint32_t> active;
+    for (int kind = 0; kind < kKinds; ++kind) {
+        b->act_first[kind] = static_cast<uint32_t>(active.size());
+        b->act_n[kind] = static_cast<uint32_t>(by_kind[kind].size());
+        active.insert(active.end(), by_kind[kind].begin(), by_kind[kind].end());
     }
     std::vector<oct::BatchItem> items;
     std::vector<oct::WarpDesc> descs;
@@ -515,12 +531,22 @@ cudaError_t enqueue_advance(oct_batch *b, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// One MCS for capture on st: the replicas of different kinds share no memory
-// and no counter, so each kind's four device steps are a branch of their own
-// (forked from st on a side stream and joined back before the MCS counters
-// advance); the branches run concurrently, so one kind's launches fill the
-// device while another's drain.
-cudaError_t enqueue_mcs(oct_batch *b, cudaStream_t st) {
+// Advances the MCS counters of the replicas of one kind.
+cudaError_t enqueue_advance_kind(oct_batch *b, int kind, cudaStream_t st) {
+    const uint32_t n = b->act_n[kind];
+    if (n == 0) return cudaSuccess;
+    const int blocks = static_cast<int>(std::min<uint32_t>(1024u, (n + 255u) / 256u));
+    oct::batch_advance_kernel<<<blocks, 256, 0, st>>>(b->d_t, b->wb[b->cur].active + b->act_first[kind], n);
+    return cudaGetLastError();
+}
+
+// nmcs MCS for capture on st.  The replicas of different kinds share no
+// memory and no counter, so each kind's device steps and its own MCS-counter
+// advances form a branch of their own (forked from st on a side stream and
+// joined back at the end); the branches run concurrently, so one kind's
+// launches fill the device while another's drain, and over several MCS no
+// branch waits for the others at MCS boundaries.
+cudaError_t enqueue_mcs(oct_batch *b, cudaStream_t st, int nmcs) {
     cudaError_t e = cudaSuccess;
     if (!b->fork_ev) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(b->fork_ev, st);
@@ -530,12 +556,30 @@ cudaError_t enqueue_mcs(oct_batch *b, cudaStream_t st) {
         if (e == cudaSuccess && !b->join_ev[kind])
             e = cudaEventCreateWithFlags(&b->join_ev[kind], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side[kind], b->fork_ev, 0);
-        for (uint32_t k = 0; k < 4 && e == cudaSuccess; ++k) e = enqueue_kind_step(b, k, kind, b->side[kind]);
+        for (int i = 0; i < nmcs && e == cudaSuccess; ++i) {
+            for (uint32_t k = 0; k < 4 && e == cudaSuccess; ++k) e = enqueue_kind_step(b, k, kind, b->side[kind]);
+            if (e == cudaSuccess) e = enqueue_advance_kind(b, kind, b->side[kind]);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(b->join_ev[kind], b->side[kind]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join_ev[kind], 0);
     }
+    return e;
+}
+
+// Captures nmcs MCS of the current membership into *graph / *exec.
+cudaError_t capture_mcs(oct_batch *b, int nmcs, cudaGraph_t *graph, cudaGraphExec_t *exec) {
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
-    return enqueue_advance(b, st);
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const cudaError_t e2 = enqueue_mcs(b, cap, nmcs);
+        e = cudaStreamEndCapture(cap, graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, *graph, 0);
+    cudaStreamDestroy(cap);
+    return e;
 }
 
 int flush_batch_timing(oct_batch *b) {
@@ -832,21 +876,24 @@ int oct_batch_run(oct_batch *b, int64_t n) {
             BATCH_CUDA(enqueue_advance(b, b->stream));
         }
     } else {
-        if (!b->exec) {
-            // one MCS captured on a private stream, replayed on the batch's stream
-            cudaStream_t cap = nullptr;
-            BATCH_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                cudaError_t e2 = enqueue_mcs(b, cap);
-                e = cudaStreamEndCapture(cap, &b->graph);
-                if (e == cudaSuccess) e = e2;
+        // kGraphMcs MCS per graph launch while that many are left, then one
+        // at a time; each graph is captured on a private stream on first use
+        // after a membership change and replayed on the batch's stream
+        int64_t left = n;
+        if (left >= oct::kGraphMcs) {
+            if (!b->exec_n) {
+                const cudaError_t e = capture_mcs(b, oct::kGraphMcs, &b->graph_n, &b->exec_n);
+                if (e != cudaSuccess) return bfail(OCT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
             }
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-            cudaStreamDestroy(cap);
-            if (e != cudaSuccess) return bfail(OCT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            for (; left >= oct::kGraphMcs; left -= oct::kGraphMcs) BATCH_CUDA(cudaGraphLaunch(b->exec_n, b->stream));
         }
-        for (int64_t i = 0; i < n; ++i) BATCH_CUDA(cudaGraphLaunch(b->exec, b->stream));
+        if (left > 0) {
+            if (!b->exec) {
+                const cudaError_t e = capture_mcs(b, 1, &b->graph, &b->exec);
+                if (e != cudaSuccess) return bfail(OCT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            }
+            for (; left > 0; --left) BATCH_CUDA(cudaGraphLaunch(b->exec, b->stream));
+        }
     }
     b->ticks += static_cast<uint64_t>(n);
     return OCT_OK;

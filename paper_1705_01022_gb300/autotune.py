@@ -281,7 +281,7 @@ def choose_cell(L: int, p: float, q: float, Bx: int, By: int, max_shift: float =
 
 # ---------------------------------------------------------------------------
 # batched replicas
-BATCH_POLICIES = ("default", "wide", "square", "large")
+BATCH_POLICIES = ("default", "wide", "square", "tall", "large")
 LARGE_MIN_SUBTILES = 1024  # sub-tiles per device step for which 'large' keeps the wide shape
 
 
@@ -293,7 +293,9 @@ def batch_shape(L: int, policy: str) -> tuple[int, int]:
     """Sub-tile of a replica of size L under a policy: 'default' is the batch
     library's own default (64 x 64 if L % 128 == 0, else 32 x 32); 'wide' and
     'square' take the most groups a valid shape allows, then the widest or the
-    most nearly square one; 'large' takes the wide shape where it still leaves
+    most nearly square one; 'tall' takes 'wide' where that fills a warp, else
+    the one-group-wide shape with the most groups (its lanes exchange no
+    columns); 'large' takes the wide shape where it still leaves
     at least LARGE_MIN_SUBTILES sub-tiles per device step (large lattices get
     full-warp sub-tiles, as in the plain kernel), else the default."""
     if policy == "default":
@@ -312,6 +314,10 @@ def batch_shape(L: int, policy: str) -> tuple[int, int]:
         return max(best, key=lambda sh: sh[0])
     if policy == "square":
         return min(best, key=lambda sh: (abs(sh[0].bit_length() - sh[1].bit_length()), -sh[0]))
+    if policy == "tall":
+        if gmax == MAX_GROUPS:  # full warps: as 'wide'
+            return max(best, key=lambda sh: sh[0])
+        return max((sh for sh in shapes if sh[0] == GROUP[0]), key=groups)
     raise ValueError(f"unknown policy {policy!r}")
 
 

@@ -84,9 +84,16 @@ def test_batch_policies_give_valid_shapes():
             Bx, By = at.batch_shape(L, pol)
             assert (Bx, By) in at.candidates(L)
             assert at.groups((Bx, By)) == max(at.groups(s) for s in at.candidates(L))
+        Bx, By = at.batch_shape(L, "tall")
+        assert (Bx, By) in at.candidates(L)
+        if at.groups(at.batch_shape(L, "wide")) == at.MAX_GROUPS:
+            assert (Bx, By) == at.batch_shape(L, "wide")
+        else:
+            assert Bx == 32 and By == max(s[1] for s in at.candidates(L) if s[0] == 32)
     assert at.batch_shape(4096, "wide") == (1024, 16)
     assert at.batch_shape(4096, "square") == (128, 128)
     assert at.batch_shape(192, "wide") == (32, 32)
+    assert at.batch_shape(384, "wide") == (64, 64) and at.batch_shape(384, "tall") == (32, 64)
     # 'large': full-warp sub-tiles only where they leave enough of them per device step
     assert at.batch_shape(4096, "large") == (64, 64)
     assert at.batch_shape(6144, "large") == (64, 64)

@@ -2,10 +2,10 @@
 oracle, through the C ABI.
 
 Bar: the integer sums (sum h(t), sum h(s), sum h(t) h(s), the occupation
-counts) are equal integers and C_h, C_s the same doubles.  Sizes cover the
-scalar load path (rows of 6 and 130 words), the 16-byte path with one and
-several 128-word chunks per row and a ragged last chunk (132 and 256 words),
-and a bare-buffer call at L = 96.  At L = 2^17 (the bench size) the oracle
+counts) are equal integers and C_h, C_s the same doubles.  The row pass takes
+rows in chunks of 256 words (8 per lane); sizes cover the scalar load path
+(rows of 6, 130 and 258 words), the 16-byte path (8, 132, 256 and 260 words),
+partial chunks alone and after a full one, and a bare-buffer call at L = 96.  At L = 2^17 (the bench size) the oracle
 cannot integrate 1.7e10 sites in a test, so properties that hold at any size
 are checked there: C_h(s,s) = W^2(s) exactly, C_s(s,s) = 1/4, symmetry in
 (t, s) and Cauchy-Schwarz."""
@@ -37,7 +37,9 @@ def _assert_ac_equal(ac, ref, what=""):
     (192, 0.95, 0.05, 2, 5),     # 6 words per row: scalar path
     (4160, 0.5, 0.5, 2, 3),      # 130 words: scalar path, ragged second chunk
     (4224, 1.0, 0.0, 4, 2),      # 132 words: vector path, ragged second chunk
-    (8192, 0.95, 0.05, 1, 1),    # 256 words: vector path, two full chunks
+    (8192, 0.95, 0.05, 1, 1),    # 256 words: vector path, one full chunk
+    (8256, 0.5, 0.5, 2, 1),      # 258 words: scalar path, a full chunk and a ragged one of 2 words
+    (8320, 0.95, 0.05, 1, 2),    # 260 words: vector path, a full chunk and a ragged one of 4 words
 ])
 def test_handle_against_oracle(g, oracle, L, p, q, s, dt):
     Bx, By = (64, 64) if L % 128 == 0 else (32, 32)

@@ -136,7 +136,11 @@ __global__ void batch_advance_kernel(uint32_t *t_of, const uint32_t *active, uin
 namespace {
 
 constexpr int kModes = 4;
-constexpr int kKinds = 2 * kModes;
+constexpr int kKinds = 2 * kModes;  // acceptance mode x (several sub-tiles per warp, or one)
+// Each kind's replicas are split into kParts parts of about equal sites; a
+// branch (kind, part) is the unit of the captured graph (see enqueue_mcs).
+constexpr int kParts = 2;
+constexpr int kBranches = kKinds * kParts;
 
 int bfail(int code, const std::string &msg) {
     oct::set_last_error(msg);
@@ -208,12 +212,13 @@ struct oct_batch {
     uint32_t n_active = 0;
     // work lists by kind = 2 * mode + (one sub-tile per warp); modes: 0 no
     // acceptance draws, 1 draws, 2 draws for both rates, 3 deposition only
-    uint32_t n_desc[kKinds] = {};
-    uint32_t desc_first[kKinds] = {};
-    // the active replicas ordered by kind: act_n[kind] of them from act_first[kind]
-    uint32_t act_first[kKinds] = {};
-    uint32_t act_n[kKinds] = {};
-    uint32_t *d_queue = nullptr;  // 4 * kKinds counters: (device step, kind)
+    // work lists by branch = kParts * kind + part
+    uint32_t n_desc[kBranches] = {};
+    uint32_t desc_first[kBranches] = {};
+    // the active replicas ordered by branch: act_n[br] of them from act_first[br]
+    uint32_t act_first[kBranches] = {};
+    uint32_t act_n[kBranches] = {};
+    uint32_t *d_queue = nullptr;  // 4 * kBranches counters: (device step, branch)
     oct::W2RowSums *d_rows = nullptr;
     int64_t rows_cap = 0;
     oct::W2Result *d_w2 = nullptr;
@@ -231,9 +236,9 @@ struct oct_batch {
     cudaGraph_t graph_n = nullptr;
     cudaGraphExec_t exec_n = nullptr;      // kGraphMcs MCS
     // side streams and events of the captured MCS: one branch per kind
-    cudaStream_t side[kKinds] = {};
+    cudaStream_t side[kBranches] = {};
     cudaEvent_t fork_ev = nullptr;
-    cudaEvent_t join_ev[kKinds] = {};
+    cudaEvent_t join_ev[kBranches] = {};
     // asynchronous measurements: a ring of records (device and pinned host)
     oct::MeasureRecord *d_req = nullptr;
     oct::MeasureRecord *h_req = nullptr;
@@ -289,9 +294,9 @@ void batch_free(oct_batch *b) {
     for (cudaEvent_t e : b->mark_ev)
         if (e) cudaEventDestroy(e);
     cudaFree(b->d_queue);
-    for (int kind = 0; kind < kKinds; ++kind) {
-        if (b->side[kind]) cudaStreamDestroy(b->side[kind]);
-        if (b->join_ev[kind]) cudaEventDestroy(b->join_ev[kind]);
+    for (int br = 0; br < kBranches; ++br) {
+        if (b->side[br]) cudaStreamDestroy(b->side[br]);
+        if (b->join_ev[br]) cudaEventDestroy(b->join_ev[br]);
     }
     if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     cudaFree(b->d_rows);
@@ -396,8 +401,9 @@ cudaError_t rebuild(oct_batch *b) {
     cudaError_t e = cudaSuccess;
     drop_graph(b);  // an executable graph still running is freed when it completes
     std::vector<oct::ReplicaDev> rd(b->capacity);
+    // replicas by kind, then each kind split into kParts parts of about equal
+    // sites (largest first, each to the lightest part)
     std::vector<uint32_t> by_kind[kKinds];
-    std::vector<oct::BatchItem> bucket[kModes][6][6];
     for (size_t slot = 0; slot < b->reps.size(); ++slot) {
         if (!b->used[slot]) continue;
         rd[slot] = replica_dev(b, static_cast<int64_t>(slot));
@@ -405,31 +411,44 @@ cudaError_t rebuild(oct_batch *b) {
         const int mode = (D.p_random && D.q_random) ? 2
                          : (D.p_random || D.q_random) ? 1
                          : (D.p_always && !D.q_always) ? 3 : 0;
-        int gxi = 0, gyi = 0;
-        while ((1u << gxi) < D.GX) ++gxi;
-        while ((1u << gyi) < D.GY) ++gyi;
-        by_kind[2 * mode + ((D.GX << gyi) == 32u ? 1 : 0)].push_back(static_cast<uint32_t>(slot));
-        for (uint32_t T = 0; T < D.tiles_x * D.tiles_y; ++T)
-            bucket[mode][gxi][gyi].push_back({static_cast<uint32_t>(slot), T});
+        by_kind[2 * mode + (D.GX * D.GY == 32u ? 1 : 0)].push_back(static_cast<uint32_t>(slot));
+    }
+    std::vector<uint32_t> by_branch[kBranches];
+    for (int kind = 0; kind < kKinds; ++kind) {
+        std::vector<uint32_t> &v = by_kind[kind];
+        std::stable_sort(v.begin(), v.end(), [&](uint32_t a, uint32_t c) { return rd[a].L > rd[c].L; });
+        uint64_t load[kParts] = {};
+        for (uint32_t slot : v) {
+            int part = 0;
+            for (int q = 1; q < kParts; ++q)
+                if (load[q] < load[part]) part = q;
+            load[part] += static_cast<uint64_t>(rd[slot].L) * rd[slot].L;
+            by_branch[kind * kParts + part].push_back(slot);
+        }
     }
     std::vector<uint32_t> active;
-    for (int kind = 0; kind < kKinds; ++kind) {
-        b->act_first[kind] = static_cast<uint32_t>(active.size());
-        b->act_n[kind] = static_cast<uint32_t>(by_kind[kind].size());
-        active.insert(active.end(), by_kind[kind].begin(), by_kind[kind].end());
-    }
     std::vector<oct::BatchItem> items;
     std::vector<oct::WarpDesc> descs;
-    for (int kind = 0; kind < kKinds; ++kind) {
-        const int mode = kind >> 1;
-        const bool full = kind & 1;
-        b->desc_first[kind] = static_cast<uint32_t>(descs.size());
+    for (int br = 0; br < kBranches; ++br) {
+        b->act_first[br] = static_cast<uint32_t>(active.size());
+        b->act_n[br] = static_cast<uint32_t>(by_branch[br].size());
+        active.insert(active.end(), by_branch[br].begin(), by_branch[br].end());
+        // the branch's items bucketed by lane layout, then packed into warps
+        std::vector<oct::BatchItem> bucket[6][6];
+        for (uint32_t slot : by_branch[br]) {
+            const oct::ReplicaDev &D = rd[slot];
+            int gxi = 0, gyi = 0;
+            while ((1u << gxi) < D.GX) ++gxi;
+            while ((1u << gyi) < D.GY) ++gyi;
+            for (uint32_t T = 0; T < D.tiles_x * D.tiles_y; ++T) bucket[gxi][gyi].push_back({slot, T});
+        }
+        b->desc_first[br] = static_cast<uint32_t>(descs.size());
         for (int gxi = 5; gxi >= 0; --gxi)
             for (int gyi = 5; gyi >= 0; --gyi) {
                 const uint32_t GX = 1u << gxi, G = GX << gyi;
-                if (G > 32u || (G == 32u) != full) continue;
+                if (G > 32u) continue;
                 const uint32_t per = 32u / G;
-                auto &bk = bucket[mode][gxi][gyi];
+                auto &bk = bucket[gxi][gyi];
                 for (size_t i = 0; i < bk.size(); i += per) {
                     oct::WarpDesc d;
                     d.first = static_cast<uint32_t>(items.size());
@@ -440,7 +459,7 @@ cudaError_t rebuild(oct_batch *b) {
                     descs.push_back(d);
                 }
             }
-        b->n_desc[kind] = static_cast<uint32_t>(descs.size()) - b->desc_first[kind];
+        b->n_desc[br] = static_cast<uint32_t>(descs.size()) - b->desc_first[br];
     }
     const int nxt = 1 - b->cur;
     oct::WorkBuf &w = b->wb[nxt];
@@ -488,14 +507,15 @@ cudaError_t rebuild(oct_batch *b) {
     return cudaSuccess;
 }
 
-// Enqueues device step k of the current MCS of the replicas of one kind.
-cudaError_t enqueue_kind_step(oct_batch *b, uint32_t k, int kind, cudaStream_t st) {
-    uint32_t *q = b->d_queue + kKinds * k + kind;
+// Enqueues device step k of the current MCS of the replicas of one branch.
+cudaError_t enqueue_branch_step(oct_batch *b, uint32_t k, int br, cudaStream_t st) {
+    uint32_t *q = b->d_queue + kBranches * k + br;
     cudaError_t e = cudaMemsetAsync(q, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     const oct::WorkBuf &w = b->wb[b->cur];
-    const oct::WarpDesc *descs = w.descs + b->desc_first[kind];
-    const uint32_t nd = b->n_desc[kind];
+    const oct::WarpDesc *descs = w.descs + b->desc_first[br];
+    const uint32_t nd = b->n_desc[br];
+    const int kind = br / kParts;
     const int blocks = std::min<int>(b->grid, static_cast<int>((nd + oct::kBatchWarps - 1) / oct::kBatchWarps));
     const dim3 grid(blocks), block(oct::kBatchWarps * 32);
 #define OCT_BATCH(R, LS, SC) \
@@ -514,11 +534,11 @@ cudaError_t enqueue_kind_step(oct_batch *b, uint32_t k, int kind, cudaStream_t s
     return cudaGetLastError();
 }
 
-// Enqueues device step k of the current MCS of every active replica, kind by kind.
+// Enqueues device step k of the current MCS of every active replica, branch by branch.
 cudaError_t enqueue_step(oct_batch *b, uint32_t k, cudaStream_t st) {
-    for (int kind = 0; kind < kKinds; ++kind) {
-        if (b->n_desc[kind] == 0) continue;
-        cudaError_t e = enqueue_kind_step(b, k, kind, st);
+    for (int br = 0; br < kBranches; ++br) {
+        if (b->n_desc[br] == 0) continue;
+        cudaError_t e = enqueue_branch_step(b, k, br, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -531,37 +551,37 @@ cudaError_t enqueue_advance(oct_batch *b, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Advances the MCS counters of the replicas of one kind.
-cudaError_t enqueue_advance_kind(oct_batch *b, int kind, cudaStream_t st) {
-    const uint32_t n = b->act_n[kind];
+// Advances the MCS counters of the replicas of one branch.
+cudaError_t enqueue_advance_branch(oct_batch *b, int br, cudaStream_t st) {
+    const uint32_t n = b->act_n[br];
     if (n == 0) return cudaSuccess;
     const int blocks = static_cast<int>(std::min<uint32_t>(1024u, (n + 255u) / 256u));
-    oct::batch_advance_kernel<<<blocks, 256, 0, st>>>(b->d_t, b->wb[b->cur].active + b->act_first[kind], n);
+    oct::batch_advance_kernel<<<blocks, 256, 0, st>>>(b->d_t, b->wb[b->cur].active + b->act_first[br], n);
     return cudaGetLastError();
 }
 
-// nmcs MCS for capture on st.  The replicas of different kinds share no
-// memory and no counter, so each kind's device steps and its own MCS-counter
-// advances form a branch of their own (forked from st on a side stream and
-// joined back at the end); the branches run concurrently, so one kind's
-// launches fill the device while another's drain, and over several MCS no
-// branch waits for the others at MCS boundaries.
+// nmcs MCS for capture on st.  The replicas of different branches (kinds,
+// and parts of a kind) share no memory and no counter, so each branch's
+// device steps and its own MCS-counter advances form a branch of the graph
+// (forked from st on a side stream and joined back at the end); the branches
+// run concurrently, so one branch's launches fill the device while another's
+// drain, and over several MCS no branch waits for the others at MCS
+// boundaries.
 cudaError_t enqueue_mcs(oct_batch *b, cudaStream_t st, int nmcs) {
     cudaError_t e = cudaSuccess;
     if (!b->fork_ev) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(b->fork_ev, st);
-    for (int kind = 0; kind < kKinds && e == cudaSuccess; ++kind) {
-        if (b->n_desc[kind] == 0) continue;
-        if (!b->side[kind]) e = cudaStreamCreateWithFlags(&b->side[kind], cudaStreamNonBlocking);
-        if (e == cudaSuccess && !b->join_ev[kind])
-            e = cudaEventCreateWithFlags(&b->join_ev[kind], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side[kind], b->fork_ev, 0);
+    for (int br = 0; br < kBranches && e == cudaSuccess; ++br) {
+        if (b->n_desc[br] == 0) continue;
+        if (!b->side[br]) e = cudaStreamCreateWithFlags(&b->side[br], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !b->join_ev[br]) e = cudaEventCreateWithFlags(&b->join_ev[br], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side[br], b->fork_ev, 0);
         for (int i = 0; i < nmcs && e == cudaSuccess; ++i) {
-            for (uint32_t k = 0; k < 4 && e == cudaSuccess; ++k) e = enqueue_kind_step(b, k, kind, b->side[kind]);
-            if (e == cudaSuccess) e = enqueue_advance_kind(b, kind, b->side[kind]);
+            for (uint32_t k = 0; k < 4 && e == cudaSuccess; ++k) e = enqueue_branch_step(b, k, br, b->side[br]);
+            if (e == cudaSuccess) e = enqueue_advance_branch(b, br, b->side[br]);
         }
-        if (e == cudaSuccess) e = cudaEventRecord(b->join_ev[kind], b->side[kind]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join_ev[kind], 0);
+        if (e == cudaSuccess) e = cudaEventRecord(b->join_ev[br], b->side[br]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join_ev[br], 0);
     }
     return e;
 }
@@ -795,7 +815,7 @@ int oct_batch_create(int64_t n, const oct_replica *reps, void *stream, oct_batch
             e = cudaMemPoolSetAttribute(b->pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
     }
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(uint32_t) * 4 * kKinds);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(uint32_t) * 4 * kBranches);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_w2, sizeof(oct::W2Result));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_small, 256);
     if (e == cudaSuccess) {

@@ -356,7 +356,7 @@ def batched_leg(a, g, _lib, torch, stream, peak_tops):
     reps = batch_replicas(a.batch_replicas, _lib)
     sites = sum(r[0] * r[0] for r in reps)
     # block tiles by the autotuner's batch policy (timed on this replica set)
-    tuned = autotune.tune_batch(reps, mcs=2, stream=stream) if a.tune_mcs > 0 else None
+    tuned = autotune.tune_batch(reps, mcs=4, stream=stream) if a.tune_mcs > 0 else None
     policy = tuned["policy"] if tuned else "default"
     shapes = [autotune.batch_shape(r[0], policy) for r in reps]
     reps = [r + sh for r, sh in zip(reps, shapes)]

@@ -328,22 +328,23 @@ def batch_key(replicas) -> str:
     return hashlib.sha256(repr(items).encode()).hexdigest()[:16]
 
 
-def measure_batch(replicas, mcs: int = 2, stream=None) -> float:
-    """Attempts per ns of the batched device steps (kernel time of every device
-    step, after one warm-up MCS) for replicas (L, p, q, seed, Bx, By)."""
-    from . import Batch, _lib
+def measure_batch(replicas, mcs: int = 4, stream=None) -> float:
+    """Attempts per ns of mcs batched MCS as they run (the captured graphs,
+    whose branches overlap on the device), after a warm-up run of the same
+    length that captures them, for replicas (L, p, q, seed, Bx, By)."""
+    from . import Batch
     sites = sum(int(r[0]) ** 2 for r in replicas)
     with Batch(replicas, stream=stream) as b:
-        b.run(1)
-        b.sync()
-        _lib.oct_batch_set_timing(b.h, True)
         b.run(mcs)
-        ms, launches = _lib.oct_batch_get_timing(b.h)
-        _lib.oct_batch_set_timing(b.h, False)
-    return (sites / 4.0) * launches / (ms * 1e6)
+        b.sync()
+        t0 = time.perf_counter()
+        b.run(mcs)
+        b.sync()
+        dt = time.perf_counter() - t0
+    return sites * mcs / (dt * 1e9)
 
 
-def tune_batch(replicas, mcs: int = 2, stream=None, policies=BATCH_POLICIES, measure_fn=None) -> dict:
+def tune_batch(replicas, mcs: int = 4, stream=None, policies=BATCH_POLICIES, measure_fn=None) -> dict:
     """Times every policy on the replica set (L, p, q, seed[, ...]) and returns
     the record of the choice, with `shapes`: the (Bx, By) for each replica."""
     replicas = [tuple(r[:4]) for r in replicas]

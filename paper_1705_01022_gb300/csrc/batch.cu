@@ -137,9 +137,11 @@ namespace {
 
 constexpr int kModes = 4;
 constexpr int kKinds = 2 * kModes;  // acceptance mode x (several sub-tiles per warp, or one)
-// Each kind's replicas are split into kParts parts of about equal sites; a
-// branch (kind, part) is the unit of the captured graph (see enqueue_mcs).
-constexpr int kParts = 2;
+// Each kind's replicas are split into up to kParts parts of about equal
+// sites, each of at least kMinPartSites sites; a branch (kind, part) is the
+// unit of the captured graph (see enqueue_mcs).
+constexpr int kParts = 3;
+constexpr uint64_t kMinPartSites = uint64_t{1} << 26;
 constexpr int kBranches = kKinds * kParts;
 
 int bfail(int code, const std::string &msg) {
@@ -401,8 +403,8 @@ cudaError_t rebuild(oct_batch *b) {
     cudaError_t e = cudaSuccess;
     drop_graph(b);  // an executable graph still running is freed when it completes
     std::vector<oct::ReplicaDev> rd(b->capacity);
-    // replicas by kind, then each kind split into kParts parts of about equal
-    // sites (largest first, each to the lightest part)
+    // replicas by kind, then each kind split into up to kParts parts of about
+    // equal sites (largest first, each to the lightest part)
     std::vector<uint32_t> by_kind[kKinds];
     for (size_t slot = 0; slot < b->reps.size(); ++slot) {
         if (!b->used[slot]) continue;
@@ -417,10 +419,13 @@ cudaError_t rebuild(oct_batch *b) {
     for (int kind = 0; kind < kKinds; ++kind) {
         std::vector<uint32_t> &v = by_kind[kind];
         std::stable_sort(v.begin(), v.end(), [&](uint32_t a, uint32_t c) { return rd[a].L > rd[c].L; });
+        uint64_t sites = 0;
+        for (uint32_t slot : v) sites += static_cast<uint64_t>(rd[slot].L) * rd[slot].L;
+        const int parts = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(kParts, sites / kMinPartSites)));
         uint64_t load[kParts] = {};
         for (uint32_t slot : v) {
             int part = 0;
-            for (int q = 1; q < kParts; ++q)
+            for (int q = 1; q < parts; ++q)
                 if (load[q] < load[part]) part = q;
             load[part] += static_cast<uint64_t>(rd[slot].L) * rd[slot].L;
             by_branch[kind * kParts + part].push_back(slot);

@@ -71,6 +71,37 @@ def test_batch_matches_oracle(g, oracle):
             assert np.array_equal(b.planes(i), oracle.pack_planar(X, Y)), i
 
 
+def test_kinds_split_into_parts_equal_plain_runs(g):
+    """Replica sets large enough that the batch splits a kind into several
+    parts (each at least 2^26 sites, at most three; each part a branch of the
+    captured graph): 13 full-warp replicas of L = 4096 with both rates random
+    (218 M sites: three parts), 9 of L = 4096 in KPZ (151 M: two parts), and
+    packed one-group-wide replicas of L = 3968 (one part).  Five MCS run as one
+    four-MCS graph and one single MCS; every replica equals its plain run."""
+    from paper_1705_01022_gb300 import _lib
+    from paper_1705_01022_gb300.autotune import batch_shape
+    reps = []
+    for i in range(13):
+        reps.append((4096, 0.95, 0.05, _lib.oct_replica_seed(21, i)))
+    for i in range(9):
+        reps.append((4096, 1.0, 0.0, _lib.oct_replica_seed(22, i)))
+    for i in range(4):
+        reps.append((3968, 0.5, 0.5, _lib.oct_replica_seed(23, i)))
+    reps = [r + batch_shape(r[0], "tall") for r in reps]
+    assert reps[0][4:] == (1024, 16) and reps[-1][4:] == (32, 64)
+    n = 5
+    with g.Batch(reps) as b:
+        b.run(n)
+        res = b.measure()
+        for i, r in enumerate(reps):
+            L, p, q, seed, Bx, By = r
+            with g.Simulation(L, p, q, seed, Bx=Bx, By=By) as sim:
+                sim.run(n)
+                assert np.array_equal(b.planes(i), sim.planes()), (i, r)
+                m = sim.measure()
+                assert (res[i].t, res[i].s1, res[i].s2, res[i].net_flips) == (n, m.s1, m.s2, m.net_flips), (i, r)
+
+
 def test_graph_and_timed_launches_agree(g):
     from paper_1705_01022_gb300 import _lib
     reps = _replicas(g, master=11)[:12]

@@ -259,3 +259,28 @@ def test_jobs_spread_over_several_batches_that_tick_independently():
     assert [n for n, _ in fbs[0].runs] != [n for n, _ in fbs[1].runs]
     # the first two jobs (both arriving while nothing runs) went to different batches
     assert jobs[0].batch != jobs[1].batch
+
+
+def test_cancel_with_several_batches():
+    """A running job leaves the batch it runs in (the engine keys running jobs
+    by batch and slot, and two batches hand out the same slot numbers); the
+    jobs of the other batch keep running to their end."""
+    clock = VirtualClock()
+    fbs = [FakeBatch(clock), FakeBatch(clock)]
+    eng = serve.ServingEngine(hbm_budget=4 * serve.footprint(128), batch=fbs, clock=clock)
+    jobs = _jobs(4)
+    for j in jobs:
+        eng.submit(j)
+    eng.tick(0.0)
+    assert {j.batch for j in eng.running.values()} == {0, 1}
+    # slot 0 exists in both batches: cancelling job 1 must remove only its own replica
+    b1, s1 = jobs[1].batch, jobs[1].slot
+    other = [j for j in jobs if j.jid != 1 and (j.batch, j.slot) != (b1, s1)]
+    assert any(j.slot == s1 for j in other)
+    assert eng.cancel(1)
+    assert s1 not in fbs[b1].slots and all(j.slot in fbs[j.batch].slots for j in other if j in eng.running.values())
+    while eng.waiting or eng.running:
+        eng.tick(clock())
+    assert sorted(j.jid for j in eng.finished) == [0, 2, 3] and eng.used == 0
+    for j in eng.finished:
+        assert [r[0] for r in j.results] == j.measure_at
